@@ -1,0 +1,16 @@
+"""Plain FP64 CPU oracle for the explicit as-S_N time step.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct
+statement of what the GPU path must compute.  Only the test suite, the smoke
+check of ``__graft_entry__`` and the CPU-baseline / reference legs of
+``bench.py`` may import it; the library under ``paper_1911_08801_gb300`` never
+does, and shares no code with it.
+
+Parity status: every function is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_pins.py`` against closed forms, invariants and special
+cases (quadrature exactness, kernel normalisation and transport moments,
+Funk-Hecke eigenvalues of the kernel matrix, exact upwind shifts and binomial
+spreading, discrete decay laws, the discrete mass balance, the eps -> 0 limit,
+and the symmetries of the line source).
+"""
+from .assn_oracle import *  # noqa: F401,F403

@@ -1,0 +1,196 @@
+"""FP64 reference of the explicit as-S_N step (test infrastructure only; see the package header).
+
+Every function follows one passage of Camminady, Frank, Hauck, Kusch,
+"Ray Effect Mitigation for the Discrete Ordinates Method Using Artificial
+Scattering" (arXiv:1911.08801), cited in its docstring.  No blocking, fusion
+or reordering: the step evaluates every term of the as-S_N equations at the
+old time level (unsplit forward Euler), applies the dense Q x Q artificial
+scattering matrix as one product, and uses first-order upwind fluxes with
+zero inflow (vacuum) ghost cells.
+
+Conventions: ``psi`` is float64 ``[ny][nx][Q]``; cell fields are ``[ny][nx]``;
+``Omega`` is ``[Q][3]`` unit vectors, ``w`` is ``[Q]`` with sum 4 pi.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "product_quadrature", "s_eps", "s_exp", "kernel_matrix", "scalar_flux",
+    "transport", "step", "run", "mass", "step_at_cells",
+]
+
+
+# --------------------------------------------------------------------------- S0
+def product_quadrature(n_polar: int, n_azim: int):
+    """Product quadrature on S^2: Gauss-Legendre in mu times uniform azimuth.
+
+    Sec. 3.1 (quadrature rule with weights w_q, sum of weights 4 pi) and
+    Sec. 4 (ordinates projected onto the x-y plane for 2D transport).
+    Ordinate q = i * n_azim + k has mu = mu_i (i-th Gauss-Legendre node),
+    azimuth phi_k = (k + 1/2) 2 pi / n_azim, direction
+    (sqrt(1-mu^2) cos phi, sqrt(1-mu^2) sin phi, mu) and weight
+    w_i^GL * 2 pi / n_azim.  Returns (Omega[Q,3], w[Q]).
+    """
+    mu, wgl = np.polynomial.legendre.leggauss(n_polar)
+    phi = (np.arange(n_azim) + 0.5) * (2.0 * math.pi / n_azim)
+    Q = n_polar * n_azim
+    Omega = np.empty((Q, 3))
+    w = np.empty(Q)
+    for i in range(n_polar):
+        st = math.sqrt(max(0.0, 1.0 - mu[i] * mu[i]))
+        for k in range(n_azim):
+            q = i * n_azim + k
+            Omega[q] = (st * math.cos(phi[k]), st * math.sin(phi[k]), mu[i])
+            w[q] = wgl[i] * 2.0 * math.pi / n_azim
+    return Omega, w
+
+
+# --------------------------------------------------------------------------- S1
+def s_eps(mu, eps: float):
+    """Artificial scattering kernel, Sec. 2.3, Eq. (scattering kernel):
+    s_eps(mu) = 2 / (sqrt(pi) eps Erf(2/eps)) * exp(-(1-mu)^2 / eps^2)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    return 2.0 / (math.sqrt(math.pi) * eps * math.erf(2.0 / eps)) * np.exp(-((1.0 - mu) ** 2) / eps ** 2)
+
+
+def s_exp(mu, eps: float):
+    """Alternative forward-peaked kernel exp((mu - 1)/eps^2), normalised to unit integral on [-1, 1]
+    (a Dirac sequence in the sense of Sec. 2.3 as eps -> 0)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    e2 = eps * eps
+    return np.exp((mu - 1.0) / e2) / (e2 * -math.expm1(-2.0 / e2))
+
+
+def kernel_matrix(Omega, w, eps: float, kind: str = "gauss", normalisation: str = "column"):
+    """Discrete artificial in-scattering matrix K (Sec. 3.2, Eq. (as-S_N equations)).
+
+    s_qp = s_eps(Omega_q . Omega_p).  The paper's gain term is
+    sum_p w_p c_q s_qp psi_p with c_q = 1 / sum_p w_p s_qp ("row": every row
+    of K sums to one).  The default "column" form normalises by the source
+    ordinate instead, K_qp = w_p c_p s_qp, so that sum_q w_q K_qp = w_p and the
+    operator conserves sum_q w_q psi_q exactly (Sec. 2.3: artificial
+    scattering preserves the number of particles).
+    """
+    Omega = np.asarray(Omega, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    mu = np.clip(Omega @ Omega.T, -1.0, 1.0)
+    s = s_eps(mu, eps) if kind == "gauss" else s_exp(mu, eps)
+    if normalisation == "column":
+        c = 1.0 / (w @ s)                    # c_p = 1 / sum_q w_q s_qp
+        return s * (w * c)[None, :]
+    if normalisation == "row":
+        c = 1.0 / (s @ w)                    # c_q = 1 / sum_p w_p s_qp
+        return s * w[None, :] * c[:, None]
+    raise ValueError(normalisation)
+
+
+# --------------------------------------------------------------------------- S3
+def scalar_flux(psi, w):
+    """Phi = sum_q w_q psi_q (Sec. 2.2 definition of Phi, discretised with the rule of Sec. 3.1)."""
+    return np.asarray(psi, dtype=np.float64) @ np.asarray(w, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------- S4
+def transport(psi, Omega, h: float, bc: str = "vacuum"):
+    """First-order upwind finite-volume approximation of Omega . grad psi (Sec. 3.1, Eq. (S_N)).
+
+    For Omega_x > 0: Omega_x (psi_i - psi_{i-1}) / h; for Omega_x < 0:
+    Omega_x (psi_{i+1} - psi_i) / h; nothing for Omega_x = 0; likewise in y.
+    Vacuum boundaries (Sec. 4.2) supply zero incoming ghost values;
+    "periodic" wraps around (used by tests only).
+    """
+    psi = np.asarray(psi, dtype=np.float64)
+    ox = np.asarray(Omega)[:, 0]
+    oy = np.asarray(Omega)[:, 1]
+    if bc == "periodic":
+        left, right = np.roll(psi, 1, axis=1), np.roll(psi, -1, axis=1)
+        down, up = np.roll(psi, 1, axis=0), np.roll(psi, -1, axis=0)
+    else:
+        z = np.zeros_like(psi[:, :1, :])
+        left = np.concatenate([z, psi[:, :-1, :]], axis=1)
+        right = np.concatenate([psi[:, 1:, :], z], axis=1)
+        zy = np.zeros_like(psi[:1, :, :])
+        down = np.concatenate([zy, psi[:-1, :, :]], axis=0)
+        up = np.concatenate([psi[1:, :, :], zy], axis=0)
+    tx = np.where(ox > 0, ox * (psi - left), np.where(ox < 0, ox * (right - psi), 0.0))
+    ty = np.where(oy > 0, oy * (psi - down), np.where(oy < 0, oy * (up - psi), 0.0))
+    return (tx + ty) / h
+
+
+# --------------------------------------------------------------------------- S2 + S5
+def step(psi, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float, dt: float,
+         bc: str = "vacuum"):
+    """One explicit Euler step of the as-S_N equations (Sec. 3.2, Eq. (as-S_N equations)).
+
+    psi^{n+1}_q = psi_q - dt [Omega_q . grad psi_q]_upwind
+                  - dt (sigma_a + sigma_s + sigma_as) psi_q
+                  + dt sigma_s sum_p w_p c s psi_p        (isotropic s = 1/(4 pi), c = 1/sum_p w_p s)
+                  + dt sigma_as sum_p K_qp psi_p          (artificial in-scattering, Eq. (S_as^+))
+                  + dt q
+    Every term at time level n.  sigma_a, sigma_s, q are per-cell [ny][nx];
+    sigma_as is a constant (Sec. 5: constant artificial scattering strength).
+    """
+    psi = np.asarray(psi, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    sa = np.asarray(sigma_a, dtype=np.float64)[..., None]
+    ss = np.asarray(sigma_s, dtype=np.float64)[..., None]
+    src = np.asarray(q, dtype=np.float64)[..., None]
+    s_iso = 1.0 / (4.0 * math.pi)
+    c_iso = 1.0 / (w.sum() * s_iso)
+    phys = (scalar_flux(psi, w) * c_iso * s_iso)[..., None]      # sum_p w_p c s psi_p
+    art = psi @ np.asarray(K, dtype=np.float64).T                 # sum_p K_qp psi_p
+    T = transport(psi, Omega, h, bc)
+    return psi - dt * T - dt * (sa + ss + sigma_as) * psi + dt * (ss * phys + sigma_as * art + src)
+
+
+def run(psi0, nsteps: int, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float,
+        dt: float, bc: str = "vacuum"):
+    """nsteps explicit steps from psi0 (Sec. 3.1 time discretisation, first order)."""
+    psi = np.array(psi0, dtype=np.float64, copy=True)
+    for _ in range(nsteps):
+        psi = step(psi, K, Omega, w, sigma_a, sigma_s, q, sigma_as, h, dt, bc)
+    return psi
+
+
+def mass(psi, w, h: float) -> float:
+    """Total particle number h^2 sum_cells sum_q w_q psi_q."""
+    return float(h * h * scalar_flux(psi, w).sum())
+
+
+def step_at_cells(psi, cells, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float,
+                  dt: float):
+    """The same update as ``step`` (vacuum boundaries), evaluated one cell at a time.
+
+    ``cells`` is a sequence of (j, i) = (y index, x index).  Returns
+    float64 [len(cells)][Q].  Lets a test check sampled outputs of a launch
+    too large to step whole on the host.
+    """
+    psi = np.asarray(psi)
+    ny, nx, Q = psi.shape
+    w = np.asarray(w, dtype=np.float64)
+    K = np.asarray(K, dtype=np.float64)
+    ox = np.asarray(Omega)[:, 0]
+    oy = np.asarray(Omega)[:, 1]
+    s_iso = 1.0 / (4.0 * math.pi)
+    c_iso = 1.0 / (w.sum() * s_iso)
+    out = np.empty((len(cells), Q))
+    zero = np.zeros(Q)
+
+    def at(j, i):
+        if 0 <= j < ny and 0 <= i < nx:
+            return np.asarray(psi[j, i], dtype=np.float64)
+        return zero
+
+    for n, (j, i) in enumerate(cells):
+        p = at(j, i)
+        tx = np.where(ox > 0, ox * (p - at(j, i - 1)), np.where(ox < 0, ox * (at(j, i + 1) - p), 0.0))
+        ty = np.where(oy > 0, oy * (p - at(j - 1, i)), np.where(oy < 0, oy * (at(j + 1, i) - p), 0.0))
+        T = (tx + ty) / h
+        phys = float(w @ p) * c_iso * s_iso
+        art = K @ p
+        sa, ss, src = float(sigma_a[j, i]), float(sigma_s[j, i]), float(q[j, i])
+        out[n] = p - dt * T - dt * (sa + ss + sigma_as) * p + dt * (ss * phys + sigma_as * art + src)
+    return out

@@ -1,0 +1,375 @@
+"""Pins of the FP64 oracle against closed forms, invariants and special cases.
+
+Each test fixes one part of the oracle by something other than the oracle's
+own formula: a closed-form integral, a textbook result (Gauss-Legendre nodes,
+Funk-Hecke), a discrete conservation law, an exact shift, or a value printed
+in the paper (the order-2 icosahedron table).  A dropped term, a wrong sign, a
+wrong index or a transposed operand in ``oracle/`` fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+import oracle as O
+import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FOUR_PI = 4.0 * math.pi
+
+
+# ----------------------------------------------------------------------------- quadrature (S0)
+@pytest.mark.parametrize("npol,naz", [(2, 4), (3, 5), (8, 16), (16, 32), (16, 16)])
+def test_quadrature_weights_and_directions(npol, naz):
+    Om, w = O.product_quadrature(npol, naz)
+    assert Om.shape == (npol * naz, 3) and w.shape == (npol * naz,)
+    assert np.all(w > 0)
+    assert abs(w.sum() - FOUR_PI) < 1e-13
+    assert np.allclose(np.linalg.norm(Om, axis=1), 1.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("npol,naz", [(3, 6), (8, 16), (16, 32)])
+def test_quadrature_polynomial_exactness(npol, naz):
+    """Gauss-Legendre with n nodes integrates mu^k exactly for k <= 2n-1:
+    int_{S^2} mu^k = 2 pi * 2/(k+1) for even k, 0 for odd k."""
+    Om, w = O.product_quadrature(npol, naz)
+    mu = Om[:, 2]
+    for k in range(2 * npol):
+        exact = 4.0 * math.pi / (k + 1) if k % 2 == 0 else 0.0
+        assert abs(w @ mu ** k - exact) < 1e-12, k
+
+
+@pytest.mark.parametrize("npol,naz", [(3, 6), (8, 16), (16, 32)])
+def test_quadrature_second_and_fourth_moments(npol, naz):
+    """int Omega_x^2 = int Omega_y^2 = 4 pi/3, int Omega_x Omega_y = 0,
+    int Omega_x^2 Omega_y^2 = 4 pi/15 (needs >= 5 azimuths and >= 3 polar nodes)."""
+    Om, w = O.product_quadrature(npol, naz)
+    x, y = Om[:, 0], Om[:, 1]
+    assert abs(w @ x ** 2 - FOUR_PI / 3) < 1e-13
+    assert abs(w @ y ** 2 - FOUR_PI / 3) < 1e-13
+    assert abs(w @ (x * y)) < 1e-13
+    assert abs(w @ x) < 1e-13 and abs(w @ y) < 1e-13
+    assert abs(w @ (x * x * y * y) - FOUR_PI / 15) < 1e-13
+
+
+def test_gauss_legendre_textbook_nodes():
+    """n = 2: mu = -+1/sqrt(3), weights 1; n = 3: 0, -+sqrt(3/5), weights 8/9, 5/9."""
+    Om, w = O.product_quadrature(2, 1)
+    assert np.allclose(np.sort(Om[:, 2]), [-1 / math.sqrt(3), 1 / math.sqrt(3)], atol=1e-15)
+    assert np.allclose(w / (2 * math.pi), [1.0, 1.0], atol=1e-15)
+    Om, w = O.product_quadrature(3, 1)
+    order = np.argsort(Om[:, 2])
+    assert np.allclose(Om[order, 2], [-math.sqrt(0.6), 0.0, math.sqrt(0.6)], atol=1e-15)
+    assert np.allclose(w[order] / (2 * math.pi), [5 / 9, 8 / 9, 5 / 9], atol=1e-15)
+
+
+def test_quadrature_azimuths_avoid_axes():
+    """phi_k = (k + 1/2) 2 pi / n: no ordinate has Omega_x = 0 or Omega_y = 0 when 4 | n."""
+    Om, _ = O.product_quadrature(8, 16)
+    assert np.min(np.abs(Om[:, 0])) > 1e-3 and np.min(np.abs(Om[:, 1])) > 1e-3
+
+
+# ----------------------------------------------------------------------------- kernel (S1)
+def p_closed(eps, i):
+    """Transport coefficient p_{eps,i} = int (1-mu)^i s_eps dmu in closed form (Sec. 2.4).
+
+    With y = (1-mu)/eps and t = y^2 the integral is
+    eps^i / (sqrt(pi) Erf(2/eps)) * gamma_lower((1+i)/2, 4/eps^2).
+    (The printed intermediate lines drop the Jacobian eps and the factor 1/2 of
+    the t = y^2 substitution; this form gives p_0 = 1, as the kernel's
+    normalisation requires.)
+    """
+    a = (1.0 + i) / 2.0
+    gl = special.gamma(a) * special.gammainc(a, 4.0 / eps ** 2)
+    return eps ** i / (math.sqrt(math.pi) * math.erf(2.0 / eps)) * gl
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.3, 1.0, 3.0])
+def test_s_eps_unit_mass_and_transport_coefficients(eps):
+    val, _ = integrate.quad(lambda m: float(O.s_eps(m, eps)), -1, 1, points=[1 - eps, 1], limit=200)
+    assert abs(val - 1.0) < 1e-10
+    for i in (1, 2, 3):
+        num, _ = integrate.quad(lambda m: (1 - m) ** i * float(O.s_eps(m, eps)), -1, 1,
+                                points=[1 - eps, 1], limit=200)
+        assert abs(num - p_closed(eps, i)) < 1e-10 * max(1.0, abs(num)), i
+    assert abs(p_closed(eps, 0) - 1.0) < 1e-13
+
+
+def test_s_eps_dirac_sequence_and_order():
+    """int s_eps f -> f(1) as eps -> 0, and p_{eps,1} = O(eps) (Sec. 2.3, 2.4)."""
+    f = lambda m: math.cos(m) + m ** 3
+    for eps in (1e-2, 1e-3):
+        val, _ = integrate.quad(lambda m: f(m) * float(O.s_eps(m, eps)), -1, 1, points=[1 - 10 * eps, 1],
+                                limit=400)
+        assert abs(val - f(1.0)) < 3 * eps
+    r = [p_closed(e, 1) / e for e in (1e-1, 1e-2, 1e-3)]
+    assert abs(r[-1] - 1 / math.sqrt(math.pi)) < 1e-6 and abs(r[1] - r[2]) < 1e-6
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.5])
+def test_s_exp_unit_mass(eps):
+    val, _ = integrate.quad(lambda m: float(O.s_exp(m, eps)), -1, 1, points=[1 - eps * eps, 1], limit=200)
+    assert abs(val - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("kind", ["gauss", "exp"])
+@pytest.mark.parametrize("npol,naz,eps", [(8, 16, 0.039), (16, 32, 0.078), (4, 8, 0.6)])
+def test_kernel_column_normalisation_conserves_mass(kind, npol, naz, eps):
+    Om, w = O.product_quadrature(npol, naz)
+    K = O.kernel_matrix(Om, w, eps, kind=kind, normalisation="column")
+    assert np.all(K >= 0)
+    assert np.allclose(w @ K, w, rtol=1e-14, atol=0)        # sum_q w_q K_qp = w_p
+    # the generator K - I has zero weighted column sums, so any psi keeps sum_q w_q psi_q
+    psi = np.random.default_rng(1).uniform(size=(5, w.size))
+    assert np.allclose((psi @ K.T) @ w, psi @ w, rtol=1e-13)
+
+
+@pytest.mark.parametrize("npol,naz,eps", [(8, 16, 0.039), (16, 32, 0.078)])
+def test_kernel_row_normalisation_preserves_constants(npol, naz, eps):
+    Om, w = O.product_quadrature(npol, naz)
+    K = O.kernel_matrix(Om, w, eps, normalisation="row")
+    assert np.allclose(K.sum(axis=1), 1.0, rtol=1e-14)
+
+
+def legendre(l, x):
+    return special.eval_legendre(l, x)
+
+
+@pytest.mark.parametrize("normalisation", ["row", "column"])
+def test_kernel_funk_hecke_eigenvalues(normalisation):
+    """Funk-Hecke: the normalised kernel maps P_l(Omega . e) to lambda_l P_l(Omega . e) with
+    lambda_l = int_{-1}^{1} s_eps(mu) P_l(mu) dmu; lambda_1 = 1 - p_1, lambda_2 = 1 - 3 p_1 + 3/2 p_2
+    (the modified-equation coefficients of Sec. 2.4).  Fine quadrature, so c_q ~ const."""
+    eps = 0.3
+    Om, w = O.product_quadrature(32, 64)
+    K = O.kernel_matrix(Om, w, eps, normalisation=normalisation)
+    e = np.array([0.3, -0.5, 0.8])
+    e /= np.linalg.norm(e)
+    x = Om @ e
+    lam = {1: 1 - p_closed(eps, 1), 2: 1 - 3 * p_closed(eps, 1) + 1.5 * p_closed(eps, 2)}
+    for l in (1, 2, 3):
+        if l not in lam:
+            lam[l], _ = integrate.quad(lambda m: float(O.s_eps(m, eps)) * legendre(l, m), -1, 1, limit=200)
+        f = legendre(l, x)
+        assert np.max(np.abs(K @ f - lam[l] * f)) < 2e-5, (l, lam[l])
+    # a transposed operand breaks it (the weights are far from uniform)
+    assert np.max(np.abs(K.T @ legendre(1, x) - lam[1] * legendre(1, x))) > 1e-2
+
+
+def test_kernel_eps_to_zero_is_identity():
+    """beta -> 0: s_eps underflows off the diagonal, K = I exactly and as-S_N is S_N (Sec. 2.4)."""
+    Om, w = O.product_quadrature(8, 16)
+    for kind in ("gauss", "exp"):
+        K = O.kernel_matrix(Om, w, 1e-4, kind=kind)
+        assert np.array_equal(K - np.diag(np.diag(K)), np.zeros_like(K))
+        assert np.max(np.abs(np.diag(K) - 1.0)) <= 2.3e-16       # w_p c_p s_pp = 1 up to one rounding
+
+
+def test_icosahedron_order2_table_from_paper():
+    """The paper's printed order-2 icosahedron quadrature (Appendix A) as an input: weights sum
+    to 4 pi, unit points, one vertex at (0,0,1); the kernel matrix on it conserves mass."""
+    rows = [list(map(float, l.split())) for l in open(os.path.join(HERE, "golden", "icosahedron_order2.txt"))
+            if l.strip() and not l.startswith("#")]
+    tab = np.array(rows)
+    Om, w = tab[:, :3], tab[:, 3]
+    assert Om.shape == (12, 3)
+    assert abs(w.sum() - FOUR_PI) < 1e-14
+    assert np.allclose(np.linalg.norm(Om, axis=1), 1.0, atol=1e-15)
+    assert any(np.allclose(p, [0, 0, 1]) for p in Om)
+    K = O.kernel_matrix(Om, w, 4.5 / 12)      # eps = beta / N_q with the paper's beta = 4.5
+    assert np.allclose(w @ K, w, rtol=1e-14)
+    Kr = O.kernel_matrix(Om, w, 4.5 / 12, normalisation="row")
+    assert np.allclose(Kr.sum(1), 1.0, rtol=1e-14)
+
+
+# ----------------------------------------------------------------------------- scalar flux (S3)
+def test_scalar_flux_moments():
+    Om, w = O.product_quadrature(8, 16)
+    psi = np.full((3, 4, w.size), 2.5)
+    assert np.allclose(O.scalar_flux(psi, w), 2.5 * FOUR_PI, rtol=1e-14)
+    assert np.allclose(O.scalar_flux(np.broadcast_to(Om[:, 0], (3, 4, w.size)), w), 0.0, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- transport (S4)
+def single_ordinate_step(psi, omega, h, dt, bc="vacuum"):
+    Om = np.array([omega], dtype=np.float64)
+    w = np.array([FOUR_PI])
+    z = np.zeros(psi.shape[:2])
+    return O.step(psi, np.eye(1), Om, w, z, z, z, 0.0, h, dt, bc)
+
+
+@pytest.mark.parametrize("omega,shift", [((1, 0, 0), (0, 1)), ((-1, 0, 0), (0, -1)),
+                                         ((0, 1, 0), (1, 0)), ((0, -1, 0), (-1, 0))])
+def test_upwind_exact_shift_at_cfl_one(omega, shift):
+    """Omega dt / h = 1 moves the solution by exactly one cell downwind; the inflow ghost is zero."""
+    rng = np.random.default_rng(3)
+    psi = rng.integers(0, 100, size=(6, 7, 1)).astype(np.float64)
+    new = single_ordinate_step(psi, omega, 0.5, 0.5)
+    expect = np.zeros_like(psi)
+    dy, dx = shift
+    src = psi[max(0, -dy):psi.shape[0] - max(0, dy), max(0, -dx):psi.shape[1] - max(0, dx)]
+    expect[max(0, dy):psi.shape[0] - max(0, -dy) if dy < 0 else None,
+           max(0, dx):psi.shape[1] - max(0, -dx) if dx < 0 else None] = src
+    assert np.array_equal(new, expect)
+
+
+def test_upwind_binomial_spreading_1d():
+    """Omega_x dt/h = 1/2: psi_i <- psi_i/2 + psi_{i-1}/2, so a unit spike becomes C(n,k)/2^n."""
+    n = 9
+    psi = np.zeros((1, 32, 1))
+    psi[0, 3, 0] = 1.0
+    for _ in range(n):
+        psi = single_ordinate_step(psi, (1, 0, 0), 1.0, 0.5)
+    expect = np.zeros(32)
+    for k in range(n + 1):
+        expect[3 + k] = math.comb(n, k) / 2 ** n
+    assert np.allclose(psi[0, :, 0], expect, atol=1e-15)
+
+
+def test_upwind_binomial_spreading_2d_diagonal():
+    """Omega = (1,1,0)/sqrt2 with Omega_x dt/h = Omega_y dt/h = 1/2: the spike splits between the
+    x- and y-upwind neighbours, giving C(n,k)/2^n on the anti-diagonal i + j = i0 + j0 + n."""
+    n = 6
+    s = 1 / math.sqrt(2)
+    psi = np.zeros((16, 16, 1))
+    psi[2, 4, 0] = 1.0
+    for _ in range(n):
+        psi = single_ordinate_step(psi, (s, s, 0), 1.0, s)
+    expect = np.zeros((16, 16))
+    for k in range(n + 1):
+        expect[2 + (n - k), 4 + k] = math.comb(n, k) / 2 ** n
+    assert np.allclose(psi[:, :, 0], expect, atol=1e-14)
+
+
+def test_transport_vacuum_mass_balance():
+    """Summing the upwind differences over a row telescopes to the outflow through the last face:
+    M^{n+1} - M^n = -dt h sum_q w_q (sum of |Omega_n| psi over the outflow boundary cells)."""
+    Om, w = O.product_quadrature(4, 8)
+    rng = np.random.default_rng(5)
+    psi = rng.uniform(size=(9, 11, w.size))
+    h, dt = 0.1, 0.03
+    z = np.zeros((9, 11))
+    new = O.step(psi, np.eye(w.size), Om, w, z, z, z, 0.0, h, dt)
+    out = 0.0
+    for q in range(w.size):
+        ox, oy = Om[q, 0], Om[q, 1]
+        bx = psi[:, -1, q] if ox > 0 else psi[:, 0, q]
+        by = psi[-1, :, q] if oy > 0 else psi[0, :, q]
+        out += w[q] * (abs(ox) * bx.sum() + abs(oy) * by.sum())
+    dM = O.mass(new, w, h) - O.mass(psi, w, h)
+    assert abs(dM - (-dt * h * out)) < 1e-13 * O.mass(psi, w, h)
+
+
+def test_transport_periodic_conserves_mass():
+    Om, w = O.product_quadrature(4, 8)
+    psi = np.random.default_rng(6).uniform(size=(6, 5, w.size))
+    T = O.transport(psi, Om, 0.2, bc="periodic")
+    assert abs((T @ w).sum()) < 1e-12
+
+
+def test_transport_no_flux_for_zero_component():
+    psi = np.random.default_rng(7).uniform(size=(4, 5, 1))
+    T = O.transport(psi, np.array([[0.0, 0.0, 1.0]]), 1.0)
+    assert np.array_equal(T, np.zeros_like(psi))
+
+
+# ----------------------------------------------------------------------------- collision (S5)
+def test_infinite_medium_discrete_decay():
+    """psi = 1 everywhere, constant-preserving kernel: both scattering gains balance their losses and
+    psi^n = (1 - sigma_a dt)^n exactly; cells farther than n from a vacuum edge do not see it."""
+    Om, w = O.product_quadrature(4, 8)
+    K = O.kernel_matrix(Om, w, 0.4, normalisation="row")
+    ny = nx = 24
+    sa = np.full((ny, nx), 0.7)
+    ss = np.full((ny, nx), 1.3)
+    q = np.zeros((ny, nx))
+    h, dt, n = 0.1, 0.05, 8
+    psi0 = np.ones((ny, nx, w.size))
+    per = O.run(psi0, n, K, Om, w, sa, ss, q, 5.0, h, dt, bc="periodic")
+    assert np.allclose(per, (1 - 0.7 * dt) ** n, rtol=1e-13)
+    vac = O.run(psi0, n, K, Om, w, sa, ss, q, 5.0, h, dt)
+    assert np.allclose(vac[n:-n, n:-n], (1 - 0.7 * dt) ** n, rtol=1e-13)
+    assert not np.allclose(vac[0, 0], (1 - 0.7 * dt) ** n)
+    # and the continuous law e^{-sigma_a t} to O(dt)
+    t = n * dt
+    assert abs(per[0, 0, 0] - math.exp(-0.7 * t)) < 0.7 ** 2 * t * dt
+
+
+def test_mass_law_with_absorption_and_source():
+    """Periodic transport and both scattering operators conserve mass, so
+    M^{n+1} = M^n - dt h^2 sum_c sigma_a,c Phi_c + dt h^2 (sum_q w_q) sum_c q_c exactly."""
+    Om, w = O.product_quadrature(8, 16)
+    K = O.kernel_matrix(Om, w, 0.2)
+    rng = np.random.default_rng(8)
+    ny, nx = 5, 6
+    psi = rng.uniform(size=(ny, nx, w.size))
+    sa, ss, q = synth.random_materials(1, ny, nx)
+    h, dt = 0.25, 0.01
+    new = O.step(psi, K, Om, w, sa, ss, q, 5.0, h, dt, bc="periodic")
+    phi = psi @ w
+    expect = O.mass(psi, w, h) - dt * h * h * (sa * phi).sum() + dt * h * h * w.sum() * q.sum()
+    assert abs(O.mass(new, w, h) - expect) < 1e-13 * O.mass(psi, w, h)
+
+
+def test_isotropic_scattering_relaxation():
+    """One periodic cell, sigma_as = sigma_a = 0: psi_q - Phi/sum(w) decays like (1 - sigma_s dt)^n
+    while Phi stays put."""
+    Om, w = O.product_quadrature(4, 8)
+    psi0 = np.random.default_rng(9).uniform(size=(1, 1, w.size))
+    ss = np.full((1, 1), 2.0)
+    z = np.zeros((1, 1))
+    dt, n = 0.05, 7
+    psi = O.run(psi0, n, np.eye(w.size), Om, w, z, ss, z, 0.0, 1.0, dt, bc="periodic")
+    mean = (psi0 @ w) / w.sum()
+    assert np.allclose(psi @ w, psi0 @ w, rtol=1e-14)
+    assert np.allclose(psi - mean[..., None], (1 - 2.0 * dt) ** n * (psi0 - mean[..., None]), atol=1e-14)
+
+
+def test_eps_to_zero_recovers_plain_sn():
+    Om, w = O.product_quadrature(8, 16)
+    rng = np.random.default_rng(10)
+    psi = rng.uniform(size=(6, 6, w.size))
+    sa, ss, q = synth.random_materials(2, 6, 6)
+    K0 = O.kernel_matrix(Om, w, 1e-4)
+    a = O.step(psi, K0, Om, w, sa, ss, q, 5.0, 0.1, 0.02)
+    b = O.step(psi, np.eye(w.size), Om, w, sa, ss, q, 0.0, 0.1, 0.02)
+    assert np.allclose(a, b, rtol=1e-14, atol=1e-15)
+
+
+def test_step_at_cells_matches_whole_step():
+    Om, w = O.product_quadrature(4, 8)
+    K = O.kernel_matrix(Om, w, 0.3)
+    rng = np.random.default_rng(11)
+    psi = rng.uniform(size=(5, 7, w.size))
+    sa, ss, q = synth.random_materials(3, 5, 7)
+    full = O.step(psi, K, Om, w, sa, ss, q, 5.0, 0.1, 0.02)
+    cells = [(0, 0), (4, 6), (2, 3), (0, 6), (4, 0), (1, 5)]
+    part = O.step_at_cells(psi, cells, K, Om, w, sa, ss, q, 5.0, 0.1, 0.02)
+    for n, (j, i) in enumerate(cells):
+        assert np.allclose(part[n], full[j, i], rtol=1e-14, atol=1e-15)
+
+
+def test_line_source_symmetries():
+    """The line source on a centred even grid with a product quadrature whose azimuths are symmetric
+    under x -> -x, y -> -y and x <-> y yields a scalar flux with the same symmetries."""
+    wl = synth.line_source(16, 4, 8, 0.5, t_final=0.2)
+    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
+    K = O.kernel_matrix(Om, w, wl.eps)
+    sa, ss, q = wl.materials()
+    n, dt = wl.steps()
+    psi = O.run(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    phi = psi @ w
+    tol = 1e-12 * np.abs(phi).max()
+    assert np.max(np.abs(phi - phi[:, ::-1])) < tol
+    assert np.max(np.abs(phi - phi[::-1, :])) < tol
+    assert np.max(np.abs(phi - phi.T)) < tol
+    assert phi.min() > 0
+
+
+def test_time_grid_lands_on_t_final():
+    n, dt = synth.time_grid(3.2, 0.5, 1 / 64)
+    assert n == 410 and abs(n * dt - 3.2) < 1e-12 and dt <= 0.5 / 64
+    n, dt = synth.time_grid(1.0, 0.5, 3 / 64)
+    assert n == 43 and abs(n * dt - 1.0) < 1e-12
