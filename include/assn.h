@@ -1,0 +1,203 @@
+/*
+ * assn.h -- C ABI of libassn: the explicit time step of the artificial-scattering
+ * S_N (as-S_N) method for 2D radiative transfer on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Camminady, Frank, Hauck, Kusch, "Ray Effect Mitigation for the Discrete
+ * Ordinates Method Using Artificial Scattering", arXiv:1911.08801.
+ *
+ * One step advances every ordinate's angular flux psi_q on a uniform Cartesian grid by
+ * forward Euler applied to the as-S_N equations (Sec. 3.2, Eq. (as-S_N equations)):
+ *
+ *   psi_q' = psi_q - dt [Omega_q . grad psi_q]_upwind          (first-order upwind, vacuum inflow)
+ *            - dt (sigma_a + sigma_s + sigma_as) psi_q
+ *            + dt sigma_s Phi / sum_p w_p                       (isotropic physical scattering)
+ *            + dt sigma_as sum_p K_qp psi_p                     (artificial in-scattering)
+ *            + dt q
+ *
+ * with Phi = sum_p w_p psi_p and K the normalised forward-peaked kernel matrix built from
+ * s_eps(mu) ~ exp(-(1-mu)^2/eps^2) (Sec. 2.3, Eq. (scattering kernel)).
+ *
+ * Conventions common to every entry point:
+ *  - Every call returns an assn_status (0 = ASSN_OK, negative = error).  No call aborts the
+ *    process or throws; assn_last_error() gives a one-line message for the last failure on
+ *    a problem.
+ *  - Host arrays are owned by the caller and are copied during the call.  Cell fields are
+ *    row-major [ny][nx] (x fastest); angular fluxes are [ny][nx][Q] (ordinate fastest),
+ *    ordinates in the order the quadrature was given.
+ *  - The library owns all device memory of a problem (allocated by assn_create and the
+ *    set_* calls, freed by assn_destroy).  Device-pointer arguments (names ending in _dev)
+ *    are caller-owned device buffers; the call only reads or writes them on the problem's
+ *    stream, asynchronously.
+ *  - Work is issued on the problem's stream (the cudaStream_t passed to assn_create, or a
+ *    stream the library creates when NULL).  Calls documented as "syncs" wait for it.
+ *  - One problem must not be used from two host threads at once.
+ */
+#ifndef ASSN_H
+#define ASSN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASSN_ABI_VERSION 1
+
+typedef enum {
+    ASSN_OK = 0,
+    ASSN_ERR_ARG = -1,          /* invalid argument (null pointer, size, range)            */
+    ASSN_ERR_OOM = -2,          /* device or host allocation failed                         */
+    ASSN_ERR_CUDA = -3,         /* a CUDA call failed; message in assn_last_error           */
+    ASSN_ERR_UNSTABLE = -4,     /* dt violates the positivity bound of the explicit step    */
+    ASSN_ERR_NONFINITE = -5,    /* NaN/Inf found in the state                               */
+    ASSN_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up                       */
+    ASSN_ERR_STATE = -7,        /* call out of order (e.g. step before quadrature is set)   */
+    ASSN_ERR_UNSUPPORTED = -8   /* size or mode not supported by the selected kernel        */
+} assn_status;
+
+/* Arithmetic of the step.  State and stencil are FP64 for ASSN_FP64 and FP32 otherwise;
+ * the artificial-scattering contraction runs in:
+ *   ASSN_FP64   FP64 CUDA cores (the plain FP64 GPU path)
+ *   ASSN_FP32   FP32 CUDA cores
+ *   ASSN_BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation (one pass)
+ *   ASSN_BF16X3 tcgen05, operands split into BF16 hi+lo, three passes (hi*hi + hi*lo + lo*hi),
+ *               FP32 accumulation: about FP32-level accuracy of the contraction.
+ * K itself is always built in FP64 on the device. */
+typedef enum {
+    ASSN_FP64 = 0,
+    ASSN_FP32 = 1,
+    ASSN_BF16 = 2,
+    ASSN_BF16X3 = 3
+} assn_precision;
+
+/* Kernel shape.  ASSN_KERNEL_GAUSS is the paper's s_eps(mu) ~ exp(-(1-mu)^2/eps^2)
+ * (Sec. 2.3); ASSN_KERNEL_EXP is exp((mu-1)/eps^2).  Constant prefactors cancel in the
+ * normalisation and are not applied. */
+typedef enum { ASSN_KERNEL_GAUSS = 0, ASSN_KERNEL_EXP = 1 } assn_kernel_kind;
+
+/* Normalisation of K.  COLUMN: K_qp = w_p c_p s_qp with c_p = 1/sum_q w_q s_qp, so
+ * sum_q w_q K_qp = w_p and the operator conserves particles exactly.  ROW: the paper's
+ * c_q = 1/sum_p w_p s_qp (Sec. 3.2, normalisation factors), rows of K sum to one. */
+typedef enum { ASSN_NORM_COLUMN = 0, ASSN_NORM_ROW = 1 } assn_normalisation;
+
+typedef enum { ASSN_BC_VACUUM = 0 } assn_boundary;
+
+typedef struct assn_problem assn_problem;
+
+/* Maximum ordinate count and grid side accepted by assn_create / set_quadrature. */
+#define ASSN_MAX_Q 1024
+#define ASSN_MAX_SIDE 32768
+
+/* Create a problem on the current CUDA device: nx x ny cells covering [x0,x1] x [y0,y1]
+ * with square cells (requires (x1-x0)/nx == (y1-y0)/ny to 1e-12 relative).
+ * precision: an assn_precision.  stream: a cudaStream_t, or NULL for a library-owned
+ * stream.  On success *out receives the handle; on error *out is NULL.
+ * Errors: ASSN_ERR_ARG for non-positive sizes, non-square cells or an unknown precision;
+ * ASSN_ERR_CUDA if no device is usable. */
+int assn_create(assn_problem** out, int nx, int ny, double x0, double x1, double y0,
+                double y1, int precision, void* stream);
+
+/* Free all device and host memory of the problem (synchronises its stream).  NULL is a no-op. */
+int assn_destroy(assn_problem* p);
+
+/* Set an arbitrary quadrature (Sec. 3.1 quadrature rule): Q ordinates, omega[Q*3] unit
+ * directions (x, y, z), w[Q] positive weights.  Transport uses the projection (x, y) onto
+ * the grid plane (Sec. 4).  Resets the state to zero and invalidates K.
+ * Errors: ASSN_ERR_ARG if Q < 1 or Q > ASSN_MAX_Q, a weight <= 0 or a direction with
+ * |norm - 1| > 1e-9. */
+int assn_set_quadrature(assn_problem* p, int Q, const double* omega, const double* w);
+
+/* Product quadrature: n_polar Gauss-Legendre nodes in mu (computed on the host by Newton
+ * iteration on P_n) times n_azim azimuths phi_k = (k+1/2) 2 pi / n_azim; weight
+ * w = w_GL * 2 pi / n_azim; ordinate q = i*n_azim + k.  Same effects as assn_set_quadrature. */
+int assn_set_product_quadrature(assn_problem* p, int n_polar, int n_azim);
+
+/* Copy the quadrature back: omega[Q*3], w[Q] (either may be NULL).  *Q_out receives Q. */
+int assn_get_quadrature(const assn_problem* p, int* Q_out, double* omega, double* w);
+
+/* Per-cell cross sections sigma_a, sigma_s >= 0 and the isotropic per-ordinate source q
+ * (added to every ordinate's equation, Eq. (1)), each [ny][nx] host FP64, copied.
+ * Errors: ASSN_ERR_ARG on NULL or a negative / non-finite cross section. */
+int assn_set_cross_sections(assn_problem* p, const double* sigma_a, const double* sigma_s,
+                            const double* q);
+
+/* Artificial scattering strength sigma_as >= 0 (Sec. 2.3, constant in space) and kernel
+ * width eps > 0 (Sec. 2.4: eps = beta/N_q in the paper; callers pass eps directly).
+ * Builds K on the device in FP64 (one block per normalised line) and derives the operands
+ * of the selected precision.  Requires a quadrature.  Errors: ASSN_ERR_ARG, ASSN_ERR_STATE. */
+int assn_set_artificial_scattering(assn_problem* p, double sigma_as, double eps, int kernel_kind,
+                                   int normalisation);
+
+/* Copy the FP64 K (row q, column p: K[q*Q + p]) to the host.  Syncs. */
+int assn_get_kernel_matrix(assn_problem* p, double* K_host);
+
+/* State.  psi[ny][nx][Q] host FP64, copied (converted to FP32 unless the precision is FP64).
+ * set_state syncs before returning; get_state syncs. */
+int assn_set_state(assn_problem* p, const double* psi_host);
+int assn_get_state(assn_problem* p, double* psi_host);
+
+/* FP32 state copies for FP32/BF16/BF16X3 problems: psi[ny][nx][Q] host FP32 (pinned host memory
+ * gives full copy bandwidth).  set_state_f32 is asynchronous on the problem's stream: the
+ * caller keeps psi alive and unchanged until the stream has passed the copy.  get_state_f32
+ * syncs.  ASSN_ERR_UNSUPPORTED on an FP64 problem. */
+int assn_set_state_f32(assn_problem* p, const float* psi_host);
+int assn_get_state_f32(assn_problem* p, float* psi_host);
+
+/* Line-source initial state (Sec. 4.1), computed on the device:
+ * psi_q(x) = max{floor, exp(-|x|^2/(4 delta)) / (4 pi delta)} at cell centres for every q. */
+int assn_init_line_source(assn_problem* p, double delta, double floor_value);
+
+/* Largest dt for which the explicit step keeps every coefficient of the update
+ * non-negative (positivity): dt * (|Omega_x|/h + |Omega_y|/h + sigma_a + sigma_s + sigma_as) <= 1
+ * for every ordinate and cell.  Requires quadrature, cross sections and sigma_as. */
+int assn_max_stable_dt(assn_problem* p, double* dt_out);
+
+/* Advance nsteps explicit steps of size dt on the problem's stream (asynchronous; the
+ * state buffers ping-pong on the device).  Errors: ASSN_ERR_STATE if quadrature, cross
+ * sections or K are missing; ASSN_ERR_UNSTABLE if dt exceeds assn_max_stable_dt by more
+ * than 1e-12 relative; ASSN_ERR_CUDA on a launch failure; ASSN_ERR_TIMEOUT if a bounded
+ * device-side wait in the tensor-core kernel gave up (reported by a later syncing call). */
+int assn_step(assn_problem* p, int nsteps, double dt);
+
+/* Same step, with the ordinate state supplied and returned by the caller in device memory
+ * laid out as the problem's own buffers ([ny][nx][Qpad] of FP32, or FP64 for ASSN_FP64;
+ * Qpad from assn_layout).  psi_in_dev and psi_out_dev must not overlap.  Asynchronous. */
+int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev, double dt);
+
+/* Device layout of the state: *Qpad = padded ordinate stride, *elem_bytes = 4 or 8. */
+int assn_layout(const assn_problem* p, int* Qpad, int* elem_bytes);
+
+/* Device pointer to the current state buffer ([ny][nx][Qpad]); valid until the next
+ * assn_step / set_state / destroy. */
+int assn_state_device(assn_problem* p, void** psi_dev);
+
+/* Scalar flux Phi = sum_q w_q psi_q per cell (Eq. for Phi, Sec. 2.2), [ny][nx].
+ * assn_scalar_flux copies FP64 to the host and syncs; assn_scalar_flux_device writes FP32
+ * to a caller-owned device buffer, asynchronously. */
+int assn_scalar_flux(assn_problem* p, double* phi_host);
+int assn_scalar_flux_device(assn_problem* p, float* phi_dev);
+
+/* Total particle number h^2 sum_cells sum_q w_q psi_q, accumulated in FP64.  Syncs. */
+int assn_mass(assn_problem* p, double* mass_out);
+
+/* Check the state for NaN/Inf: ASSN_OK or ASSN_ERR_NONFINITE.  Syncs. */
+int assn_check_finite(assn_problem* p);
+
+/* Message of the last failure on p (never NULL; "" when none).  With p == NULL, the last
+ * failure of assn_create on this thread. */
+const char* assn_last_error(const assn_problem* p);
+
+/* Static name of a status code. */
+const char* assn_status_string(int status);
+
+/* Number of kernel launches this problem has issued so far (for launch accounting). */
+int64_t assn_launch_count(const assn_problem* p);
+
+int assn_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASSN_H */

@@ -1,0 +1,109 @@
+"""GB300-native explicit as-S_N time step (arXiv:1911.08801) behind a C ABI.
+
+``_lib`` binds every entry point of ``include/assn.h`` under its own name; ``Problem`` is a
+small owner object around one problem handle.  All arithmetic of the step runs in the CUDA
+kernels of ``libassn.so``; importing this package fails when that library is not built.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ASSN_BF16, ASSN_BF16X3, ASSN_FP32, ASSN_FP64, ASSN_KERNEL_EXP, ASSN_KERNEL_GAUSS,
+                   ASSN_NORM_COLUMN, ASSN_NORM_ROW, PRECISIONS, AssnError)
+
+__all__ = ["Problem", "AssnError", "PRECISIONS", "ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
+           "ASSN_KERNEL_GAUSS", "ASSN_KERNEL_EXP", "ASSN_NORM_COLUMN", "ASSN_NORM_ROW"]
+
+
+class Problem:
+    """One as-S_N problem on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, nx: int, ny: int, x0: float, x1: float, y0: float, y1: float,
+                 precision="bf16", stream=None):
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.nx, self.ny = nx, ny
+        self.h = (x1 - x0) / nx
+        self.Q = 0
+        self.handle = _lib.assn_create(nx, ny, x0, x1, y0, y1, self.precision, stream)
+
+    # -- set-up
+    def set_product_quadrature(self, n_polar: int, n_azim: int):
+        _lib.assn_set_product_quadrature(self.handle, n_polar, n_azim)
+        self.Q = n_polar * n_azim
+        return self
+
+    def set_quadrature(self, omega, w):
+        _lib.assn_set_quadrature(self.handle, omega, w)
+        self.Q = len(w)
+        return self
+
+    def quadrature(self):
+        return _lib.assn_get_quadrature(self.handle)
+
+    def set_cross_sections(self, sigma_a, sigma_s, q):
+        _lib.assn_set_cross_sections(self.handle, sigma_a, sigma_s, q)
+        return self
+
+    def set_artificial_scattering(self, sigma_as: float, eps: float, kernel_kind: int = ASSN_KERNEL_GAUSS,
+                                  normalisation: int = ASSN_NORM_COLUMN):
+        _lib.assn_set_artificial_scattering(self.handle, sigma_as, eps, kernel_kind, normalisation)
+        return self
+
+    def kernel_matrix(self) -> np.ndarray:
+        return _lib.assn_get_kernel_matrix(self.handle, self.Q)
+
+    # -- state
+    def set_state(self, psi):
+        _lib.assn_set_state(self.handle, psi)
+        return self
+
+    def state(self) -> np.ndarray:
+        return _lib.assn_get_state(self.handle, (self.ny, self.nx, self.Q))
+
+    def init_line_source(self, delta: float = 0.03 ** 2, floor_value: float = 1e-4):
+        _lib.assn_init_line_source(self.handle, delta, floor_value)
+        return self
+
+    # -- stepping and diagnostics
+    def max_stable_dt(self) -> float:
+        return _lib.assn_max_stable_dt(self.handle)
+
+    def step(self, nsteps: int, dt: float):
+        _lib.assn_step(self.handle, nsteps, dt)
+        return self
+
+    def scalar_flux(self) -> np.ndarray:
+        return _lib.assn_scalar_flux(self.handle, (self.ny, self.nx))
+
+    def mass(self) -> float:
+        return _lib.assn_mass(self.handle)
+
+    def check_finite(self):
+        _lib.assn_check_finite(self.handle)
+
+    def layout(self):
+        return _lib.assn_layout(self.handle)
+
+    def state_device_ptr(self) -> int:
+        return _lib.assn_state_device(self.handle)
+
+    def launch_count(self) -> int:
+        return _lib.assn_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            _lib.assn_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

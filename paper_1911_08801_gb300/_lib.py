@@ -1,0 +1,248 @@
+"""ctypes binding of libassn (include/assn.h): the same entry points, argument marshalling only.
+
+Every function here converts Python/numpy arguments to the C types, calls the entry point of
+the same name and raises ``AssnError`` on a non-zero status.  No step of the method runs in
+Python.  Importing fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libassn.so")
+
+ASSN_OK = 0
+ASSN_ERR_ARG = -1
+ASSN_ERR_OOM = -2
+ASSN_ERR_CUDA = -3
+ASSN_ERR_UNSTABLE = -4
+ASSN_ERR_NONFINITE = -5
+ASSN_ERR_TIMEOUT = -6
+ASSN_ERR_STATE = -7
+ASSN_ERR_UNSUPPORTED = -8
+
+ASSN_FP64, ASSN_FP32, ASSN_BF16, ASSN_BF16X3 = 0, 1, 2, 3
+ASSN_KERNEL_GAUSS, ASSN_KERNEL_EXP = 0, 1
+ASSN_NORM_COLUMN, ASSN_NORM_ROW = 0, 1
+
+PRECISIONS = {"fp64": ASSN_FP64, "fp32": ASSN_FP32, "bf16": ASSN_BF16, "bf16x3": ASSN_BF16X3}
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_vp = C.c_void_p
+_h = C.c_void_p
+
+# name -> (restype, argtypes); every function declared in include/assn.h
+SIGNATURES = {
+    "assn_create": (C.c_int, [C.POINTER(_h), C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                              C.c_int, _vp]),
+    "assn_destroy": (C.c_int, [_h]),
+    "assn_set_quadrature": (C.c_int, [_h, C.c_int, _dp, _dp]),
+    "assn_set_product_quadrature": (C.c_int, [_h, C.c_int, C.c_int]),
+    "assn_get_quadrature": (C.c_int, [_h, C.POINTER(C.c_int), _dp, _dp]),
+    "assn_set_cross_sections": (C.c_int, [_h, _dp, _dp, _dp]),
+    "assn_set_artificial_scattering": (C.c_int, [_h, C.c_double, C.c_double, C.c_int, C.c_int]),
+    "assn_get_kernel_matrix": (C.c_int, [_h, _dp]),
+    "assn_set_state": (C.c_int, [_h, _dp]),
+    "assn_get_state": (C.c_int, [_h, _dp]),
+    "assn_set_state_f32": (C.c_int, [_h, _fp]),
+    "assn_get_state_f32": (C.c_int, [_h, _fp]),
+    "assn_init_line_source": (C.c_int, [_h, C.c_double, C.c_double]),
+    "assn_max_stable_dt": (C.c_int, [_h, _dp]),
+    "assn_step": (C.c_int, [_h, C.c_int, C.c_double]),
+    "assn_step_device": (C.c_int, [_h, _vp, _vp, C.c_double]),
+    "assn_layout": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "assn_state_device": (C.c_int, [_h, C.POINTER(_vp)]),
+    "assn_scalar_flux": (C.c_int, [_h, _dp]),
+    "assn_scalar_flux_device": (C.c_int, [_h, _vp]),
+    "assn_mass": (C.c_int, [_h, _dp]),
+    "assn_check_finite": (C.c_int, [_h]),
+    "assn_last_error": (C.c_char_p, [_h]),
+    "assn_status_string": (C.c_char_p, [C.c_int]),
+    "assn_launch_count": (C.c_int64, [_h]),
+    "assn_abi_version": (C.c_int, []),
+}
+
+
+class AssnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libassn.so is not built ({LIB_PATH}); run paper_1911_08801_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_string(status: int) -> str:
+    return lib.assn_status_string(status).decode()
+
+
+def _check(status: int, handle=None):
+    if status != ASSN_OK:
+        raise AssnError(status, lib.assn_last_error(handle).decode())
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _contig(a, dtype=np.float64) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def assn_create(nx: int, ny: int, x0: float, x1: float, y0: float, y1: float, precision: int,
+                stream=None) -> int:
+    h = _h()
+    _check(lib.assn_create(C.byref(h), nx, ny, x0, x1, y0, y1, precision, _stream_ptr(stream)), None)
+    return h.value
+
+
+def assn_destroy(h: int) -> None:
+    _check(lib.assn_destroy(h), h)
+
+
+def assn_set_quadrature(h: int, omega, w) -> None:
+    om = _contig(omega).reshape(-1, 3)
+    ww = _contig(w)
+    _check(lib.assn_set_quadrature(h, len(ww), _d(om), _d(ww)), h)
+
+
+def assn_set_product_quadrature(h: int, n_polar: int, n_azim: int) -> None:
+    _check(lib.assn_set_product_quadrature(h, n_polar, n_azim), h)
+
+
+def assn_get_quadrature(h: int):
+    q = C.c_int(0)
+    _check(lib.assn_get_quadrature(h, C.byref(q), None, None), h)
+    om = np.empty((q.value, 3))
+    w = np.empty(q.value)
+    _check(lib.assn_get_quadrature(h, C.byref(q), _d(om), _d(w)), h)
+    return om, w
+
+
+def assn_set_cross_sections(h: int, sigma_a, sigma_s, q) -> None:
+    a, s, src = _contig(sigma_a), _contig(sigma_s), _contig(q)
+    _check(lib.assn_set_cross_sections(h, _d(a), _d(s), _d(src)), h)
+
+
+def assn_set_artificial_scattering(h: int, sigma_as: float, eps: float, kernel_kind: int = ASSN_KERNEL_GAUSS,
+                                   normalisation: int = ASSN_NORM_COLUMN) -> None:
+    _check(lib.assn_set_artificial_scattering(h, sigma_as, eps, kernel_kind, normalisation), h)
+
+
+def assn_get_kernel_matrix(h: int, Q: int) -> np.ndarray:
+    K = np.empty((Q, Q))
+    _check(lib.assn_get_kernel_matrix(h, _d(K)), h)
+    return K
+
+
+def assn_set_state(h: int, psi) -> None:
+    a = _contig(psi)
+    _check(lib.assn_set_state(h, _d(a)), h)
+
+
+def assn_get_state(h: int, shape) -> np.ndarray:
+    out = np.empty(shape)
+    _check(lib.assn_get_state(h, _d(out)), h)
+    return out
+
+
+def assn_set_state_f32(h: int, psi: np.ndarray) -> None:
+    """``psi`` must stay alive and unchanged until the problem's stream has passed the copy."""
+    assert psi.dtype == np.float32 and psi.flags.c_contiguous
+    _check(lib.assn_set_state_f32(h, psi.ctypes.data_as(_fp)), h)
+
+
+def assn_get_state_f32(h: int, out: np.ndarray) -> np.ndarray:
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    _check(lib.assn_get_state_f32(h, out.ctypes.data_as(_fp)), h)
+    return out
+
+
+def assn_init_line_source(h: int, delta: float = 0.03 ** 2, floor_value: float = 1e-4) -> None:
+    _check(lib.assn_init_line_source(h, delta, floor_value), h)
+
+
+def assn_max_stable_dt(h: int) -> float:
+    v = C.c_double(0)
+    _check(lib.assn_max_stable_dt(h, C.byref(v)), h)
+    return v.value
+
+
+def assn_step(h: int, nsteps: int, dt: float) -> None:
+    _check(lib.assn_step(h, nsteps, dt), h)
+
+
+def assn_step_device(h: int, psi_in_dev: int, psi_out_dev: int, dt: float) -> None:
+    _check(lib.assn_step_device(h, psi_in_dev, psi_out_dev, dt), h)
+
+
+def assn_layout(h: int):
+    qp, eb = C.c_int(0), C.c_int(0)
+    _check(lib.assn_layout(h, C.byref(qp), C.byref(eb)), h)
+    return qp.value, eb.value
+
+
+def assn_state_device(h: int) -> int:
+    p = _vp()
+    _check(lib.assn_state_device(h, C.byref(p)), h)
+    return p.value
+
+
+def assn_scalar_flux(h: int, shape) -> np.ndarray:
+    out = np.empty(shape)
+    _check(lib.assn_scalar_flux(h, _d(out)), h)
+    return out
+
+
+def assn_scalar_flux_device(h: int, phi_dev: int) -> None:
+    _check(lib.assn_scalar_flux_device(h, phi_dev), h)
+
+
+def assn_mass(h: int) -> float:
+    v = C.c_double(0)
+    _check(lib.assn_mass(h, C.byref(v)), h)
+    return v.value
+
+
+def assn_check_finite(h: int) -> None:
+    _check(lib.assn_check_finite(h), h)
+
+
+def assn_last_error(h: int | None) -> str:
+    return lib.assn_last_error(h).decode()
+
+
+def assn_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def assn_launch_count(h: int) -> int:
+    return int(lib.assn_launch_count(h))
+
+
+def assn_abi_version() -> int:
+    return int(lib.assn_abi_version())

@@ -1,0 +1,89 @@
+// Internal definitions shared by the translation units of libassn (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/assn.h"
+
+namespace assn {
+
+// Per-ordinate constants of one step (transport part depends on dt).
+//   nux = dt * Omega_x / h, nuy = dt * Omega_y / h   (signed: the sign picks the upwind side)
+//   w   = quadrature weight (0 on padded ordinates)
+//   e   = out-scattering rate of the artificial generator: 1 - K_qq evaluated from the
+//         rounded off-diagonal operand so that the chosen normalisation's invariant holds
+//         exactly for the operand the contraction actually uses.
+struct OrdF { float nux, nuy, w, e; };
+struct OrdD { double nux, nuy, w, e; };
+
+// Per-cell constants: sigma_t = sigma_a + sigma_s, sigma_s / sum_q w_q, q, unused.
+struct CellF { float sig_t, sig_s_over_wsum, q, pad; };
+struct CellD { double sig_t, sig_s_over_wsum, q, pad; };
+
+// Arguments of one fused step launch.
+template <typename T, typename OrdT, typename CellT>
+struct StepArgs {
+    const T* psi;        // [ny][nx][Qp], time level n
+    T* psi_out;          // [ny][nx][Qp], time level n+1
+    const OrdT* ord;     // [Qp]
+    const CellT* cell;   // [ny][nx]
+    const T* KT;         // SIMT paths: [Qp][Qp], KT[p*Qp + q] = K_qp for p != q, 0 on the diagonal
+    int nx, ny, Q, Qp;
+    T dt, dt_sigma_as;
+};
+
+// Tensor-core operands of the BF16 paths.
+struct TcOperands {
+    __nv_bfloat16* G_hi = nullptr;   // [Mp][Qp] row q, column p: off-diagonal K rounded to BF16
+    __nv_bfloat16* G_lo = nullptr;   // [Mp][Qp] residual K - G_hi rounded to BF16 (BF16X3 only)
+    int Mp = 0;                      // Q rounded up to 128 (the MMA M dimension)
+};
+
+// Launchers (each returns cudaSuccess or the launch error).
+cudaError_t launch_build_K(const double* omega, const double* w, int Q, double eps, int kind,
+                           int norm, double* K64, cudaStream_t s);
+cudaError_t launch_derive_simt_f64(const double* K64, const double* w, int Q, int Qp, int norm,
+                                   double* KT, double* e, cudaStream_t s);
+cudaError_t launch_derive_simt_f32(const double* K64, const double* w, int Q, int Qp, int norm,
+                                   float* KT, double* e, cudaStream_t s);
+cudaError_t launch_derive_tc(const double* K64, const double* w, int Q, int Qp, int Mp, int norm,
+                             bool split, __nv_bfloat16* G_hi, __nv_bfloat16* G_lo, double* e,
+                             cudaStream_t s);
+
+cudaError_t launch_step_simt_f64(const StepArgs<double, OrdD, CellD>& a, cudaStream_t s);
+cudaError_t launch_step_simt_f32(const StepArgs<float, OrdF, CellF>& a, cudaStream_t s);
+
+// Tensor-core step.  Returns cudaErrorNotSupported for shapes the kernel does not cover.
+struct TcPlan;
+cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* G_hi, const __nv_bfloat16* G_lo,
+                           int Q, int Qp, int Mp, int nx, int ny, bool split);
+void tc_plan_destroy(TcPlan* plan);
+cudaError_t launch_step_tc(TcPlan* plan, const StepArgs<float, OrdF, CellF>& a, const float* w,
+                           unsigned int* err_flag, cudaStream_t s);
+int tc_plan_tile_cells(const TcPlan* plan);
+
+template <typename T>
+cudaError_t launch_scalar_flux(const T* psi, const T* w, int ncell, int Qp, float* out_f,
+                               double* out_d, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mass_partials(const T* psi, const T* w, int ncell, int Qp, double* partials,
+                                 int nblocks, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double* partials, int n, double* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_check_finite(const T* psi, size_t n, unsigned int* flag, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init_line_source(T* psi, int nx, int ny, int Q, int Qp, double x0, double y0,
+                                    double h, double delta, double floor_value, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pack_state(const double* src, T* dst, size_t ncell, int Q, int Qp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unpack_state(const T* src, double* dst, size_t ncell, int Q, int Qp, cudaStream_t s);
+
+constexpr int kMassBlocks = 1024;
+
+}  // namespace assn

@@ -1,0 +1,81 @@
+"""Shared set-up for the GPU tests: build problems from synthetic workloads, run the oracle."""
+from __future__ import annotations
+
+import math
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+import synth  # noqa: E402
+
+
+def ensure_built():
+    from paper_1911_08801_gb300 import build as B
+    B.build()
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_problem(A, wl: synth.Workload, precision: str, psi0=None, sigma_as=None, normalisation=0, kind=0):
+    p = A.Problem(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1, precision)
+    p.set_product_quadrature(wl.n_polar, wl.n_azim)
+    sa, ss, q = wl.materials()
+    p.set_cross_sections(sa, ss, q)
+    p.set_artificial_scattering(wl.sigma_as if sigma_as is None else sigma_as, wl.eps, kind, normalisation)
+    p.set_state(wl.psi0() if psi0 is None else psi0)
+    return p
+
+
+def oracle_setup(wl: synth.Workload, normalisation="column", kind="gauss"):
+    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
+    K = O.kernel_matrix(Om, w, wl.eps, kind=kind, normalisation=normalisation)
+    sa, ss, q = wl.materials()
+    return Om, w, K, sa, ss, q
+
+
+def oracle_run(wl: synth.Workload, nsteps: int, dt: float, psi0=None, normalisation="column", sigma_as=None):
+    Om, w, K, sa, ss, q = oracle_setup(wl, normalisation)
+    psi = wl.psi0() if psi0 is None else psi0
+    s_as = wl.sigma_as if sigma_as is None else sigma_as
+    return O.run(psi, nsteps, K, Om, w, sa, ss, q, s_as, wl.h, dt), w
+
+
+def step_tolerance(precision: str, dt: float, sigma_as: float, scale: float, rowsum: float = 1.0) -> float:
+    """Per-element bound on |GPU - FP64| after ONE step from the same state.
+
+    ``scale`` bounds |psi|; ``rowsum`` bounds sum_{p != q} K_qp (above 1 for the column
+    normalisation).  FP32 state arithmetic: a few ulps of the largest term (~1e-6 relative).
+    BF16 contraction: both operands rounded to nearest BF16 (relative error <= 2^-9 each), so the
+    gain sum_p G_qp psi_p is off by <= 2^-8 * rowsum * max|psi|, and the loss term uses the same
+    rounded psi (<= 2^-9 * max|psi|); both enter multiplied by dt * sigma_as.  BF16X3 carries the
+    residuals, leaving ~2^-16 relative per operand.
+    """
+    fp32 = 4e-6 * scale
+    if precision == "fp64":
+        return 1e-13 * scale
+    if precision == "fp32":
+        return fp32
+    if precision == "bf16":
+        return dt * sigma_as * (2.0 ** -8 * rowsum + 2.0 ** -9) * scale * 1.05 + fp32
+    if precision == "bf16x3":
+        return dt * sigma_as * 2.0 ** -14 * (rowsum + 1.0) * scale + fp32
+    raise ValueError(precision)
+
+
+def offdiag_rowsum(K) -> float:
+    K = np.asarray(K)
+    return float((K.sum(axis=1) - np.diag(K)).max())
+
+
+# relative L2 tolerance on the scalar flux of a whole run against the FP64 oracle
+RUN_TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 1e-5, "bf16": 1e-3}
