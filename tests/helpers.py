@@ -16,8 +16,8 @@ import synth  # noqa: E402
 
 
 def ensure_built():
-    from paper_1911_08801_gb300 import build as B
-    B.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
 
 
 def rel_l2(a, b) -> float:
