@@ -149,8 +149,8 @@ int assn_get_state_f32(assn_problem* p, float* psi_host);
 int assn_init_line_source(assn_problem* p, double delta, double floor_value);
 
 /* Largest dt for which the explicit step keeps every coefficient of the update
- * non-negative (positivity): dt * (|Omega_x|/h + |Omega_y|/h + sigma_a + sigma_s + sigma_as) <= 1
- * for every ordinate and cell.  Requires quadrature, cross sections and sigma_as. */
+ * non-negative (positivity): dt * (max_q [(|Omega_x,q| + |Omega_y,q|)/h + sigma_as (1 - K_qq)]
+ * + max_cells [sigma_a + sigma_s]) <= 1.  Requires quadrature, cross sections and K. */
 int assn_max_stable_dt(assn_problem* p, double* dt_out);
 
 /* Advance nsteps explicit steps of size dt on the problem's stream (asynchronous; the

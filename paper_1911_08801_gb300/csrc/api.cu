@@ -200,13 +200,16 @@ int upload_ord(assn_problem* p, double dt) {
     return ASSN_OK;
 }
 
+// Largest dt keeping the coefficient of psi_q in its own update non-negative (all other
+// coefficients are non-negative): 1 - dt (|Omega_x| + |Omega_y|)/h - dt sigma_as e_q
+// - dt (sigma_a + sigma_s) >= 0, maximised over ordinates and cells separately.
 double max_stable_dt(const assn_problem* p) {
     double vmax = 0;
     for (int q = 0; q < p->Q; ++q)
-        vmax = std::max(vmax, (fabs(p->omega[3 * q]) + fabs(p->omega[3 * q + 1])) / p->h);
+        vmax = std::max(vmax, (fabs(p->omega[3 * q]) + fabs(p->omega[3 * q + 1])) / p->h + p->sigma_as * p->e[q]);
     double smax = 0;
     for (size_t c = 0; c < p->ncell(); ++c) smax = std::max(smax, p->sa[c] + p->ss[c]);
-    const double rate = vmax + smax + p->sigma_as;
+    const double rate = vmax + smax;
     return rate > 0 ? 1.0 / rate : INFINITY;
 }
 

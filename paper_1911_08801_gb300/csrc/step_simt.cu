@@ -42,7 +42,7 @@ step_simt_kernel(const StepArgs<T, OrdT, CellT> a) {
     for (int idx = threadIdx.x; idx < (TN + 2) * Qp; idx += blockDim.x) {
         const int sl = idx / Qp, q = idx - sl * Qp;
         const int x = x0 - 1 + sl;
-        ps[idx] = (x >= 0 && x < nx && sl <= nt) ? a.psi[(row + x) * Qp + q] : T(0);
+        ps[idx] = (x >= 0 && x < nx) ? a.psi[(row + x) * Qp + q] : T(0);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;

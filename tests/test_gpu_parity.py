@@ -64,7 +64,11 @@ def test_kernel_matrix_matches_oracle(A, kind, norm, npol, naz, eps):
     Om, w = O.product_quadrature(npol, naz)
     Ko = O.kernel_matrix(Om, w, eps, kind="gauss" if kind == 0 else "exp",
                          normalisation="column" if norm == 0 else "row")
-    assert np.allclose(K, Ko, rtol=1e-13, atol=1e-300)
+    # exp(-(1-mu)^2/eps^2) amplifies the last-bit difference of the dot product mu by
+    # 2 (1-mu)/eps^2: compare entries relative to the largest one, and the significant ones tightly
+    assert np.abs(K - Ko).max() <= 1e-14 * Ko.max()
+    big = Ko > 1e-8 * Ko.max()
+    assert np.max(np.abs(K[big] - Ko[big]) / Ko[big]) <= 1e-11
     p.close()
 
 
@@ -121,8 +125,10 @@ def test_line_source_64_full_run(A, precision):
 
 @pytest.mark.parametrize("precision", PRECS)
 def test_lattice_small_full_run(A, precision):
-    """Lattice layout at 7 cells per block (49 x 49), Q = 64, to t = 0.8 against the oracle."""
+    """Lattice layout at 7 cells per block (49 x 49), Q = 64, to t = 0.8 against the oracle
+    (CFL 0.2: the absorbers' sigma_t = 10 needs the smaller step at this coarse h)."""
     wl = synth.lattice(49, 8, 8, 0.5, t_final=0.8)
+    wl.cfl = 0.2
     n, dt = wl.steps()
     p = gpu_problem(A, wl, precision)
     p.step(n, dt)
