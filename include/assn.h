@@ -165,6 +165,11 @@ int assn_step(assn_problem* p, int nsteps, double dt);
  * Qpad from assn_layout).  psi_in_dev and psi_out_dev must not overlap.  Asynchronous. */
 int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev, double dt);
 
+/* One call from host data to host result: upload psi0 (FP32 [ny][nx][Q] host; pinned memory gives
+ * full copy bandwidth), take nsteps steps of size dt on the device, and return the scalar flux
+ * [ny][nx] in FP64.  Syncs.  FP32/BF16/BF16X3 problems only (ASSN_ERR_UNSUPPORTED on FP64). */
+int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt, double* phi_host);
+
 /* Device layout of the state: *Qpad = padded ordinate stride, *elem_bytes = 4 or 8. */
 int assn_layout(const assn_problem* p, int* Qpad, int* elem_bytes);
 

@@ -54,6 +54,7 @@ SIGNATURES = {
     "assn_max_stable_dt": (C.c_int, [_h, _dp]),
     "assn_step": (C.c_int, [_h, C.c_int, C.c_double]),
     "assn_step_device": (C.c_int, [_h, _vp, _vp, C.c_double]),
+    "assn_run_f32": (C.c_int, [_h, _fp, C.c_int, C.c_double, _dp]),
     "assn_layout": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "assn_state_device": (C.c_int, [_h, C.POINTER(_vp)]),
     "assn_scalar_flux": (C.c_int, [_h, _dp]),
@@ -198,6 +199,13 @@ def assn_step(h: int, nsteps: int, dt: float) -> None:
 
 def assn_step_device(h: int, psi_in_dev: int, psi_out_dev: int, dt: float) -> None:
     _check(lib.assn_step_device(h, psi_in_dev, psi_out_dev, dt), h)
+
+
+def assn_run_f32(h: int, psi0: np.ndarray, nsteps: int, dt: float, phi_out: np.ndarray) -> np.ndarray:
+    assert psi0.dtype == np.float32 and psi0.flags.c_contiguous
+    assert phi_out.dtype == np.float64 and phi_out.flags.c_contiguous
+    _check(lib.assn_run_f32(h, psi0.ctypes.data_as(_fp), nsteps, dt, _d(phi_out)), h)
+    return phi_out
 
 
 def assn_layout(h: int):

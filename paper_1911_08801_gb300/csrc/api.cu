@@ -633,6 +633,18 @@ int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev,
     return step_once(p, psi_in_dev, psi_out_dev, dt);
 }
 
+int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt, double* phi_host) {
+    if (!p || !psi0_host || !phi_host) return ASSN_ERR_ARG;
+    if (nsteps < 0) return fail(p, ASSN_ERR_ARG, "nsteps < 0");
+    int r = prepare_step(p, dt);
+    if (r) return r;
+    r = assn_set_state_f32(p, psi0_host);
+    if (r) return r;
+    r = assn_step(p, nsteps, dt);
+    if (r) return r;
+    return assn_scalar_flux(p, phi_host);
+}
+
 int assn_scalar_flux(assn_problem* p, double* phi_host) {
     if (!p || !phi_host) return ASSN_ERR_ARG;
     if (!p->have_quad) return fail(p, ASSN_ERR_STATE, "no quadrature set");
