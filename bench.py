@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default=synth.LATTICE_448.name, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64/e2e/CPU legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tile", type=int, default=0, help="tensor-core tile cells (0 = automatic)")
+    ap.add_argument("--stages", type=int, default=0, help="tensor-core kernel-matrix ring depth (0 = automatic)")
     return ap.parse_args()
 
 
@@ -139,6 +141,10 @@ def run_ours(args, rank, world, dist):
     n_total, dt = wl.steps()
     stream = torch.cuda.Stream()
     prob = make_problem(A, wl, args.precision, stream)
+    tiling = None
+    if args.precision.startswith("bf16"):
+        prob.set_tiling(args.tile, args.stages)
+        tiling = prob.tiling()
     psi0 = torch.from_numpy(seeded_state_f32(wl, seed=rank)).pin_memory().numpy()
     if args.precision == "fp64":
         prob.set_state(psi0.astype(np.float64))
@@ -197,7 +203,7 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": wl.name, "cells": f"{wl.nx}x{wl.ny}", "Q": wl.Q, "beta": wl.beta,
                    "eps": wl.eps, "sigma_as": wl.sigma_as, "dt": dt, "precision": args.precision,
                    "l2": "state larger than L2 (%.0f MB per buffer)" % (units * 4 / 1e6),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "tiling": tiling},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],

@@ -22,10 +22,11 @@ class Problem:
     def __init__(self, nx: int, ny: int, x0: float, x1: float, y0: float, y1: float,
                  precision="bf16", stream=None):
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.handle = None
+        self.handle = _lib.assn_create(nx, ny, x0, x1, y0, y1, self.precision, stream)
         self.nx, self.ny = nx, ny
         self.h = (x1 - x0) / nx
         self.Q = 0
-        self.handle = _lib.assn_create(nx, ny, x0, x1, y0, y1, self.precision, stream)
 
     # -- set-up
     def set_product_quadrature(self, n_polar: int, n_azim: int):
@@ -81,6 +82,13 @@ class Problem:
 
     def check_finite(self):
         _lib.assn_check_finite(self.handle)
+
+    def set_tiling(self, tile_cells: int = 0, stages: int = 0):
+        _lib.assn_set_tiling(self.handle, tile_cells, stages)
+        return self
+
+    def tiling(self) -> dict:
+        return _lib.assn_get_tiling(self.handle)
 
     def layout(self):
         return _lib.assn_layout(self.handle)

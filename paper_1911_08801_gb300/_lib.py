@@ -55,6 +55,9 @@ SIGNATURES = {
     "assn_step": (C.c_int, [_h, C.c_int, C.c_double]),
     "assn_step_device": (C.c_int, [_h, _vp, _vp, C.c_double]),
     "assn_run_f32": (C.c_int, [_h, _fp, C.c_int, C.c_double, _dp]),
+    "assn_set_tiling": (C.c_int, [_h, C.c_int, C.c_int]),
+    "assn_get_tiling": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int64)]),
     "assn_layout": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "assn_state_device": (C.c_int, [_h, C.POINTER(_vp)]),
     "assn_scalar_flux": (C.c_int, [_h, _dp]),
@@ -206,6 +209,16 @@ def assn_run_f32(h: int, psi0: np.ndarray, nsteps: int, dt: float, phi_out: np.n
     assert phi_out.dtype == np.float64 and phi_out.flags.c_contiguous
     _check(lib.assn_run_f32(h, psi0.ctypes.data_as(_fp), nsteps, dt, _d(phi_out)), h)
     return phi_out
+
+
+def assn_set_tiling(h: int, tile_cells: int = 0, stages: int = 0) -> None:
+    _check(lib.assn_set_tiling(h, tile_cells, stages), h)
+
+
+def assn_get_tiling(h: int) -> dict:
+    t, s, c, m = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int64(0)
+    _check(lib.assn_get_tiling(h, C.byref(t), C.byref(s), C.byref(c), C.byref(m)), h)
+    return {"tile_cells": t.value, "stages": s.value, "tmem_cols": c.value, "smem_bytes": m.value}
 
 
 def assn_layout(h: int):

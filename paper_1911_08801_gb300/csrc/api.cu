@@ -55,6 +55,8 @@ struct assn_problem {
     double* d_stage = nullptr;
     size_t stage_elems = 0;
 
+    int want_nt = 0, want_stages = 0;   // tensor-core tiling request (0 = automatic)
+
     std::string err;
     int64_t launches = 0;
 
@@ -605,7 +607,7 @@ static int prepare_step(assn_problem* p, double dt) {
     if (r) return r;
     if (p->tensor() && !p->plan) {
         cudaError_t e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
-                                       p->precision == ASSN_BF16X3);
+                                       p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
         if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: Q = %d not supported", p->Q);
         CK(p, e);
     }
@@ -631,6 +633,37 @@ int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev,
     int r = prepare_step(p, dt);
     if (r) return r;
     return step_once(p, psi_in_dev, psi_out_dev, dt);
+}
+
+int assn_set_tiling(assn_problem* p, int tile_cells, int stages) {
+    if (!p) return ASSN_ERR_ARG;
+    if (tile_cells != 0 && tile_cells != 32 && tile_cells != 64 && tile_cells != 128)
+        return fail(p, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64 or 128");
+    if (stages != 0 && (stages < 2 || stages > 8)) return fail(p, ASSN_ERR_ARG, "stages must be 0 or 2..8");
+    p->want_nt = tile_cells;
+    p->want_stages = stages;
+    if (p->plan) tc_plan_destroy(p->plan);
+    p->plan = nullptr;
+    return ASSN_OK;
+}
+
+int assn_get_tiling(assn_problem* p, int* tile_cells, int* stages, int* tmem_cols, int64_t* smem_bytes) {
+    if (!p) return ASSN_ERR_ARG;
+    if (!p->tensor()) return fail(p, ASSN_ERR_UNSUPPORTED, "tiling applies to the tensor-core precisions");
+    int r = ready(p);
+    if (r) return r;
+    if (!p->plan) {
+        r = set_device(p);
+        if (r) return r;
+        cudaError_t e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
+                                       p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
+        if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tiling not supported for Q = %d", p->Q);
+        CK(p, e);
+    }
+    size_t sm = 0;
+    tc_plan_describe(p->plan, tile_cells, stages, tmem_cols, &sm);
+    if (smem_bytes) *smem_bytes = (int64_t)sm;
+    return ASSN_OK;
 }
 
 int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt, double* phi_host) {

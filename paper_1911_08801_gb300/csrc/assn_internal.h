@@ -61,11 +61,11 @@ cudaError_t launch_step_simt_f32(const StepArgs<float, OrdF, CellF>& a, cudaStre
 // Tensor-core step.  Returns cudaErrorNotSupported for shapes the kernel does not cover.
 struct TcPlan;
 cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* G_hi, const __nv_bfloat16* G_lo,
-                           int Q, int Qp, int Mp, int nx, int ny, bool split);
+                           int Q, int Qp, int Mp, int nx, int ny, bool split, int want_nt, int want_stages);
+void tc_plan_describe(const TcPlan* plan, int* tile_cells, int* stages, int* tmem_cols, size_t* smem);
 void tc_plan_destroy(TcPlan* plan);
 cudaError_t launch_step_tc(TcPlan* plan, const StepArgs<float, OrdF, CellF>& a, const float* w,
                            unsigned int* err_flag, cudaStream_t s);
-int tc_plan_tile_cells(const TcPlan* plan);
 
 template <typename T>
 cudaError_t launch_scalar_flux(const T* psi, const T* w, int ncell, int Qp, float* out_f,

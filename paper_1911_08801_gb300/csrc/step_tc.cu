@@ -311,37 +311,57 @@ step_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
     go = __shfl_sync(0xffffffffu, go, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (go) {
+        const float* __restrict__ psi = a.psi;
+        float* __restrict__ psi_out = a.psi_out;
         const int lq = warp & 3;                 // TMEM lane quarter of this warp
         const int half = warp >> 2;              // which half of the tile's cells
         const int cbeg = half * (NT / 2), cend = cbeg + NT / 2;
+        const size_t ystride = (size_t)a.nx * Qp;
         for (int m = 0; m < a.MB; ++m) {
             const int q = m * 128 + lq * 32 + lane;
             const bool qv = q < a.Q;
-            const bool qp = q < Qp;
-            OrdF o = qp ? a.ord[q] : OrdF{0.f, 0.f, 0.f, 0.f};
+            const OrdF o = q < Qp ? a.ord[q] : OrdF{0.f, 0.f, 0.f, 0.f};
             const float ax = fabsf(o.nux), ay = fabsf(o.nuy);
+            // upwind neighbour offsets (in elements) and whether the neighbour is inside the grid
+            const long dx = o.nux > 0.f ? -(long)Qp : (long)Qp;
+            const long dy = o.nuy > 0.f ? -(long)ystride : (long)ystride;
+            const bool ybound = o.nuy > 0.f ? (j > 0) : (j + 1 < a.ny);
+            const bool use_y = o.nuy != 0.f && ybound;
             for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 float y[16];
                 tmem_ld16(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(m * NT + c0), y);
+                if (!qv) {
+                    if (q < Qp) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (c0 + i < nt) psi_out[(row + x0 + c0 + i) * Qp + q] = 0.0f;
+                    }
+                    continue;
+                }
+                float self[16], upx[16], upy[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {       // issue every load of the chunk first
+                    const int c = c0 + i;
+                    const int x = x0 + c;
+                    const bool in = c < nt;
+                    const size_t idx = (row + (in ? x : x0)) * Qp + q;
+                    self[i] = in ? psi[idx] : 0.0f;
+                    const int xn = o.nux > 0.f ? x - 1 : x + 1;
+                    upx[i] = (in && o.nux != 0.f && xn >= 0 && xn < a.nx) ? psi[idx + dx] : 0.0f;
+                    upy[i] = (in && use_y) ? psi[idx + dy] : 0.0f;
+                }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int c = c0 + i;
-                    if (c >= nt || !qp) continue;
+                    if (c >= nt) continue;
                     const int x = x0 + c;
-                    const size_t idx = (row + x) * Qp + q;
-                    if (!qv) { a.psi_out[idx] = 0.0f; continue; }
-                    const float self = a.psi[idx];
-                    float upx = 0.0f, upy = 0.0f;
-                    if (o.nux > 0.f) { if (x > 0) upx = a.psi[idx - Qp]; }
-                    else if (o.nux < 0.f) { if (x + 1 < a.nx) upx = a.psi[idx + Qp]; }
-                    if (o.nuy > 0.f) { if (j > 0) upy = a.psi[idx - (size_t)a.nx * Qp]; }
-                    else if (o.nuy < 0.f) { if (j + 1 < a.ny) upy = a.psi[idx + (size_t)a.nx * Qp]; }
                     const CellF cl = a.cell[row + x];
-                    const float st = SPLIT ? self : __bfloat162float(__float2bfloat16_rn(self));
-                    const float out = self - ax * (self - upx) - ay * (self - upy) - a.dt * cl.sig_t * self +
+                    const float sf = self[i];
+                    const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
+                    const float out = sf - ax * (sf - upx[i]) - ay * (sf - upy[i]) - a.dt * cl.sig_t * sf +
                                       a.dt * (cl.sig_s_over_wsum * phi[c] + cl.q) +
                                       a.dt_sigma_as * (y[i] - o.e * st);
-                    a.psi_out[idx] = out;
+                    psi_out[(row + x) * Qp + q] = out;
                 }
             }
         }
@@ -398,20 +418,30 @@ struct TcPlan {
     size_t smem;
 };
 
-int tc_plan_tile_cells(const TcPlan* plan) { return plan ? plan->NT : 0; }
+void tc_plan_describe(const TcPlan* p, int* tile_cells, int* stages, int* tmem_cols, size_t* smem) {
+    if (tile_cells) *tile_cells = p ? p->NT : 0;
+    if (stages) *stages = p ? p->S : 0;
+    if (tmem_cols) *tmem_cols = p ? p->tmem_cols : 0;
+    if (smem) *smem = p ? p->smem : 0;
+}
 
 cudaError_t tc_plan_create(TcPlan** out, const __nv_bfloat16* G_hi, const __nv_bfloat16* G_lo, int Q, int Qp,
-                           int Mp, int nx, int ny, bool split) {
+                           int Mp, int nx, int ny, bool split, int want_nt, int want_stages) {
     *out = nullptr;
     TcPlan* p = new TcPlan();
     p->Q = Q; p->Qp = Qp; p->Mp = Mp; p->MB = Mp / 128; p->nx = nx; p->ny = ny; p->split = split;
-    // Tile width: the widest of 128 / 64 / 32 cells whose accumulators fit the 512 TMEM columns
-    // and whose B operand plus a 2-stage A ring fits 200 KB of shared memory.
+    // Tile width: the widest of 128 / 64 / 32 cells (or the requested one) whose accumulators use at
+    // most half of the 512 TMEM columns (two CTAs per SM overlap their phases) -- or all of them
+    // when nothing smaller fits -- and whose B operand plus a 2-stage A ring fits 200 KB of smem.
     p->NT = 0;
-    for (int nt : {128, 64, 32}) {
-        const size_t b = (size_t)nt * Qp * 2 * (split ? 2 : 1);
-        const size_t a2 = (size_t)2 * kStageBytes * (split ? 2 : 1);
-        if (p->MB * nt <= 512 && b + a2 <= 200 * 1024) { p->NT = nt; break; }
+    for (int pass = 0; pass < 2 && p->NT == 0; ++pass) {
+        for (int nt : {128, 64, 32}) {
+            if (want_nt && nt != want_nt) continue;
+            const size_t b = (size_t)nt * Qp * 2 * (split ? 2 : 1);
+            const size_t a2 = (size_t)2 * kStageBytes * (split ? 2 : 1);
+            const int cap = (pass == 0 && !want_nt) ? 256 : 512;
+            if (p->MB * nt <= cap && b + a2 <= 200 * 1024) { p->NT = nt; break; }
+        }
     }
     if (p->NT == 0) { delete p; return cudaErrorNotSupported; }
     int cols = p->MB * p->NT;
@@ -422,6 +452,9 @@ cudaError_t tc_plan_create(TcPlan** out, const __nv_bfloat16* G_hi, const __nv_b
     const size_t b = (size_t)p->NT * Qp * 2 * (split ? 2 : 1);
     p->S = 2;
     while (p->S < 4 && b + (size_t)(p->S + 1) * kStageBytes * (split ? 2 : 1) <= 100 * 1024) p->S++;
+    if (want_stages >= 2 && want_stages <= 8 &&
+        b + (size_t)want_stages * kStageBytes * (split ? 2 : 1) <= 200 * 1024)
+        p->S = want_stages;
     // Residency: never more CTAs per SM than TMEM can hold at once.
     const int max_ctas = 512 / tc;
     size_t sm = 0;
