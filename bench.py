@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile", type=int, default=0, help="tensor-core tile cells (0 = automatic)")
     ap.add_argument("--stages", type=int, default=0, help="tensor-core kernel-matrix ring depth (0 = automatic)")
+    ap.add_argument("--variant", type=int, default=0, help="tensor-core kernel: 0 persistent, 1 one tile per CTA")
     return ap.parse_args()
 
 
@@ -143,7 +144,7 @@ def run_ours(args, rank, world, dist):
     prob = make_problem(A, wl, args.precision, stream)
     tiling = None
     if args.precision.startswith("bf16"):
-        prob.set_tiling(args.tile, args.stages)
+        prob.set_tiling(args.tile, args.stages, args.variant)
         tiling = prob.tiling()
     psi0 = torch.from_numpy(seeded_state_f32(wl, seed=rank)).pin_memory().numpy()
     if args.precision == "fp64":
@@ -207,7 +208,8 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
-                     "kernel": "step_tc_kernel" if args.precision.startswith("bf16") else "step_simt_kernel"},
+                     "kernel": ("step_tc2_kernel" if args.variant == 0 else "step_tc_kernel") if args.precision.startswith("bf16")
+                     else "step_simt_kernel"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "wall_s_timed": wall,

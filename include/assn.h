@@ -170,10 +170,13 @@ int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev,
  * [ny][nx] in FP64.  Syncs.  FP32/BF16/BF16X3 problems only (ASSN_ERR_UNSUPPORTED on FP64). */
 int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt, double* phi_host);
 
-/* Tensor-core tiling (BF16 / BF16X3 problems): cells per CTA tile (32, 64 or 128; 0 = automatic)
- * and depth of the shared-memory ring that streams the kernel matrix (2..8; 0 = automatic).
- * Takes effect at the next step.  Results do not depend on the tiling. */
-int assn_set_tiling(assn_problem* p, int tile_cells, int stages);
+/* Tensor-core kernel and tiling (BF16 / BF16X3 problems).  variant 0 (default): persistent
+ * warp-specialised kernel, one CTA per SM, TMA-fed rings and two TMEM accumulator buffers;
+ * variant 1: one tile per CTA (simpler, slower).  tile_cells: cells per tile (32, 64, 128 or 256;
+ * 0 = automatic).  stages: ring depth (2..8; 0 = automatic).  Takes effect at the next step; the
+ * results do not depend on these choices.  ASSN_ERR_UNSUPPORTED at the next step if the
+ * combination does not fit the SM. */
+int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant);
 
 /* The tiling the next step will use (resolving automatic choices): tile cells, ring stages,
  * tensor-memory columns and dynamic shared memory per CTA.  Any output pointer may be NULL. */

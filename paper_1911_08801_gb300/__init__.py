@@ -83,8 +83,8 @@ class Problem:
     def check_finite(self):
         _lib.assn_check_finite(self.handle)
 
-    def set_tiling(self, tile_cells: int = 0, stages: int = 0):
-        _lib.assn_set_tiling(self.handle, tile_cells, stages)
+    def set_tiling(self, tile_cells: int = 0, stages: int = 0, variant: int = 0):
+        _lib.assn_set_tiling(self.handle, tile_cells, stages, variant)
         return self
 
     def tiling(self) -> dict:

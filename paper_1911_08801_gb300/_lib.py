@@ -55,7 +55,7 @@ SIGNATURES = {
     "assn_step": (C.c_int, [_h, C.c_int, C.c_double]),
     "assn_step_device": (C.c_int, [_h, _vp, _vp, C.c_double]),
     "assn_run_f32": (C.c_int, [_h, _fp, C.c_int, C.c_double, _dp]),
-    "assn_set_tiling": (C.c_int, [_h, C.c_int, C.c_int]),
+    "assn_set_tiling": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
     "assn_get_tiling": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int64)]),
     "assn_layout": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -211,8 +211,8 @@ def assn_run_f32(h: int, psi0: np.ndarray, nsteps: int, dt: float, phi_out: np.n
     return phi_out
 
 
-def assn_set_tiling(h: int, tile_cells: int = 0, stages: int = 0) -> None:
-    _check(lib.assn_set_tiling(h, tile_cells, stages), h)
+def assn_set_tiling(h: int, tile_cells: int = 0, stages: int = 0, variant: int = 0) -> None:
+    _check(lib.assn_set_tiling(h, tile_cells, stages, variant), h)
 
 
 def assn_get_tiling(h: int) -> dict:

@@ -42,7 +42,9 @@ struct assn_problem {
     double* d_KT64 = nullptr;
     float* d_KT32 = nullptr;
     TcOperands tc;
-    TcPlan* plan = nullptr;
+    TcPlan* plan = nullptr;      // one-tile-per-CTA tensor-core kernel (variant 1)
+    Tc2Plan* plan2 = nullptr;    // persistent warp-specialised kernel (variant 0, default)
+    int variant = 0;
     double* d_e = nullptr;
     void* d_ord = nullptr;
     double ord_dt = -1.0;
@@ -64,6 +66,7 @@ struct assn_problem {
     size_t elem() const { return precision == ASSN_FP64 ? 8 : 4; }
     bool tensor() const { return precision == ASSN_BF16 || precision == ASSN_BF16X3; }
 };
+
 
 namespace {
 
@@ -144,6 +147,8 @@ void free_operands(assn_problem* p) {
     dfree(p->d_e);
     if (p->plan) tc_plan_destroy(p->plan);
     p->plan = nullptr;
+    if (p->plan2) tc2_plan_destroy(p->plan2);
+    p->plan2 = nullptr;
     p->have_K = false;
 }
 
@@ -585,12 +590,28 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
         if (p->precision == ASSN_FP32) {
             CK(p, launch_step_simt_f32(a, p->stream));
         } else {
-            cudaError_t e = launch_step_tc(p->plan, a, p->d_w32, p->d_flags + 1, p->stream);
+            cudaError_t e = p->variant == 1 ? launch_step_tc(p->plan, a, p->d_w32, p->d_flags + 1, p->stream)
+                                            : launch_step_tc2(p->plan2, a, p->d_w32, p->d_flags + 1, p->stream);
             if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: shape not supported");
             CK(p, e);
         }
     }
     p->launches++;
+    return ASSN_OK;
+}
+
+static int ensure_plan(assn_problem* p) {
+    cudaError_t e = cudaSuccess;
+    if (p->variant == 1 && !p->plan)
+        e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
+                           p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
+    else if (p->variant == 0 && !p->plan2)
+        e = tc2_plan_create(&p->plan2, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
+                            p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
+    if (e == cudaErrorNotSupported)
+        return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: Q = %d with tile %d / stages %d not supported", p->Q,
+                    p->want_nt, p->want_stages);
+    CK(p, e);
     return ASSN_OK;
 }
 
@@ -605,11 +626,9 @@ static int prepare_step(assn_problem* p, double dt) {
     if (r) return r;
     r = upload_ord(p, dt);
     if (r) return r;
-    if (p->tensor() && !p->plan) {
-        cudaError_t e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
-                                       p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
-        if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: Q = %d not supported", p->Q);
-        CK(p, e);
+    if (p->tensor()) {
+        r = ensure_plan(p);
+        if (r) return r;
     }
     return ASSN_OK;
 }
@@ -635,15 +654,19 @@ int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev,
     return step_once(p, psi_in_dev, psi_out_dev, dt);
 }
 
-int assn_set_tiling(assn_problem* p, int tile_cells, int stages) {
+int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant) {
     if (!p) return ASSN_ERR_ARG;
-    if (tile_cells != 0 && tile_cells != 32 && tile_cells != 64 && tile_cells != 128)
-        return fail(p, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64 or 128");
+    if (tile_cells != 0 && tile_cells != 32 && tile_cells != 64 && tile_cells != 128 && tile_cells != 256)
+        return fail(p, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64, 128 or 256");
     if (stages != 0 && (stages < 2 || stages > 8)) return fail(p, ASSN_ERR_ARG, "stages must be 0 or 2..8");
+    if (variant != 0 && variant != 1) return fail(p, ASSN_ERR_ARG, "variant must be 0 or 1");
     p->want_nt = tile_cells;
     p->want_stages = stages;
+    p->variant = variant;
     if (p->plan) tc_plan_destroy(p->plan);
     p->plan = nullptr;
+    if (p->plan2) tc2_plan_destroy(p->plan2);
+    p->plan2 = nullptr;
     return ASSN_OK;
 }
 
@@ -652,16 +675,13 @@ int assn_get_tiling(assn_problem* p, int* tile_cells, int* stages, int* tmem_col
     if (!p->tensor()) return fail(p, ASSN_ERR_UNSUPPORTED, "tiling applies to the tensor-core precisions");
     int r = ready(p);
     if (r) return r;
-    if (!p->plan) {
-        r = set_device(p);
-        if (r) return r;
-        cudaError_t e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
-                                       p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
-        if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tiling not supported for Q = %d", p->Q);
-        CK(p, e);
-    }
+    r = set_device(p);
+    if (r) return r;
+    r = ensure_plan(p);
+    if (r) return r;
     size_t sm = 0;
-    tc_plan_describe(p->plan, tile_cells, stages, tmem_cols, &sm);
+    if (p->variant == 1) tc_plan_describe(p->plan, tile_cells, stages, tmem_cols, &sm);
+    else tc2_plan_describe(p->plan2, tile_cells, stages, tmem_cols, &sm);
     if (smem_bytes) *smem_bytes = (int64_t)sm;
     return ASSN_OK;
 }

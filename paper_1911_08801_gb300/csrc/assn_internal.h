@@ -67,6 +67,15 @@ void tc_plan_destroy(TcPlan* plan);
 cudaError_t launch_step_tc(TcPlan* plan, const StepArgs<float, OrdF, CellF>& a, const float* w,
                            unsigned int* err_flag, cudaStream_t s);
 
+// Persistent warp-specialised tensor-core step (the default tensor-core kernel).
+struct Tc2Plan;
+cudaError_t tc2_plan_create(Tc2Plan** plan, const __nv_bfloat16* G_hi, const __nv_bfloat16* G_lo,
+                            int Q, int Qp, int Mp, int nx, int ny, bool split, int want_nt, int want_stages);
+void tc2_plan_destroy(Tc2Plan* plan);
+void tc2_plan_describe(const Tc2Plan* plan, int* tile_cells, int* stages, int* tmem_cols, size_t* smem);
+cudaError_t launch_step_tc2(Tc2Plan* plan, const StepArgs<float, OrdF, CellF>& a, const float* w,
+                            unsigned int* err_flag, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_scalar_flux(const T* psi, const T* w, int ncell, int Qp, float* out_f,
                                double* out_d, cudaStream_t s);

@@ -329,6 +329,7 @@ step_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
             const bool use_y = o.nuy != 0.f && ybound;
             for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 float y[16];
+                __syncwarp();
                 tmem_ld16(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(m * NT + c0), y);
                 if (!qv) {
                     if (q < Qp) {

@@ -258,3 +258,33 @@ def test_launch_count_and_finite(A):
     assert p.launch_count() - c0 == 4
     p.check_finite()
     p.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16), (8, 8)])
+def test_tensor_kernel_variants_and_tilings_agree(A, precision, npol, naz):
+    """The persistent kernel at every tile width it accepts and the one-tile-per-CTA kernel give the
+    same step (up to FP32 summation order of Phi) and each matches the oracle."""
+    wl = random_workload(150, 7, npol, naz, seed=21)
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    outs = []
+    dt = None
+    for variant, tile, stages in [(0, 0, 0), (0, 32, 2), (0, 64, 3), (1, 0, 0), (1, 64, 2)]:
+        p = gpu_problem(A, wl, precision)
+        try:
+            p.set_tiling(tile, stages, variant)
+            p.tiling()
+        except A.AssnError:
+            p.close()
+            continue
+        if dt is None:
+            dt = 0.9 * p.max_stable_dt()
+        p.step(2, dt)
+        outs.append(((variant, tile, stages), p.state()))
+        p.close()
+    assert len(outs) >= 3
+    ref = O.run(wl.psi0(), 2, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    tol = 2 * step_tolerance(precision, dt, wl.sigma_as, 1.0, offdiag_rowsum(K))
+    for cfg, s in outs:
+        assert np.abs(s - ref).max() <= tol, cfg
+        assert np.abs(s - outs[0][1]).max() <= 1e-5, cfg
