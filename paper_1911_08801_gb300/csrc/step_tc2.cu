@@ -63,8 +63,8 @@ struct Layout {
         blo = bhi + SB * kB;
         a = blo + (SPLIT ? SB * kB : 0);
         w = a + SA * kA;
-        phi = w + Qp * 4;
-        bars = (phi + 2 * NT * 4 + 7) & ~7;
+        phi = w + Qp * 4;                                        // [2][NT] float4 cell coefficients
+        bars = (phi + 2 * NT * 16 + 7) & ~7;
         // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2]
         end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 8) + 16;
     }
@@ -82,7 +82,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     unsigned char* blo = base + L.blo;
     unsigned char* aring = base + L.a;
     float* wsm = reinterpret_cast<float*>(base + L.w);
-    float* phi = reinterpret_cast<float*>(base + L.phi);
+    float4* coef = reinterpret_cast<float4*>(base + L.phi);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* stg_full = bars;
     uint64_t* stg_empty = stg_full + a.SS;
@@ -167,6 +167,8 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------------------- flux TMA producer
+            // evict-last: the epilogue re-reads these lines (own values and y-neighbours) shortly
+            const uint64_t pol = policy_evict_last();
             int ns = 0;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
                 bool ok = true;
@@ -174,7 +176,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                     const int ss = ns % a.SS;
                     if (!mbar_wait(&stg_empty[ss], ((uint32_t)(ns / a.SS) & 1u) ^ 1u, abort_flag, a.err, 0x1u)) { ok = false; break; }
                     mbar_expect_tx(&stg_full[ss], Layout<NT, SPLIT>::kStg);
-                    tma_load_2d(stg + (size_t)ss * NT * 64, &tm_psi, &stg_full[ss], kc * 64, tile * NT);
+                    tma_load_2d_hint(stg + (size_t)ss * NT * 64, &tm_psi, &stg_full[ss], kc * 64, tile * NT, pol);
                 }
                 if (!ok) break;
             }
@@ -182,6 +184,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     } else if (warp == 2) {
         if (lane == 0) {
             // ---------------------------------------------------------------- kernel-matrix TMA producer
+            const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
             int na = 0;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
                 bool ok = true;
@@ -191,8 +194,8 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                         if (!mbar_wait(&a_empty[sa], ((uint32_t)(na / a.SA) & 1u) ^ 1u, abort_flag, a.err, 0x2u)) { ok = false; break; }
                         unsigned char* dst = aring + sa * Layout<NT, SPLIT>::kA;
                         mbar_expect_tx(&a_full[sa], Layout<NT, SPLIT>::kA);
-                        tma_load_2d(dst, &tm_hi, &a_full[sa], kc * 64, m * 128);
-                        if (SPLIT) tma_load_2d(dst + kAStage, &tm_lo, &a_full[sa], kc * 64, m * 128);
+                        tma_load_2d_hint(dst, &tm_hi, &a_full[sa], kc * 64, m * 128, pol);
+                        if (SPLIT) tma_load_2d_hint(dst + kAStage, &tm_lo, &a_full[sa], kc * 64, m * 128, pol);
                     }
                 }
                 if (!ok) break;
@@ -262,8 +265,23 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             const uint32_t use = (uint32_t)(it >> 1);
             if (!mbar_wait(&phi_empty[buf], (use & 1u) ^ 1u, abort_flag, a.err, 0x400u)) break;
             if (col4 == 0) {
+                // per cell: x = 1 - dt sigma_t, y = dt (sigma_s Phi / sum w + q),
+                // z = neighbour bits (1 left, 2 right, 4 below, 8 above exist; 16 cell exists)
 #pragma unroll
-                for (int i = 0; i < NR; ++i) phi[buf * NT + rsub + 8 * i] = part[i];
+                for (int i = 0; i < NR; ++i) {
+                    const int r = rsub + 8 * i;
+                    const int f = tile * NT + r;
+                    float4 cf = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+                    if (f < a.ncell) {
+                        const CellF cl = a.cell[f];
+                        const int yy = f / a.nx, xx = f - yy * a.nx;
+                        const int bits = (xx > 0 ? 1 : 0) | (xx + 1 < a.nx ? 2 : 0) | (yy > 0 ? 4 : 0) |
+                                         (yy + 1 < a.ny ? 8 : 0) | 16;
+                        cf = make_float4(1.0f - a.dt * cl.sig_t, a.dt * (cl.sig_s_over_wsum * part[i] + cl.q),
+                                         __int_as_float(bits), 0.0f);
+                    }
+                    coef[buf * NT + r] = cf;
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&phi_full[buf]);
@@ -274,7 +292,8 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         float* __restrict__ psi_out = a.psi_out;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
         const int half = (warp - 7) >> 2;      // which half of the tile's cells
-        const int nx = a.nx, ny = a.ny, ncell = a.ncell;
+        const int ncell = a.ncell;
+        const long ystep = (long)a.nx * Qp;
         int it = 0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
             const int buf = it & 1;
@@ -287,63 +306,59 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             if (!go) break;
             tc_fence_after();
             const int f0 = tile * NT;
+            const float4* cbuf = coef + buf * NT;
             for (int m = 0; m < MB; ++m) {
                 const int q = m * 128 + lq * 32 + lane;
                 const bool qv = q < a.Q;
                 const OrdF o = q < Qp ? a.ord[q] : OrdF{0.f, 0.f, 0.f, 0.f};
-                const float ax = fabsf(o.nux), ay = fabsf(o.nuy);
+                const float ax = fabsf(o.nux), ay = fabsf(o.nuy), axy = ax + ay;
+                const float es = o.e;
+                // which neighbour bit this lane's upwind side needs
+                const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
+                const int ybit = o.nuy > 0.f ? 4 : (o.nuy < 0.f ? 8 : 0);
+                const long dy = o.nuy > 0.f ? -ystep : ystep;
                 for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 16) {
                     float y[16];
                     __syncwarp();
                     tmem_ld16(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * MB * NT + m * NT + c0), y);
                     const int fb = f0 + c0;
                     if (fb >= ncell) continue;          // warp-uniform
+                    const float* pc = psi + (size_t)fb * Qp + q;
+                    float* po = psi_out + (size_t)fb * Qp + q;
                     if (!qv) {
                         if (q < Qp) {
 #pragma unroll
                             for (int i = 0; i < 16; ++i)
-                                if (fb + i < ncell) psi_out[(size_t)(fb + i) * Qp + q] = 0.0f;
+                                if (fb + i < ncell) __stcs(po + (size_t)i * Qp, 0.0f);
                         }
-                    } else {
-                        float self[16], upy[16];
+                        continue;
+                    }
+                    float self[16], upy[16];
+                    int bits[16];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int f = fb + i;
-                            self[i] = f < ncell ? psi[(size_t)f * Qp + q] : 0.0f;
-                        }
-                        float left = 0.0f, right = 0.0f;
-                        if (o.nux > 0.f && fb >= 1) left = psi[(size_t)(fb - 1) * Qp + q];
-                        if (o.nux < 0.f && fb + 16 < ncell) right = psi[(size_t)(fb + 16) * Qp + q];
+                    for (int i = 0; i < 16; ++i) bits[i] = __float_as_int(cbuf[c0 + i].z);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int f = fb + i;
-                            const int yy = f / nx;
-                            float v = 0.0f;
-                            if (f < ncell) {
-                                if (o.nuy > 0.f && yy > 0) v = psi[(size_t)(f - nx) * Qp + q];
-                                else if (o.nuy < 0.f && yy + 1 < ny) v = psi[(size_t)(f + nx) * Qp + q];
-                            }
-                            upy[i] = v;
-                        }
+                    for (int i = 0; i < 16; ++i) {
+                        self[i] = (bits[i] & 16) ? pc[(size_t)i * Qp] : 0.0f;
+                        upy[i] = (bits[i] & ybit) ? pc[(size_t)i * Qp + dy] : 0.0f;
+                    }
+                    const float left = (xbit == 1 && (bits[0] & 1)) ? pc[-(long)Qp] : 0.0f;
+                    const float right = (xbit == 2 && (bits[15] & 2)) ? pc[(size_t)16 * Qp] : 0.0f;
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int f = fb + i;
-                            if (f >= ncell) break;
-                            const int xx = f - (f / nx) * nx;
-                            float upx = 0.0f;
-                            if (o.nux > 0.f) {
-                                if (xx > 0) upx = i > 0 ? self[i - 1] : left;
-                            } else if (o.nux < 0.f) {
-                                if (xx + 1 < nx) upx = i < 15 ? self[i + 1] : right;
-                            }
-                            const CellF cl = a.cell[f];
-                            const float sf = self[i];
-                            const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
-                            const float out = sf - ax * (sf - upx) - ay * (sf - upy[i]) - a.dt * cl.sig_t * sf +
-                                              a.dt * (cl.sig_s_over_wsum * phi[buf * NT + c0 + i] + cl.q) +
-                                              a.dt_sigma_as * (y[i] - o.e * st);
-                            psi_out[(size_t)f * Qp + q] = out;
-                        }
+                    for (int i = 0; i < 16; ++i) {
+                        if (!(bits[i] & 16)) continue;
+                        const float prev = i > 0 ? self[i - 1] : left;
+                        const float next = i < 15 ? self[i + 1] : right;
+                        float upx = xbit == 1 ? prev : next;
+                        upx = (bits[i] & xbit) ? upx : 0.0f;
+                        const float sf = self[i];
+                        const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
+                        const float2 cxy = *reinterpret_cast<const float2*>(&cbuf[c0 + i]);
+                        float out = fmaf(sf, cxy.x - axy, cxy.y);
+                        out = fmaf(ax, upx, out);
+                        out = fmaf(ay, upy[i], out);
+                        out = fmaf(a.dt_sigma_as, fmaf(-es, st, y[i]), out);
+                        __stcs(po + (size_t)i * Qp, out);
                     }
                 }
             }
@@ -435,26 +450,35 @@ cudaError_t tc2_plan_create(Tc2Plan** out, const __nv_bfloat16* G_hi, const __nv
     p->Q = Q; p->Qp = Qp; p->Mp = Mp; p->MB = Mp / 128; p->KC = Qp / 64; p->nx = nx; p->ny = ny;
     p->split = split; p->nkeys = 0;
     p->ncell = nx * ny;
-    // Tile width: two accumulator buffers of MB x NT columns fill the 512 TMEM columns.
+    // Tile width: two accumulator buffers of MB x NT columns fill the 512 TMEM columns; narrower
+    // when the rings do not fit shared memory.  Ring depths start at 4 / 4 / 4 and the largest
+    // ring shrinks (to 2 at least) until the layout fits.
     int nt = 512 / (2 * p->MB);
     if (nt > 256) nt = 256;
     if (want_nt) nt = want_nt;
-    if (nt < 32 || (nt & (nt - 1)) || 2 * p->MB * nt > 512) { delete p; return cudaErrorNotSupported; }
-    p->NT = nt;
-    // Ring depths: start at 4 / 4 / 4 and shrink the largest consumer until the layout fits.
-    int SS = 4, SB = 4, SA = 4;
-    if (want_stages >= 2) SS = SB = SA = want_stages;
     const size_t limit = 227 * 1024;
-    while (smem_for(nt, split, SS, SB, SA, Qp) > limit) {
-        const size_t s_stg = (size_t)nt * 256 * SS, s_a = (size_t)kAStage * (split ? 2 : 1) * SA,
-                     s_b = (size_t)nt * 128 * (split ? 2 : 1) * SB;
-        if (s_stg >= s_a && s_stg >= s_b && SS > 2) --SS;
-        else if (s_a >= s_b && SA > 2) --SA;
-        else if (SB > 2) --SB;
-        else if (SS > 2) --SS;
-        else if (SA > 2) --SA;
-        else { delete p; return cudaErrorNotSupported; }
+    int SS = 4, SB = 4, SA = 4;
+    bool fits = false;
+    while (!fits) {
+        if (nt < 32 || (nt & (nt - 1)) || 2 * p->MB * nt > 512) { delete p; return cudaErrorNotSupported; }
+        SS = SB = SA = (want_stages >= 2 ? want_stages : 4);
+        while (true) {
+            if (smem_for(nt, split, SS, SB, SA, Qp) <= limit) { fits = true; break; }
+            const size_t s_stg = (size_t)nt * 256 * SS, s_a = (size_t)kAStage * (split ? 2 : 1) * SA,
+                         s_b = (size_t)nt * 128 * (split ? 2 : 1) * SB;
+            if (s_stg >= s_a && s_stg >= s_b && SS > 2) --SS;
+            else if (s_a >= s_b && SA > 2) --SA;
+            else if (SB > 2) --SB;
+            else if (SS > 2) --SS;
+            else if (SA > 2) --SA;
+            else break;
+        }
+        if (!fits) {
+            if (want_nt) { delete p; return cudaErrorNotSupported; }
+            nt /= 2;
+        }
     }
+    p->NT = nt;
     p->SS = SS; p->SB = SB; p->SA = SA;
     p->smem = smem_for(nt, split, SS, SB, SA, Qp);
     p->ntiles = (p->ncell + nt - 1) / nt;
