@@ -264,10 +264,13 @@ def test_launch_count_and_finite(A):
 @pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16), (8, 8)])
 def test_tensor_kernel_variants_and_tilings_agree(A, precision, npol, naz):
     """The persistent kernel at every tile width it accepts and the one-tile-per-CTA kernel give the
-    same step (up to FP32 summation order of Phi) and each matches the oracle."""
+    same step from the same state (they differ only in the FP32 summation order of Phi) and each
+    matches the oracle over two steps.  (After the first step the states may differ in the last
+    bit, which can move a value across a BF16 rounding boundary in the second step, so the
+    variants are compared after one step.)"""
     wl = random_workload(150, 7, npol, naz, seed=21)
     Om, w, K, sa, ss, q = oracle_setup(wl)
-    outs = []
+    one, two = [], []
     dt = None
     for variant, tile, stages in [(0, 0, 0), (0, 32, 2), (0, 64, 3), (1, 0, 0), (1, 64, 2)]:
         p = gpu_problem(A, wl, precision)
@@ -279,12 +282,15 @@ def test_tensor_kernel_variants_and_tilings_agree(A, precision, npol, naz):
             continue
         if dt is None:
             dt = 0.9 * p.max_stable_dt()
-        p.step(2, dt)
-        outs.append(((variant, tile, stages), p.state()))
+        p.step(1, dt)
+        one.append(((variant, tile, stages), p.state()))
+        p.step(1, dt)
+        two.append(((variant, tile, stages), p.state()))
         p.close()
-    assert len(outs) >= 3
+    assert len(one) >= 3
     ref = O.run(wl.psi0(), 2, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
     tol = 2 * step_tolerance(precision, dt, wl.sigma_as, 1.0, offdiag_rowsum(K))
-    for cfg, s in outs:
+    for cfg, s in two:
         assert np.abs(s - ref).max() <= tol, cfg
-        assert np.abs(s - outs[0][1]).max() <= 1e-5, cfg
+    for cfg, s in one:
+        assert np.abs(s - one[0][1]).max() <= 1e-6, cfg
