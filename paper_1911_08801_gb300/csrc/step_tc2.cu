@@ -47,24 +47,30 @@ struct Tc2Args {
     const float* w;
     unsigned int* err;
     int nx, ny, Q, Qp, MB, KC, ntiles, ncell;
-    int SS, SB, SA;
+    int SS, SB, SA, R;
     float dt, dt_sigma_as;
 };
+
+constexpr int kEpiWarps = 8;
+constexpr int kEpiSlots = 34;     // per chunk and lane: cells fb-1 .. fb+16, then 16 y-neighbours
+constexpr int kEpiChunkBytes = kEpiSlots * 32 * 4;
+constexpr int kEpiRingMax = 3;    // chunks in flight per epilogue warp (2 or 3)
 
 template <int NT, bool SPLIT>
 struct Layout {
     static constexpr int kStg = NT * 256;                       // FP32 staging stage
     static constexpr int kB = NT * 128;                         // BF16 B stage (one of hi / lo)
     static constexpr int kA = kAStage * (SPLIT ? 2 : 1);        // A stage (hi [+ lo])
-    int stg, bhi, blo, a, w, phi, bars, end;
-    __host__ __device__ Layout(int SS, int SB, int SA, int Qp) {
+    int stg, bhi, blo, a, w, phi, epi, bars, end;
+    __host__ __device__ Layout(int SS, int SB, int SA, int R, int Qp) {
         stg = 0;
         bhi = stg + SS * kStg;
         blo = bhi + SB * kB;
         a = blo + (SPLIT ? SB * kB : 0);
         w = a + SA * kA;
         phi = w + Qp * 4;                                        // [2][NT] float4 cell coefficients
-        bars = (phi + 2 * NT * 16 + 7) & ~7;
+        epi = phi + 2 * NT * 16;                                 // [8 warps][ring][34][32] floats
+        bars = epi + kEpiWarps * R * kEpiChunkBytes;
         // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2]
         end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 8) + 16;
     }
@@ -76,13 +82,14 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                 const __grid_constant__ CUtensorMap tm_lo, const Tc2Args a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, a.Qp);
+    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, a.R, a.Qp);
     float* stg = reinterpret_cast<float*>(base + L.stg);
     unsigned char* bhi = base + L.bhi;
     unsigned char* blo = base + L.blo;
     unsigned char* aring = base + L.a;
     float* wsm = reinterpret_cast<float*>(base + L.w);
     float4* coef = reinterpret_cast<float4*>(base + L.phi);
+    float* epi = reinterpret_cast<float*>(base + L.epi);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* stg_full = bars;
     uint64_t* stg_empty = stg_full + a.SS;
@@ -288,87 +295,119 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         }
     } else {
         // -------------------------------------------------------------------- epilogue
-        const float* __restrict__ psi = a.psi;
+        // Each warp owns a ring of kEpiRing chunk buffers and prefetches, with cp.async, the flux
+        // values its next chunks need (own cells with both x-edge cells, and the upwind y-neighbours)
+        // while it computes the current one.  The flux input is read-only during the launch, so the
+        // prefetch may run ahead of the MMA.
         float* __restrict__ psi_out = a.psi_out;
+        const float* psi = a.psi;
+        const int e = warp - 7;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
-        const int half = (warp - 7) >> 2;      // which half of the tile's cells
-        const int ncell = a.ncell;
-        const long ystep = (long)a.nx * Qp;
-        int it = 0;
-        for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
-            const int buf = it & 1;
-            const uint32_t use = (uint32_t)(it >> 1);
-            int go = 1;
-            if (lane == 0)
-                go = mbar_wait(&phi_full[buf], use & 1u, abort_flag, a.err, 0x1000u) &&
-                     mbar_wait(&tm_full[buf], use & 1u, abort_flag, a.err, 0x2000u);
-            go = __shfl_sync(0xffffffffu, go, 0);
-            if (!go) break;
-            tc_fence_after();
-            const int f0 = tile * NT;
-            const float4* cbuf = coef + buf * NT;
-            for (int m = 0; m < MB; ++m) {
-                const int q = m * 128 + lq * 32 + lane;
-                const bool qv = q < a.Q;
-                const OrdF o = q < Qp ? a.ord[q] : OrdF{0.f, 0.f, 0.f, 0.f};
-                const float ax = fabsf(o.nux), ay = fabsf(o.nuy), axy = ax + ay;
-                const float es = o.e;
-                // which neighbour bit this lane's upwind side needs
-                const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
-                const int ybit = o.nuy > 0.f ? 4 : (o.nuy < 0.f ? 8 : 0);
-                const long dy = o.nuy > 0.f ? -ystep : ystep;
-                for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 16) {
-                    float y[16];
-                    __syncwarp();
-                    tmem_ld16(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * MB * NT + m * NT + c0), y);
-                    const int fb = f0 + c0;
-                    if (fb >= ncell) continue;          // warp-uniform
-                    const float* pc = psi + (size_t)fb * Qp + q;
-                    float* po = psi_out + (size_t)fb * Qp + q;
-                    if (!qv) {
-                        if (q < Qp) {
+        const int half = e >> 2;               // which half of the tile's cells
+        const int ncell = a.ncell, nx = a.nx, ny = a.ny;
+        constexpr int CPH = NT / 32;           // chunks of 16 cells per half tile
+        const int cpt = MB * CPH;              // chunks per tile for this warp
+        const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+        const int total = my_tiles * cpt;
+        const int R = a.R;
+        float* ring = epi + (size_t)e * R * kEpiSlots * 32;
+
+        auto issue = [&](int k) {
+            const int t = k / cpt, r = k - t * cpt;
+            const int m = r / CPH;
+            const int c0 = half * (NT / 2) + (r - m * CPH) * 16;
+            const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
+            const int q = m * 128 + lq * 32 + lane;
+            const bool qv = q < a.Q;
+            float nuy = 0.f;
+            if (qv) nuy = a.ord[q].nuy;
+            const uint32_t sb = smem_u32(ring + (size_t)(k % R) * kEpiSlots * 32 + lane);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                if (fb + i < ncell) __stcs(po + (size_t)i * Qp, 0.0f);
-                        }
-                        continue;
-                    }
-                    float self[16], upy[16];
-                    int bits[16];
+            for (int j = 0; j < 18; ++j) {
+                const int g = fb - 1 + j;
+                const bool ok = qv && g >= 0 && g < ncell;
+                cp_async4(sb + j * 128, ok ? psi + (size_t)g * Qp + q : psi, ok ? 4u : 0u);
+            }
+            int yy = fb / nx, xx = fb - yy * nx;
+            const long dyc = nuy > 0.f ? -(long)nx : (long)nx;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) bits[i] = __float_as_int(cbuf[c0 + i].z);
+            for (int i = 0; i < 16; ++i) {
+                const int g = fb + i;
+                const bool rowok = nuy > 0.f ? yy > 0 : (nuy < 0.f ? yy + 1 < ny : false);
+                const bool ok = qv && g < ncell && rowok;
+                cp_async4(sb + (18 + i) * 128, ok ? psi + ((long)g + dyc) * Qp + q : psi, ok ? 4u : 0u);
+                if (++xx >= nx) { xx -= nx; ++yy; while (xx >= nx) { xx -= nx; ++yy; } }
+            }
+            cp_async_commit();
+        };
+
+        int k_issue = 0;
+        for (; k_issue < R - 1 && k_issue < total; ++k_issue) issue(k_issue);
+        for (int k = 0; k < total; ++k) {
+            if (k_issue < total) issue(k_issue++);
+            else cp_async_commit();            // keep one group per iteration
+            if (R == 3) cp_async_wait<2>();
+            else cp_async_wait<1>();
+            const int t = k / cpt, r = k - t * cpt;
+            const int m = r / CPH;
+            const int c0 = half * (NT / 2) + (r - m * CPH) * 16;
+            const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+            const int buf = t & 1;
+            const uint32_t use = (uint32_t)(t >> 1);
+            if (r == 0) {
+                int go = 1;
+                if (lane == 0)
+                    go = mbar_wait(&phi_full[buf], use & 1u, abort_flag, a.err, 0x1000u) &&
+                         mbar_wait(&tm_full[buf], use & 1u, abort_flag, a.err, 0x2000u);
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (!go) break;
+                tc_fence_after();
+            }
+            float y[16];
+            __syncwarp();
+            tmem_ld16(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * MB * NT + m * NT + c0), y);
+            const int fb = tile * NT + c0;
+            const int q = m * 128 + lq * 32 + lane;
+            if (fb < ncell && q < Qp) {
+                float* po = psi_out + (size_t)fb * Qp + q;
+                const float4* cbuf = coef + buf * NT + c0;
+                if (q >= a.Q) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (fb + i < ncell) __stcs(po + (size_t)i * Qp, 0.0f);
+                } else {
+                    const OrdF o = a.ord[q];
+                    const float ax = fabsf(o.nux), ay = fabsf(o.nuy), axy = ax + ay;
+                    const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
+                    const float* sl = ring + (size_t)(k % R) * kEpiSlots * 32 + lane;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        self[i] = (bits[i] & 16) ? pc[(size_t)i * Qp] : 0.0f;
-                        upy[i] = (bits[i] & ybit) ? pc[(size_t)i * Qp + dy] : 0.0f;
-                    }
-                    const float left = (xbit == 1 && (bits[0] & 1)) ? pc[-(long)Qp] : 0.0f;
-                    const float right = (xbit == 2 && (bits[15] & 2)) ? pc[(size_t)16 * Qp] : 0.0f;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        if (!(bits[i] & 16)) continue;
-                        const float prev = i > 0 ? self[i - 1] : left;
-                        const float next = i < 15 ? self[i + 1] : right;
-                        float upx = xbit == 1 ? prev : next;
-                        upx = (bits[i] & xbit) ? upx : 0.0f;
-                        const float sf = self[i];
+                        const float4 cf = cbuf[i];
+                        const int bits = __float_as_int(cf.z);
+                        if (!(bits & 16)) continue;
+                        const float sf = sl[(1 + i) * 32];
+                        float upx = xbit == 1 ? sl[i * 32] : sl[(i + 2) * 32];
+                        upx = (bits & xbit) ? upx : 0.0f;
+                        const float upy = sl[(18 + i) * 32];
                         const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
-                        const float2 cxy = *reinterpret_cast<const float2*>(&cbuf[c0 + i]);
-                        float out = fmaf(sf, cxy.x - axy, cxy.y);
+                        float out = fmaf(sf, cf.x - axy, cf.y);
                         out = fmaf(ax, upx, out);
-                        out = fmaf(ay, upy[i], out);
-                        out = fmaf(a.dt_sigma_as, fmaf(-es, st, y[i]), out);
+                        out = fmaf(ay, upy, out);
+                        out = fmaf(a.dt_sigma_as, fmaf(-o.e, st, y[i]), out);
                         __stcs(po + (size_t)i * Qp, out);
                     }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&tm_empty[buf]);
-                mbar_arrive(&phi_empty[buf]);
+            if (r == cpt - 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&tm_empty[buf]);
+                    mbar_arrive(&phi_empty[buf]);
+                }
             }
         }
+        cp_async_wait<0>();
     }
 
     __syncthreads();
@@ -414,20 +453,20 @@ bool encode_2d(CUtensorMap* map, CUtensorMapDataType type, const void* ptr, uint
 }
 
 template <int NT, bool SPLIT>
-size_t smem_need(int SS, int SB, int SA, int Qp) {
-    return 1024 + (size_t)Layout<NT, SPLIT>(SS, SB, SA, Qp).end;
+size_t smem_need(int SS, int SB, int SA, int R, int Qp) {
+    return 1024 + (size_t)Layout<NT, SPLIT>(SS, SB, SA, R, Qp).end;
 }
 
-size_t smem_for(int NT, bool split, int SS, int SB, int SA, int Qp) {
+size_t smem_for(int NT, bool split, int SS, int SB, int SA, int R, int Qp) {
     switch (NT * 2 + (split ? 1 : 0)) {
-        case 64: return smem_need<32, false>(SS, SB, SA, Qp);
-        case 65: return smem_need<32, true>(SS, SB, SA, Qp);
-        case 128: return smem_need<64, false>(SS, SB, SA, Qp);
-        case 129: return smem_need<64, true>(SS, SB, SA, Qp);
-        case 256: return smem_need<128, false>(SS, SB, SA, Qp);
-        case 257: return smem_need<128, true>(SS, SB, SA, Qp);
-        case 512: return smem_need<256, false>(SS, SB, SA, Qp);
-        default: return smem_need<256, true>(SS, SB, SA, Qp);
+        case 64: return smem_need<32, false>(SS, SB, SA, R, Qp);
+        case 65: return smem_need<32, true>(SS, SB, SA, R, Qp);
+        case 128: return smem_need<64, false>(SS, SB, SA, R, Qp);
+        case 129: return smem_need<64, true>(SS, SB, SA, R, Qp);
+        case 256: return smem_need<128, false>(SS, SB, SA, R, Qp);
+        case 257: return smem_need<128, true>(SS, SB, SA, R, Qp);
+        case 512: return smem_need<256, false>(SS, SB, SA, R, Qp);
+        default: return smem_need<256, true>(SS, SB, SA, R, Qp);
     }
 }
 
@@ -438,7 +477,7 @@ struct Tc2Plan {
     CUtensorMap tm_psi[4];
     const void* psi_key[4];
     int nkeys;
-    int Q, Qp, Mp, MB, KC, NT, SS, SB, SA, nx, ny, ncell, ntiles, grid;
+    int Q, Qp, Mp, MB, KC, NT, SS, SB, SA, R, nx, ny, ncell, ntiles, grid;
     bool split;
     size_t smem;
 };
@@ -457,30 +496,35 @@ cudaError_t tc2_plan_create(Tc2Plan** out, const __nv_bfloat16* G_hi, const __nv
     if (nt > 256) nt = 256;
     if (want_nt) nt = want_nt;
     const size_t limit = 227 * 1024;
-    int SS = 4, SB = 4, SA = 4;
+    int SS = 2, SB = 2, SA = 2, R = 2;
     bool fits = false;
     while (!fits) {
         if (nt < 32 || (nt & (nt - 1)) || 2 * p->MB * nt > 512) { delete p; return cudaErrorNotSupported; }
-        SS = SB = SA = (want_stages >= 2 ? want_stages : 4);
-        while (true) {
-            if (smem_for(nt, split, SS, SB, SA, Qp) <= limit) { fits = true; break; }
-            const size_t s_stg = (size_t)nt * 256 * SS, s_a = (size_t)kAStage * (split ? 2 : 1) * SA,
-                         s_b = (size_t)nt * 128 * (split ? 2 : 1) * SB;
-            if (s_stg >= s_a && s_stg >= s_b && SS > 2) --SS;
-            else if (s_a >= s_b && SA > 2) --SA;
-            else if (SB > 2) --SB;
-            else if (SS > 2) --SS;
-            else if (SA > 2) --SA;
-            else break;
+        for (R = kEpiRingMax; R >= 2 && !fits; --R) {
+            if (want_stages >= 2) {
+                SS = SB = SA = want_stages;
+                fits = smem_for(nt, split, SS, SB, SA, R, Qp) <= limit;
+            } else if (smem_for(nt, split, 2, 2, 2, R, Qp) <= limit) {
+                // deepest balanced rings that fit, then deepen A, the staging ring and B (max 4)
+                fits = true;
+                SS = SB = SA = 2;
+                for (int k = 4; k >= 3; --k)
+                    if (smem_for(nt, split, k, k, k, R, Qp) <= limit) { SS = SB = SA = k; break; }
+                while (SA < 4 && smem_for(nt, split, SS, SB, SA + 1, R, Qp) <= limit) ++SA;
+                while (SS < 4 && smem_for(nt, split, SS + 1, SB, SA, R, Qp) <= limit) ++SS;
+                while (SB < 4 && smem_for(nt, split, SS, SB + 1, SA, R, Qp) <= limit) ++SB;
+            }
+            if (fits) break;
         }
         if (!fits) {
             if (want_nt) { delete p; return cudaErrorNotSupported; }
             nt /= 2;
         }
     }
+    p->R = R;
     p->NT = nt;
     p->SS = SS; p->SB = SB; p->SA = SA;
-    p->smem = smem_for(nt, split, SS, SB, SA, Qp);
+    p->smem = smem_for(nt, split, SS, SB, SA, R, Qp);
     p->ntiles = (p->ncell + nt - 1) / nt;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -533,7 +577,7 @@ cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, c
     const CUtensorMap* mpsi = psi_map(p, s.psi);
     if (!mpsi) return cudaErrorInvalidValue;
     Tc2Args a{s.psi, s.psi_out, s.ord, s.cell, w, err_flag, s.nx, s.ny, s.Q, s.Qp, p->MB, p->KC, p->ntiles,
-              p->ncell, p->SS, p->SB, p->SA, s.dt, s.dt_sigma_as};
+              p->ncell, p->SS, p->SB, p->SA, p->R, s.dt, s.dt_sigma_as};
     switch (p->NT * 2 + (p->split ? 1 : 0)) {
         case 64: return launch2<32, false>(p, mpsi, a, stream);
         case 65: return launch2<32, true>(p, mpsi, a, stream);

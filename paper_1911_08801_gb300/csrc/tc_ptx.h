@@ -107,6 +107,18 @@ __device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* m
         : "memory");
 }
 
+// 4-byte asynchronous global -> shared copy; nbytes = 0 writes zeros without reading `src`.
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* src, uint32_t nbytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(src), "r"(nbytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand in the canonical 128-byte-swizzled layout
 // (rows of 128 bytes, 8-row groups 1024 bytes apart); addresses and strides in 16-byte units.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
