@@ -7,21 +7,25 @@
 // is one [Mp x Qp] x [Qp x NT] product per tile on tcgen05 (kind::f16, M = 128 ordinates,
 // N = NT cells, K = 16, BF16 in, FP32 accumulate in TMEM).  Roles:
 //   warp 0      TMEM owner; lane 0 issues the MMAs (k-chunk outer, ordinate block inner) into
-//               one of two TMEM accumulator buffers (2 x Mp/128 x NT columns = 512).
+//               one of two TMEM accumulator buffers (2 x Mp/128 x NT columns <= 512).
 //   warp 1      lane 0: TMA producer of the FP32 flux: [NT cells x 64 ordinates] chunks into an
 //               SS-stage staging ring.
 //   warp 2      lane 0: TMA producer of the kernel-matrix operand G (off-diagonal K in BF16,
 //               [128 x 64] chunks, 128-byte swizzle) into an SA-stage ring.
 //   warps 3-6   converters: staging chunk -> BF16 B operand (K-major, 128-byte swizzle, written
-//               directly in the canonical layout) in an SB-stage ring, and the scalar flux
-//               Phi_c = sum_p w_p psi_p(c) accumulated in FP32 over the tile's chunks.
+//               directly in the canonical layout) in an SB-stage ring; the scalar flux
+//               Phi_c = sum_p w_p psi_p(c) accumulated in FP32 over the tile's chunks, and from it
+//               the per-cell coefficients of the update.
 //   warps 7-14  epilogue: drain a TMEM buffer (lane = ordinate, column = cell) and apply upwind
 //               transport (Sec. 3.1), collision, isotropic scattering, the source and the
 //               generator diagonal:
-//                 psi' = psi - a_x (psi - psi_upx) - a_y (psi - psi_upy) - dt sigma_t psi
+//                 psi' = psi (1 - dt sigma_t - a_x - a_y) + a_x psi_upx + a_y psi_upy
 //                        + dt (sigma_s Phi / sum w + q) + dt sigma_as (D - e psi~)
-//               while the MMA of the next tile fills the other buffer.
+//               while the MMA of the next tile fills the other buffer.  Each epilogue warp keeps
+//               the flux values of its next 16-cell chunk in flight (register double buffer).
 // SPLIT (BF16X3) keeps BF16 residuals of both operands and issues hi*hi + hi*lo + lo*hi.
+// QP > 0 fixes the ordinate stride at compile time (immediate address offsets); QP = 0 reads it
+// from the arguments.
 //
 // Every mbarrier wait is bounded (about 1 s); on expiry the CTA records the event in err_flag,
 // all roles stop issuing, the CTA waits briefly for copies and MMAs in flight, frees its tensor
@@ -47,49 +51,57 @@ struct Tc2Args {
     const float* w;
     unsigned int* err;
     int nx, ny, Q, Qp, MB, KC, ntiles, ncell;
-    int SS, SB, SA, R;
+    int SS, SB, SA;
     float dt, dt_sigma_as;
 };
-
-constexpr int kEpiWarps = 8;
-constexpr int kEpiSlots = 34;     // per chunk and lane: cells fb-1 .. fb+16, then 16 y-neighbours
-constexpr int kEpiChunkBytes = kEpiSlots * 32 * 4;
-constexpr int kEpiRingMax = 3;    // chunks in flight per epilogue warp (2 or 3)
 
 template <int NT, bool SPLIT>
 struct Layout {
     static constexpr int kStg = NT * 256;                       // FP32 staging stage
     static constexpr int kB = NT * 128;                         // BF16 B stage (one of hi / lo)
     static constexpr int kA = kAStage * (SPLIT ? 2 : 1);        // A stage (hi [+ lo])
-    int stg, bhi, blo, a, w, phi, epi, bars, end;
-    __host__ __device__ Layout(int SS, int SB, int SA, int R, int Qp) {
+    int stg, bhi, blo, a, w, coef, bars, end;
+    __host__ __device__ Layout(int SS, int SB, int SA, int Qp) {
         stg = 0;
         bhi = stg + SS * kStg;
         blo = bhi + SB * kB;
         a = blo + (SPLIT ? SB * kB : 0);
         w = a + SA * kA;
-        phi = w + Qp * 4;                                        // [2][NT] float4 cell coefficients
-        epi = phi + 2 * NT * 16;                                 // [8 warps][ring][34][32] floats
-        bars = epi + kEpiWarps * R * kEpiChunkBytes;
+        coef = w + Qp * 4;                                       // [2][NT] float4 cell coefficients
+        bars = coef + 2 * NT * 16;
         // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2]
         end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 8) + 16;
     }
 };
 
-template <int NT, bool SPLIT>
+// Fast path inline, slow (bounded, sleeping) path out of line.
+#define WAITB(bar, parity, code) \
+    (mbar_try_wait((bar), (parity)) || mbar_wait((bar), (parity), abort_flag, a.err, (code)))
+
+// Ring position: index into an S-deep ring plus the parity of the current pass.
+struct Ring {
+    int s = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next(int S) {
+        if (++s == S) { s = 0; ph ^= 1u; }
+    }
+};
+
+template <int NT, bool SPLIT, int QP>
 __global__ void __launch_bounds__(kThreads2, 1)
 step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constant__ CUtensorMap tm_hi,
                 const __grid_constant__ CUtensorMap tm_lo, const Tc2Args a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, a.R, a.Qp);
+    const int Qp = QP > 0 ? QP : a.Qp;
+    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, Qp);
+    using LT = Layout<NT, SPLIT>;
     float* stg = reinterpret_cast<float*>(base + L.stg);
     unsigned char* bhi = base + L.bhi;
     unsigned char* blo = base + L.blo;
     unsigned char* aring = base + L.a;
     float* wsm = reinterpret_cast<float*>(base + L.w);
-    float4* coef = reinterpret_cast<float4*>(base + L.phi);
-    float* epi = reinterpret_cast<float*>(base + L.epi);
+    float4* coef = reinterpret_cast<float4*>(base + L.coef);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* stg_full = bars;
     uint64_t* stg_empty = stg_full + a.SS;
@@ -105,7 +117,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int Qp = a.Qp, KC = a.KC, MB = a.MB;
+    const int KC = Qp / 64, MB = a.MB;
 
     for (int i = tid; i < Qp; i += blockDim.x) wsm[i] = a.w[i];
     if (tid == 0) {
@@ -133,39 +145,43 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         if (lane == 0) {
             // ---------------------------------------------------------------- MMA issuer
             const uint32_t idesc = idesc_bf16(128, NT);
-            int nb = 0, na = 0, it = 0;
+            // descriptors of stage 0 / k-step 0; other stages and k-steps add (byte offset >> 4)
+            const uint64_t a0 = sw128_desc(smem_u32(aring));
+            const uint64_t b0 = sw128_desc(smem_u32(bhi));
+            const uint64_t l0 = sw128_desc(smem_u32(blo));
+            Ring rb, ra;
+            int it = 0;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
                 const int buf = it & 1;
                 const uint32_t use = (uint32_t)(it >> 1);
-                if (!mbar_wait(&tm_empty[buf], (use & 1u) ^ 1u, abort_flag, a.err, 0x10u)) break;
+                if (!WAITB(&tm_empty[buf], (use & 1u) ^ 1u, 0x10u)) break;
                 tc_fence_after();
                 const uint32_t dbase = tmem_base + (uint32_t)(buf * MB * NT);
                 bool ok = true;
-                for (int kc = 0; kc < KC && ok; ++kc, ++nb) {
-                    const int sb = nb % a.SB;
-                    if (!mbar_wait(&bf_full[sb], (uint32_t)(nb / a.SB) & 1u, abort_flag, a.err, 0x20u)) { ok = false; break; }
+                for (int kc = 0; kc < KC && ok; ++kc) {
+                    if (!WAITB(&bf_full[rb.s], rb.ph, 0x20u)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t b_hi = smem_u32(bhi + sb * Layout<NT, SPLIT>::kB);
-                    const uint32_t b_lo = smem_u32(blo + sb * Layout<NT, SPLIT>::kB);
-                    for (int m = 0; m < MB; ++m, ++na) {
-                        const int sa = na % a.SA;
-                        if (!mbar_wait(&a_full[sa], (uint32_t)(na / a.SA) & 1u, abort_flag, a.err, 0x40u)) { ok = false; break; }
+                    const uint64_t bd0 = b0 + (uint64_t)((rb.s * LT::kB) >> 4);
+                    const uint64_t bl0 = l0 + (uint64_t)((rb.s * LT::kB) >> 4);
+                    for (int m = 0; m < MB; ++m) {
+                        if (!WAITB(&a_full[ra.s], ra.ph, 0x40u)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t a_hi = smem_u32(aring + sa * Layout<NT, SPLIT>::kA);
+                        const uint64_t ad0 = a0 + (uint64_t)((ra.s * LT::kA) >> 4);
                         const uint32_t d = dbase + (uint32_t)(m * NT);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ad = sw128_desc(a_hi + kk * 32);
-                            const uint64_t bd = sw128_desc(b_hi + kk * 32);
+                            const uint64_t ad = ad0 + (uint64_t)(kk * 2), bd = bd0 + (uint64_t)(kk * 2);
                             mma_bf16(d, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                             if (SPLIT) {
-                                mma_bf16(d, ad, sw128_desc(b_lo + kk * 32), idesc, 1u);
-                                mma_bf16(d, sw128_desc(a_hi + kAStage + kk * 32), bd, idesc, 1u);
+                                mma_bf16(d, ad, bl0 + (uint64_t)(kk * 2), idesc, 1u);
+                                mma_bf16(d, ad + (uint64_t)(kAStage >> 4), bd, idesc, 1u);
                             }
                         }
-                        mma_commit(&a_empty[sa]);
+                        mma_commit(&a_empty[ra.s]);
+                        ra.next(a.SA);
                     }
-                    mma_commit(&bf_empty[sb]);
+                    mma_commit(&bf_empty[rb.s]);
+                    rb.next(a.SB);
                 }
                 mma_commit(&tm_full[buf]);
                 if (!ok) break;
@@ -176,14 +192,14 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             // ---------------------------------------------------------------- flux TMA producer
             // evict-last: the epilogue re-reads these lines (own values and y-neighbours) shortly
             const uint64_t pol = policy_evict_last();
-            int ns = 0;
+            Ring rs;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
                 bool ok = true;
-                for (int kc = 0; kc < KC; ++kc, ++ns) {
-                    const int ss = ns % a.SS;
-                    if (!mbar_wait(&stg_empty[ss], ((uint32_t)(ns / a.SS) & 1u) ^ 1u, abort_flag, a.err, 0x1u)) { ok = false; break; }
-                    mbar_expect_tx(&stg_full[ss], Layout<NT, SPLIT>::kStg);
-                    tma_load_2d_hint(stg + (size_t)ss * NT * 64, &tm_psi, &stg_full[ss], kc * 64, tile * NT, pol);
+                for (int kc = 0; kc < KC; ++kc) {
+                    if (!WAITB(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
+                    mbar_expect_tx(&stg_full[rs.s], LT::kStg);
+                    tma_load_2d_hint(stg + (size_t)rs.s * NT * 64, &tm_psi, &stg_full[rs.s], kc * 64, tile * NT, pol);
+                    rs.next(a.SS);
                 }
                 if (!ok) break;
             }
@@ -192,17 +208,17 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         if (lane == 0) {
             // ---------------------------------------------------------------- kernel-matrix TMA producer
             const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
-            int na = 0;
+            Ring ra;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
                 bool ok = true;
                 for (int kc = 0; kc < KC && ok; ++kc) {
-                    for (int m = 0; m < MB; ++m, ++na) {
-                        const int sa = na % a.SA;
-                        if (!mbar_wait(&a_empty[sa], ((uint32_t)(na / a.SA) & 1u) ^ 1u, abort_flag, a.err, 0x2u)) { ok = false; break; }
-                        unsigned char* dst = aring + sa * Layout<NT, SPLIT>::kA;
-                        mbar_expect_tx(&a_full[sa], Layout<NT, SPLIT>::kA);
-                        tma_load_2d_hint(dst, &tm_hi, &a_full[sa], kc * 64, m * 128, pol);
-                        if (SPLIT) tma_load_2d_hint(dst + kAStage, &tm_lo, &a_full[sa], kc * 64, m * 128, pol);
+                    for (int m = 0; m < MB; ++m) {
+                        if (!WAITB(&a_empty[ra.s], ra.ph ^ 1u, 0x2u)) { ok = false; break; }
+                        unsigned char* dst = aring + ra.s * LT::kA;
+                        mbar_expect_tx(&a_full[ra.s], LT::kA);
+                        tma_load_2d_hint(dst, &tm_hi, &a_full[ra.s], kc * 64, m * 128, pol);
+                        if (SPLIT) tma_load_2d_hint(dst + kAStage, &tm_lo, &a_full[ra.s], kc * 64, m * 128, pol);
+                        ra.next(a.SA);
                     }
                 }
                 if (!ok) break;
@@ -214,23 +230,22 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         const int ct = tid - 96;               // 0..127
         const int rsub = ct >> 4;              // 0..7
         const int col4 = ct & 15;              // float4 column within the 64-ordinate chunk
-        int ns = 0, nb = 0, it = 0;
+        Ring rs, rb;
+        int it = 0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
             float part[NR];
 #pragma unroll
             for (int i = 0; i < NR; ++i) part[i] = 0.0f;
             bool ok = true;
-            for (int kc = 0; kc < KC; ++kc, ++ns, ++nb) {
-                const int ss = ns % a.SS, sb = nb % a.SB;
-                if (!mbar_wait(&stg_full[ss], (uint32_t)(ns / a.SS) & 1u, abort_flag, a.err, 0x100u) ||
-                    !mbar_wait(&bf_empty[sb], ((uint32_t)(nb / a.SB) & 1u) ^ 1u, abort_flag, a.err, 0x200u)) {
+            for (int kc = 0; kc < KC; ++kc) {
+                if (!WAITB(&stg_full[rs.s], rs.ph, 0x100u) || !WAITB(&bf_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
                     ok = false;
                     break;
                 }
-                const float4* src = reinterpret_cast<const float4*>(stg + (size_t)ss * NT * 64);
+                const float4* src = reinterpret_cast<const float4*>(stg + (size_t)rs.s * NT * 64);
                 const float4 w4 = reinterpret_cast<const float4*>(wsm + kc * 64)[col4];
-                unsigned char* dhi = bhi + sb * Layout<NT, SPLIT>::kB;
-                unsigned char* dlo = blo + sb * Layout<NT, SPLIT>::kB;
+                unsigned char* dhi = bhi + rb.s * LT::kB;
+                unsigned char* dlo = blo + rb.s * LT::kB;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
                     const int r = rsub + 8 * i;
@@ -253,9 +268,11 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(&bf_full[sb]);
-                    mbar_arrive(&stg_empty[ss]);
+                    mbar_arrive(&bf_full[rb.s]);
+                    mbar_arrive(&stg_empty[rs.s]);
                 }
+                rs.next(a.SS);
+                rb.next(a.SB);
             }
             if (!ok) break;
             // Phi of the tile: sum the 16 column partials of each row.
@@ -270,7 +287,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             }
             const int buf = it & 1;
             const uint32_t use = (uint32_t)(it >> 1);
-            if (!mbar_wait(&phi_empty[buf], (use & 1u) ^ 1u, abort_flag, a.err, 0x400u)) break;
+            if (!WAITB(&phi_empty[buf], (use & 1u) ^ 1u, 0x400u)) break;
             if (col4 == 0) {
                 // per cell: x = 1 - dt sigma_t, y = dt (sigma_s Phi / sum w + q),
                 // z = neighbour bits (1 left, 2 right, 4 below, 8 above exist; 16 cell exists)
@@ -295,106 +312,98 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         }
     } else {
         // -------------------------------------------------------------------- epilogue
-        // Each warp owns a ring of kEpiRing chunk buffers and prefetches, with cp.async, the flux
-        // values its next chunks need (own cells with both x-edge cells, and the upwind y-neighbours)
-        // while it computes the current one.  The flux input is read-only during the launch, so the
-        // prefetch may run ahead of the MMA.
+        // Chunks of 16 cells x 32 ordinates.  The flux values of chunk k+1 (own cells, the two
+        // x-edge cells, the upwind y-neighbours) are loaded into registers while chunk k is
+        // computed.  The flux input is read-only during the launch, so these loads may run ahead
+        // of the MMA (and into the next tile).
+        const float* __restrict__ psi = a.psi;
         float* __restrict__ psi_out = a.psi_out;
-        const float* psi = a.psi;
         const int e = warp - 7;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
         const int half = e >> 2;               // which half of the tile's cells
-        const int ncell = a.ncell, nx = a.nx, ny = a.ny;
+        const int ncell = a.ncell, nx = a.nx;
         constexpr int CPH = NT / 32;           // chunks of 16 cells per half tile
         const int cpt = MB * CPH;              // chunks per tile for this warp
         const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
         const int total = my_tiles * cpt;
-        const int R = a.R;
-        float* ring = epi + (size_t)e * R * kEpiSlots * 32;
 
-        auto issue = [&](int k) {
-            const int t = k / cpt, r = k - t * cpt;
-            const int m = r / CPH;
-            const int c0 = half * (NT / 2) + (r - m * CPH) * 16;
+        // chunk k of this warp: tile index t (within this CTA), ordinate block m, first cell c0
+        auto decode = [&](int k, int& t, int& m, int& c0) {
+            t = k / cpt;
+            const int r = k - t * cpt;
+            m = r / CPH;
+            c0 = half * (NT / 2) + (r - m * CPH) * 16;
+        };
+        auto load = [&](int k, float (&s)[16], float (&u)[16], float& lft, float& rgt) {
+            int t, m, c0;
+            decode(k, t, m, c0);
             const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
             const int q = m * 128 + lq * 32 + lane;
-            const bool qv = q < a.Q;
-            float nuy = 0.f;
-            if (qv) nuy = a.ord[q].nuy;
-            const uint32_t sb = smem_u32(ring + (size_t)(k % R) * kEpiSlots * 32 + lane);
+            const bool live = q < a.Q && fb < ncell;
+            const float nuy = live ? a.ord[q].nuy : 0.0f;
+            const float* b = psi + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
+            const bool full = fb + 16 <= ncell;
 #pragma unroll
-            for (int j = 0; j < 18; ++j) {
-                const int g = fb - 1 + j;
-                const bool ok = qv && g >= 0 && g < ncell;
-                cp_async4(sb + j * 128, ok ? psi + (size_t)g * Qp + q : psi, ok ? 4u : 0u);
-            }
-            int yy = fb / nx, xx = fb - yy * nx;
-            const long dyc = nuy > 0.f ? -(long)nx : (long)nx;
+            for (int i = 0; i < 16; ++i) s[i] = (live && (full || fb + i < ncell)) ? b[i * Qp] : 0.0f;
+            // y-neighbour of cell f: below (f - nx) for nuy > 0, above (f + nx) for nuy < 0
+            const long dyo = nuy > 0.f ? -(long)nx * Qp : (long)nx * Qp;
+            const float* by = b + dyo;
+            const bool yall = nuy > 0.f ? fb >= nx : fb + 16 + nx <= ncell;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const int g = fb + i;
-                const bool rowok = nuy > 0.f ? yy > 0 : (nuy < 0.f ? yy + 1 < ny : false);
-                const bool ok = qv && g < ncell && rowok;
-                cp_async4(sb + (18 + i) * 128, ok ? psi + ((long)g + dyc) * Qp + q : psi, ok ? 4u : 0u);
-                if (++xx >= nx) { xx -= nx; ++yy; while (xx >= nx) { xx -= nx; ++yy; } }
+                const int f = fb + i;
+                const bool ok = live && nuy != 0.f && (yall || (nuy > 0.f ? f >= nx : f + nx < ncell));
+                u[i] = ok ? by[i * Qp] : 0.0f;
             }
-            cp_async_commit();
+            lft = (live && fb >= 1) ? b[-Qp] : 0.0f;
+            rgt = (live && fb + 16 < ncell) ? b[16 * Qp] : 0.0f;
         };
-
-        int k_issue = 0;
-        for (; k_issue < R - 1 && k_issue < total; ++k_issue) issue(k_issue);
-        for (int k = 0; k < total; ++k) {
-            if (k_issue < total) issue(k_issue++);
-            else cp_async_commit();            // keep one group per iteration
-            if (R == 3) cp_async_wait<2>();
-            else cp_async_wait<1>();
-            const int t = k / cpt, r = k - t * cpt;
-            const int m = r / CPH;
-            const int c0 = half * (NT / 2) + (r - m * CPH) * 16;
-            const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+        auto compute = [&](int k, const float (&s)[16], const float (&u)[16], float lft, float rgt) -> bool {
+            int t, m, c0;
+            decode(k, t, m, c0);
+            const int r = k - t * cpt;
             const int buf = t & 1;
-            const uint32_t use = (uint32_t)(t >> 1);
             if (r == 0) {
+                const uint32_t use = (uint32_t)(t >> 1);
                 int go = 1;
                 if (lane == 0)
-                    go = mbar_wait(&phi_full[buf], use & 1u, abort_flag, a.err, 0x1000u) &&
-                         mbar_wait(&tm_full[buf], use & 1u, abort_flag, a.err, 0x2000u);
+                    go = WAITB(&phi_full[buf], use & 1u, 0x1000u) && WAITB(&tm_full[buf], use & 1u, 0x2000u);
                 go = __shfl_sync(0xffffffffu, go, 0);
-                if (!go) break;
+                if (!go) return false;
                 tc_fence_after();
             }
             float y[16];
             __syncwarp();
             tmem_ld16(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * MB * NT + m * NT + c0), y);
-            const int fb = tile * NT + c0;
+            const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
             const int q = m * 128 + lq * 32 + lane;
             if (fb < ncell && q < Qp) {
                 float* po = psi_out + (size_t)fb * Qp + q;
-                const float4* cbuf = coef + buf * NT + c0;
+                const float4* cb = coef + buf * NT + c0;
                 if (q >= a.Q) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        if (fb + i < ncell) __stcs(po + (size_t)i * Qp, 0.0f);
+                        if (fb + i < ncell) __stcs(po + i * Qp, 0.0f);
                 } else {
                     const OrdF o = a.ord[q];
                     const float ax = fabsf(o.nux), ay = fabsf(o.nuy), axy = ax + ay;
+                    const float ge = a.dt_sigma_as * o.e;
                     const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
-                    const float* sl = ring + (size_t)(k % R) * kEpiSlots * 32 + lane;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        const float4 cf = cbuf[i];
+                        const float4 cf = cb[i];
                         const int bits = __float_as_int(cf.z);
                         if (!(bits & 16)) continue;
-                        const float sf = sl[(1 + i) * 32];
-                        float upx = xbit == 1 ? sl[i * 32] : sl[(i + 2) * 32];
+                        const float sf = s[i];
+                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < 15 ? s[i + 1] : rgt);
                         upx = (bits & xbit) ? upx : 0.0f;
-                        const float upy = sl[(18 + i) * 32];
                         const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
                         float out = fmaf(sf, cf.x - axy, cf.y);
                         out = fmaf(ax, upx, out);
-                        out = fmaf(ay, upy, out);
-                        out = fmaf(a.dt_sigma_as, fmaf(-o.e, st, y[i]), out);
-                        __stcs(po + (size_t)i * Qp, out);
+                        out = fmaf(ay, u[i], out);
+                        out = fmaf(a.dt_sigma_as, y[i], out);
+                        out = fmaf(-ge, st, out);
+                        __stcs(po + i * Qp, out);
                     }
                 }
             }
@@ -406,8 +415,18 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                     mbar_arrive(&phi_empty[buf]);
                 }
             }
+            return true;
+        };
+
+        float s0[16], u0[16], l0 = 0.f, r0 = 0.f, s1[16], u1[16], l1 = 0.f, r1 = 0.f;
+        if (total > 0) load(0, s0, u0, l0, r0);
+        for (int k = 0; k < total; k += 2) {
+            if (k + 1 < total) load(k + 1, s1, u1, l1, r1);
+            if (!compute(k, s0, u0, l0, r0)) break;
+            if (k + 1 >= total) break;
+            if (k + 2 < total) load(k + 2, s0, u0, l0, r0);
+            if (!compute(k + 1, s1, u1, l1, r1)) break;
         }
-        cp_async_wait<0>();
     }
 
     __syncthreads();
@@ -422,6 +441,8 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         tmem_dealloc(tmem_base, 512);
     }
 }
+
+#undef WAITB
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -452,21 +473,17 @@ bool encode_2d(CUtensorMap* map, CUtensorMapDataType type, const void* ptr, uint
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NT, bool SPLIT>
-size_t smem_need(int SS, int SB, int SA, int R, int Qp) {
-    return 1024 + (size_t)Layout<NT, SPLIT>(SS, SB, SA, R, Qp).end;
-}
-
-size_t smem_for(int NT, bool split, int SS, int SB, int SA, int R, int Qp) {
+size_t smem_for(int NT, bool split, int SS, int SB, int SA, int Qp) {
+    auto need = [&](auto L) { return (size_t)1024 + (size_t)L.end; };
     switch (NT * 2 + (split ? 1 : 0)) {
-        case 64: return smem_need<32, false>(SS, SB, SA, R, Qp);
-        case 65: return smem_need<32, true>(SS, SB, SA, R, Qp);
-        case 128: return smem_need<64, false>(SS, SB, SA, R, Qp);
-        case 129: return smem_need<64, true>(SS, SB, SA, R, Qp);
-        case 256: return smem_need<128, false>(SS, SB, SA, R, Qp);
-        case 257: return smem_need<128, true>(SS, SB, SA, R, Qp);
-        case 512: return smem_need<256, false>(SS, SB, SA, R, Qp);
-        default: return smem_need<256, true>(SS, SB, SA, R, Qp);
+        case 64: return need(Layout<32, false>(SS, SB, SA, Qp));
+        case 65: return need(Layout<32, true>(SS, SB, SA, Qp));
+        case 128: return need(Layout<64, false>(SS, SB, SA, Qp));
+        case 129: return need(Layout<64, true>(SS, SB, SA, Qp));
+        case 256: return need(Layout<128, false>(SS, SB, SA, Qp));
+        case 257: return need(Layout<128, true>(SS, SB, SA, Qp));
+        case 512: return need(Layout<256, false>(SS, SB, SA, Qp));
+        default: return need(Layout<256, true>(SS, SB, SA, Qp));
     }
 }
 
@@ -477,7 +494,7 @@ struct Tc2Plan {
     CUtensorMap tm_psi[4];
     const void* psi_key[4];
     int nkeys;
-    int Q, Qp, Mp, MB, KC, NT, SS, SB, SA, R, nx, ny, ncell, ntiles, grid;
+    int Q, Qp, Mp, MB, KC, NT, SS, SB, SA, nx, ny, ncell, ntiles, grid;
     bool split;
     size_t smem;
 };
@@ -490,41 +507,36 @@ cudaError_t tc2_plan_create(Tc2Plan** out, const __nv_bfloat16* G_hi, const __nv
     p->split = split; p->nkeys = 0;
     p->ncell = nx * ny;
     // Tile width: two accumulator buffers of MB x NT columns fill the 512 TMEM columns; narrower
-    // when the rings do not fit shared memory.  Ring depths start at 4 / 4 / 4 and the largest
-    // ring shrinks (to 2 at least) until the layout fits.
+    // when the rings do not fit shared memory.  Ring depths: the deepest balanced rings that
+    // fit (up to 4), then deeper kernel-matrix, staging and B rings (up to 8 / 6 / 4).
     int nt = 512 / (2 * p->MB);
     if (nt > 256) nt = 256;
     if (want_nt) nt = want_nt;
     const size_t limit = 227 * 1024;
-    int SS = 2, SB = 2, SA = 2, R = 2;
+    int SS = 2, SB = 2, SA = 2;
     bool fits = false;
     while (!fits) {
         if (nt < 32 || (nt & (nt - 1)) || 2 * p->MB * nt > 512) { delete p; return cudaErrorNotSupported; }
-        for (R = kEpiRingMax; R >= 2 && !fits; --R) {
-            if (want_stages >= 2) {
-                SS = SB = SA = want_stages;
-                fits = smem_for(nt, split, SS, SB, SA, R, Qp) <= limit;
-            } else if (smem_for(nt, split, 2, 2, 2, R, Qp) <= limit) {
-                // deepest balanced rings that fit, then deepen A, the staging ring and B (max 4)
-                fits = true;
-                SS = SB = SA = 2;
-                for (int k = 4; k >= 3; --k)
-                    if (smem_for(nt, split, k, k, k, R, Qp) <= limit) { SS = SB = SA = k; break; }
-                while (SA < 4 && smem_for(nt, split, SS, SB, SA + 1, R, Qp) <= limit) ++SA;
-                while (SS < 4 && smem_for(nt, split, SS + 1, SB, SA, R, Qp) <= limit) ++SS;
-                while (SB < 4 && smem_for(nt, split, SS, SB + 1, SA, R, Qp) <= limit) ++SB;
-            }
-            if (fits) break;
+        if (want_stages >= 2) {
+            SS = SB = SA = want_stages;
+            fits = smem_for(nt, split, SS, SB, SA, Qp) <= limit;
+        } else if (smem_for(nt, split, 2, 2, 2, Qp) <= limit) {
+            fits = true;
+            SS = SB = SA = 2;
+            for (int k = 4; k >= 3; --k)
+                if (smem_for(nt, split, k, k, k, Qp) <= limit) { SS = SB = SA = k; break; }
+            while (SA < 8 && smem_for(nt, split, SS, SB, SA + 1, Qp) <= limit) ++SA;
+            while (SS < 6 && smem_for(nt, split, SS + 1, SB, SA, Qp) <= limit) ++SS;
+            while (SB < 4 && smem_for(nt, split, SS, SB + 1, SA, Qp) <= limit) ++SB;
         }
         if (!fits) {
             if (want_nt) { delete p; return cudaErrorNotSupported; }
             nt /= 2;
         }
     }
-    p->R = R;
     p->NT = nt;
     p->SS = SS; p->SB = SB; p->SA = SA;
-    p->smem = smem_for(nt, split, SS, SB, SA, R, Qp);
+    p->smem = smem_for(nt, split, SS, SB, SA, Qp);
     p->ntiles = (p->ncell + nt - 1) / nt;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -562,13 +574,37 @@ static const CUtensorMap* psi_map(Tc2Plan* p, const float* psi) {
     return &p->tm_psi[slot];
 }
 
-template <int NT, bool SPLIT>
+template <int NT, bool SPLIT, int QP>
 static cudaError_t launch2(const Tc2Plan* p, const CUtensorMap* mpsi, const Tc2Args& a, cudaStream_t s) {
-    auto kern = step_tc2_kernel<NT, SPLIT>;
+    auto kern = step_tc2_kernel<NT, SPLIT, QP>;
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (r != cudaSuccess) return r;
     kern<<<p->grid, kThreads2, p->smem, s>>>(*mpsi, p->tm_hi, p->tm_lo, a);
     return cudaGetLastError();
+}
+
+// Compile-time ordinate strides for the common quadratures (at their automatic tile widths and
+// half of them); everything else runs the runtime-stride instance.
+template <bool SPLIT>
+static cudaError_t dispatch(const Tc2Plan* p, const CUtensorMap* m, const Tc2Args& a, cudaStream_t s) {
+    const int key = p->Qp * 1000 + p->NT;
+    switch (key) {
+        case 512 * 1000 + 64: return launch2<64, SPLIT, 512>(p, m, a, s);
+        case 512 * 1000 + 32: return launch2<32, SPLIT, 512>(p, m, a, s);
+        case 256 * 1000 + 128: return launch2<128, SPLIT, 256>(p, m, a, s);
+        case 256 * 1000 + 64: return launch2<64, SPLIT, 256>(p, m, a, s);
+        case 128 * 1000 + 256: return launch2<256, SPLIT, 128>(p, m, a, s);
+        case 128 * 1000 + 128: return launch2<128, SPLIT, 128>(p, m, a, s);
+        case 64 * 1000 + 256: return launch2<256, SPLIT, 64>(p, m, a, s);
+        case 64 * 1000 + 128: return launch2<128, SPLIT, 64>(p, m, a, s);
+        default: break;
+    }
+    switch (p->NT) {
+        case 32: return launch2<32, SPLIT, 0>(p, m, a, s);
+        case 64: return launch2<64, SPLIT, 0>(p, m, a, s);
+        case 128: return launch2<128, SPLIT, 0>(p, m, a, s);
+        default: return launch2<256, SPLIT, 0>(p, m, a, s);
+    }
 }
 
 cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, const float* w, unsigned int* err_flag,
@@ -577,17 +613,8 @@ cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, c
     const CUtensorMap* mpsi = psi_map(p, s.psi);
     if (!mpsi) return cudaErrorInvalidValue;
     Tc2Args a{s.psi, s.psi_out, s.ord, s.cell, w, err_flag, s.nx, s.ny, s.Q, s.Qp, p->MB, p->KC, p->ntiles,
-              p->ncell, p->SS, p->SB, p->SA, p->R, s.dt, s.dt_sigma_as};
-    switch (p->NT * 2 + (p->split ? 1 : 0)) {
-        case 64: return launch2<32, false>(p, mpsi, a, stream);
-        case 65: return launch2<32, true>(p, mpsi, a, stream);
-        case 128: return launch2<64, false>(p, mpsi, a, stream);
-        case 129: return launch2<64, true>(p, mpsi, a, stream);
-        case 256: return launch2<128, false>(p, mpsi, a, stream);
-        case 257: return launch2<128, true>(p, mpsi, a, stream);
-        case 512: return launch2<256, false>(p, mpsi, a, stream);
-        default: return launch2<256, true>(p, mpsi, a, stream);
-    }
+              p->ncell, p->SS, p->SB, p->SA, s.dt, s.dt_sigma_as};
+    return p->split ? dispatch<true>(p, mpsi, a, stream) : dispatch<false>(p, mpsi, a, stream);
 }
 
 }  // namespace assn
