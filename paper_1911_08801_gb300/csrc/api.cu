@@ -36,6 +36,7 @@ struct assn_problem {
 
     // device memory
     double* d_omega = nullptr;
+    unsigned char* d_ydir = nullptr;   // [Qp/4] upwind y side per group of 4 ordinates (tensor-core epilogue)
     double* d_w64 = nullptr;
     float* d_w32 = nullptr;
     double* d_K64 = nullptr;
@@ -233,6 +234,7 @@ int install_quadrature(assn_problem* p, int Q, const double* omega, const double
     dfree(p->d_w64);
     dfree(p->d_w32);
     dfree(p->d_ord);
+    dfree(p->d_ydir);
     p->ord_dt = -1;
     p->Q = Q;
     p->Qp = (Q + 63) / 64 * 64;
@@ -249,6 +251,16 @@ int install_quadrature(assn_problem* p, int Q, const double* omega, const double
     CK(p, cudaMemcpyAsync(p->d_omega, omega, sizeof(double) * 3 * Q, cudaMemcpyHostToDevice, p->stream));
     CK(p, cudaMemcpyAsync(p->d_w64, wp.data(), sizeof(double) * p->Qp, cudaMemcpyHostToDevice, p->stream));
     CK(p, cudaMemcpyAsync(p->d_w32, wf.data(), sizeof(float) * p->Qp, cudaMemcpyHostToDevice, p->stream));
+    // Upwind y side per aligned group of 4 ordinates, taken from its first ordinate with Omega_y != 0:
+    // 1 = the cell below (Omega_y > 0), 2 = the cell above, 0 = no y transport in the group.
+    std::vector<unsigned char> yd(p->Qp / 4, 0);
+    for (int g = 0; g < p->Qp / 4; ++g)
+        for (int j = 0; j < 4 && 4 * g + j < Q; ++j) {
+            const double oy = omega[3 * (4 * g + j) + 1];
+            if (oy != 0.0) { yd[g] = oy > 0 ? 1 : 2; break; }
+        }
+    CK(p, cudaMalloc(&p->d_ydir, p->Qp / 4));
+    CK(p, cudaMemcpyAsync(p->d_ydir, yd.data(), p->Qp / 4, cudaMemcpyHostToDevice, p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     int r = alloc_state(p);
     if (r) return r;
@@ -332,7 +344,7 @@ int assn_destroy(assn_problem* p) {
     cudaSetDevice(p->dev);
     if (p->stream) cudaStreamSynchronize(p->stream);
     free_operands(p);
-    dfree(p->d_omega); dfree(p->d_w64); dfree(p->d_w32); dfree(p->d_ord); dfree(p->d_cell);
+    dfree(p->d_omega); dfree(p->d_w64); dfree(p->d_w32); dfree(p->d_ord); dfree(p->d_cell); dfree(p->d_ydir);
     dfree(p->d_psi[0]); dfree(p->d_psi[1]); dfree(p->d_partials); dfree(p->d_scalar); dfree(p->d_flags);
     dfree(p->d_stage);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -591,7 +603,7 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
             CK(p, launch_step_simt_f32(a, p->stream));
         } else {
             cudaError_t e = p->variant == 1 ? launch_step_tc(p->plan, a, p->d_w32, p->d_flags + 1, p->stream)
-                                            : launch_step_tc2(p->plan2, a, p->d_w32, p->d_flags + 1, p->stream);
+                                            : launch_step_tc2(p->plan2, a, p->d_w32, p->d_ydir, p->d_flags + 1, p->stream);
             if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: shape not supported");
             CK(p, e);
         }

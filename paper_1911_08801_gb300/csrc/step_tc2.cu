@@ -49,18 +49,27 @@ struct Tc2Args {
     const OrdF* ord;
     const CellF* cell;
     const float* w;
+    const __nv_bfloat16* G_hi;      // [Mp][Qp] kernel-matrix operand (and residual for SPLIT)
+    const __nv_bfloat16* G_lo;
+    const unsigned char* ydir;      // [Qp/4] per group of 4 ordinates: 0 none, 1 below, 2 above
     unsigned int* err;
     int nx, ny, Q, Qp, MB, KC, ntiles, ncell;
     int SS, SB, SA;
     float dt, dt_sigma_as;
 };
 
+constexpr int kCPS = 2;            // 64-ordinate chunks per staging stage (one TMA request)
+constexpr int kEpiWarps = 8;
+constexpr int kEpiRows = 34;       // per chunk: cells fb-1 .. fb+16, then 16 y-neighbour rows
+constexpr int kEpiChunk = kEpiRows * 128;
+constexpr int kEpiRing = 2;        // chunks in flight per epilogue warp
+
 template <int NT, bool SPLIT>
 struct Layout {
-    static constexpr int kStg = NT * 256;                       // FP32 staging stage
+    static constexpr int kStg = kCPS * NT * 256;                // FP32 staging stage (kCPS chunks)
     static constexpr int kB = NT * 128;                         // BF16 B stage (one of hi / lo)
     static constexpr int kA = kAStage * (SPLIT ? 2 : 1);        // A stage (hi [+ lo])
-    int stg, bhi, blo, a, w, coef, bars, end;
+    int stg, bhi, blo, a, w, coef, epi, bars, end;
     __host__ __device__ Layout(int SS, int SB, int SA, int Qp) {
         stg = 0;
         bhi = stg + SS * kStg;
@@ -68,7 +77,8 @@ struct Layout {
         a = blo + (SPLIT ? SB * kB : 0);
         w = a + SA * kA;
         coef = w + Qp * 4;                                       // [2][NT] float4 cell coefficients
-        bars = coef + 2 * NT * 16;
+        epi = coef + 2 * NT * 16;                                // [8 warps][ring][34 rows][128 B]
+        bars = epi + kEpiWarps * kEpiRing * kEpiChunk;
         // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2]
         end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 8) + 16;
     }
@@ -102,6 +112,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     unsigned char* aring = base + L.a;
     float* wsm = reinterpret_cast<float*>(base + L.w);
     float4* coef = reinterpret_cast<float4*>(base + L.coef);
+    unsigned char* epi = base + L.epi;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* stg_full = bars;
     uint64_t* stg_empty = stg_full + a.SS;
@@ -123,7 +134,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     if (tid == 0) {
         for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], 4); }
         for (int s = 0; s < a.SB; ++s) { mbar_init(&bf_full[s], 4); mbar_init(&bf_empty[s], 1); }
-        for (int s = 0; s < a.SA; ++s) { mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], 1); }
+        for (int s = 0; s < a.SA; ++s) { mbar_init(&a_full[s], 32); mbar_init(&a_empty[s], 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tm_full[b], 1);
             mbar_init(&tm_empty[b], 8);
@@ -165,6 +176,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                     const uint64_t bl0 = l0 + (uint64_t)((rb.s * LT::kB) >> 4);
                     for (int m = 0; m < MB; ++m) {
                         if (!WAITB(&a_full[ra.s], ra.ph, 0x40u)) { ok = false; break; }
+                        fence_proxy_async();   // cp.async wrote the stage through the generic proxy
                         tc_fence_after();
                         const uint64_t ad0 = a0 + (uint64_t)((ra.s * LT::kA) >> 4);
                         const uint32_t d = dbase + (uint32_t)(m * NT);
@@ -190,40 +202,53 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------------------- flux TMA producer
-            // evict-last: the epilogue re-reads these lines (own values and y-neighbours) shortly
+            // one request per kCPS chunks ([kCPS][NT cells][64 ordinates]); evict-last because the
+            // epilogue re-reads these lines (own values and y-neighbours) shortly
             const uint64_t pol = policy_evict_last();
             Ring rs;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
                 bool ok = true;
-                for (int kc = 0; kc < KC; ++kc) {
+                for (int kc = 0; kc < KC; kc += kCPS) {
                     if (!WAITB(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
                     mbar_expect_tx(&stg_full[rs.s], LT::kStg);
-                    tma_load_2d_hint(stg + (size_t)rs.s * NT * 64, &tm_psi, &stg_full[rs.s], kc * 64, tile * NT, pol);
+                    tma_load_3d_hint(stg + (size_t)rs.s * kCPS * NT * 64, &tm_psi, &stg_full[rs.s], 0, tile * NT,
+                                     kc, pol);
                     rs.next(a.SS);
                 }
                 if (!ok) break;
             }
         }
     } else if (warp == 2) {
-        if (lane == 0) {
-            // ---------------------------------------------------------------- kernel-matrix TMA producer
-            const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
-            Ring ra;
-            for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-                bool ok = true;
-                for (int kc = 0; kc < KC && ok; ++kc) {
-                    for (int m = 0; m < MB; ++m) {
-                        if (!WAITB(&a_empty[ra.s], ra.ph ^ 1u, 0x2u)) { ok = false; break; }
-                        unsigned char* dst = aring + ra.s * LT::kA;
-                        mbar_expect_tx(&a_full[ra.s], LT::kA);
-                        tma_load_2d_hint(dst, &tm_hi, &a_full[ra.s], kc * 64, m * 128, pol);
-                        if (SPLIT) tma_load_2d_hint(dst + kAStage, &tm_lo, &a_full[ra.s], kc * 64, m * 128, pol);
-                        ra.next(a.SA);
+        // -------------------------------------------------------------------- kernel-matrix producer
+        // The whole warp copies each [128 x 64] BF16 chunk of G with 16-byte cp.async straight into
+        // the 128-byte-swizzled K-major layout (row r at r * 128, 16-byte piece c at (c ^ (r & 7)));
+        // each lane's copies arrive on the stage's barrier when they land (32 arrivals per phase).
+        Ring ra;
+        const int c = lane & 7, r0 = lane >> 3;
+        for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+            bool ok = true;
+            for (int kc = 0; kc < KC && ok; ++kc) {
+                for (int m = 0; m < MB; ++m) {
+                    int go = 1;
+                    if (lane == 0) go = WAITB(&a_empty[ra.s], ra.ph ^ 1u, 0x2u);
+                    go = __shfl_sync(0xffffffffu, go, 0);
+                    if (!go) { ok = false; break; }
+                    const uint32_t dst = smem_u32(aring + ra.s * LT::kA);
+                    const size_t gbase = (size_t)(m * 128) * Qp + kc * 64 + c * 8;   // elements
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int r = r0 + 4 * j;
+                        const uint32_t d = dst + r * 128 + ((c ^ (r & 7)) << 4);
+                        cp_async16(d, a.G_hi + gbase + (size_t)r * Qp, 16u);
+                        if (SPLIT) cp_async16(d + kAStage, a.G_lo + gbase + (size_t)r * Qp, 16u);
                     }
+                    cp_async_mbar_arrive(&a_full[ra.s]);
+                    ra.next(a.SA);
                 }
-                if (!ok) break;
             }
+            if (!ok) break;
         }
+        cp_async_wait<0>();
     } else if (warp < 7) {
         // -------------------------------------------------------------------- converters
         constexpr int NR = NT / 8;             // rows (cells) per thread
@@ -238,11 +263,13 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             for (int i = 0; i < NR; ++i) part[i] = 0.0f;
             bool ok = true;
             for (int kc = 0; kc < KC; ++kc) {
-                if (!WAITB(&stg_full[rs.s], rs.ph, 0x100u) || !WAITB(&bf_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
+                const int sub = kc % kCPS;           // chunk within the staging stage
+                if ((sub == 0 && !WAITB(&stg_full[rs.s], rs.ph, 0x100u)) ||
+                    !WAITB(&bf_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
                     ok = false;
                     break;
                 }
-                const float4* src = reinterpret_cast<const float4*>(stg + (size_t)rs.s * NT * 64);
+                const float4* src = reinterpret_cast<const float4*>(stg + ((size_t)rs.s * kCPS + sub) * NT * 64);
                 const float4 w4 = reinterpret_cast<const float4*>(wsm + kc * 64)[col4];
                 unsigned char* dhi = bhi + rb.s * LT::kB;
                 unsigned char* dlo = blo + rb.s * LT::kB;
@@ -267,11 +294,12 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                 }
                 fence_proxy_async();
                 __syncwarp();
+                const bool last_of_stage = sub == kCPS - 1 || kc == KC - 1;
                 if (lane == 0) {
                     mbar_arrive(&bf_full[rb.s]);
-                    mbar_arrive(&stg_empty[rs.s]);
+                    if (last_of_stage) mbar_arrive(&stg_empty[rs.s]);
                 }
-                rs.next(a.SS);
+                if (last_of_stage) rs.next(a.SS);
                 rb.next(a.SB);
             }
             if (!ok) break;
@@ -312,10 +340,10 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         }
     } else {
         // -------------------------------------------------------------------- epilogue
-        // Chunks of 16 cells x 32 ordinates.  The flux values of chunk k+1 (own cells, the two
-        // x-edge cells, the upwind y-neighbours) are loaded into registers while chunk k is
-        // computed.  The flux input is read-only during the launch, so these loads may run ahead
-        // of the MMA (and into the next tile).
+        // Chunks of 16 cells x 32 ordinates.  While chunk k is computed, the warp copies the flux
+        // values chunk k+1 needs (own cells with both x-edge cells, and the upwind y-neighbour of
+        // each group of 4 ordinates) with 16-byte cp.async into its ring in shared memory.  The flux
+        // input is read-only during the launch, so these copies may run ahead of the MMA.
         const float* __restrict__ psi = a.psi;
         float* __restrict__ psi_out = a.psi_out;
         const int e = warp - 7;
@@ -326,39 +354,48 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         const int cpt = MB * CPH;              // chunks per tile for this warp
         const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
         const int total = my_tiles * cpt;
+        unsigned char* ring = epi + e * kEpiRing * kEpiChunk;
+        const int pc = lane & 7;               // 16-byte piece (4 ordinates) this lane copies
+        const int prow = lane >> 3;            // row offset of this lane's copies (4 rows per instruction)
 
-        // chunk k of this warp: tile index t (within this CTA), ordinate block m, first cell c0
         auto decode = [&](int k, int& t, int& m, int& c0) {
             t = k / cpt;
             const int r = k - t * cpt;
             m = r / CPH;
             c0 = half * (NT / 2) + (r - m * CPH) * 16;
         };
-        auto load = [&](int k, float (&s)[16], float (&u)[16], float& lft, float& rgt) {
+        auto issue = [&](int k) {
             int t, m, c0;
             decode(k, t, m, c0);
             const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
-            const int q = m * 128 + lq * 32 + lane;
-            const bool live = q < a.Q && fb < ncell;
-            const float nuy = live ? a.ord[q].nuy : 0.0f;
-            const float* b = psi + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
-            const bool full = fb + 16 <= ncell;
+            const int q0 = m * 128 + lq * 32;  // first ordinate of this warp
+            const uint32_t sb = smem_u32(ring + (k % kEpiRing) * kEpiChunk);
+            const bool qok = q0 < Qp;
+            const float* col = psi + (qok ? q0 + pc * 4 : 0);
+            // own cells fb-1 .. fb+16 (rows 0..17)
 #pragma unroll
-            for (int i = 0; i < 16; ++i) s[i] = (live && (full || fb + i < ncell)) ? b[i * Qp] : 0.0f;
-            // y-neighbour of cell f: below (f - nx) for nuy > 0, above (f + nx) for nuy < 0
-            const long dyo = nuy > 0.f ? -(long)nx * Qp : (long)nx * Qp;
-            const float* by = b + dyo;
-            const bool yall = nuy > 0.f ? fb >= nx : fb + 16 + nx <= ncell;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int f = fb + i;
-                const bool ok = live && nuy != 0.f && (yall || (nuy > 0.f ? f >= nx : f + nx < ncell));
-                u[i] = ok ? by[i * Qp] : 0.0f;
+            for (int j = 0; j < 5; ++j) {
+                const int row = prow + 4 * j;
+                if (row < 18) {
+                    const int f = fb - 1 + row;
+                    const bool ok = qok && f >= 0 && f < ncell;
+                    cp_async16(sb + row * 128 + pc * 16, ok ? col + (size_t)f * Qp : psi, ok ? 16u : 0u);
+                }
             }
-            lft = (live && fb >= 1) ? b[-Qp] : 0.0f;
-            rgt = (live && fb + 16 < ncell) ? b[16 * Qp] : 0.0f;
+            // upwind y-neighbours of cells fb .. fb+15 (rows 18..33), per group of 4 ordinates
+            const int dir = qok ? a.ydir[(q0 >> 2) + pc] : 0;
+            const int dn = dir == 1 ? -nx : nx;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = prow + 4 * j;
+                const int f = fb + i;
+                const int g = f + dn;
+                const bool ok = dir != 0 && f < ncell && g >= 0 && g < ncell;
+                cp_async16(sb + (18 + i) * 128 + pc * 16, ok ? col + (size_t)g * Qp : psi, ok ? 16u : 0u);
+            }
+            cp_async_commit();
         };
-        auto compute = [&](int k, const float (&s)[16], const float (&u)[16], float lft, float rgt) -> bool {
+        auto compute = [&](int k) -> bool {
             int t, m, c0;
             decode(k, t, m, c0);
             const int r = k - t * cpt;
@@ -385,22 +422,32 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                     for (int i = 0; i < 16; ++i)
                         if (fb + i < ncell) __stcs(po + i * Qp, 0.0f);
                 } else {
+                    const float* sl = reinterpret_cast<const float*>(ring + (k % kEpiRing) * kEpiChunk) + lane;
                     const OrdF o = a.ord[q];
                     const float ax = fabsf(o.nux), ay = fabsf(o.nuy), axy = ax + ay;
                     const float ge = a.dt_sigma_as * o.e;
                     const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
+                    // the group's copied y-neighbour is this lane's upwind one unless the group mixes signs
+                    const int mydir = o.nuy > 0.f ? 1 : (o.nuy < 0.f ? 2 : 0);
+                    const bool yslot = mydir == 0 || a.ydir[q >> 2] == mydir;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const float4 cf = cb[i];
                         const int bits = __float_as_int(cf.z);
                         if (!(bits & 16)) continue;
-                        const float sf = s[i];
-                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < 15 ? s[i + 1] : rgt);
+                        const float sf = sl[(1 + i) * 32];
+                        float upx = xbit == 1 ? sl[i * 32] : sl[(i + 2) * 32];
                         upx = (bits & xbit) ? upx : 0.0f;
+                        float upy = sl[(18 + i) * 32];
+                        if (!yslot) {
+                            const int f = fb + i;
+                            const int g = mydir == 1 ? f - nx : f + nx;
+                            upy = (g >= 0 && g < ncell) ? psi[(size_t)g * Qp + q] : 0.0f;
+                        }
                         const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
                         float out = fmaf(sf, cf.x - axy, cf.y);
                         out = fmaf(ax, upx, out);
-                        out = fmaf(ay, u[i], out);
+                        out = fmaf(ay, upy, out);
                         out = fmaf(a.dt_sigma_as, y[i], out);
                         out = fmaf(-ge, st, out);
                         __stcs(po + i * Qp, out);
@@ -418,15 +465,14 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             return true;
         };
 
-        float s0[16], u0[16], l0 = 0.f, r0 = 0.f, s1[16], u1[16], l1 = 0.f, r1 = 0.f;
-        if (total > 0) load(0, s0, u0, l0, r0);
-        for (int k = 0; k < total; k += 2) {
-            if (k + 1 < total) load(k + 1, s1, u1, l1, r1);
-            if (!compute(k, s0, u0, l0, r0)) break;
-            if (k + 1 >= total) break;
-            if (k + 2 < total) load(k + 2, s0, u0, l0, r0);
-            if (!compute(k + 1, s1, u1, l1, r1)) break;
+        if (total > 0) issue(0);
+        for (int k = 0; k < total; ++k) {
+            if (k + 1 < total) issue(k + 1);
+            else cp_async_commit();
+            cp_async_wait<1>();
+            if (!compute(k)) break;
         }
+        cp_async_wait<0>();
     }
 
     __syncthreads();
@@ -491,6 +537,8 @@ size_t smem_for(int NT, bool split, int SS, int SB, int SA, int Qp) {
 
 struct Tc2Plan {
     CUtensorMap tm_hi, tm_lo;
+    const __nv_bfloat16* G_hi;
+    const __nv_bfloat16* G_lo;
     CUtensorMap tm_psi[4];
     const void* psi_key[4];
     int nkeys;
@@ -506,6 +554,8 @@ cudaError_t tc2_plan_create(Tc2Plan** out, const __nv_bfloat16* G_hi, const __nv
     p->Q = Q; p->Qp = Qp; p->Mp = Mp; p->MB = Mp / 128; p->KC = Qp / 64; p->nx = nx; p->ny = ny;
     p->split = split; p->nkeys = 0;
     p->ncell = nx * ny;
+    p->G_hi = G_hi;
+    p->G_lo = G_lo;
     // Tile width: two accumulator buffers of MB x NT columns fill the 512 TMEM columns; narrower
     // when the rings do not fit shared memory.  Ring depths: the deepest balanced rings that
     // fit (up to 4), then deeper kernel-matrix, staging and B rings (up to 8 / 6 / 4).
@@ -567,8 +617,16 @@ static const CUtensorMap* psi_map(Tc2Plan* p, const float* psi) {
     for (int i = 0; i < p->nkeys; ++i)
         if (p->psi_key[i] == psi) return &p->tm_psi[i];
     const int slot = p->nkeys < 4 ? p->nkeys++ : 3;
-    if (!encode_2d(&p->tm_psi[slot], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, psi, p->Qp, p->ncell, (uint64_t)p->Qp * 4, 64,
-                   p->NT, CU_TENSOR_MAP_SWIZZLE_NONE))
+    // 3D view of the flux: x = ordinate within a 64-chunk, y = cell, z = chunk; box {64, NT, kCPS}
+    EncodeFn enc = get_encode();
+    if (!enc) return nullptr;
+    const cuuint64_t dims[3] = {64, (cuuint64_t)p->ncell, (cuuint64_t)p->KC};
+    const cuuint64_t strides[2] = {(cuuint64_t)p->Qp * 4, 256};
+    const cuuint32_t box[3] = {64, (cuuint32_t)p->NT, (cuuint32_t)kCPS};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&p->tm_psi[slot], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(psi), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return nullptr;
     p->psi_key[slot] = psi;
     return &p->tm_psi[slot];
@@ -607,12 +665,12 @@ static cudaError_t dispatch(const Tc2Plan* p, const CUtensorMap* m, const Tc2Arg
     }
 }
 
-cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, const float* w, unsigned int* err_flag,
-                            cudaStream_t stream) {
+cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, const float* w,
+                            const unsigned char* ydir, unsigned int* err_flag, cudaStream_t stream) {
     if (!p) return cudaErrorInvalidValue;
     const CUtensorMap* mpsi = psi_map(p, s.psi);
     if (!mpsi) return cudaErrorInvalidValue;
-    Tc2Args a{s.psi, s.psi_out, s.ord, s.cell, w, err_flag, s.nx, s.ny, s.Q, s.Qp, p->MB, p->KC, p->ntiles,
+    Tc2Args a{s.psi, s.psi_out, s.ord, s.cell, w, p->G_hi, p->split ? p->G_lo : p->G_hi, ydir, err_flag, s.nx, s.ny, s.Q, s.Qp, p->MB, p->KC, p->ntiles,
               p->ncell, p->SS, p->SB, p->SA, s.dt, s.dt_sigma_as};
     return p->split ? dispatch<true>(p, mpsi, a, stream) : dispatch<false>(p, mpsi, a, stream);
 }
