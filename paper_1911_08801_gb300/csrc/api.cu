@@ -603,7 +603,7 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
             CK(p, launch_step_simt_f32(a, p->stream));
         } else {
             cudaError_t e = p->variant == 1 ? launch_step_tc(p->plan, a, p->d_w32, p->d_flags + 1, p->stream)
-                                            : launch_step_tc2(p->plan2, a, p->d_w32, p->d_ydir, p->d_flags + 1, p->stream);
+                                            : launch_step_tc2(p->plan2, a, p->d_w32, p->d_flags + 1, p->stream);
             if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: shape not supported");
             CK(p, e);
         }

@@ -74,7 +74,7 @@ cudaError_t tc2_plan_create(Tc2Plan** plan, const __nv_bfloat16* G_hi, const __n
 void tc2_plan_destroy(Tc2Plan* plan);
 void tc2_plan_describe(const Tc2Plan* plan, int* tile_cells, int* stages, int* tmem_cols, size_t* smem);
 cudaError_t launch_step_tc2(Tc2Plan* plan, const StepArgs<float, OrdF, CellF>& a, const float* w,
-                            const unsigned char* ydir, unsigned int* err_flag, cudaStream_t s);
+                            unsigned int* err_flag, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_scalar_flux(const T* psi, const T* w, int ncell, int Qp, float* out_f,

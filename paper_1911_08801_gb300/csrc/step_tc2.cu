@@ -11,7 +11,9 @@
 //   warp 1      lane 0: TMA producer of the FP32 flux: [NT cells x 64 ordinates] chunks into an
 //               SS-stage staging ring.
 //   warp 2      lane 0: TMA producer of the kernel-matrix operand G (off-diagonal K in BF16,
-//               [128 x 64] chunks, 128-byte swizzle) into an SA-stage ring.
+//               128-byte swizzle) into an SA-stage ring; one 4D request brings the [128 x 64]
+//               chunks of MPR ordinate blocks for one k-chunk (a TMA request costs about the same
+//               time whatever its size, so requests are made as large as shared memory allows).
 //   warps 3-6   converters: staging chunk -> BF16 B operand (K-major, 128-byte swizzle, written
 //               directly in the canonical layout) in an SB-stage ring; the scalar flux
 //               Phi_c = sum_p w_p psi_p(c) accumulated in FP32 over the tile's chunks, and from it
@@ -49,36 +51,27 @@ struct Tc2Args {
     const OrdF* ord;
     const CellF* cell;
     const float* w;
-    const __nv_bfloat16* G_hi;      // [Mp][Qp] kernel-matrix operand (and residual for SPLIT)
-    const __nv_bfloat16* G_lo;
-    const unsigned char* ydir;      // [Qp/4] per group of 4 ordinates: 0 none, 1 below, 2 above
     unsigned int* err;
     int nx, ny, Q, Qp, MB, KC, ntiles, ncell;
-    int SS, SB, SA;
+    int SS, SB, SA, MPR;
     float dt, dt_sigma_as;
 };
 
-constexpr int kCPS = 2;            // 64-ordinate chunks per staging stage (one TMA request)
-constexpr int kEpiWarps = 8;
-constexpr int kEpiRows = 34;       // per chunk: cells fb-1 .. fb+16, then 16 y-neighbour rows
-constexpr int kEpiChunk = kEpiRows * 128;
-constexpr int kEpiRing = 2;        // chunks in flight per epilogue warp
-
 template <int NT, bool SPLIT>
 struct Layout {
-    static constexpr int kStg = kCPS * NT * 256;                // FP32 staging stage (kCPS chunks)
+    static constexpr int kStg = NT * 256;                       // FP32 staging stage
     static constexpr int kB = NT * 128;                         // BF16 B stage (one of hi / lo)
-    static constexpr int kA = kAStage * (SPLIT ? 2 : 1);        // A stage (hi [+ lo])
-    int stg, bhi, blo, a, w, coef, epi, bars, end;
-    __host__ __device__ Layout(int SS, int SB, int SA, int Qp) {
+    int kA;                                                     // A stage: MPR blocks (hi [+ lo])
+    int stg, bhi, blo, a, w, coef, bars, end;
+    __host__ __device__ Layout(int SS, int SB, int SA, int Qp, int MPR) {
+        kA = MPR * kAStage * (SPLIT ? 2 : 1);
         stg = 0;
         bhi = stg + SS * kStg;
         blo = bhi + SB * kB;
         a = blo + (SPLIT ? SB * kB : 0);
         w = a + SA * kA;
         coef = w + Qp * 4;                                       // [2][NT] float4 cell coefficients
-        epi = coef + 2 * NT * 16;                                // [8 warps][ring][34 rows][128 B]
-        bars = epi + kEpiWarps * kEpiRing * kEpiChunk;
+        bars = coef + 2 * NT * 16;
         // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2]
         end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 8) + 16;
     }
@@ -104,7 +97,8 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int Qp = QP > 0 ? QP : a.Qp;
-    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, Qp);
+    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, Qp, a.MPR);
+    const int MPR = a.MPR;
     using LT = Layout<NT, SPLIT>;
     float* stg = reinterpret_cast<float*>(base + L.stg);
     unsigned char* bhi = base + L.bhi;
@@ -112,7 +106,6 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     unsigned char* aring = base + L.a;
     float* wsm = reinterpret_cast<float*>(base + L.w);
     float4* coef = reinterpret_cast<float4*>(base + L.coef);
-    unsigned char* epi = base + L.epi;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* stg_full = bars;
     uint64_t* stg_empty = stg_full + a.SS;
@@ -134,7 +127,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     if (tid == 0) {
         for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], 4); }
         for (int s = 0; s < a.SB; ++s) { mbar_init(&bf_full[s], 4); mbar_init(&bf_empty[s], 1); }
-        for (int s = 0; s < a.SA; ++s) { mbar_init(&a_full[s], 32); mbar_init(&a_empty[s], 1); }
+        for (int s = 0; s < a.SA; ++s) { mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tm_full[b], 1);
             mbar_init(&tm_empty[b], 8);
@@ -174,19 +167,21 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                     tc_fence_after();
                     const uint64_t bd0 = b0 + (uint64_t)((rb.s * LT::kB) >> 4);
                     const uint64_t bl0 = l0 + (uint64_t)((rb.s * LT::kB) >> 4);
-                    for (int m = 0; m < MB; ++m) {
+                    for (int mg = 0; mg < MB; mg += MPR) {
                         if (!WAITB(&a_full[ra.s], ra.ph, 0x40u)) { ok = false; break; }
-                        fence_proxy_async();   // cp.async wrote the stage through the generic proxy
                         tc_fence_after();
-                        const uint64_t ad0 = a0 + (uint64_t)((ra.s * LT::kA) >> 4);
-                        const uint32_t d = dbase + (uint32_t)(m * NT);
+                        const uint64_t as0 = a0 + (uint64_t)((ra.s * L.kA) >> 4);
+                        for (int mm = 0; mm < MPR; ++mm) {
+                            const uint64_t ad0 = as0 + (uint64_t)((mm * kAStage) >> 4);
+                            const uint32_t d = dbase + (uint32_t)((mg + mm) * NT);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ad = ad0 + (uint64_t)(kk * 2), bd = bd0 + (uint64_t)(kk * 2);
-                            mma_bf16(d, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                            if (SPLIT) {
-                                mma_bf16(d, ad, bl0 + (uint64_t)(kk * 2), idesc, 1u);
-                                mma_bf16(d, ad + (uint64_t)(kAStage >> 4), bd, idesc, 1u);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = ad0 + (uint64_t)(kk * 2), bd = bd0 + (uint64_t)(kk * 2);
+                                mma_bf16(d, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                                if (SPLIT) {
+                                    mma_bf16(d, ad, bl0 + (uint64_t)(kk * 2), idesc, 1u);
+                                    mma_bf16(d, ad + (uint64_t)((MPR * kAStage) >> 4), bd, idesc, 1u);
+                                }
                             }
                         }
                         mma_commit(&a_empty[ra.s]);
@@ -202,54 +197,41 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------------------- flux TMA producer
-            // one request per kCPS chunks ([kCPS][NT cells][64 ordinates]); evict-last because the
-            // epilogue re-reads these lines (own values and y-neighbours) shortly
+            // evict-last: the epilogue re-reads these lines (own values and y-neighbours) shortly
             const uint64_t pol = policy_evict_last();
             Ring rs;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
                 bool ok = true;
-                for (int kc = 0; kc < KC; kc += kCPS) {
+                for (int kc = 0; kc < KC; ++kc) {
                     if (!WAITB(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
                     mbar_expect_tx(&stg_full[rs.s], LT::kStg);
-                    tma_load_3d_hint(stg + (size_t)rs.s * kCPS * NT * 64, &tm_psi, &stg_full[rs.s], 0, tile * NT,
-                                     kc, pol);
+                    tma_load_2d_hint(stg + (size_t)rs.s * NT * 64, &tm_psi, &stg_full[rs.s], kc * 64, tile * NT, pol);
                     rs.next(a.SS);
                 }
                 if (!ok) break;
             }
         }
     } else if (warp == 2) {
-        // -------------------------------------------------------------------- kernel-matrix producer
-        // The whole warp copies each [128 x 64] BF16 chunk of G with 16-byte cp.async straight into
-        // the 128-byte-swizzled K-major layout (row r at r * 128, 16-byte piece c at (c ^ (r & 7)));
-        // each lane's copies arrive on the stage's barrier when they land (32 arrivals per phase).
-        Ring ra;
-        const int c = lane & 7, r0 = lane >> 3;
-        for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-            bool ok = true;
-            for (int kc = 0; kc < KC && ok; ++kc) {
-                for (int m = 0; m < MB; ++m) {
-                    int go = 1;
-                    if (lane == 0) go = WAITB(&a_empty[ra.s], ra.ph ^ 1u, 0x2u);
-                    go = __shfl_sync(0xffffffffu, go, 0);
-                    if (!go) { ok = false; break; }
-                    const uint32_t dst = smem_u32(aring + ra.s * LT::kA);
-                    const size_t gbase = (size_t)(m * 128) * Qp + kc * 64 + c * 8;   // elements
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int r = r0 + 4 * j;
-                        const uint32_t d = dst + r * 128 + ((c ^ (r & 7)) << 4);
-                        cp_async16(d, a.G_hi + gbase + (size_t)r * Qp, 16u);
-                        if (SPLIT) cp_async16(d + kAStage, a.G_lo + gbase + (size_t)r * Qp, 16u);
+        if (lane == 0) {
+            // ---------------------------------------------------------------- kernel-matrix TMA producer
+            const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
+            Ring ra;
+            for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+                bool ok = true;
+                for (int kc = 0; kc < KC && ok; ++kc) {
+                    for (int mg = 0; mg < MB; mg += MPR) {
+                        if (!WAITB(&a_empty[ra.s], ra.ph ^ 1u, 0x2u)) { ok = false; break; }
+                        unsigned char* dst = aring + ra.s * L.kA;
+                        mbar_expect_tx(&a_full[ra.s], L.kA);
+                        tma_load_4d_hint(dst, &tm_hi, &a_full[ra.s], 0, 0, mg, kc, pol);
+                        if (SPLIT) tma_load_4d_hint(dst + MPR * kAStage, &tm_lo, &a_full[ra.s], 0, 0, mg, kc, pol);
+                        ra.next(a.SA);
                     }
-                    cp_async_mbar_arrive(&a_full[ra.s]);
-                    ra.next(a.SA);
                 }
+                if (!ok) break;
             }
-            if (!ok) break;
         }
-        cp_async_wait<0>();
-    } else if (warp < 7) {
+        } else if (warp < 7) {
         // -------------------------------------------------------------------- converters
         constexpr int NR = NT / 8;             // rows (cells) per thread
         const int ct = tid - 96;               // 0..127
@@ -263,13 +245,11 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             for (int i = 0; i < NR; ++i) part[i] = 0.0f;
             bool ok = true;
             for (int kc = 0; kc < KC; ++kc) {
-                const int sub = kc % kCPS;           // chunk within the staging stage
-                if ((sub == 0 && !WAITB(&stg_full[rs.s], rs.ph, 0x100u)) ||
-                    !WAITB(&bf_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
+                if (!WAITB(&stg_full[rs.s], rs.ph, 0x100u) || !WAITB(&bf_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
                     ok = false;
                     break;
                 }
-                const float4* src = reinterpret_cast<const float4*>(stg + ((size_t)rs.s * kCPS + sub) * NT * 64);
+                const float4* src = reinterpret_cast<const float4*>(stg + (size_t)rs.s * NT * 64);
                 const float4 w4 = reinterpret_cast<const float4*>(wsm + kc * 64)[col4];
                 unsigned char* dhi = bhi + rb.s * LT::kB;
                 unsigned char* dlo = blo + rb.s * LT::kB;
@@ -294,12 +274,11 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                 }
                 fence_proxy_async();
                 __syncwarp();
-                const bool last_of_stage = sub == kCPS - 1 || kc == KC - 1;
                 if (lane == 0) {
                     mbar_arrive(&bf_full[rb.s]);
-                    if (last_of_stage) mbar_arrive(&stg_empty[rs.s]);
+                    mbar_arrive(&stg_empty[rs.s]);
                 }
-                if (last_of_stage) rs.next(a.SS);
+                rs.next(a.SS);
                 rb.next(a.SB);
             }
             if (!ok) break;
@@ -340,10 +319,10 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         }
     } else {
         // -------------------------------------------------------------------- epilogue
-        // Chunks of 16 cells x 32 ordinates.  While chunk k is computed, the warp copies the flux
-        // values chunk k+1 needs (own cells with both x-edge cells, and the upwind y-neighbour of
-        // each group of 4 ordinates) with 16-byte cp.async into its ring in shared memory.  The flux
-        // input is read-only during the launch, so these copies may run ahead of the MMA.
+        // Chunks of 16 cells x 32 ordinates.  The flux values of chunk k+1 (own cells, the two
+        // x-edge cells, the upwind y-neighbours) are loaded into registers while chunk k is
+        // computed.  The flux input is read-only during the launch, so these loads may run ahead
+        // of the MMA (and into the next tile).
         const float* __restrict__ psi = a.psi;
         float* __restrict__ psi_out = a.psi_out;
         const int e = warp - 7;
@@ -354,48 +333,39 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         const int cpt = MB * CPH;              // chunks per tile for this warp
         const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
         const int total = my_tiles * cpt;
-        unsigned char* ring = epi + e * kEpiRing * kEpiChunk;
-        const int pc = lane & 7;               // 16-byte piece (4 ordinates) this lane copies
-        const int prow = lane >> 3;            // row offset of this lane's copies (4 rows per instruction)
 
+        // chunk k of this warp: tile index t (within this CTA), ordinate block m, first cell c0
         auto decode = [&](int k, int& t, int& m, int& c0) {
             t = k / cpt;
             const int r = k - t * cpt;
             m = r / CPH;
             c0 = half * (NT / 2) + (r - m * CPH) * 16;
         };
-        auto issue = [&](int k) {
+        auto load = [&](int k, float (&s)[16], float (&u)[16], float& lft, float& rgt) {
             int t, m, c0;
             decode(k, t, m, c0);
             const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
-            const int q0 = m * 128 + lq * 32;  // first ordinate of this warp
-            const uint32_t sb = smem_u32(ring + (k % kEpiRing) * kEpiChunk);
-            const bool qok = q0 < Qp;
-            const float* col = psi + (qok ? q0 + pc * 4 : 0);
-            // own cells fb-1 .. fb+16 (rows 0..17)
+            const int q = m * 128 + lq * 32 + lane;
+            const bool live = q < a.Q && fb < ncell;
+            const float nuy = live ? a.ord[q].nuy : 0.0f;
+            const float* b = psi + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
+            const bool full = fb + 16 <= ncell;
 #pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                const int row = prow + 4 * j;
-                if (row < 18) {
-                    const int f = fb - 1 + row;
-                    const bool ok = qok && f >= 0 && f < ncell;
-                    cp_async16(sb + row * 128 + pc * 16, ok ? col + (size_t)f * Qp : psi, ok ? 16u : 0u);
-                }
-            }
-            // upwind y-neighbours of cells fb .. fb+15 (rows 18..33), per group of 4 ordinates
-            const int dir = qok ? a.ydir[(q0 >> 2) + pc] : 0;
-            const int dn = dir == 1 ? -nx : nx;
+            for (int i = 0; i < 16; ++i) s[i] = (live && (full || fb + i < ncell)) ? b[i * Qp] : 0.0f;
+            // y-neighbour of cell f: below (f - nx) for nuy > 0, above (f + nx) for nuy < 0
+            const long dyo = nuy > 0.f ? -(long)nx * Qp : (long)nx * Qp;
+            const float* by = b + dyo;
+            const bool yall = nuy > 0.f ? fb >= nx : fb + 16 + nx <= ncell;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = prow + 4 * j;
+            for (int i = 0; i < 16; ++i) {
                 const int f = fb + i;
-                const int g = f + dn;
-                const bool ok = dir != 0 && f < ncell && g >= 0 && g < ncell;
-                cp_async16(sb + (18 + i) * 128 + pc * 16, ok ? col + (size_t)g * Qp : psi, ok ? 16u : 0u);
+                const bool ok = live && nuy != 0.f && (yall || (nuy > 0.f ? f >= nx : f + nx < ncell));
+                u[i] = ok ? by[i * Qp] : 0.0f;
             }
-            cp_async_commit();
+            lft = (live && fb >= 1) ? b[-Qp] : 0.0f;
+            rgt = (live && fb + 16 < ncell) ? b[16 * Qp] : 0.0f;
         };
-        auto compute = [&](int k) -> bool {
+        auto compute = [&](int k, const float (&s)[16], const float (&u)[16], float lft, float rgt) -> bool {
             int t, m, c0;
             decode(k, t, m, c0);
             const int r = k - t * cpt;
@@ -422,32 +392,22 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                     for (int i = 0; i < 16; ++i)
                         if (fb + i < ncell) __stcs(po + i * Qp, 0.0f);
                 } else {
-                    const float* sl = reinterpret_cast<const float*>(ring + (k % kEpiRing) * kEpiChunk) + lane;
                     const OrdF o = a.ord[q];
                     const float ax = fabsf(o.nux), ay = fabsf(o.nuy), axy = ax + ay;
                     const float ge = a.dt_sigma_as * o.e;
                     const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
-                    // the group's copied y-neighbour is this lane's upwind one unless the group mixes signs
-                    const int mydir = o.nuy > 0.f ? 1 : (o.nuy < 0.f ? 2 : 0);
-                    const bool yslot = mydir == 0 || a.ydir[q >> 2] == mydir;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const float4 cf = cb[i];
                         const int bits = __float_as_int(cf.z);
                         if (!(bits & 16)) continue;
-                        const float sf = sl[(1 + i) * 32];
-                        float upx = xbit == 1 ? sl[i * 32] : sl[(i + 2) * 32];
+                        const float sf = s[i];
+                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < 15 ? s[i + 1] : rgt);
                         upx = (bits & xbit) ? upx : 0.0f;
-                        float upy = sl[(18 + i) * 32];
-                        if (!yslot) {
-                            const int f = fb + i;
-                            const int g = mydir == 1 ? f - nx : f + nx;
-                            upy = (g >= 0 && g < ncell) ? psi[(size_t)g * Qp + q] : 0.0f;
-                        }
                         const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
                         float out = fmaf(sf, cf.x - axy, cf.y);
                         out = fmaf(ax, upx, out);
-                        out = fmaf(ay, upy, out);
+                        out = fmaf(ay, u[i], out);
                         out = fmaf(a.dt_sigma_as, y[i], out);
                         out = fmaf(-ge, st, out);
                         __stcs(po + i * Qp, out);
@@ -465,14 +425,15 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             return true;
         };
 
-        if (total > 0) issue(0);
-        for (int k = 0; k < total; ++k) {
-            if (k + 1 < total) issue(k + 1);
-            else cp_async_commit();
-            cp_async_wait<1>();
-            if (!compute(k)) break;
+        float s0[16], u0[16], l0 = 0.f, r0 = 0.f, s1[16], u1[16], l1 = 0.f, r1 = 0.f;
+        if (total > 0) load(0, s0, u0, l0, r0);
+        for (int k = 0; k < total; k += 2) {
+            if (k + 1 < total) load(k + 1, s1, u1, l1, r1);
+            if (!compute(k, s0, u0, l0, r0)) break;
+            if (k + 1 >= total) break;
+            if (k + 2 < total) load(k + 2, s0, u0, l0, r0);
+            if (!compute(k + 1, s1, u1, l1, r1)) break;
         }
-        cp_async_wait<0>();
     }
 
     __syncthreads();
@@ -519,17 +480,32 @@ bool encode_2d(CUtensorMap* map, CUtensorMapDataType type, const void* ptr, uint
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t smem_for(int NT, bool split, int SS, int SB, int SA, int Qp) {
+// 4D view of G [Mp][Qp] BF16: x = column within a 64-column chunk, y = row within a 128-row
+// ordinate block, z = ordinate block, w = chunk; box {64, 128, MPR, 1} with 128-byte swizzle lands
+// as MPR consecutive canonical [128 x 64] K-major tiles.
+bool encode_G4(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MB, int MPR) {
+    EncodeFn enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {64, 128, (cuuint64_t)MB, (cuuint64_t)(Qp / 64)};
+    const cuuint64_t strides[3] = {(cuuint64_t)Qp * 2, (cuuint64_t)Qp * 2 * 128, 128};
+    const cuuint32_t box[4] = {64, 128, (cuuint32_t)MPR, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(G), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t smem_for(int NT, bool split, int SS, int SB, int SA, int Qp, int MPR) {
     auto need = [&](auto L) { return (size_t)1024 + (size_t)L.end; };
     switch (NT * 2 + (split ? 1 : 0)) {
-        case 64: return need(Layout<32, false>(SS, SB, SA, Qp));
-        case 65: return need(Layout<32, true>(SS, SB, SA, Qp));
-        case 128: return need(Layout<64, false>(SS, SB, SA, Qp));
-        case 129: return need(Layout<64, true>(SS, SB, SA, Qp));
-        case 256: return need(Layout<128, false>(SS, SB, SA, Qp));
-        case 257: return need(Layout<128, true>(SS, SB, SA, Qp));
-        case 512: return need(Layout<256, false>(SS, SB, SA, Qp));
-        default: return need(Layout<256, true>(SS, SB, SA, Qp));
+        case 64: return need(Layout<32, false>(SS, SB, SA, Qp, MPR));
+        case 65: return need(Layout<32, true>(SS, SB, SA, Qp, MPR));
+        case 128: return need(Layout<64, false>(SS, SB, SA, Qp, MPR));
+        case 129: return need(Layout<64, true>(SS, SB, SA, Qp, MPR));
+        case 256: return need(Layout<128, false>(SS, SB, SA, Qp, MPR));
+        case 257: return need(Layout<128, true>(SS, SB, SA, Qp, MPR));
+        case 512: return need(Layout<256, false>(SS, SB, SA, Qp, MPR));
+        default: return need(Layout<256, true>(SS, SB, SA, Qp, MPR));
     }
 }
 
@@ -537,12 +513,10 @@ size_t smem_for(int NT, bool split, int SS, int SB, int SA, int Qp) {
 
 struct Tc2Plan {
     CUtensorMap tm_hi, tm_lo;
-    const __nv_bfloat16* G_hi;
-    const __nv_bfloat16* G_lo;
     CUtensorMap tm_psi[4];
     const void* psi_key[4];
     int nkeys;
-    int Q, Qp, Mp, MB, KC, NT, SS, SB, SA, nx, ny, ncell, ntiles, grid;
+    int Q, Qp, Mp, MB, KC, NT, SS, SB, SA, MPR, nx, ny, ncell, ntiles, grid;
     bool split;
     size_t smem;
 };
@@ -554,48 +528,47 @@ cudaError_t tc2_plan_create(Tc2Plan** out, const __nv_bfloat16* G_hi, const __nv
     p->Q = Q; p->Qp = Qp; p->Mp = Mp; p->MB = Mp / 128; p->KC = Qp / 64; p->nx = nx; p->ny = ny;
     p->split = split; p->nkeys = 0;
     p->ncell = nx * ny;
-    p->G_hi = G_hi;
-    p->G_lo = G_lo;
     // Tile width: two accumulator buffers of MB x NT columns fill the 512 TMEM columns; narrower
-    // when the rings do not fit shared memory.  Ring depths: the deepest balanced rings that
-    // fit (up to 4), then deeper kernel-matrix, staging and B rings (up to 8 / 6 / 4).
+    // when the rings do not fit shared memory.  Kernel-matrix requests: as many ordinate blocks per
+    // request (MPR) as two stages allow.  Then the deepest balanced staging / B rings that fit (up
+    // to 4), then a deeper kernel-matrix ring (up to 4).
     int nt = 512 / (2 * p->MB);
     if (nt > 256) nt = 256;
     if (want_nt) nt = want_nt;
     const size_t limit = 227 * 1024;
-    int SS = 2, SB = 2, SA = 2;
+    int SS = 2, SB = 2, SA = 2, MPR = 1;
     bool fits = false;
     while (!fits) {
         if (nt < 32 || (nt & (nt - 1)) || 2 * p->MB * nt > 512) { delete p; return cudaErrorNotSupported; }
-        if (want_stages >= 2) {
-            SS = SB = SA = want_stages;
-            fits = smem_for(nt, split, SS, SB, SA, Qp) <= limit;
-        } else if (smem_for(nt, split, 2, 2, 2, Qp) <= limit) {
-            fits = true;
-            SS = SB = SA = 2;
-            for (int k = 4; k >= 3; --k)
-                if (smem_for(nt, split, k, k, k, Qp) <= limit) { SS = SB = SA = k; break; }
-            while (SA < 8 && smem_for(nt, split, SS, SB, SA + 1, Qp) <= limit) ++SA;
-            while (SS < 6 && smem_for(nt, split, SS + 1, SB, SA, Qp) <= limit) ++SS;
-            while (SB < 4 && smem_for(nt, split, SS, SB + 1, SA, Qp) <= limit) ++SB;
+        for (MPR = p->MB; MPR >= 1 && !fits; MPR /= 2) {
+            if (p->MB % MPR) continue;
+            if (want_stages >= 2) {
+                SS = SB = SA = want_stages;
+                fits = smem_for(nt, split, SS, SB, SA, Qp, MPR) <= limit;
+            } else if (smem_for(nt, split, 2, 2, 2, Qp, MPR) <= limit) {
+                fits = true;
+                SS = SB = SA = 2;
+                for (int k = 4; k >= 3; --k)
+                    if (smem_for(nt, split, k, k, 2, Qp, MPR) <= limit) { SS = SB = k; break; }
+                while (SA < 4 && smem_for(nt, split, SS, SB, SA + 1, Qp, MPR) <= limit) ++SA;
+            }
+            if (fits) break;
         }
         if (!fits) {
             if (want_nt) { delete p; return cudaErrorNotSupported; }
             nt /= 2;
         }
     }
+    p->MPR = MPR;
     p->NT = nt;
     p->SS = SS; p->SB = SB; p->SA = SA;
-    p->smem = smem_for(nt, split, SS, SB, SA, Qp);
+    p->smem = smem_for(nt, split, SS, SB, SA, Qp, MPR);
     p->ntiles = (p->ncell + nt - 1) / nt;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     p->grid = p->ntiles < sms ? p->ntiles : sms;
-    if (!encode_2d(&p->tm_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, G_hi, Qp, Mp, (uint64_t)Qp * 2, 64, 128,
-                   CU_TENSOR_MAP_SWIZZLE_128B) ||
-        (split && !encode_2d(&p->tm_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, G_lo, Qp, Mp, (uint64_t)Qp * 2, 64, 128,
-                             CU_TENSOR_MAP_SWIZZLE_128B))) {
+    if (!encode_G4(&p->tm_hi, G_hi, Qp, p->MB, MPR) || (split && !encode_G4(&p->tm_lo, G_lo, Qp, p->MB, MPR))) {
         delete p;
         return cudaErrorInvalidValue;
     }
@@ -617,16 +590,8 @@ static const CUtensorMap* psi_map(Tc2Plan* p, const float* psi) {
     for (int i = 0; i < p->nkeys; ++i)
         if (p->psi_key[i] == psi) return &p->tm_psi[i];
     const int slot = p->nkeys < 4 ? p->nkeys++ : 3;
-    // 3D view of the flux: x = ordinate within a 64-chunk, y = cell, z = chunk; box {64, NT, kCPS}
-    EncodeFn enc = get_encode();
-    if (!enc) return nullptr;
-    const cuuint64_t dims[3] = {64, (cuuint64_t)p->ncell, (cuuint64_t)p->KC};
-    const cuuint64_t strides[2] = {(cuuint64_t)p->Qp * 4, 256};
-    const cuuint32_t box[3] = {64, (cuuint32_t)p->NT, (cuuint32_t)kCPS};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&p->tm_psi[slot], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(psi), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    if (!encode_2d(&p->tm_psi[slot], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, psi, p->Qp, p->ncell, (uint64_t)p->Qp * 4, 64,
+                   p->NT, CU_TENSOR_MAP_SWIZZLE_NONE))
         return nullptr;
     p->psi_key[slot] = psi;
     return &p->tm_psi[slot];
@@ -665,13 +630,13 @@ static cudaError_t dispatch(const Tc2Plan* p, const CUtensorMap* m, const Tc2Arg
     }
 }
 
-cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, const float* w,
-                            const unsigned char* ydir, unsigned int* err_flag, cudaStream_t stream) {
+cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, const float* w, unsigned int* err_flag,
+                            cudaStream_t stream) {
     if (!p) return cudaErrorInvalidValue;
     const CUtensorMap* mpsi = psi_map(p, s.psi);
     if (!mpsi) return cudaErrorInvalidValue;
-    Tc2Args a{s.psi, s.psi_out, s.ord, s.cell, w, p->G_hi, p->split ? p->G_lo : p->G_hi, ydir, err_flag, s.nx, s.ny, s.Q, s.Qp, p->MB, p->KC, p->ntiles,
-              p->ncell, p->SS, p->SB, p->SA, s.dt, s.dt_sigma_as};
+    Tc2Args a{s.psi, s.psi_out, s.ord, s.cell, w, err_flag, s.nx, s.ny, s.Q, s.Qp, p->MB, p->KC, p->ntiles,
+              p->ncell, p->SS, p->SB, p->SA, p->MPR, s.dt, s.dt_sigma_as};
     return p->split ? dispatch<true>(p, mpsi, a, stream) : dispatch<false>(p, mpsi, a, stream);
 }
 
