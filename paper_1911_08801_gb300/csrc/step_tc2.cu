@@ -18,13 +18,14 @@
 //               directly in the canonical layout) in an SB-stage ring; the scalar flux
 //               Phi_c = sum_p w_p psi_p(c) accumulated in FP32 over the tile's chunks, and from it
 //               the per-cell coefficients of the update.
-//   warps 7-14  epilogue: drain a TMEM buffer (lane = ordinate, column = cell) and apply upwind
+//   warps 7-22  epilogue: drain a TMEM buffer (lane = ordinate, column = cell) and apply upwind
 //               transport (Sec. 3.1), collision, isotropic scattering, the source and the
 //               generator diagonal:
 //                 psi' = psi (1 - dt sigma_t - a_x - a_y) + a_x psi_upx + a_y psi_upy
 //                        + dt (sigma_s Phi / sum w + q) + dt sigma_as (D - e psi~)
-//               while the MMA of the next tile fills the other buffer.  Each epilogue warp keeps
-//               the flux values of its next 16-cell chunk in flight (register double buffer).
+//               while the MMA of the next tile fills the other buffer.  Four warps share each
+//               TMEM lane quarter; each keeps the flux values of its next 8-cell chunk in flight
+//               (register double buffer).
 // SPLIT (BF16X3) keeps BF16 residuals of both operands and issues hi*hi + hi*lo + lo*hi.
 // QP > 0 fixes the ordinate stride at compile time (immediate address offsets); QP = 0 reads it
 // from the arguments.
@@ -41,7 +42,10 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kWarps = 15;
+constexpr int kEW = 4;                  // epilogue warps per TMEM lane quarter
+constexpr int kCH = 8;                  // cells per epilogue chunk
+constexpr int kEpiWarps = 4 * kEW;
+constexpr int kWarps = 7 + kEpiWarps;
 constexpr int kThreads2 = kWarps * 32;
 constexpr int kAStage = 128 * 64 * 2;   // one [128 x 64] BF16 chunk of G
 
@@ -130,9 +134,9 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         for (int s = 0; s < a.SA; ++s) { mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tm_full[b], 1);
-            mbar_init(&tm_empty[b], 8);
+            mbar_init(&tm_empty[b], kEpiWarps);
             mbar_init(&phi_full[b], 4);
-            mbar_init(&phi_empty[b], 8);
+            mbar_init(&phi_empty[b], kEpiWarps);
         }
         *abort_flag = 0;
         fence_barrier_init();
@@ -319,7 +323,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         }
     } else {
         // -------------------------------------------------------------------- epilogue
-        // Chunks of 16 cells x 32 ordinates.  The flux values of chunk k+1 (own cells, the two
+        // Chunks of kCH cells x 32 ordinates.  The flux values of chunk k+1 (own cells, the two
         // x-edge cells, the upwind y-neighbours) are loaded into registers while chunk k is
         // computed.  The flux input is read-only during the launch, so these loads may run ahead
         // of the MMA (and into the next tile).
@@ -327,9 +331,9 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         float* __restrict__ psi_out = a.psi_out;
         const int e = warp - 7;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
-        const int half = e >> 2;               // which half of the tile's cells
+        const int grp = e >> 2;                // which part (of kEW) of the tile's cells
         const int ncell = a.ncell, nx = a.nx;
-        constexpr int CPH = NT / 32;           // chunks of 16 cells per half tile
+        constexpr int CPH = NT / (kEW * kCH);  // chunks per part of the tile and ordinate block
         const int cpt = MB * CPH;              // chunks per tile for this warp
         const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
         const int total = my_tiles * cpt;
@@ -339,9 +343,9 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             t = k / cpt;
             const int r = k - t * cpt;
             m = r / CPH;
-            c0 = half * (NT / 2) + (r - m * CPH) * 16;
+            c0 = grp * (NT / kEW) + (r - m * CPH) * kCH;
         };
-        auto load = [&](int k, float (&s)[16], float (&u)[16], float& lft, float& rgt) {
+        auto load = [&](int k, float (&s)[kCH], float (&u)[kCH], float& lft, float& rgt) {
             int t, m, c0;
             decode(k, t, m, c0);
             const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
@@ -349,23 +353,23 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             const bool live = q < a.Q && fb < ncell;
             const float nuy = live ? a.ord[q].nuy : 0.0f;
             const float* b = psi + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
-            const bool full = fb + 16 <= ncell;
+            const bool full = fb + kCH <= ncell;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) s[i] = (live && (full || fb + i < ncell)) ? b[i * Qp] : 0.0f;
+            for (int i = 0; i < kCH; ++i) s[i] = (live && (full || fb + i < ncell)) ? b[i * Qp] : 0.0f;
             // y-neighbour of cell f: below (f - nx) for nuy > 0, above (f + nx) for nuy < 0
             const long dyo = nuy > 0.f ? -(long)nx * Qp : (long)nx * Qp;
             const float* by = b + dyo;
-            const bool yall = nuy > 0.f ? fb >= nx : fb + 16 + nx <= ncell;
+            const bool yall = nuy > 0.f ? fb >= nx : fb + kCH + nx <= ncell;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < kCH; ++i) {
                 const int f = fb + i;
                 const bool ok = live && nuy != 0.f && (yall || (nuy > 0.f ? f >= nx : f + nx < ncell));
                 u[i] = ok ? by[i * Qp] : 0.0f;
             }
             lft = (live && fb >= 1) ? b[-Qp] : 0.0f;
-            rgt = (live && fb + 16 < ncell) ? b[16 * Qp] : 0.0f;
+            rgt = (live && fb + kCH < ncell) ? b[kCH * Qp] : 0.0f;
         };
-        auto compute = [&](int k, const float (&s)[16], const float (&u)[16], float lft, float rgt) -> bool {
+        auto compute = [&](int k, const float (&s)[kCH], const float (&u)[kCH], float lft, float rgt) -> bool {
             int t, m, c0;
             decode(k, t, m, c0);
             const int r = k - t * cpt;
@@ -379,9 +383,9 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                 if (!go) return false;
                 tc_fence_after();
             }
-            float y[16];
+            float y[kCH];
             __syncwarp();
-            tmem_ld16(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * MB * NT + m * NT + c0), y);
+            tmem_ld<kCH>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * MB * NT + m * NT + c0), y);
             const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
             const int q = m * 128 + lq * 32 + lane;
             if (fb < ncell && q < Qp) {
@@ -389,7 +393,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                 const float4* cb = coef + buf * NT + c0;
                 if (q >= a.Q) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
+                    for (int i = 0; i < kCH; ++i)
                         if (fb + i < ncell) __stcs(po + i * Qp, 0.0f);
                 } else {
                     const OrdF o = a.ord[q];
@@ -397,12 +401,12 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                     const float ge = a.dt_sigma_as * o.e;
                     const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
+                    for (int i = 0; i < kCH; ++i) {
                         const float4 cf = cb[i];
                         const int bits = __float_as_int(cf.z);
                         if (!(bits & 16)) continue;
                         const float sf = s[i];
-                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < 15 ? s[i + 1] : rgt);
+                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < kCH - 1 ? s[i + 1] : rgt);
                         upx = (bits & xbit) ? upx : 0.0f;
                         const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
                         float out = fmaf(sf, cf.x - axy, cf.y);
@@ -425,7 +429,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             return true;
         };
 
-        float s0[16], u0[16], l0 = 0.f, r0 = 0.f, s1[16], u1[16], l1 = 0.f, r1 = 0.f;
+        float s0[kCH], u0[kCH], l0 = 0.f, r0 = 0.f, s1[kCH], u1[kCH], l1 = 0.f, r1 = 0.f;
         if (total > 0) load(0, s0, u0, l0, r0);
         for (int k = 0; k < total; k += 2) {
             if (k + 1 < total) load(k + 1, s1, u1, l1, r1);
