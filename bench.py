@@ -52,6 +52,20 @@ def parse():
     return ap.parse_args()
 
 
+def kernel_traffic(precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source still matches."""
+    import hashlib
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["step_tc2_kernel"]
+        src = b"".join(open(os.path.join(ROOT, "paper_1911_08801_gb300", "csrc", f), "rb").read()
+                       for f in ("step_tc2.cu", "tc_ptx.h"))
+        if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"] or precision != d["precision"]:
+            return None
+        return d["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -206,7 +220,8 @@ def run_ours(args, rank, world, dist):
                    "l2": "state larger than L2 (%.0f MB per buffer)" % (units * 4 / 1e6),
                    "parallelism": f"replicas x{world}", "tiling": tiling},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": kernel_traffic(args.precision) if args.variant == 0 and args.workload == synth.LATTICE_448.name else None,
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
                      "kernel": ("step_tc2_kernel" if args.variant == 0 else "step_tc_kernel") if args.precision.startswith("bf16")
                      else "step_simt_kernel"},
