@@ -201,6 +201,29 @@ int assn_mass(assn_problem* p, double* mass_out);
 /* Check the state for NaN/Inf: ASSN_OK or ASSN_ERR_NONFINITE.  Syncs. */
 int assn_check_finite(assn_problem* p);
 
+/* ---- Allocation-free total mass (the paper has no counterpart; this serves library users).
+ * Some callers cannot allocate device memory during a call: code between the begin and end of a
+ * CUDA stream capture, real-time loops that forbid allocator calls, or hosts that run the library
+ * under a foreign memory pool.  assn_mass_noalloc computes h^2 sum_cells sum_q w_q psi_q of a
+ * caller-owned device state without allocating anything: its partial sums go to a fixed
+ * file-scope device array of ASSN_NOALLOC_MASS_MAX_BLOCKS doubles (128 KB), one per 256 cells,
+ * which every device that loads the library holds until process exit.
+ *   psi_dev    [ncell][Qp] state on the current device, FP32 (elem_bytes 4) or FP64 (8)
+ *   w_dev      [Qp] FP64 quadrature weights on the device (0 on padded ordinates)
+ *   mass_dev   one FP64 result on the device, written asynchronously on `stream`
+ * Errors: ASSN_ERR_ARG for NULL pointers, elem_bytes not 4 or 8, ncell > ASSN_NOALLOC_MASS_MAX_CELLS
+ * or Qp > ASSN_MAX_Q; ASSN_ERR_CUDA if the launch fails (message in assn_noalloc_last_error()).
+ * The first call on a device looks up the scratch array's device address (with that device
+ * current), so make it before any stream capture.  Every call shares the scratch array and
+ * overwrites it completely before reading it; calls whose work overlaps on one device race, so
+ * serialise them (same stream, or events). */
+#define ASSN_NOALLOC_MASS_CELLS_PER_BLOCK 256
+#define ASSN_NOALLOC_MASS_MAX_BLOCKS 16384
+#define ASSN_NOALLOC_MASS_MAX_CELLS (ASSN_NOALLOC_MASS_CELLS_PER_BLOCK * ASSN_NOALLOC_MASS_MAX_BLOCKS)
+int assn_mass_noalloc(const void* psi_dev, int elem_bytes, const double* w_dev, int ncell, int Qp,
+                      double h, double* mass_dev, void* stream);
+const char* assn_noalloc_last_error(void);
+
 /* Message of the last failure on p (never NULL; "" when none).  With p == NULL, the last
  * failure of assn_create on this thread. */
 const char* assn_last_error(const assn_problem* p);

@@ -68,6 +68,8 @@ SIGNATURES = {
     "assn_status_string": (C.c_char_p, [C.c_int]),
     "assn_launch_count": (C.c_int64, [_h]),
     "assn_abi_version": (C.c_int, []),
+    "assn_mass_noalloc": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.c_double, _vp, _vp]),
+    "assn_noalloc_last_error": (C.c_char_p, []),
 }
 
 
@@ -263,6 +265,18 @@ def assn_status_string(status: int) -> str:
 
 def assn_launch_count(h: int) -> int:
     return int(lib.assn_launch_count(h))
+
+
+def assn_mass_noalloc(psi_dev: int, elem_bytes: int, w_dev: int, ncell: int, Qp: int, h: float, mass_dev: int,
+                      stream=None) -> None:
+    """Allocation-free total mass of a device state (see include/assn.h); result written to mass_dev."""
+    st = lib.assn_mass_noalloc(psi_dev, elem_bytes, w_dev, ncell, Qp, h, mass_dev, _stream_ptr(stream))
+    if st != ASSN_OK:
+        raise AssnError(st, lib.assn_noalloc_last_error().decode())
+
+
+def assn_noalloc_last_error() -> str:
+    return lib.assn_noalloc_last_error().decode()
 
 
 def assn_abi_version() -> int:
