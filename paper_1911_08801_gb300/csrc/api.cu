@@ -59,6 +59,9 @@ struct assn_problem {
     size_t stage_elems = 0;
 
     int want_nt = 0, want_stages = 0;   // tensor-core tiling request (0 = automatic)
+    int* d_counter = nullptr;           // device step counter of the persistent tensor-core kernel
+    int counter_host = 0;               // last value written to / advanced on d_counter
+    double plan2_dt = -1.0;             // dt the persistent plan was built for
 
     std::string err;
     int64_t launches = 0;
@@ -329,6 +332,8 @@ int assn_create(assn_problem** out, int nx, int ny, double x0, double x1, double
         (ce = cudaMalloc(&p->d_partials, sizeof(double) * kMassBlocks)) != cudaSuccess ||
         (ce = cudaMalloc(&p->d_scalar, sizeof(double))) != cudaSuccess ||
         (ce = cudaMalloc(&p->d_flags, 2 * sizeof(unsigned int))) != cudaSuccess ||
+        (ce = cudaMalloc(&p->d_counter, sizeof(int))) != cudaSuccess ||
+        (ce = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->stream)) != cudaSuccess ||
         (ce = cudaMemsetAsync(p->d_flags, 0, 2 * sizeof(unsigned int), p->stream)) != cudaSuccess) {
         r = fail(nullptr, ce == cudaErrorMemoryAllocation ? ASSN_ERR_OOM : ASSN_ERR_CUDA, "create: %s",
                  cudaGetErrorString(ce));
@@ -346,6 +351,7 @@ int assn_destroy(assn_problem* p) {
     free_operands(p);
     dfree(p->d_omega); dfree(p->d_w64); dfree(p->d_w32); dfree(p->d_ord); dfree(p->d_cell); dfree(p->d_ydir);
     dfree(p->d_psi[0]); dfree(p->d_psi[1]); dfree(p->d_partials); dfree(p->d_scalar); dfree(p->d_flags);
+    dfree(p->d_counter);
     dfree(p->d_stage);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -602,8 +608,20 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
         if (p->precision == ASSN_FP32) {
             CK(p, launch_step_simt_f32(a, p->stream));
         } else {
-            cudaError_t e = p->variant == 1 ? launch_step_tc(p->plan, a, p->d_w32, p->d_flags + 1, p->stream)
-                                            : launch_step_tc2(p->plan2, a, p->d_w32, p->d_flags + 1, p->stream);
+            const bool own = in == p->d_psi[p->cur] && out == p->d_psi[p->cur ^ 1];
+            cudaError_t e;
+            if (p->variant == 0 && own) {
+                // the persistent kernel takes its buffer parity from the device step counter
+                if ((p->counter_host & 1) != p->cur) {
+                    p->counter_host = p->cur;
+                    CK(p, cudaMemcpyAsync(p->d_counter, &p->counter_host, sizeof(int), cudaMemcpyHostToDevice,
+                                          p->stream));
+                }
+                e = launch_step_tc2(p->plan2, p->d_flags + 1, p->cur, p->stream);
+                p->counter_host += 1;
+            } else {
+                e = launch_step_tc(p->plan, a, p->d_w32, p->d_flags + 1, p->stream);
+            }
             if (e == cudaErrorNotSupported) return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: shape not supported");
             CK(p, e);
         }
@@ -612,14 +630,34 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
     return ASSN_OK;
 }
 
-static int ensure_plan(assn_problem* p) {
+static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
     cudaError_t e = cudaSuccess;
-    if (p->variant == 1 && !p->plan)
+    if ((p->variant == 1 || need_v1) && !p->plan)
         e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
                            p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
-    else if (p->variant == 0 && !p->plan2)
-        e = tc2_plan_create(&p->plan2, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
-                            p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
+    if (e == cudaSuccess && p->variant == 0 && (!p->plan2 || p->plan2_dt != dt)) {
+        if (p->plan2) tc2_plan_destroy(p->plan2);
+        p->plan2 = nullptr;
+        Tc2Problem d;
+        d.buf[0] = (const float*)p->d_psi[0];
+        d.buf[1] = (const float*)p->d_psi[1];
+        d.ord = (const OrdF*)p->d_ord;
+        d.cell = (const CellF*)p->d_cell;
+        d.w = p->d_w32;
+        d.G_hi = p->tc.G_hi;
+        d.G_lo = p->tc.G_lo;
+        d.counter = p->d_counter;
+        d.target = 0x7fffffff;
+        d.nx = p->nx;
+        d.ny = p->ny;
+        d.Q = p->Q;
+        d.Qp = p->Qp;
+        d.Mp = p->tc.Mp;
+        d.dt = (float)dt;
+        d.dt_sigma_as = (float)(dt * p->sigma_as);
+        e = tc2_plan_create(&p->plan2, &d, 1, p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
+        if (e == cudaSuccess) p->plan2_dt = dt;
+    }
     if (e == cudaErrorNotSupported)
         return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: Q = %d with tile %d / stages %d not supported", p->Q,
                     p->want_nt, p->want_stages);
@@ -639,7 +677,7 @@ static int prepare_step(assn_problem* p, double dt) {
     r = upload_ord(p, dt);
     if (r) return r;
     if (p->tensor()) {
-        r = ensure_plan(p);
+        r = ensure_plan(p, dt, false);
         if (r) return r;
     }
     return ASSN_OK;
@@ -663,6 +701,10 @@ int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev,
     if (psi_in_dev == psi_out_dev) return fail(p, ASSN_ERR_ARG, "input and output buffers must differ");
     int r = prepare_step(p, dt);
     if (r) return r;
+    if (p->tensor()) {   // caller-owned buffers run on the one-tile-per-CTA kernel
+        r = ensure_plan(p, dt, true);
+        if (r) return r;
+    }
     return step_once(p, psi_in_dev, psi_out_dev, dt);
 }
 
@@ -689,7 +731,7 @@ int assn_get_tiling(assn_problem* p, int* tile_cells, int* stages, int* tmem_col
     if (r) return r;
     r = set_device(p);
     if (r) return r;
-    r = ensure_plan(p);
+    r = ensure_plan(p, p->plan2_dt > 0 ? p->plan2_dt : 1.0, false);
     if (r) return r;
     size_t sm = 0;
     if (p->variant == 1) tc_plan_describe(p->plan, tile_cells, stages, tmem_cols, &sm);

@@ -67,14 +67,30 @@ void tc_plan_destroy(TcPlan* plan);
 cudaError_t launch_step_tc(TcPlan* plan, const StepArgs<float, OrdF, CellF>& a, const float* w,
                            unsigned int* err_flag, cudaStream_t s);
 
-// Persistent warp-specialised tensor-core step (the default tensor-core kernel).
+// Persistent warp-specialised tensor-core step (the default tensor-core kernel), for one problem
+// or a batch.  Each problem's flux buffer parity and activity come from a device step counter that
+// the launch advances for the problems it stepped.
+struct Tc2Problem {
+    const float* buf[2];            // the problem's two FP32 flux buffers [ncell][Qp]
+    const OrdF* ord;                // [Qp] per-ordinate constants for dt
+    const CellF* cell;              // [ncell]
+    const float* w;                 // [Qp]
+    const __nv_bfloat16* G_hi;      // [Mp][Qp]
+    const __nv_bfloat16* G_lo;      // [Mp][Qp] (BF16X3) or null
+    int* counter;                   // device step counter
+    int target;                     // stepped while counter < target
+    int nx, ny, Q, Qp, Mp;
+    float dt, dt_sigma_as;
+};
 struct Tc2Plan;
-cudaError_t tc2_plan_create(Tc2Plan** plan, const __nv_bfloat16* G_hi, const __nv_bfloat16* G_lo,
-                            int Q, int Qp, int Mp, int nx, int ny, bool split, int want_nt, int want_stages);
+cudaError_t tc2_plan_create(Tc2Plan** plan, const Tc2Problem* probs, int nprob, bool split, int want_nt,
+                            int want_stages);
 void tc2_plan_destroy(Tc2Plan* plan);
 void tc2_plan_describe(const Tc2Plan* plan, int* tile_cells, int* stages, int* tmem_cols, size_t* smem);
-cudaError_t launch_step_tc2(Tc2Plan* plan, const StepArgs<float, OrdF, CellF>& a, const float* w,
-                            unsigned int* err_flag, cudaStream_t s);
+int tc2_plan_total_tiles(const Tc2Plan* plan);
+// parity0: parity of problem 0's step counter at launch (one-problem plans read the flux from
+// buffer parity0 and write buffer parity0 ^ 1; batch plans take every parity from the device).
+cudaError_t launch_step_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_scalar_flux(const T* psi, const T* w, int ncell, int Qp, float* out_f,

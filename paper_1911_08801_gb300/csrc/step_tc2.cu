@@ -1,11 +1,20 @@
-// Persistent, warp-specialised tensor-core as-S_N step (sm_103a).
+// Persistent, warp-specialised tensor-core as-S_N step (sm_103a), for one problem or a batch of
+// problems of different grid size, ordinate count and kernel width in the same launch.
 //
-// Work unit: a tile of NT consecutive cells in row-major cell order (tiles may span grid rows),
-// all Qp ordinates.  One CTA per SM walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// The artificial in-scattering gain without its diagonal (Sec. 3.2, Eq. (as-S_N equations))
+// Work unit: a tile of NT consecutive cells (row-major cell order; tiles may span grid rows) of
+// one problem, all its Qp ordinates.  The tiles of all problems form one list; one CTA per SM walks
+// it (tile blockIdx.x, blockIdx.x + gridDim.x, ...).  Each problem is described by a ProbDesc in
+// device memory (tensor maps, pointers, sizes) and a device step counter: the launch reads the
+// flux from buffer (counter & 1), writes buffer (counter & 1) ^ 1, skips problems whose counter
+// has reached their target, and the last CTA to finish advances the counters of the problems it
+// stepped.  A CUDA graph of such launches therefore steps every solve of an ensemble to its own
+// step count.
+//
+// Per tile, the artificial in-scattering gain without its diagonal (Sec. 3.2, Eq. (as-S_N
+// equations))
 //   D[q][c] = sum_{p != q} K_qp psi~_p(c)
-// is one [Mp x Qp] x [Qp x NT] product per tile on tcgen05 (kind::f16, M = 128 ordinates,
-// N = NT cells, K = 16, BF16 in, FP32 accumulate in TMEM).  Roles:
+// is one [Mp x Qp] x [Qp x NT] product on tcgen05 (kind::f16, M = 128 ordinates, N = NT cells,
+// K = 16, BF16 in, FP32 accumulate in TMEM).  Roles:
 //   warp 0      TMEM owner; lane 0 issues the MMAs (k-chunk outer, ordinate block inner) into
 //               one of two TMEM accumulator buffers (2 x Mp/128 x NT columns <= 512).
 //   warp 1      lane 0: TMA producer of the FP32 flux: [NT cells x 64 ordinates] chunks into an
@@ -27,16 +36,36 @@
 //               TMEM lane quarter; each keeps the flux values of its next 8-cell chunk in flight
 //               (register double buffer).
 // SPLIT (BF16X3) keeps BF16 residuals of both operands and issues hi*hi + hi*lo + lo*hi.
-// QP > 0 fixes the ordinate stride at compile time (immediate address offsets); QP = 0 reads it
-// from the arguments.
+// QP > 0 fixes the ordinate stride at compile time (launches whose problems share one of the
+// common strides); QP = 0 reads it per problem.
 //
 // Every mbarrier wait is bounded (about 1 s); on expiry the CTA records the event in err_flag,
 // all roles stop issuing, the CTA waits briefly for copies and MMAs in flight, frees its tensor
 // memory and returns.
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
 #include "assn_internal.h"
 #include "tc_ptx.h"
 
 namespace assn {
+
+// Per-problem descriptor (device memory; aligned as its tensor maps require).
+struct ProbDesc {
+    CUtensorMap tm_psi[2];      // flux buffer b as [ncell][Qp] FP32, box {64, NT}
+    CUtensorMap tm_hi, tm_lo;   // kernel-matrix operand, 4D box {64, 128, MPR, 1}
+    const float* buf[2];        // flux buffers
+    const OrdF* ord;            // [Qp]
+    const CellF* cell;          // [ncell]
+    const float* w;             // [Qp]
+    int* counter;               // steps taken; the launch reads buffer (counter & 1)
+    int target;                 // stepped while counter < target
+    int nx, ny, ncell, Q, Qp, MB, KC, MPR, ntiles, tile0;
+    float dt, dt_sigma_as;
+};
 
 namespace {
 
@@ -48,34 +77,53 @@ constexpr int kEpiWarps = 4 * kEW;
 constexpr int kWarps = 7 + kEpiWarps;
 constexpr int kThreads2 = kWarps * 32;
 constexpr int kAStage = 128 * 64 * 2;   // one [128 x 64] BF16 chunk of G
+constexpr int kMaxProbs = 1024;         // problems per launch
+constexpr int kParamProbs = 4;          // problems whose tensor maps also travel as kernel parameters
 
-struct Tc2Args {
-    const float* psi;
-    float* psi_out;
+// Tensor maps of one problem, as kernel parameters (the TMA unit reads parameter-space
+// descriptors through the constant cache; the copies in ProbDesc serve the other problems).
+struct ParamMaps {
+    CUtensorMap psi[2], hi, lo;
+};
+
+// Scalar parameters of problem 0, read by the epilogue of a one-problem launch (flux buffers
+// already resolved by the host from the step parity).
+struct OneProb {
+    const float* in;
+    float* out;
     const OrdF* ord;
-    const CellF* cell;
-    const float* w;
+    int ncell, nx, Q, Qp, MB;
+    float dts;
+};
+
+struct BatchArgs {
+    ParamMaps pm[kParamProbs];
+    OneProb one;
+    const ProbDesc* probs;
+    int nprob, total_tiles;
     unsigned int* err;
-    int nx, ny, Q, Qp, MB, KC, ntiles, ncell;
-    int SS, SB, SA, MPR;
-    float dt, dt_sigma_as;
+    unsigned int* ticket;               // CTAs finished; the last one advances the counters
+    int SS, SB, SA, MPRmax;
 };
 
 template <int NT, bool SPLIT>
 struct Layout {
     static constexpr int kStg = NT * 256;                       // FP32 staging stage
     static constexpr int kB = NT * 128;                         // BF16 B stage (one of hi / lo)
-    int kA;                                                     // A stage: MPR blocks (hi [+ lo])
-    int stg, bhi, blo, a, w, coef, bars, end;
-    __host__ __device__ Layout(int SS, int SB, int SA, int Qp, int MPR) {
-        kA = MPR * kAStage * (SPLIT ? 2 : 1);
+    int kA;                                                     // A stage: MPRmax blocks (hi [+ lo])
+    int stg, bhi, blo, a, coef, cstage, tparm, pinfo, bars, end;
+    __host__ __device__ Layout(int SS, int SB, int SA, int MPRmax) {
+        kA = MPRmax * kAStage * (SPLIT ? 2 : 1);
         stg = 0;
         bhi = stg + SS * kStg;
         blo = bhi + SB * kB;
         a = blo + (SPLIT ? SB * kB : 0);
-        w = a + SA * kA;
-        coef = w + Qp * 4;                                       // [2][NT] float4 cell coefficients
-        bars = coef + 2 * NT * 16;
+        coef = a + SA * kA;                                      // [2][NT] float4 cell coefficients
+        cstage = coef + 2 * NT * 16;                             // [NT] cell constants of the tile
+        tparm = cstage + NT * 16;                                // [epilogue warps][2] tile parameters
+        pinfo = tparm + kEpiWarps * 2 * 64;                      // [kMaxProbs] first tile, [kMaxProbs] info
+        bars = pinfo + kMaxProbs * 8;
+        bars = (bars + 7) & ~7;
         // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2]
         end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 8) + 16;
     }
@@ -94,22 +142,31 @@ struct Ring {
     }
 };
 
+// Problem owning global tile T: the last problem whose first tile is <= T.
+__device__ __forceinline__ int find_prob(const int* tile0, int nprob, int T) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile0[mid] <= T) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <int NT, bool SPLIT, int QP>
 __global__ void __launch_bounds__(kThreads2, 1)
-step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constant__ CUtensorMap tm_hi,
-                const __grid_constant__ CUtensorMap tm_lo, const Tc2Args a) {
+step_tc2_kernel(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int Qp = QP > 0 ? QP : a.Qp;
-    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, Qp, a.MPR);
-    const int MPR = a.MPR;
+    const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, a.MPRmax);
     using LT = Layout<NT, SPLIT>;
     float* stg = reinterpret_cast<float*>(base + L.stg);
     unsigned char* bhi = base + L.bhi;
     unsigned char* blo = base + L.blo;
     unsigned char* aring = base + L.a;
-    float* wsm = reinterpret_cast<float*>(base + L.w);
     float4* coef = reinterpret_cast<float4*>(base + L.coef);
+    int* s_tile0 = reinterpret_cast<int*>(base + L.pinfo);
+    // per problem: bit 0 parity, bit 1 active, bits 8-15 KC, 16-23 MB, 24-31 MPR
+    int* s_info = reinterpret_cast<int*>(base + L.pinfo + kMaxProbs * 4);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* stg_full = bars;
     uint64_t* stg_empty = stg_full + a.SS;
@@ -125,9 +182,14 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int KC = Qp / 64, MB = a.MB;
+    const int nprob = a.nprob, total = a.total_tiles;
 
-    for (int i = tid; i < Qp; i += blockDim.x) wsm[i] = a.w[i];
+    for (int i = tid; i < nprob; i += blockDim.x) {
+        const ProbDesc& d = a.probs[i];
+        const int c = *d.counter;
+        s_tile0[i] = d.tile0;
+        s_info[i] = (c & 1) | (c < d.target ? 2 : 0) | (d.KC << 8) | (d.MB << 16) | (d.MPR << 24);
+    }
     if (tid == 0) {
         for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], 4); }
         for (int s = 0; s < a.SB; ++s) { mbar_init(&bf_full[s], 4); mbar_init(&bf_empty[s], 1); }
@@ -149,6 +211,15 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
 
+    // Next active tile of this CTA at or after T (total when none); its problem id in pid.
+    auto next_tile = [&](int T, int& pid) -> int {
+        for (; T < total; T += gridDim.x) {
+            pid = find_prob(s_tile0, nprob, T);
+            if (s_info[pid] & 2) return T;
+        }
+        return total;
+    };
+
     if (warp == 0) {
         if (lane == 0) {
             // ---------------------------------------------------------------- MMA issuer
@@ -158,8 +229,10 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             const uint64_t b0 = sw128_desc(smem_u32(bhi));
             const uint64_t l0 = sw128_desc(smem_u32(blo));
             Ring rb, ra;
-            int it = 0;
-            for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+            int it = 0, pid = 0;
+            for (int T = next_tile(blockIdx.x, pid); T < total; T = next_tile(T + gridDim.x, pid), ++it) {
+                const int info = s_info[pid];
+                const int KC = QP > 0 ? QP / 64 : (info >> 8) & 255, MB = (info >> 16) & 255, MPR = (info >> 24) & 255;
                 const int buf = it & 1;
                 const uint32_t use = (uint32_t)(it >> 1);
                 if (!WAITB(&tm_empty[buf], (use & 1u) ^ 1u, 0x10u)) break;
@@ -177,14 +250,14 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                         const uint64_t as0 = a0 + (uint64_t)((ra.s * L.kA) >> 4);
                         for (int mm = 0; mm < MPR; ++mm) {
                             const uint64_t ad0 = as0 + (uint64_t)((mm * kAStage) >> 4);
-                            const uint32_t d = dbase + (uint32_t)((mg + mm) * NT);
+                            const uint32_t dd = dbase + (uint32_t)((mg + mm) * NT);
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
                                 const uint64_t ad = ad0 + (uint64_t)(kk * 2), bd = bd0 + (uint64_t)(kk * 2);
-                                mma_bf16(d, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                                mma_bf16(dd, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                                 if (SPLIT) {
-                                    mma_bf16(d, ad, bl0 + (uint64_t)(kk * 2), idesc, 1u);
-                                    mma_bf16(d, ad + (uint64_t)((MPR * kAStage) >> 4), bd, idesc, 1u);
+                                    mma_bf16(dd, ad, bl0 + (uint64_t)(kk * 2), idesc, 1u);
+                                    mma_bf16(dd, ad + (uint64_t)((MPR * kAStage) >> 4), bd, idesc, 1u);
                                 }
                             }
                         }
@@ -204,12 +277,17 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             // evict-last: the epilogue re-reads these lines (own values and y-neighbours) shortly
             const uint64_t pol = policy_evict_last();
             Ring rs;
-            for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+            int pid = 0;
+            for (int T = next_tile(blockIdx.x, pid); T < total; T = next_tile(T + gridDim.x, pid)) {
+                const int info = s_info[pid];
+                const int KC = QP > 0 ? QP / 64 : (info >> 8) & 255;
+                const int tile = T - s_tile0[pid];
+                const CUtensorMap* map = pid < kParamProbs ? &a.pm[pid].psi[info & 1] : &a.probs[pid].tm_psi[info & 1];
                 bool ok = true;
                 for (int kc = 0; kc < KC; ++kc) {
                     if (!WAITB(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
                     mbar_expect_tx(&stg_full[rs.s], LT::kStg);
-                    tma_load_2d_hint(stg + (size_t)rs.s * NT * 64, &tm_psi, &stg_full[rs.s], kc * 64, tile * NT, pol);
+                    tma_load_2d_hint(stg + (size_t)rs.s * NT * 64, map, &stg_full[rs.s], kc * 64, tile * NT, pol);
                     rs.next(a.SS);
                 }
                 if (!ok) break;
@@ -220,41 +298,79 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             // ---------------------------------------------------------------- kernel-matrix TMA producer
             const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
             Ring ra;
-            for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+            int pid = 0;
+            for (int T = next_tile(blockIdx.x, pid); T < total; T = next_tile(T + gridDim.x, pid)) {
+                const int info = s_info[pid];
+                const int KC = QP > 0 ? QP / 64 : (info >> 8) & 255, MB = (info >> 16) & 255, MPR = (info >> 24) & 255;
+                const int bytes = MPR * kAStage * (SPLIT ? 2 : 1);
+                const CUtensorMap* mhi = pid < kParamProbs ? &a.pm[pid].hi : &a.probs[pid].tm_hi;
+                const CUtensorMap* mlo = pid < kParamProbs ? &a.pm[pid].lo : &a.probs[pid].tm_lo;
                 bool ok = true;
                 for (int kc = 0; kc < KC && ok; ++kc) {
                     for (int mg = 0; mg < MB; mg += MPR) {
                         if (!WAITB(&a_empty[ra.s], ra.ph ^ 1u, 0x2u)) { ok = false; break; }
                         unsigned char* dst = aring + ra.s * L.kA;
-                        mbar_expect_tx(&a_full[ra.s], L.kA);
-                        tma_load_4d_hint(dst, &tm_hi, &a_full[ra.s], 0, 0, mg, kc, pol);
-                        if (SPLIT) tma_load_4d_hint(dst + MPR * kAStage, &tm_lo, &a_full[ra.s], 0, 0, mg, kc, pol);
+                        mbar_expect_tx(&a_full[ra.s], bytes);
+                        tma_load_4d_hint(dst, mhi, &a_full[ra.s], 0, 0, mg, kc, pol);
+                        if (SPLIT) tma_load_4d_hint(dst + MPR * kAStage, mlo, &a_full[ra.s], 0, 0, mg, kc, pol);
                         ra.next(a.SA);
                     }
                 }
                 if (!ok) break;
             }
         }
-        } else if (warp < 7) {
+    } else if (warp < 7) {
         // -------------------------------------------------------------------- converters
         constexpr int NR = NT / 8;             // rows (cells) per thread
         const int ct = tid - 96;               // 0..127
         const int rsub = ct >> 4;              // 0..7
         const int col4 = ct & 15;              // float4 column within the 64-ordinate chunk
+        // Problem fields are refetched only when the tile's problem changes; the weights of the
+        // next chunk (across tile ends) and the cell constants of the tile (cp.async into this
+        // thread's own rows of cstage) are requested ahead of use.
+        CellF* cstage = reinterpret_cast<CellF*>(base + L.cstage);
         Ring rs, rb;
-        int it = 0;
-        for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+        int it = 0, pid = 0, cpid = -1;
+        const float4* wp = nullptr;
+        const CellF* cellp = nullptr;
+        int nx = 1, ny = 1, ncell = 0;
+        float dt = 0.0f;
+        float4 wn = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int T = next_tile(blockIdx.x, pid); T < total; T = next_tile(T + gridDim.x, pid), ++it) {
+            if (pid != cpid) {
+                const ProbDesc& d = a.probs[pid];
+                wp = reinterpret_cast<const float4*>(d.w) + col4;
+                cellp = d.cell;
+                nx = d.nx;
+                ny = d.ny;
+                ncell = d.ncell;
+                dt = d.dt;
+                wn = __ldg(wp);
+                cpid = pid;
+            }
+            const int KC = QP > 0 ? QP / 64 : (s_info[pid] >> 8) & 255;
+            const int tile = T - s_tile0[pid];
+            if (col4 == 0) {
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const int r = rsub + 8 * i;
+                    const int f = tile * NT + r;
+                    if (f < ncell) cp_async16(smem_u32(cstage + r), cellp + f, 16u);
+                }
+                cp_async_commit();
+            }
             float part[NR];
 #pragma unroll
             for (int i = 0; i < NR; ++i) part[i] = 0.0f;
             bool ok = true;
             for (int kc = 0; kc < KC; ++kc) {
+                const float4 w4 = wn;
+                wn = __ldg(wp + (kc + 1 < KC ? kc + 1 : 0) * 16);
                 if (!WAITB(&stg_full[rs.s], rs.ph, 0x100u) || !WAITB(&bf_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
                     ok = false;
                     break;
                 }
                 const float4* src = reinterpret_cast<const float4*>(stg + (size_t)rs.s * NT * 64);
-                const float4 w4 = reinterpret_cast<const float4*>(wsm + kc * 64)[col4];
                 unsigned char* dhi = bhi + rb.s * LT::kB;
                 unsigned char* dlo = blo + rb.s * LT::kB;
 #pragma unroll
@@ -302,17 +418,18 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             if (col4 == 0) {
                 // per cell: x = 1 - dt sigma_t, y = dt (sigma_s Phi / sum w + q),
                 // z = neighbour bits (1 left, 2 right, 4 below, 8 above exist; 16 cell exists)
+                cp_async_wait<0>();
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
                     const int r = rsub + 8 * i;
                     const int f = tile * NT + r;
                     float4 cf = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-                    if (f < a.ncell) {
-                        const CellF cl = a.cell[f];
-                        const int yy = f / a.nx, xx = f - yy * a.nx;
-                        const int bits = (xx > 0 ? 1 : 0) | (xx + 1 < a.nx ? 2 : 0) | (yy > 0 ? 4 : 0) |
-                                         (yy + 1 < a.ny ? 8 : 0) | 16;
-                        cf = make_float4(1.0f - a.dt * cl.sig_t, a.dt * (cl.sig_s_over_wsum * part[i] + cl.q),
+                    if (f < ncell) {
+                        const CellF cl = cstage[r];
+                        const int yy = f / nx, xx = f - yy * nx;
+                        const int bits = (xx > 0 ? 1 : 0) | (xx + 1 < nx ? 2 : 0) | (yy > 0 ? 4 : 0) |
+                                         (yy + 1 < ny ? 8 : 0) | 16;
+                        cf = make_float4(1.0f - dt * cl.sig_t, dt * (cl.sig_s_over_wsum * part[i] + cl.q),
                                          __int_as_float(bits), 0.0f);
                     }
                     coef[buf * NT + r] = cf;
@@ -323,39 +440,44 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         }
     } else {
         // -------------------------------------------------------------------- epilogue
-        // Chunks of kCH cells x 32 ordinates.  The flux values of chunk k+1 (own cells, the two
-        // x-edge cells, the upwind y-neighbours) are loaded into registers while chunk k is
-        // computed.  The flux input is read-only during the launch, so these loads may run ahead
-        // of the MMA (and into the next tile).
-        const float* __restrict__ psi = a.psi;
-        float* __restrict__ psi_out = a.psi_out;
+        // Chunks of kCH cells x 32 ordinates.  The flux values of the next chunk (own cells, the
+        // two x-edge cells, the upwind y-neighbours) are loaded into registers while the current
+        // one is computed.  The flux input is read-only during the launch, so these loads may run
+        // ahead of the MMA (and into the next tile).
         const int e = warp - 7;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
         const int grp = e >> 2;                // which part (of kEW) of the tile's cells
-        const int ncell = a.ncell, nx = a.nx;
         constexpr int CPH = NT / (kEW * kCH);  // chunks per part of the tile and ordinate block
-        const int cpt = MB * CPH;              // chunks per tile for this warp
-        const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-        const int total = my_tiles * cpt;
 
-        // chunk k of this warp: tile index t (within this CTA), ordinate block m, first cell c0
-        auto decode = [&](int k, int& t, int& m, int& c0) {
-            t = k / cpt;
-            const int r = k - t * cpt;
-            m = r / CPH;
-            c0 = grp * (NT / kEW) + (r - m * CPH) * kCH;
+        // Position of a chunk: global tile T of problem pid, the it-th active tile of this CTA,
+        // chunk r within that tile (cpt chunks per tile).
+        struct Pos {
+            int T, pid, it, r, cpt;
         };
-        auto load = [&](int k, float (&s)[kCH], float (&u)[kCH], float& lft, float& rgt) {
-            int t, m, c0;
-            decode(k, t, m, c0);
-            const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
+        // Problem parameters of a tile as the chunk code uses them.
+        struct alignas(16) TileP {
+            const float* in;
+            float* out;
+            const OrdF* ord;
+            int fb0, ncell, nx, Q, Qp;
+            float dts;
+        };
+        static_assert(sizeof(TileP) <= 64, "tile parameter slot");
+
+        // Flux loads of chunk r (ordinate block m = r / CPH) of a tile into registers.
+        auto load = [&](const TileP& t, int r, float (&s)[kCH], float (&u)[kCH], float& lft, float& rgt) {
+            const int Qp = QP > 0 ? QP : t.Qp;
+            const int m = r / CPH;
+            const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCH;
+            const int ncell = t.ncell, nx = t.nx;
+            const int fb = t.fb0 + c0;
             const int q = m * 128 + lq * 32 + lane;
-            const bool live = q < a.Q && fb < ncell;
-            const float nuy = live ? a.ord[q].nuy : 0.0f;
-            const float* b = psi + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
+            const bool live = q < t.Q && fb < ncell;
+            const float nuy = live ? __ldg(&t.ord[q].nuy) : 0.0f;
+            const float* b = t.in + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
             const bool full = fb + kCH <= ncell;
 #pragma unroll
-            for (int i = 0; i < kCH; ++i) s[i] = (live && (full || fb + i < ncell)) ? b[i * Qp] : 0.0f;
+            for (int i = 0; i < kCH; ++i) s[i] = (live && (full || fb + i < ncell)) ? __ldg(b + i * Qp) : 0.0f;
             // y-neighbour of cell f: below (f - nx) for nuy > 0, above (f + nx) for nuy < 0
             const long dyo = nuy > 0.f ? -(long)nx * Qp : (long)nx * Qp;
             const float* by = b + dyo;
@@ -364,18 +486,19 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             for (int i = 0; i < kCH; ++i) {
                 const int f = fb + i;
                 const bool ok = live && nuy != 0.f && (yall || (nuy > 0.f ? f >= nx : f + nx < ncell));
-                u[i] = ok ? by[i * Qp] : 0.0f;
+                u[i] = ok ? __ldg(by + i * Qp) : 0.0f;
             }
-            lft = (live && fb >= 1) ? b[-Qp] : 0.0f;
-            rgt = (live && fb + kCH < ncell) ? b[kCH * Qp] : 0.0f;
+            lft = (live && fb >= 1) ? __ldg(b - Qp) : 0.0f;
+            rgt = (live && fb + kCH < ncell) ? __ldg(b + kCH * Qp) : 0.0f;
         };
-        auto compute = [&](int k, const float (&s)[kCH], const float (&u)[kCH], float lft, float rgt) -> bool {
-            int t, m, c0;
-            decode(k, t, m, c0);
-            const int r = k - t * cpt;
-            const int buf = t & 1;
+        // Update of chunk r of the it-th tile of this CTA (cpt chunks per tile); false on abort.
+        auto compute = [&](const TileP& t, int it, int r, int cpt, const float (&s)[kCH], const float (&u)[kCH],
+                           float lft, float rgt) -> bool {
+            const int m = r / CPH;
+            const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCH;
+            const int buf = it & 1;
             if (r == 0) {
-                const uint32_t use = (uint32_t)(t >> 1);
+                const uint32_t use = (uint32_t)(it >> 1);
                 int go = 1;
                 if (lane == 0)
                     go = WAITB(&phi_full[buf], use & 1u, 0x1000u) && WAITB(&tm_full[buf], use & 1u, 0x2000u);
@@ -385,21 +508,24 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
             }
             float y[kCH];
             __syncwarp();
-            tmem_ld<kCH>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * MB * NT + m * NT + c0), y);
-            const int fb = ((int)blockIdx.x + t * (int)gridDim.x) * NT + c0;
+            tmem_ld<kCH>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0), y);
+            const int Qp = QP > 0 ? QP : t.Qp;
+            const int ncell = t.ncell;
+            const int fb = t.fb0 + c0;
             const int q = m * 128 + lq * 32 + lane;
             if (fb < ncell && q < Qp) {
-                float* po = psi_out + (size_t)fb * Qp + q;
+                float* po = t.out + (size_t)fb * Qp + q;
                 const float4* cb = coef + buf * NT + c0;
-                if (q >= a.Q) {
+                if (q >= t.Q) {
 #pragma unroll
                     for (int i = 0; i < kCH; ++i)
                         if (fb + i < ncell) __stcs(po + i * Qp, 0.0f);
                 } else {
-                    const OrdF o = a.ord[q];
-                    const float ax = fabsf(o.nux), ay = fabsf(o.nuy), axy = ax + ay;
-                    const float ge = a.dt_sigma_as * o.e;
-                    const int xbit = o.nux > 0.f ? 1 : (o.nux < 0.f ? 2 : 0);
+                    const float4 o4 = __ldg(reinterpret_cast<const float4*>(t.ord) + q);
+                    const float ax = fabsf(o4.x), ay = fabsf(o4.y), axy = ax + ay;
+                    const float dts = t.dts;
+                    const float ge = dts * o4.w;
+                    const int xbit = o4.x > 0.f ? 1 : (o4.x < 0.f ? 2 : 0);
 #pragma unroll
                     for (int i = 0; i < kCH; ++i) {
                         const float4 cf = cb[i];
@@ -412,7 +538,7 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
                         float out = fmaf(sf, cf.x - axy, cf.y);
                         out = fmaf(ax, upx, out);
                         out = fmaf(ay, u[i], out);
-                        out = fmaf(a.dt_sigma_as, y[i], out);
+                        out = fmaf(dts, y[i], out);
                         out = fmaf(-ge, st, out);
                         __stcs(po + i * Qp, out);
                     }
@@ -430,13 +556,97 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         };
 
         float s0[kCH], u0[kCH], l0 = 0.f, r0 = 0.f, s1[kCH], u1[kCH], l1 = 0.f, r1 = 0.f;
-        if (total > 0) load(0, s0, u0, l0, r0);
-        for (int k = 0; k < total; k += 2) {
-            if (k + 1 < total) load(k + 1, s1, u1, l1, r1);
-            if (!compute(k, s0, u0, l0, r0)) break;
-            if (k + 1 >= total) break;
-            if (k + 2 < total) load(k + 2, s0, u0, l0, r0);
-            if (!compute(k + 1, s1, u1, l1, r1)) break;
+        if (nprob == 1) {
+            // One problem: its tiles blockIdx.x, blockIdx.x + gridDim.x, ... (all or none active);
+            // chunk k of this warp is chunk k % cpt of the (k / cpt)-th of them.
+            const int ntl = (s_info[0] & 2) ? total : 0;
+            const int my_tiles = ntl > (int)blockIdx.x ? (ntl - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+            const int cpt = a.one.MB * CPH;
+            const int nchunk = my_tiles * cpt;
+            auto view = [&](int k, int& it, int& r) -> TileP {
+                it = k / cpt;
+                r = k - it * cpt;
+                return TileP{a.one.in, a.one.out, a.one.ord, ((int)blockIdx.x + it * (int)gridDim.x) * NT, a.one.ncell, a.one.nx, a.one.Q,
+                             QP > 0 ? QP : a.one.Qp, a.one.dts};
+            };
+            int it, r;
+            if (nchunk > 0) load(view(0, it, r), r, s0, u0, l0, r0);
+            for (int k = 0; k < nchunk; k += 2) {
+                if (k + 1 < nchunk) { const TileP t = view(k + 1, it, r); load(t, r, s1, u1, l1, r1); }
+                { const TileP t = view(k, it, r); if (!compute(t, it, r, cpt, s0, u0, l0, r0)) break; }
+                if (k + 1 >= nchunk) break;
+                if (k + 2 < nchunk) { const TileP t = view(k + 2, it, r); load(t, r, s0, u0, l0, r0); }
+                { const TileP t = view(k + 1, it, r); if (!compute(t, it, r, cpt, s1, u1, l1, r1)) break; }
+            }
+        } else {
+            // Several problems: walk the active tiles; the tile's parameters sit in this warp's
+            // shared-memory slot (it & 1), rewritten from global memory only when the problem
+            // changes (else copied from the other slot or kept).
+            struct Pos {
+                int T, pid, it, r, cpt;
+            };
+            TileP* tslot = reinterpret_cast<TileP*>(base + L.tparm + e * 2 * 64);
+            auto slot = [&](int it) -> const TileP& {
+                return *reinterpret_cast<const TileP*>(reinterpret_cast<const unsigned char*>(tslot) + (it & 1) * 64);
+            };
+            int spid0 = -1, spid1 = -1;
+            auto fill = [&](Pos& p) {
+                if (p.T >= total) return;
+                const int info = s_info[p.pid];
+                p.cpt = ((info >> 16) & 255) * CPH;
+                const int k = p.it & 1;
+                TileP* t = reinterpret_cast<TileP*>(reinterpret_cast<unsigned char*>(tslot) + k * 64);
+                const int mine = k ? spid1 : spid0, other = k ? spid0 : spid1;
+                if (lane == 0) {
+                    if (mine != p.pid) {
+                        if (other == p.pid) {
+                            *t = slot(p.it + 1);
+                        } else {
+                            const ProbDesc& d = a.probs[p.pid];
+                            const int par = info & 1;
+                            t->in = d.buf[par];
+                            t->out = const_cast<float*>(d.buf[par ^ 1]);
+                            t->ord = d.ord;
+                            t->ncell = d.ncell;
+                            t->nx = d.nx;
+                            t->Q = d.Q;
+                            t->Qp = QP > 0 ? QP : d.Qp;
+                            t->dts = d.dt_sigma_as;
+                        }
+                    }
+                    t->fb0 = (p.T - s_tile0[p.pid]) * NT;
+                }
+                if (k) spid1 = p.pid; else spid0 = p.pid;
+                __syncwarp();
+            };
+            auto advance = [&](Pos& p) {
+                if (++p.r < p.cpt) return;
+                p.r = 0;
+                ++p.it;
+                p.T = next_tile(p.T + gridDim.x, p.pid);
+                fill(p);
+            };
+            Pos cur;
+            cur.it = 0;
+            cur.r = 0;
+            cur.pid = 0;
+            cur.cpt = 1;
+            cur.T = next_tile(blockIdx.x, cur.pid);
+            fill(cur);
+            if (cur.T < total) load(slot(cur.it), cur.r, s0, u0, l0, r0);
+            while (cur.T < total) {
+                Pos nxt = cur;
+                advance(nxt);
+                if (nxt.T < total) load(slot(nxt.it), nxt.r, s1, u1, l1, r1);
+                if (!compute(slot(cur.it), cur.it, cur.r, cur.cpt, s0, u0, l0, r0)) break;
+                cur = nxt;
+                if (cur.T >= total) break;
+                nxt = cur;
+                advance(nxt);
+                if (nxt.T < total) load(slot(nxt.it), nxt.r, s0, u0, l0, r0);
+                if (!compute(slot(cur.it), cur.it, cur.r, cur.cpt, s1, u1, l1, r1)) break;
+                cur = nxt;
+            }
         }
     }
 
@@ -450,6 +660,18 @@ step_tc2_kernel(const __grid_constant__ CUtensorMap tm_psi, const __grid_constan
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem_base, 512);
+    }
+    // The last CTA to finish advances the step counters of the problems this launch stepped.
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(a.ticket, 1u);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            for (int i = 0; i < nprob; ++i)
+                if (s_info[i] & 2) *a.probs[i].counter += 1;
+            *a.ticket = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -472,16 +694,17 @@ EncodeFn get_encode() {
     return fn;
 }
 
-bool encode_2d(CUtensorMap* map, CUtensorMapDataType type, const void* ptr, uint64_t inner, uint64_t outer,
-               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
+// Flux buffer [ncell][Qp] FP32, box {64 ordinates, NT cells}, no swizzle.
+bool encode_psi(CUtensorMap* map, const float* psi, int Qp, int ncell, int NT) {
     EncodeFn enc = get_encode();
     if (!enc) return false;
-    const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {row_bytes};
-    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint64_t dims[2] = {(cuuint64_t)Qp, (cuuint64_t)ncell};
+    const cuuint64_t strides[1] = {(cuuint64_t)Qp * 4};
+    const cuuint32_t box[2] = {64, (cuuint32_t)NT};
     const cuuint32_t estr[2] = {1, 1};
-    return enc(map, type, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(psi), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // 4D view of G [Mp][Qp] BF16: x = column within a 64-column chunk, y = row within a 128-row
@@ -499,89 +722,143 @@ bool encode_G4(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MB, int MPR
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t smem_for(int NT, bool split, int SS, int SB, int SA, int Qp, int MPR) {
+size_t smem_for(int NT, bool split, int SS, int SB, int SA, int MPRmax) {
     auto need = [&](auto L) { return (size_t)1024 + (size_t)L.end; };
     switch (NT * 2 + (split ? 1 : 0)) {
-        case 64: return need(Layout<32, false>(SS, SB, SA, Qp, MPR));
-        case 65: return need(Layout<32, true>(SS, SB, SA, Qp, MPR));
-        case 128: return need(Layout<64, false>(SS, SB, SA, Qp, MPR));
-        case 129: return need(Layout<64, true>(SS, SB, SA, Qp, MPR));
-        case 256: return need(Layout<128, false>(SS, SB, SA, Qp, MPR));
-        case 257: return need(Layout<128, true>(SS, SB, SA, Qp, MPR));
-        case 512: return need(Layout<256, false>(SS, SB, SA, Qp, MPR));
-        default: return need(Layout<256, true>(SS, SB, SA, Qp, MPR));
+        case 64: return need(Layout<32, false>(SS, SB, SA, MPRmax));
+        case 65: return need(Layout<32, true>(SS, SB, SA, MPRmax));
+        case 128: return need(Layout<64, false>(SS, SB, SA, MPRmax));
+        case 129: return need(Layout<64, true>(SS, SB, SA, MPRmax));
+        case 256: return need(Layout<128, false>(SS, SB, SA, MPRmax));
+        case 257: return need(Layout<128, true>(SS, SB, SA, MPRmax));
+        case 512: return need(Layout<256, false>(SS, SB, SA, MPRmax));
+        default: return need(Layout<256, true>(SS, SB, SA, MPRmax));
+    }
+}
+
+// Tile width, ring depths and request sizes for a set of problems.  Tile width: two accumulator
+// buffers of MBmax x NT columns fill the 512 TMEM columns (or the requested width); narrower when
+// the rings do not fit shared memory.  Kernel-matrix requests cover as many ordinate blocks (MPR)
+// as two stages allow; then the deepest balanced staging / B rings (up to 4), then a deeper
+// kernel-matrix ring (up to 4).
+bool choose_tiling(int MBmax, bool split, int want_nt, int want_stages, int& NT, int& SS, int& SB, int& SA,
+                   int& MPRmax) {
+    int nt = 512 / (2 * MBmax);
+    if (nt > 256) nt = 256;
+    if (want_nt) nt = want_nt;
+    const size_t limit = 227 * 1024;
+    while (true) {
+        if (nt < 32 || (nt & (nt - 1)) || 2 * MBmax * nt > 512) return false;
+        for (int mpr = MBmax; mpr >= 1; mpr /= 2) {
+            if (MBmax % mpr) continue;
+            if (want_stages >= 2) {
+                if (smem_for(nt, split, want_stages, want_stages, want_stages, mpr) <= limit) {
+                    NT = nt; SS = SB = SA = want_stages; MPRmax = mpr;
+                    return true;
+                }
+            } else if (smem_for(nt, split, 2, 2, 2, mpr) <= limit) {
+                int ss = 2, sb = 2, sa = 2;
+                for (int k = 4; k >= 3; --k)
+                    if (smem_for(nt, split, k, k, 2, mpr) <= limit) { ss = sb = k; break; }
+                while (sa < 4 && smem_for(nt, split, ss, sb, sa + 1, mpr) <= limit) ++sa;
+                NT = nt; SS = ss; SB = sb; SA = sa; MPRmax = mpr;
+                return true;
+            }
+        }
+        if (want_nt) return false;
+        nt /= 2;
     }
 }
 
 }  // namespace
 
 struct Tc2Plan {
-    CUtensorMap tm_hi, tm_lo;
-    CUtensorMap tm_psi[4];
-    const void* psi_key[4];
-    int nkeys;
-    int Q, Qp, Mp, MB, KC, NT, SS, SB, SA, MPR, nx, ny, ncell, ntiles, grid;
-    bool split;
-    size_t smem;
+    int NT = 0, SS = 2, SB = 2, SA = 2, MPRmax = 1, QP = 0, grid = 0, total_tiles = 0, nprob = 0;
+    bool split = false;
+    size_t smem = 0;
+    std::vector<ProbDesc> host;   // descriptors as uploaded
+    ProbDesc* d_probs = nullptr;
+    unsigned int* d_ticket = nullptr;
 };
 
-cudaError_t tc2_plan_create(Tc2Plan** out, const __nv_bfloat16* G_hi, const __nv_bfloat16* G_lo, int Q, int Qp,
-                            int Mp, int nx, int ny, bool split, int want_nt, int want_stages) {
+cudaError_t tc2_plan_create(Tc2Plan** out, const Tc2Problem* probs, int nprob, bool split, int want_nt,
+                            int want_stages) {
     *out = nullptr;
+    if (nprob < 1 || nprob > kMaxProbs) return cudaErrorNotSupported;
+    int MBmax = 1;
+    for (int i = 0; i < nprob; ++i) MBmax = std::max(MBmax, probs[i].Mp / 128);
     Tc2Plan* p = new Tc2Plan();
-    p->Q = Q; p->Qp = Qp; p->Mp = Mp; p->MB = Mp / 128; p->KC = Qp / 64; p->nx = nx; p->ny = ny;
-    p->split = split; p->nkeys = 0;
-    p->ncell = nx * ny;
-    // Tile width: two accumulator buffers of MB x NT columns fill the 512 TMEM columns; narrower
-    // when the rings do not fit shared memory.  Kernel-matrix requests: as many ordinate blocks per
-    // request (MPR) as two stages allow.  Then the deepest balanced staging / B rings that fit (up
-    // to 4), then a deeper kernel-matrix ring (up to 4).
-    int nt = 512 / (2 * p->MB);
-    if (nt > 256) nt = 256;
-    if (want_nt) nt = want_nt;
-    const size_t limit = 227 * 1024;
-    int SS = 2, SB = 2, SA = 2, MPR = 1;
-    bool fits = false;
-    while (!fits) {
-        if (nt < 32 || (nt & (nt - 1)) || 2 * p->MB * nt > 512) { delete p; return cudaErrorNotSupported; }
-        for (MPR = p->MB; MPR >= 1 && !fits; MPR /= 2) {
-            if (p->MB % MPR) continue;
-            if (want_stages >= 2) {
-                SS = SB = SA = want_stages;
-                fits = smem_for(nt, split, SS, SB, SA, Qp, MPR) <= limit;
-            } else if (smem_for(nt, split, 2, 2, 2, Qp, MPR) <= limit) {
-                fits = true;
-                SS = SB = SA = 2;
-                for (int k = 4; k >= 3; --k)
-                    if (smem_for(nt, split, k, k, 2, Qp, MPR) <= limit) { SS = SB = k; break; }
-                while (SA < 4 && smem_for(nt, split, SS, SB, SA + 1, Qp, MPR) <= limit) ++SA;
-            }
-            if (fits) break;
-        }
-        if (!fits) {
-            if (want_nt) { delete p; return cudaErrorNotSupported; }
-            nt /= 2;
-        }
+    p->split = split;
+    if (!choose_tiling(MBmax, split, want_nt, want_stages, p->NT, p->SS, p->SB, p->SA, p->MPRmax)) {
+        delete p;
+        return cudaErrorNotSupported;
     }
-    p->MPR = MPR;
-    p->NT = nt;
-    p->SS = SS; p->SB = SB; p->SA = SA;
-    p->smem = smem_for(nt, split, SS, SB, SA, Qp, MPR);
-    p->ntiles = (p->ncell + nt - 1) / nt;
+    p->smem = smem_for(p->NT, split, p->SS, p->SB, p->SA, p->MPRmax);
+    p->nprob = nprob;
+    p->host.resize(nprob);
+    int tile0 = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const Tc2Problem& s = probs[i];
+        ProbDesc& d = p->host[i];
+        memset(&d, 0, sizeof d);
+        d.MB = s.Mp / 128;
+        d.MPR = std::min(p->MPRmax, d.MB);
+        while (d.MB % d.MPR) d.MPR /= 2;
+        if (!encode_psi(&d.tm_psi[0], s.buf[0], s.Qp, s.nx * s.ny, p->NT) ||
+            !encode_psi(&d.tm_psi[1], s.buf[1], s.Qp, s.nx * s.ny, p->NT) ||
+            !encode_G4(&d.tm_hi, s.G_hi, s.Qp, d.MB, d.MPR) ||
+            (split && !encode_G4(&d.tm_lo, s.G_lo, s.Qp, d.MB, d.MPR))) {
+            delete p;
+            return cudaErrorInvalidValue;
+        }
+        if (!split) d.tm_lo = d.tm_hi;
+        d.buf[0] = s.buf[0];
+        d.buf[1] = s.buf[1];
+        d.ord = s.ord;
+        d.cell = s.cell;
+        d.w = s.w;
+        d.counter = s.counter;
+        d.target = s.target;
+        d.nx = s.nx;
+        d.ny = s.ny;
+        d.ncell = s.nx * s.ny;
+        d.Q = s.Q;
+        d.Qp = s.Qp;
+        d.KC = s.Qp / 64;
+        d.ntiles = (d.ncell + p->NT - 1) / p->NT;
+        d.tile0 = tile0;
+        d.dt = s.dt;
+        d.dt_sigma_as = s.dt_sigma_as;
+        tile0 += d.ntiles;
+    }
+    p->total_tiles = tile0;
+    // compile-time stride when every problem shares one ordinate stride
+    p->QP = probs[0].Qp;
+    for (int i = 1; i < nprob; ++i)
+        if (probs[i].Qp != p->QP) p->QP = 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    p->grid = p->ntiles < sms ? p->ntiles : sms;
-    if (!encode_G4(&p->tm_hi, G_hi, Qp, p->MB, MPR) || (split && !encode_G4(&p->tm_lo, G_lo, Qp, p->MB, MPR))) {
-        delete p;
-        return cudaErrorInvalidValue;
+    p->grid = std::min(p->total_tiles, sms);
+    cudaError_t e = cudaMalloc(&p->d_probs, sizeof(ProbDesc) * nprob);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_ticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_probs, p->host.data(), sizeof(ProbDesc) * nprob, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        tc2_plan_destroy(p);
+        return e;
     }
-    if (!split) p->tm_lo = p->tm_hi;
     *out = p;
     return cudaSuccess;
 }
 
-void tc2_plan_destroy(Tc2Plan* p) { delete p; }
+void tc2_plan_destroy(Tc2Plan* p) {
+    if (!p) return;
+    if (p->d_probs) cudaFree(p->d_probs);
+    if (p->d_ticket) cudaFree(p->d_ticket);
+    delete p;
+}
 
 void tc2_plan_describe(const Tc2Plan* p, int* tile_cells, int* stages, int* tmem_cols, size_t* smem) {
     if (tile_cells) *tile_cells = p ? p->NT : 0;
@@ -590,58 +867,73 @@ void tc2_plan_describe(const Tc2Plan* p, int* tile_cells, int* stages, int* tmem
     if (smem) *smem = p ? p->smem : 0;
 }
 
-static const CUtensorMap* psi_map(Tc2Plan* p, const float* psi) {
-    for (int i = 0; i < p->nkeys; ++i)
-        if (p->psi_key[i] == psi) return &p->tm_psi[i];
-    const int slot = p->nkeys < 4 ? p->nkeys++ : 3;
-    if (!encode_2d(&p->tm_psi[slot], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, psi, p->Qp, p->ncell, (uint64_t)p->Qp * 4, 64,
-                   p->NT, CU_TENSOR_MAP_SWIZZLE_NONE))
-        return nullptr;
-    p->psi_key[slot] = psi;
-    return &p->tm_psi[slot];
-}
+int tc2_plan_total_tiles(const Tc2Plan* p) { return p ? p->total_tiles : 0; }
 
 template <int NT, bool SPLIT, int QP>
-static cudaError_t launch2(const Tc2Plan* p, const CUtensorMap* mpsi, const Tc2Args& a, cudaStream_t s) {
+static cudaError_t launch2(const Tc2Plan* p, const BatchArgs& a, cudaStream_t s) {
     auto kern = step_tc2_kernel<NT, SPLIT, QP>;
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (r != cudaSuccess) return r;
-    kern<<<p->grid, kThreads2, p->smem, s>>>(*mpsi, p->tm_hi, p->tm_lo, a);
+    kern<<<p->grid, kThreads2, p->smem, s>>>(a);
     return cudaGetLastError();
 }
 
 // Compile-time ordinate strides for the common quadratures (at their automatic tile widths and
 // half of them); everything else runs the runtime-stride instance.
 template <bool SPLIT>
-static cudaError_t dispatch(const Tc2Plan* p, const CUtensorMap* m, const Tc2Args& a, cudaStream_t s) {
-    const int key = p->Qp * 1000 + p->NT;
+static cudaError_t dispatch(const Tc2Plan* p, const BatchArgs& a, cudaStream_t s) {
+    const int key = p->QP * 1000 + p->NT;
     switch (key) {
-        case 512 * 1000 + 64: return launch2<64, SPLIT, 512>(p, m, a, s);
-        case 512 * 1000 + 32: return launch2<32, SPLIT, 512>(p, m, a, s);
-        case 256 * 1000 + 128: return launch2<128, SPLIT, 256>(p, m, a, s);
-        case 256 * 1000 + 64: return launch2<64, SPLIT, 256>(p, m, a, s);
-        case 128 * 1000 + 256: return launch2<256, SPLIT, 128>(p, m, a, s);
-        case 128 * 1000 + 128: return launch2<128, SPLIT, 128>(p, m, a, s);
-        case 64 * 1000 + 256: return launch2<256, SPLIT, 64>(p, m, a, s);
-        case 64 * 1000 + 128: return launch2<128, SPLIT, 64>(p, m, a, s);
+        case 512 * 1000 + 64: return launch2<64, SPLIT, 512>(p, a, s);
+        case 512 * 1000 + 32: return launch2<32, SPLIT, 512>(p, a, s);
+        case 256 * 1000 + 128: return launch2<128, SPLIT, 256>(p, a, s);
+        case 256 * 1000 + 64: return launch2<64, SPLIT, 256>(p, a, s);
+        case 128 * 1000 + 256: return launch2<256, SPLIT, 128>(p, a, s);
+        case 128 * 1000 + 128: return launch2<128, SPLIT, 128>(p, a, s);
+        case 64 * 1000 + 256: return launch2<256, SPLIT, 64>(p, a, s);
+        case 64 * 1000 + 128: return launch2<128, SPLIT, 64>(p, a, s);
         default: break;
     }
     switch (p->NT) {
-        case 32: return launch2<32, SPLIT, 0>(p, m, a, s);
-        case 64: return launch2<64, SPLIT, 0>(p, m, a, s);
-        case 128: return launch2<128, SPLIT, 0>(p, m, a, s);
-        default: return launch2<256, SPLIT, 0>(p, m, a, s);
+        case 32: return launch2<32, SPLIT, 0>(p, a, s);
+        case 64: return launch2<64, SPLIT, 0>(p, a, s);
+        case 128: return launch2<128, SPLIT, 0>(p, a, s);
+        default: return launch2<256, SPLIT, 0>(p, a, s);
     }
 }
 
-cudaError_t launch_step_tc2(Tc2Plan* p, const StepArgs<float, OrdF, CellF>& s, const float* w, unsigned int* err_flag,
-                            cudaStream_t stream) {
+cudaError_t launch_step_tc2(Tc2Plan* p, unsigned int* err_flag, int parity0, cudaStream_t stream) {
     if (!p) return cudaErrorInvalidValue;
-    const CUtensorMap* mpsi = psi_map(p, s.psi);
-    if (!mpsi) return cudaErrorInvalidValue;
-    Tc2Args a{s.psi, s.psi_out, s.ord, s.cell, w, err_flag, s.nx, s.ny, s.Q, s.Qp, p->MB, p->KC, p->ntiles,
-              p->ncell, p->SS, p->SB, p->SA, p->MPR, s.dt, s.dt_sigma_as};
-    return p->split ? dispatch<true>(p, mpsi, a, stream) : dispatch<false>(p, mpsi, a, stream);
+    BatchArgs a;
+    for (int i = 0; i < kParamProbs && i < p->nprob; ++i) {
+        const ProbDesc& d = p->host[i];
+        a.pm[i].psi[0] = d.tm_psi[0];
+        a.pm[i].psi[1] = d.tm_psi[1];
+        a.pm[i].hi = d.tm_hi;
+        a.pm[i].lo = d.tm_lo;
+    }
+    {
+        const ProbDesc& d = p->host[0];
+        a.one.in = d.buf[parity0 & 1];
+        a.one.out = const_cast<float*>(d.buf[(parity0 & 1) ^ 1]);
+        a.one.ord = d.ord;
+        a.one.ncell = d.ncell;
+        a.one.nx = d.nx;
+        a.one.Q = d.Q;
+        a.one.Qp = d.Qp;
+        a.one.MB = d.MB;
+        a.one.dts = d.dt_sigma_as;
+    }
+    a.probs = p->d_probs;
+    a.nprob = p->nprob;
+    a.total_tiles = p->total_tiles;
+    a.err = err_flag;
+    a.ticket = p->d_ticket;
+    a.SS = p->SS;
+    a.SB = p->SB;
+    a.SA = p->SA;
+    a.MPRmax = p->MPRmax;
+    return p->split ? dispatch<true>(p, a, stream) : dispatch<false>(p, a, stream);
 }
 
 }  // namespace assn
