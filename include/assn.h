@@ -201,6 +201,53 @@ int assn_mass(assn_problem* p, double* mass_out);
 /* Check the state for NaN/Inf: ASSN_OK or ASSN_ERR_NONFINITE.  Syncs. */
 int assn_check_finite(assn_problem* p);
 
+/* ---- Batches: several problems stepped by one persistent launch per step.
+ * The members may differ in grid size, quadrature (ordinate count), kernel width eps, cross
+ * sections and dt; they share the device and one tensor-core precision (ASSN_BF16 or
+ * ASSN_BF16X3).  Each launch applies the same explicit step as assn_step (Sec. 3.2, forward Euler
+ * of the as-S_N equations) to every member that still has steps left; a member's step count is
+ * kept on the device, so members finish at their own counts within one run.  After
+ * assn_batch_run each member is exactly as if assn_step(p, nsteps, dt) had been called on it
+ * (bitwise, at the same tiling).  Members stay owned by the caller and must outlive their
+ * membership; while in a batch they are stepped only through it.
+ *
+ * create:     stream = a cudaStream_t or NULL (library stream).  Errors: ASSN_ERR_CUDA / OOM.
+ * add:        add p, to be advanced nsteps >= 0 steps of size dt per run.  Checks p is complete
+ *             and dt admissible (as assn_step).  Errors: ASSN_ERR_ARG (NULL, duplicate, other
+ *             device, mixed precision, more than 1024 members), ASSN_ERR_UNSUPPORTED (not a
+ *             tensor-core precision), or p's own error (ASSN_ERR_STATE, ASSN_ERR_UNSTABLE).
+ * set_steps:  change a member's nsteps / dt for later runs.
+ * remove:     drop a member (syncs the batch stream).
+ * set_tiling: tile cells (0, 32, 64, 128, 256) and ring depth (0 or 2..8) for all members.
+ * autotune:   time one launch of every candidate tiling on the members' current states (outputs
+ *             go to scratch buffers, no state changes; syncs) and apply the fastest.  With
+ *             use_cache != 0 a previous result for the same precision and multiset of
+ *             (cells, padded Q) is reused without timing (*ms_per_launch = -1 then).
+ * run:        enqueue max_i nsteps_i launches on the batch stream (ordered after each member's
+ *             stream; members' streams wait for the run).  use_graph != 0 captures them once as a
+ *             CUDA graph and replays it while the membership, tiling, dt and max nsteps stay
+ *             the same.  Asynchronous.
+ * sync:       wait for the batch stream; ASSN_ERR_TIMEOUT if a bounded device wait gave up.
+ * info:       members, tile cells, stages, tiles per launch, launches issued (outputs may be NULL).
+ * last_error: message of the last failure on b (b == NULL: last failed create on this thread). */
+typedef struct assn_batch assn_batch;
+int assn_batch_create(assn_batch** out, void* stream);
+int assn_batch_destroy(assn_batch* b);
+int assn_batch_add(assn_batch* b, assn_problem* p, int nsteps, double dt);
+int assn_batch_set_steps(assn_batch* b, assn_problem* p, int nsteps, double dt);
+int assn_batch_remove(assn_batch* b, assn_problem* p);
+int assn_batch_set_tiling(assn_batch* b, int tile_cells, int stages);
+int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stages, double* ms_per_launch);
+int assn_batch_run(assn_batch* b, int use_graph);
+int assn_batch_sync(assn_batch* b);
+int assn_batch_info(assn_batch* b, int* members, int* tile_cells, int* stages, int* total_tiles,
+                    int64_t* launches);
+const char* assn_batch_last_error(const assn_batch* b);
+
+/* Autotune one problem's tiling for step size dt the same way (no state change; syncs) and apply
+ * it as assn_set_tiling(p, tile_cells, stages, 0) would.  Outputs may be NULL. */
+int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, int* stages, double* ms_per_step);
+
 /* ---- Allocation-free total mass (the paper has no counterpart; this serves library users).
  * Some callers cannot allocate device memory during a call: code between the begin and end of a
  * CUDA stream capture, real-time loops that forbid allocator calls, or hosts that run the library

@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import (ASSN_BF16, ASSN_BF16X3, ASSN_FP32, ASSN_FP64, ASSN_KERNEL_EXP, ASSN_KERNEL_GAUSS,
                    ASSN_NORM_COLUMN, ASSN_NORM_ROW, PRECISIONS, AssnError)
 
-__all__ = ["Problem", "AssnError", "PRECISIONS", "ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
+__all__ = ["Problem", "Batch", "AssnError", "PRECISIONS", "ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
            "ASSN_KERNEL_GAUSS", "ASSN_KERNEL_EXP", "ASSN_NORM_COLUMN", "ASSN_NORM_ROW"]
 
 
@@ -90,6 +90,9 @@ class Problem:
     def tiling(self) -> dict:
         return _lib.assn_get_tiling(self.handle)
 
+    def autotune(self, dt: float, use_cache: bool = True) -> dict:
+        return _lib.assn_autotune(self.handle, dt, use_cache)
+
     def layout(self):
         return _lib.assn_layout(self.handle)
 
@@ -102,6 +105,64 @@ class Problem:
     def close(self):
         if self.handle:
             _lib.assn_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several problems advanced by one persistent tensor-core launch per step (include/assn.h)."""
+
+    def __init__(self, stream=None):
+        self.handle = None
+        self.handle = _lib.assn_batch_create(stream)
+        self.members: list[Problem] = []
+
+    def add(self, problem: Problem, nsteps: int, dt: float):
+        _lib.assn_batch_add(self.handle, problem.handle, nsteps, dt)
+        self.members.append(problem)
+        return self
+
+    def set_steps(self, problem: Problem, nsteps: int, dt: float):
+        _lib.assn_batch_set_steps(self.handle, problem.handle, nsteps, dt)
+        return self
+
+    def remove(self, problem: Problem):
+        _lib.assn_batch_remove(self.handle, problem.handle)
+        self.members.remove(problem)
+        return self
+
+    def set_tiling(self, tile_cells: int = 0, stages: int = 0):
+        _lib.assn_batch_set_tiling(self.handle, tile_cells, stages)
+        return self
+
+    def autotune(self, use_cache: bool = True) -> dict:
+        return _lib.assn_batch_autotune(self.handle, use_cache)
+
+    def run(self, use_graph: bool = True):
+        _lib.assn_batch_run(self.handle, use_graph)
+        return self
+
+    def sync(self):
+        _lib.assn_batch_sync(self.handle)
+        return self
+
+    def info(self) -> dict:
+        return _lib.assn_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            _lib.assn_batch_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -68,6 +68,19 @@ SIGNATURES = {
     "assn_status_string": (C.c_char_p, [C.c_int]),
     "assn_launch_count": (C.c_int64, [_h]),
     "assn_abi_version": (C.c_int, []),
+    "assn_batch_create": (C.c_int, [C.POINTER(_h), _vp]),
+    "assn_batch_destroy": (C.c_int, [_h]),
+    "assn_batch_add": (C.c_int, [_h, _h, C.c_int, C.c_double]),
+    "assn_batch_set_steps": (C.c_int, [_h, _h, C.c_int, C.c_double]),
+    "assn_batch_remove": (C.c_int, [_h, _h]),
+    "assn_batch_set_tiling": (C.c_int, [_h, C.c_int, C.c_int]),
+    "assn_batch_autotune": (C.c_int, [_h, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
+    "assn_batch_run": (C.c_int, [_h, C.c_int]),
+    "assn_batch_sync": (C.c_int, [_h]),
+    "assn_batch_info": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "assn_batch_last_error": (C.c_char_p, [_h]),
+    "assn_autotune": (C.c_int, [_h, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "assn_mass_noalloc": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.c_double, _vp, _vp]),
     "assn_noalloc_last_error": (C.c_char_p, []),
 }
@@ -265,6 +278,69 @@ def assn_status_string(status: int) -> str:
 
 def assn_launch_count(h: int) -> int:
     return int(lib.assn_launch_count(h))
+
+
+def _bcheck(status: int, b=None):
+    if status != ASSN_OK:
+        raise AssnError(status, lib.assn_batch_last_error(b).decode())
+
+
+def assn_batch_create(stream=None) -> int:
+    b = _h()
+    _bcheck(lib.assn_batch_create(C.byref(b), _stream_ptr(stream)), None)
+    return b.value
+
+
+def assn_batch_destroy(b: int) -> None:
+    _bcheck(lib.assn_batch_destroy(b), b)
+
+
+def assn_batch_add(b: int, p: int, nsteps: int, dt: float) -> None:
+    _bcheck(lib.assn_batch_add(b, p, nsteps, dt), b)
+
+
+def assn_batch_set_steps(b: int, p: int, nsteps: int, dt: float) -> None:
+    _bcheck(lib.assn_batch_set_steps(b, p, nsteps, dt), b)
+
+
+def assn_batch_remove(b: int, p: int) -> None:
+    _bcheck(lib.assn_batch_remove(b, p), b)
+
+
+def assn_batch_set_tiling(b: int, tile_cells: int = 0, stages: int = 0) -> None:
+    _bcheck(lib.assn_batch_set_tiling(b, tile_cells, stages), b)
+
+
+def assn_batch_autotune(b: int, use_cache: bool = True) -> dict:
+    t, s, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+    _bcheck(lib.assn_batch_autotune(b, int(use_cache), C.byref(t), C.byref(s), C.byref(ms)), b)
+    return {"tile_cells": t.value, "stages": s.value, "ms_per_launch": ms.value}
+
+
+def assn_batch_run(b: int, use_graph: bool = True) -> None:
+    _bcheck(lib.assn_batch_run(b, int(use_graph)), b)
+
+
+def assn_batch_sync(b: int) -> None:
+    _bcheck(lib.assn_batch_sync(b), b)
+
+
+def assn_batch_info(b: int) -> dict:
+    m, t, s, n = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
+    L = C.c_int64(0)
+    _bcheck(lib.assn_batch_info(b, C.byref(m), C.byref(t), C.byref(s), C.byref(n), C.byref(L)), b)
+    return {"members": m.value, "tile_cells": t.value, "stages": s.value, "total_tiles": n.value,
+            "launches": L.value}
+
+
+def assn_batch_last_error(b: int | None) -> str:
+    return lib.assn_batch_last_error(b).decode()
+
+
+def assn_autotune(h: int, dt: float, use_cache: bool = True) -> dict:
+    t, s, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+    _check(lib.assn_autotune(h, dt, int(use_cache), C.byref(t), C.byref(s), C.byref(ms)), h)
+    return {"tile_cells": t.value, "stages": s.value, "ms_per_step": ms.value}
 
 
 def assn_mass_noalloc(psi_dev: int, elem_bytes: int, w_dev: int, ncell: int, Qp: int, h: float, mass_dev: int,

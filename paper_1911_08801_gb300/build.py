@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libassn.so")
-SOURCES = ["api.cu", "kbuild.cu", "step_simt.cu", "step_tc.cu", "step_tc2.cu", "misc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "batch.cu", "kbuild.cu", "step_simt.cu", "step_tc.cu", "step_tc2.cu", "misc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
@@ -38,7 +38,7 @@ def _newer(target: str, deps: list[str]) -> bool:
 
 def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "assn_internal.h"), os.path.join(CSRC, "tc_ptx.h"), os.path.join(ROOT, "include", "assn.h")]
+    headers = [os.path.join(CSRC, "assn_internal.h"), os.path.join(CSRC, "problem.h"), os.path.join(CSRC, "tc_ptx.h"), os.path.join(ROOT, "include", "assn.h")]
     nv = nvcc()
     extra = extra or []
 

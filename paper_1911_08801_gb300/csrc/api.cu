@@ -9,68 +9,9 @@
 #include <string>
 #include <vector>
 
-#include "assn_internal.h"
+#include "problem.h"
 
 using namespace assn;
-
-struct assn_problem {
-    int dev = 0;
-    int nx = 0, ny = 0;
-    double x0 = 0, x1 = 0, y0 = 0, y1 = 0, h = 0;
-    int precision = ASSN_FP32;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-
-    int Q = 0, Qp = 0;
-    std::vector<double> omega, w;   // host copies, [Q*3], [Q]
-    double wsum = 0;
-    bool have_quad = false;
-
-    std::vector<double> sa, ss, src;
-    bool have_xs = false;
-
-    double sigma_as = 0, eps = 0;
-    int kind = 0, norm = 0;
-    bool have_K = false;
-    std::vector<double> e;          // generator diagonal per ordinate
-
-    // device memory
-    double* d_omega = nullptr;
-    unsigned char* d_ydir = nullptr;   // [Qp/4] upwind y side per group of 4 ordinates (tensor-core epilogue)
-    double* d_w64 = nullptr;
-    float* d_w32 = nullptr;
-    double* d_K64 = nullptr;
-    double* d_KT64 = nullptr;
-    float* d_KT32 = nullptr;
-    TcOperands tc;
-    TcPlan* plan = nullptr;      // one-tile-per-CTA tensor-core kernel (variant 1)
-    Tc2Plan* plan2 = nullptr;    // persistent warp-specialised kernel (variant 0, default)
-    int variant = 0;
-    double* d_e = nullptr;
-    void* d_ord = nullptr;
-    double ord_dt = -1.0;
-    void* d_cell = nullptr;
-    void* d_psi[2] = {nullptr, nullptr};
-    int cur = 0;
-    double* d_partials = nullptr;
-    double* d_scalar = nullptr;
-    unsigned int* d_flags = nullptr;   // [0] finite check, [1] tensor-core timeout
-    double* d_stage = nullptr;
-    size_t stage_elems = 0;
-
-    int want_nt = 0, want_stages = 0;   // tensor-core tiling request (0 = automatic)
-    int* d_counter = nullptr;           // device step counter of the persistent tensor-core kernel
-    int counter_host = 0;               // last value written to / advanced on d_counter
-    double plan2_dt = -1.0;             // dt the persistent plan was built for
-
-    std::string err;
-    int64_t launches = 0;
-
-    size_t ncell() const { return (size_t)nx * ny; }
-    size_t elem() const { return precision == ASSN_FP64 ? 8 : 4; }
-    bool tensor() const { return precision == ASSN_BF16 || precision == ASSN_BF16X3; }
-};
-
 
 namespace {
 
@@ -278,6 +219,37 @@ int install_quadrature(assn_problem* p, int Q, const double* omega, const double
 }
 
 }  // namespace
+
+namespace assn {
+
+int problem_fail(assn_problem* p, int status, const char* msg) { return fail(p, status, "%s", msg); }
+
+int problem_prepare(assn_problem* p, double dt);   // defined after the step entry points
+
+int problem_check_flags(assn_problem* p) { return check_flags(p); }
+
+Tc2Problem problem_tc2(const assn_problem* p, double dt, int target) {
+    Tc2Problem d;
+    d.buf[0] = (const float*)p->d_psi[0];
+    d.buf[1] = (const float*)p->d_psi[1];
+    d.ord = (const OrdF*)p->d_ord;
+    d.cell = (const CellF*)p->d_cell;
+    d.w = p->d_w32;
+    d.G_hi = p->tc.G_hi;
+    d.G_lo = p->tc.G_lo;
+    d.counter = p->d_counter;
+    d.target = target;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.Q = p->Q;
+    d.Qp = p->Qp;
+    d.Mp = p->tc.Mp;
+    d.dt = (float)dt;
+    d.dt_sigma_as = (float)(dt * p->sigma_as);
+    return d;
+}
+
+}  // namespace assn
 
 extern "C" {
 
@@ -638,23 +610,7 @@ static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
     if (e == cudaSuccess && p->variant == 0 && (!p->plan2 || p->plan2_dt != dt)) {
         if (p->plan2) tc2_plan_destroy(p->plan2);
         p->plan2 = nullptr;
-        Tc2Problem d;
-        d.buf[0] = (const float*)p->d_psi[0];
-        d.buf[1] = (const float*)p->d_psi[1];
-        d.ord = (const OrdF*)p->d_ord;
-        d.cell = (const CellF*)p->d_cell;
-        d.w = p->d_w32;
-        d.G_hi = p->tc.G_hi;
-        d.G_lo = p->tc.G_lo;
-        d.counter = p->d_counter;
-        d.target = 0x7fffffff;
-        d.nx = p->nx;
-        d.ny = p->ny;
-        d.Q = p->Q;
-        d.Qp = p->Qp;
-        d.Mp = p->tc.Mp;
-        d.dt = (float)dt;
-        d.dt_sigma_as = (float)(dt * p->sigma_as);
+        const Tc2Problem d = problem_tc2(p, dt, 0x7fffffff);
         e = tc2_plan_create(&p->plan2, &d, 1, p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
         if (e == cudaSuccess) p->plan2_dt = dt;
     }
@@ -666,6 +622,18 @@ static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
 }
 
 static int prepare_step(assn_problem* p, double dt) {
+    int r = assn::problem_prepare(p, dt);
+    if (r) return r;
+    if (p->tensor()) {
+        r = ensure_plan(p, dt, false);
+        if (r) return r;
+    }
+    return ASSN_OK;
+}
+
+}  // extern "C"
+
+int assn::problem_prepare(assn_problem* p, double dt) {
     int r = ready(p);
     if (r) return r;
     if (!(dt > 0) || !isfinite(dt)) return fail(p, ASSN_ERR_ARG, "dt must be > 0");
@@ -674,14 +642,10 @@ static int prepare_step(assn_problem* p, double dt) {
         return fail(p, ASSN_ERR_UNSTABLE, "dt = %.17g exceeds the positivity bound %.17g", dt, dmax);
     r = set_device(p);
     if (r) return r;
-    r = upload_ord(p, dt);
-    if (r) return r;
-    if (p->tensor()) {
-        r = ensure_plan(p, dt, false);
-        if (r) return r;
-    }
-    return ASSN_OK;
+    return upload_ord(p, dt);
 }
+
+extern "C" {
 
 int assn_step(assn_problem* p, int nsteps, double dt) {
     if (!p) return ASSN_ERR_ARG;

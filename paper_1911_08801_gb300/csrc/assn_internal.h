@@ -88,8 +88,11 @@ cudaError_t tc2_plan_create(Tc2Plan** plan, const Tc2Problem* probs, int nprob, 
 void tc2_plan_destroy(Tc2Plan* plan);
 void tc2_plan_describe(const Tc2Plan* plan, int* tile_cells, int* stages, int* tmem_cols, size_t* smem);
 int tc2_plan_total_tiles(const Tc2Plan* plan);
-// parity0: parity of problem 0's step counter at launch (one-problem plans read the flux from
-// buffer parity0 and write buffer parity0 ^ 1; batch plans take every parity from the device).
+// New step targets (one per problem, in plan order) for later launches on `s`.
+cudaError_t tc2_plan_set_targets(Tc2Plan* plan, const int* targets, cudaStream_t s);
+// parity0 >= 0 (one-problem plans launched by the host step by step): problem 0's counter parity
+// at launch, so the flux is read from buffer parity0 and written to parity0 ^ 1; parity0 < 0:
+// every parity comes from the device counters (batches, CUDA graphs).
 cudaError_t launch_step_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, cudaStream_t s);
 
 template <typename T>

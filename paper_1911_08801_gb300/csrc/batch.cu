@@ -1,0 +1,457 @@
+// Batched stepping of several as-S_N problems (uneven grids, ordinate counts and kernel widths)
+// by the persistent tensor-core kernel, optionally as a CUDA graph, and the tile-shape autotuner.
+//
+// Every launch advances each member whose device step counter is below its target by one
+// explicit step (Sec. 3: upwind transport, collision and isotropic scattering, and the
+// artificial-scattering contraction of Sec. 3.2 in one pass); members that reached their
+// target are skipped on the device, so a run of max(nsteps) launches, captured once as a
+// graph, completes every member at its own step count with no host round trip in between.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "problem.h"
+
+using namespace assn;
+
+struct assn_batch {
+    int dev = 0;
+    int precision = -1;                 // of the members (BF16 or BF16X3)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    struct Member {
+        assn_problem* p;
+        int nsteps;
+        double dt;
+    };
+    std::vector<Member> members;
+    Tc2Plan* plan = nullptr;            // for the current membership and tiling
+    std::vector<int> targets;
+    cudaGraphExec_t graph = nullptr;    // nlaunch launches of `plan`
+    int graph_len = 0;
+    unsigned int* d_err = nullptr;
+    cudaEvent_t done = nullptr;
+    int want_nt = 0, want_stages = 0;   // 0 = automatic
+    std::string err;
+    int64_t launches = 0;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int bfail(assn_batch* b, int status, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int bfail(assn_batch* b, int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf; else g_batch_error = buf;
+    return status;
+}
+
+#define BK(b, call)                                                                                    \
+    do {                                                                                               \
+        cudaError_t _e = (call);                                                                       \
+        if (_e != cudaSuccess)                                                                         \
+            return bfail((b), _e == cudaErrorMemoryAllocation ? ASSN_ERR_OOM : ASSN_ERR_CUDA, "%s: %s", \
+                         #call, cudaGetErrorString(_e));                                               \
+    } while (0)
+
+void drop_plan(assn_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_len = 0;
+    if (b->plan) tc2_plan_destroy(b->plan);
+    b->plan = nullptr;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner: times one launch of each candidate tiling (tile width NT, ring depths) on the
+// problems' current states, writing into scratch buffers so no state changes, and keeps the
+// fastest.  Results are cached per (precision, multiset of grid size x ordinate stride).
+
+struct TuneKey {
+    std::string s;
+    bool operator<(const TuneKey& o) const { return s < o.s; }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+TuneKey tune_key(const std::vector<Tc2Problem>& probs, bool split) {
+    std::vector<std::pair<int, int>> v;
+    for (const Tc2Problem& p : probs) v.push_back({p.nx * p.ny, p.Qp});
+    std::sort(v.begin(), v.end());
+    std::string s = split ? "x3" : "b1";
+    char buf[48];
+    for (auto& e : v) {
+        snprintf(buf, sizeof buf, ":%dx%d", e.first, e.second);
+        s += buf;
+    }
+    return TuneKey{s};
+}
+
+// probs: descriptions of the problems as they will be stepped (buf[parity] is read); par[i] the
+// parity of problem i's current state.  Returns cudaSuccess and the best (nt, stages), or an
+// error; ms_out gets the best launch time.
+cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int>& par, bool split,
+                     cudaStream_t s, int* nt_out, int* stages_out, float* ms_out, bool use_cache) {
+    const TuneKey key = tune_key(probs, split);
+    if (use_cache) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *nt_out = it->second.first;
+            *stages_out = it->second.second;
+            if (ms_out) *ms_out = -1.0f;
+            return cudaSuccess;
+        }
+    }
+    const int n = (int)probs.size();
+    int MBmax = 1;
+    for (const Tc2Problem& p : probs) MBmax = std::max(MBmax, p.Mp / 128);
+    std::vector<float*> scratch(n, nullptr);
+    int* d_cnt = nullptr;
+    unsigned int* d_err = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaSuccess;
+    float best = INFINITY;
+    int best_nt = 0, best_st = 0;
+    do {
+        for (int i = 0; i < n && err == cudaSuccess; ++i)
+            err = cudaMalloc(&scratch[i], (size_t)probs[i].nx * probs[i].ny * probs[i].Qp * sizeof(float));
+        if (err != cudaSuccess) break;
+        if ((err = cudaMalloc(&d_cnt, sizeof(int) * n)) != cudaSuccess) break;
+        if ((err = cudaMalloc(&d_err, sizeof(unsigned int))) != cudaSuccess) break;
+        if ((err = cudaMemsetAsync(d_err, 0, sizeof(unsigned int), s)) != cudaSuccess) break;
+        if ((err = cudaEventCreate(&e0)) != cudaSuccess || (err = cudaEventCreate(&e1)) != cudaSuccess) break;
+        std::vector<Tc2Problem> trial(probs);
+        for (int i = 0; i < n; ++i) {
+            // counter 0 -> read buf[0] (the current state), write buf[1] (scratch)
+            trial[i].buf[0] = probs[i].buf[par[i]];
+            trial[i].buf[1] = scratch[i];
+            trial[i].counter = d_cnt + i;
+            trial[i].target = 1;
+        }
+        for (int nt = 32; nt <= 256 && err == cudaSuccess; nt *= 2) {
+            if (2 * MBmax * nt > 512) break;
+            for (int st : {0, 2, 3, 4}) {
+                Tc2Plan* plan = nullptr;
+                cudaError_t ce = tc2_plan_create(&plan, trial.data(), n, split, nt, st);
+                if (ce == cudaErrorNotSupported) continue;
+                if (ce != cudaSuccess) { err = ce; break; }
+                float tot = 0.0f;
+                for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+                    err = cudaMemsetAsync(d_cnt, 0, sizeof(int) * n, s);
+                    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+                    if (err == cudaSuccess) err = launch_step_tc2(plan, d_err, n == 1 ? 0 : -1, s);
+                    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+                    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tot += ms;   // first launch is the warm-up
+                }
+                tc2_plan_destroy(plan);
+                if (err != cudaSuccess) break;
+                unsigned int flag = 0;
+                err = cudaMemcpy(&flag, d_err, sizeof flag, cudaMemcpyDeviceToHost);
+                if (err == cudaSuccess && flag) err = cudaErrorLaunchTimeout;
+                if (err != cudaSuccess) break;
+                if (tot / 3.0f < best) {
+                    best = tot / 3.0f;
+                    best_nt = nt;
+                    best_st = st;
+                }
+            }
+        }
+    } while (false);
+    for (float* p : scratch)
+        if (p) cudaFree(p);
+    if (d_cnt) cudaFree(d_cnt);
+    if (d_err) cudaFree(d_err);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return err;
+    if (best_nt == 0) return cudaErrorNotSupported;
+    *nt_out = best_nt;
+    *stages_out = best_st;
+    if (ms_out) *ms_out = best;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = {best_nt, best_st};
+    return cudaSuccess;
+}
+
+// Builds the plan for the current membership (targets from each member's state and nsteps).
+int ensure_batch_plan(assn_batch* b) {
+    const int n = (int)b->members.size();
+    b->targets.resize(n);
+    for (int i = 0; i < n; ++i) b->targets[i] = b->members[i].p->cur + b->members[i].nsteps;
+    if (b->plan) {
+        BK(b, tc2_plan_set_targets(b->plan, b->targets.data(), b->stream));
+        return ASSN_OK;
+    }
+    std::vector<Tc2Problem> d(n);
+    for (int i = 0; i < n; ++i) d[i] = problem_tc2(b->members[i].p, b->members[i].dt, b->targets[i]);
+    cudaError_t e = tc2_plan_create(&b->plan, d.data(), n, b->precision == ASSN_BF16X3, b->want_nt, b->want_stages);
+    if (e == cudaErrorNotSupported)
+        return bfail(b, ASSN_ERR_UNSUPPORTED, "batch: tiling %d / %d not supported for these members", b->want_nt,
+                     b->want_stages);
+    BK(b, e);
+    return ASSN_OK;
+}
+
+int index_of(const assn_batch* b, const assn_problem* p) {
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->members[i].p == p) return (int)i;
+    return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int assn_batch_create(assn_batch** out, void* cuda_stream) {
+    if (!out) return bfail(nullptr, ASSN_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    assn_batch* b = new (std::nothrow) assn_batch();
+    if (!b) return bfail(nullptr, ASSN_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&b->dev);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            b->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned int), b->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        bfail(nullptr, e == cudaErrorMemoryAllocation ? ASSN_ERR_OOM : ASSN_ERR_CUDA, "batch create: %s",
+              cudaGetErrorString(e));
+        if (b->d_err) cudaFree(b->d_err);
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? ASSN_ERR_OOM : ASSN_ERR_CUDA;
+    }
+    *out = b;
+    return ASSN_OK;
+}
+
+int assn_batch_destroy(assn_batch* b) {
+    if (!b) return ASSN_OK;
+    cudaSetDevice(b->dev);
+    cudaStreamSynchronize(b->stream);
+    drop_plan(b);
+    if (b->d_err) cudaFree(b->d_err);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return ASSN_OK;
+}
+
+int assn_batch_add(assn_batch* b, assn_problem* p, int nsteps, double dt) {
+    if (!b || !p) return bfail(b, ASSN_ERR_ARG, "batch or problem is NULL");
+    if (nsteps < 0) return bfail(b, ASSN_ERR_ARG, "nsteps < 0");
+    if (p->precision != ASSN_BF16 && p->precision != ASSN_BF16X3)
+        return bfail(b, ASSN_ERR_UNSUPPORTED, "batches step the tensor-core precisions (BF16, BF16X3) only");
+    if (b->precision >= 0 && p->precision != b->precision)
+        return bfail(b, ASSN_ERR_ARG, "all members of a batch share one precision");
+    if (p->dev != b->dev) return bfail(b, ASSN_ERR_ARG, "problem lives on another device");
+    if (index_of(b, p) >= 0) return bfail(b, ASSN_ERR_ARG, "problem is already a member");
+    if ((int)b->members.size() >= 1024) return bfail(b, ASSN_ERR_ARG, "a batch holds at most 1024 problems");
+    const int r = problem_prepare(p, dt);
+    if (r) return bfail(b, r, "member: %s", p->err.c_str());
+    b->precision = p->precision;
+    b->members.push_back({p, nsteps, dt});
+    drop_plan(b);
+    return ASSN_OK;
+}
+
+int assn_batch_set_steps(assn_batch* b, assn_problem* p, int nsteps, double dt) {
+    if (!b || !p) return bfail(b, ASSN_ERR_ARG, "batch or problem is NULL");
+    const int i = index_of(b, p);
+    if (i < 0) return bfail(b, ASSN_ERR_ARG, "problem is not a member");
+    if (nsteps < 0) return bfail(b, ASSN_ERR_ARG, "nsteps < 0");
+    if (dt != b->members[i].dt) {
+        const int r = problem_prepare(p, dt);
+        if (r) return bfail(b, r, "member: %s", p->err.c_str());
+        b->members[i].dt = dt;
+        drop_plan(b);   // dt is baked into the descriptors
+    }
+    b->members[i].nsteps = nsteps;
+    return ASSN_OK;
+}
+
+int assn_batch_remove(assn_batch* b, assn_problem* p) {
+    if (!b || !p) return bfail(b, ASSN_ERR_ARG, "batch or problem is NULL");
+    const int i = index_of(b, p);
+    if (i < 0) return bfail(b, ASSN_ERR_ARG, "problem is not a member");
+    BK(b, cudaStreamSynchronize(b->stream));
+    b->members.erase(b->members.begin() + i);
+    if (b->members.empty()) b->precision = -1;
+    drop_plan(b);
+    return ASSN_OK;
+}
+
+int assn_batch_set_tiling(assn_batch* b, int tile_cells, int stages) {
+    if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    if (tile_cells != 0 && tile_cells != 32 && tile_cells != 64 && tile_cells != 128 && tile_cells != 256)
+        return bfail(b, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64, 128 or 256");
+    if (stages != 0 && (stages < 2 || stages > 8)) return bfail(b, ASSN_ERR_ARG, "stages must be 0 or 2..8");
+    b->want_nt = tile_cells;
+    b->want_stages = stages;
+    drop_plan(b);
+    return ASSN_OK;
+}
+
+int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stages, double* ms_per_launch) {
+    if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    if (b->members.empty()) return bfail(b, ASSN_ERR_STATE, "batch has no members");
+    BK(b, cudaSetDevice(b->dev));
+    for (auto& m : b->members) {   // the tuner reads the members' current states
+        if (m.p->stream != b->stream) {
+            BK(b, cudaStreamSynchronize(m.p->stream));
+        }
+    }
+    std::vector<Tc2Problem> d;
+    std::vector<int> par;
+    for (auto& m : b->members) {
+        d.push_back(problem_tc2(m.p, m.dt, 1));
+        par.push_back(m.p->cur);
+    }
+    int nt = 0, st = 0;
+    float ms = 0.0f;
+    cudaError_t e = autotune(d, par, b->precision == ASSN_BF16X3, b->stream, &nt, &st, &ms, use_cache != 0);
+    if (e == cudaErrorLaunchTimeout) return bfail(b, ASSN_ERR_TIMEOUT, "autotune: a bounded device wait gave up");
+    if (e == cudaErrorNotSupported) return bfail(b, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits these members");
+    BK(b, e);
+    b->want_nt = nt;
+    b->want_stages = st;
+    drop_plan(b);
+    if (tile_cells) *tile_cells = nt;
+    if (stages) *stages = st;
+    if (ms_per_launch) *ms_per_launch = ms;
+    return ASSN_OK;
+}
+
+int assn_batch_run(assn_batch* b, int use_graph) {
+    if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    if (b->members.empty()) return ASSN_OK;
+    BK(b, cudaSetDevice(b->dev));
+    int nmax = 0;
+    for (auto& m : b->members) nmax = std::max(nmax, m.nsteps);
+    if (nmax == 0) return ASSN_OK;
+    // order after each member's pending work; set each device counter to the member's parity
+    for (auto& m : b->members) {
+        assn_problem* p = m.p;
+        if (p->stream != b->stream) {
+            BK(b, cudaEventRecord(b->done, p->stream));
+            BK(b, cudaStreamWaitEvent(b->stream, b->done, 0));
+        }
+        if (p->counter_host != p->cur) {
+            p->counter_host = p->cur;
+            BK(b, cudaMemcpyAsync(p->d_counter, &p->counter_host, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        }
+    }
+    int r = ensure_batch_plan(b);
+    if (r) return r;
+    if (use_graph) {
+        if (!b->graph || b->graph_len != nmax) {
+            if (b->graph) cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+            cudaGraph_t g = nullptr;
+            BK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < nmax && e == cudaSuccess; ++i) e = launch_step_tc2(b->plan, b->d_err, -1, b->stream);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            BK(b, e);
+            b->graph_len = nmax;
+        }
+        BK(b, cudaGraphLaunch(b->graph, b->stream));
+    } else {
+        for (int i = 0; i < nmax; ++i) BK(b, launch_step_tc2(b->plan, b->d_err, -1, b->stream));
+    }
+    b->launches += nmax;
+    BK(b, cudaEventRecord(b->done, b->stream));
+    for (auto& m : b->members) {
+        assn_problem* p = m.p;
+        p->counter_host = p->cur + m.nsteps;
+        p->cur = p->counter_host & 1;
+        p->launches += m.nsteps;
+        if (p->stream != b->stream) BK(b, cudaStreamWaitEvent(p->stream, b->done, 0));
+    }
+    return ASSN_OK;
+}
+
+int assn_batch_sync(assn_batch* b) {
+    if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    BK(b, cudaSetDevice(b->dev));
+    BK(b, cudaStreamSynchronize(b->stream));
+    unsigned int f = 0;
+    BK(b, cudaMemcpy(&f, b->d_err, sizeof f, cudaMemcpyDeviceToHost));
+    if (f) {
+        BK(b, cudaMemset(b->d_err, 0, sizeof f));
+        return bfail(b, ASSN_ERR_TIMEOUT, "batch step: a bounded device wait gave up (flag 0x%x)", f);
+    }
+    return ASSN_OK;
+}
+
+int assn_batch_info(assn_batch* b, int* members, int* tile_cells, int* stages, int* total_tiles,
+                    int64_t* launches) {
+    if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    if (members) *members = (int)b->members.size();
+    int nt = 0, st = 0, cols = 0, tiles = 0;
+    size_t sm = 0;
+    if (!b->members.empty()) {
+        BK(b, cudaSetDevice(b->dev));
+        int r = ensure_batch_plan(b);
+        if (r) return r;
+        tc2_plan_describe(b->plan, &nt, &st, &cols, &sm);
+        tiles = tc2_plan_total_tiles(b->plan);
+    }
+    if (tile_cells) *tile_cells = nt;
+    if (stages) *stages = st;
+    if (total_tiles) *total_tiles = tiles;
+    if (launches) *launches = b->launches;
+    return ASSN_OK;
+}
+
+const char* assn_batch_last_error(const assn_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+// Single problem: tune its tiling the same way and apply it (assn_set_tiling with the result).
+int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, int* stages, double* ms_per_step) {
+    if (!p) return ASSN_ERR_ARG;
+    if (!p->tensor()) return problem_fail(p, ASSN_ERR_UNSUPPORTED, "autotune applies to the tensor-core precisions");
+    int r = problem_prepare(p, dt);
+    if (r) return r;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return problem_fail(p, ASSN_ERR_CUDA, cudaGetErrorString(e));
+    std::vector<Tc2Problem> d{problem_tc2(p, dt, 1)};
+    std::vector<int> par{p->cur};
+    int nt = 0, st = 0;
+    float ms = 0.0f;
+    e = autotune(d, par, p->precision == ASSN_BF16X3, p->stream, &nt, &st, &ms, use_cache != 0);
+    if (e == cudaErrorLaunchTimeout) return problem_fail(p, ASSN_ERR_TIMEOUT, "autotune: a bounded device wait gave up");
+    if (e == cudaErrorNotSupported) return problem_fail(p, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits");
+    if (e != cudaSuccess) return problem_fail(p, ASSN_ERR_CUDA, cudaGetErrorString(e));
+    r = assn_set_tiling(p, nt, st, 0);
+    if (r) return r;
+    if (tile_cells) *tile_cells = nt;
+    if (stages) *stages = st;
+    if (ms_per_step) *ms_per_step = ms;
+    return ASSN_OK;
+}
+
+}  // extern "C"

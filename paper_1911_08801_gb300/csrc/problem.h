@@ -1,0 +1,79 @@
+// Problem object shared by the host-side translation units of libassn (not part of the ABI).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "assn_internal.h"
+
+struct assn_problem {
+    int dev = 0;
+    int nx = 0, ny = 0;
+    double x0 = 0, x1 = 0, y0 = 0, y1 = 0, h = 0;
+    int precision = ASSN_FP32;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    int Q = 0, Qp = 0;
+    std::vector<double> omega, w;   // host copies, [Q*3], [Q]
+    double wsum = 0;
+    bool have_quad = false;
+
+    std::vector<double> sa, ss, src;
+    bool have_xs = false;
+
+    double sigma_as = 0, eps = 0;
+    int kind = 0, norm = 0;
+    bool have_K = false;
+    std::vector<double> e;          // generator diagonal per ordinate
+
+    // device memory
+    double* d_omega = nullptr;
+    unsigned char* d_ydir = nullptr;   // [Qp/4] upwind y side per group of 4 ordinates (tensor-core epilogue)
+    double* d_w64 = nullptr;
+    float* d_w32 = nullptr;
+    double* d_K64 = nullptr;
+    double* d_KT64 = nullptr;
+    float* d_KT32 = nullptr;
+    assn::TcOperands tc;
+    assn::TcPlan* plan = nullptr;      // one-tile-per-CTA tensor-core kernel (variant 1)
+    assn::Tc2Plan* plan2 = nullptr;    // persistent warp-specialised kernel (variant 0, default)
+    int variant = 0;
+    double* d_e = nullptr;
+    void* d_ord = nullptr;
+    double ord_dt = -1.0;
+    void* d_cell = nullptr;
+    void* d_psi[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* d_partials = nullptr;
+    double* d_scalar = nullptr;
+    unsigned int* d_flags = nullptr;   // [0] finite check, [1] tensor-core timeout
+    double* d_stage = nullptr;
+    size_t stage_elems = 0;
+
+    int want_nt = 0, want_stages = 0;   // tensor-core tiling request (0 = automatic)
+    int* d_counter = nullptr;           // device step counter of the persistent tensor-core kernel
+    int counter_host = 0;               // last value written to / advanced on d_counter
+    double plan2_dt = -1.0;             // dt the persistent plan was built for
+
+    std::string err;
+    int64_t launches = 0;
+
+    size_t ncell() const { return (size_t)nx * ny; }
+    size_t elem() const { return precision == ASSN_FP64 ? 8 : 4; }
+    bool tensor() const { return precision == ASSN_BF16 || precision == ASSN_BF16X3; }
+};
+
+namespace assn {
+
+// Set p's error message; returns status.
+int problem_fail(assn_problem* p, int status, const char* msg);
+// Checks that p is complete and dt admissible, uploads the per-ordinate constants for dt.
+int problem_prepare(assn_problem* p, double dt);
+// Reads and clears the device-wait timeout flag of p (synchronises p's stream).
+int problem_check_flags(assn_problem* p);
+// Description of p for the persistent tensor-core kernel: buffers, constants, step counter,
+// stepped while the counter is below target.
+Tc2Problem problem_tc2(const assn_problem* p, double dt, int target);
+
+}  // namespace assn

@@ -99,6 +99,7 @@ struct OneProb {
 struct BatchArgs {
     ParamMaps pm[kParamProbs];
     OneProb one;
+    int one_fixed;                      // one problem, flux buffers resolved by the host
     const ProbDesc* probs;
     int nprob, total_tiles;
     unsigned int* err;
@@ -556,7 +557,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
         };
 
         float s0[kCH], u0[kCH], l0 = 0.f, r0 = 0.f, s1[kCH], u1[kCH], l1 = 0.f, r1 = 0.f;
-        if (nprob == 1) {
+        if (a.one_fixed) {
             // One problem: its tiles blockIdx.x, blockIdx.x + gridDim.x, ... (all or none active);
             // chunk k of this warp is chunk k % cpt of the (k / cpt)-th of them.
             const int ntl = (s_info[0] & 2) ? total : 0;
@@ -869,6 +870,18 @@ void tc2_plan_describe(const Tc2Plan* p, int* tile_cells, int* stages, int* tmem
 
 int tc2_plan_total_tiles(const Tc2Plan* p) { return p ? p->total_tiles : 0; }
 
+cudaError_t tc2_plan_set_targets(Tc2Plan* p, const int* targets, cudaStream_t stream) {
+    if (!p) return cudaErrorInvalidValue;
+    bool changed = false;
+    for (int i = 0; i < p->nprob; ++i) {
+        if (p->host[i].target != targets[i]) changed = true;
+        p->host[i].target = targets[i];
+    }
+    if (!changed) return cudaSuccess;
+    // the host table outlives the copy (pageable source: staged before the call returns)
+    return cudaMemcpyAsync(p->d_probs, p->host.data(), sizeof(ProbDesc) * p->nprob, cudaMemcpyHostToDevice, stream);
+}
+
 template <int NT, bool SPLIT, int QP>
 static cudaError_t launch2(const Tc2Plan* p, const BatchArgs& a, cudaStream_t s) {
     auto kern = step_tc2_kernel<NT, SPLIT, QP>;
@@ -912,6 +925,7 @@ cudaError_t launch_step_tc2(Tc2Plan* p, unsigned int* err_flag, int parity0, cud
         a.pm[i].hi = d.tm_hi;
         a.pm[i].lo = d.tm_lo;
     }
+    a.one_fixed = (p->nprob == 1 && parity0 >= 0) ? 1 : 0;
     {
         const ProbDesc& d = p->host[0];
         a.one.in = d.buf[parity0 & 1];
