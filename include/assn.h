@@ -248,6 +248,79 @@ const char* assn_batch_last_error(const assn_batch* b);
  * it as assn_set_tiling(p, tile_cells, stages, 0) would.  Outputs may be NULL. */
 int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, int* stages, double* ms_per_step);
 
+/* ---- Serving: a request loop over whole solves (continuous batching).
+ * A server owns one host thread that does all device work.  Requests (one complete as-S_N solve
+ * each: grid, product quadrature, eps, cross sections, initial state, nsteps steps of size dt)
+ * wait in arrival order and are admitted while fewer than max_active solves are on the device
+ * and the estimated device memory of the admitted solves (assn_footprint_bytes) stays within
+ * the budget; an admitted solve keeps its flux state on the device until it finishes.  The loop
+ * advances all admitted solves together, chunk_steps steps at a time, with one persistent launch
+ * per step (the batch path, optionally as CUDA graphs); requests that arrive meanwhile join at
+ * the next chunk, and finished solves return the scalar flux Phi = sum_q w_q psi_q (FP64 on the
+ * host, [ny][nx]) and free their memory.  A solve's result does not depend on which other solves
+ * share its launches (each is bitwise equal to assn_step on the same problem).
+ *
+ * Thread safety: submit, wait and stats may be called from any host threads concurrently;
+ * assn_server_last_error returns the message of the calling thread's last failed server call. */
+typedef enum {
+    ASSN_INIT_LINE_SOURCE = 0,   /* assn_init_line_source(delta, floor_value) (Sec. 4.1)   */
+    ASSN_INIT_ZERO = 1,          /* psi = 0                                                 */
+    ASSN_INIT_STATE = 2          /* psi0: [ny][nx][Q] host FP32, copied at submit            */
+} assn_init_kind;
+
+typedef struct {
+    int nx, ny;                          /* grid (square cells, as assn_create)               */
+    double x0, x1, y0, y1;
+    int n_polar, n_azim;                 /* product quadrature, Q = n_polar * n_azim <= 1024 */
+    double sigma_as, eps;                /* artificial scattering (assn_set_artificial_scattering) */
+    int kernel_kind, normalisation;
+    const double* sigma_a;               /* [ny][nx] host, copied at submit                  */
+    const double* sigma_s;
+    const double* q;
+    int init_kind;                       /* an assn_init_kind                                 */
+    double delta, floor_value;           /* ASSN_INIT_LINE_SOURCE parameters                  */
+    const float* psi0;                   /* ASSN_INIT_STATE state                             */
+    int nsteps;                          /* steps of size dt (checked against the positivity  */
+    double dt;                           /* bound at admission: the request then fails)       */
+} assn_request;
+
+typedef struct {
+    int64_t submitted, completed, failed, active, queued, max_active_seen, launches;
+    double p50_latency_s, p99_latency_s, mean_latency_s;   /* submit -> result, completed solves */
+    double busy_s;                       /* host time spent in chunks with solves on the device */
+    double wall_s;                       /* first submit -> last completion                   */
+    double updates;                      /* cell-ordinate updates of completed solves         */
+    double updates_per_s;                /* updates / wall_s                                   */
+    int64_t budget_bytes, peak_bytes;    /* footprint budget and the largest admitted total   */
+} assn_server_stats;
+
+typedef struct assn_server assn_server;
+
+/* Estimated device memory of one problem (state ping-pong, cell constants, K and its operands,
+ * staging), rounded up to 2 MiB.  ASSN_ERR_ARG on invalid sizes. */
+int assn_footprint_bytes(int nx, int ny, int Q, int precision, size_t* bytes);
+
+/* precision: ASSN_BF16 or ASSN_BF16X3.  hbm_budget_bytes: admission budget (0 = 85% of the
+ * device memory free at creation).  max_active: 1..1024 solves on the device at once.
+ * chunk_steps >= 1: steps per admission round.  use_graph: replay chunks as CUDA graphs. */
+int assn_server_create(assn_server** out, int precision, size_t hbm_budget_bytes, int max_active,
+                       int chunk_steps, int use_graph);
+/* Queue a request (inputs copied); *id receives its handle.  ASSN_ERR_ARG on an invalid request,
+ * ASSN_ERR_OOM if its footprint exceeds the whole budget, ASSN_ERR_STATE while stopping. */
+int assn_server_submit(assn_server* s, const assn_request* r, int64_t* id);
+/* Wait for request id (timeout_s < 0: no limit), then release it: phi_host[ny*nx] receives the
+ * scalar flux (may be NULL), *latency_s the submit-to-result time, *queue_s the time before
+ * admission.  Returns the request's status (e.g. ASSN_ERR_UNSTABLE for an inadmissible dt),
+ * ASSN_ERR_TIMEOUT if not finished in time (the request stays pending), ASSN_ERR_ARG for an
+ * unknown id. */
+int assn_server_wait(assn_server* s, int64_t id, double timeout_s, double* phi_host, double* latency_s,
+                     double* queue_s);
+int assn_server_get_stats(assn_server* s, assn_server_stats* out);
+/* Finish every queued and admitted request, stop the loop and free the server.  Results not
+ * collected by assn_server_wait are dropped. */
+int assn_server_destroy(assn_server* s);
+const char* assn_server_last_error(void);
+
 /* ---- Allocation-free total mass (the paper has no counterpart; this serves library users).
  * Some callers cannot allocate device memory during a call: code between the begin and end of a
  * CUDA stream capture, real-time loops that forbid allocator calls, or hosts that run the library

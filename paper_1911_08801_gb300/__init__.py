@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import (ASSN_BF16, ASSN_BF16X3, ASSN_FP32, ASSN_FP64, ASSN_KERNEL_EXP, ASSN_KERNEL_GAUSS,
                    ASSN_NORM_COLUMN, ASSN_NORM_ROW, PRECISIONS, AssnError)
 
-__all__ = ["Problem", "Batch", "AssnError", "PRECISIONS", "ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
+__all__ = ["Problem", "Batch", "Server", "AssnError", "PRECISIONS", "ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
            "ASSN_KERNEL_GAUSS", "ASSN_KERNEL_EXP", "ASSN_NORM_COLUMN", "ASSN_NORM_ROW"]
 
 
@@ -163,6 +163,70 @@ class Batch:
     def close(self):
         if self.handle:
             _lib.assn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop over whole solves with continuous batching (include/assn.h, assn_server_*)."""
+
+    def __init__(self, precision="bf16", hbm_budget_bytes: int = 0, max_active: int = 64, chunk_steps: int = 8,
+                 use_graph: bool = True):
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.handle = None
+        self.handle = _lib.assn_server_create(self.precision, hbm_budget_bytes, max_active, chunk_steps, use_graph)
+        self._shapes: dict[int, tuple[int, int]] = {}
+
+    def submit(self, nx: int, ny: int, x0: float, x1: float, y0: float, y1: float, n_polar: int, n_azim: int,
+               sigma_as: float, eps: float, sigma_a, sigma_s, q, nsteps: int, dt: float, init="line_source",
+               delta: float = 0.03 ** 2, floor_value: float = 1e-4, kernel_kind: int = ASSN_KERNEL_GAUSS,
+               normalisation: int = ASSN_NORM_COLUMN) -> int:
+        """Queue one solve; ``init`` is "line_source", "zero" or a [ny][nx][Q] state.  Returns its id."""
+        sa = np.ascontiguousarray(sigma_a, dtype=np.float64)
+        ss = np.ascontiguousarray(sigma_s, dtype=np.float64)
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        for a in (sa, ss, qq):
+            if a.size != nx * ny:
+                raise ValueError("cell fields must hold ny*nx values")
+        psi = None
+        if isinstance(init, str):
+            kind = {"line_source": _lib.ASSN_INIT_LINE_SOURCE, "zero": _lib.ASSN_INIT_ZERO}[init]
+        else:
+            kind = _lib.ASSN_INIT_STATE
+            psi = np.ascontiguousarray(init, dtype=np.float32)
+            if psi.size != nx * ny * n_polar * n_azim:
+                raise ValueError("state must hold ny*nx*Q values")
+        req = _lib.AssnRequest(nx, ny, x0, x1, y0, y1, n_polar, n_azim, sigma_as, eps, kernel_kind, normalisation,
+                               _lib._d(sa), _lib._d(ss), _lib._d(qq), kind, delta, floor_value,
+                               psi.ctypes.data_as(_lib._fp) if psi is not None else None, nsteps, dt)
+        rid = _lib.assn_server_submit(self.handle, req)
+        self._shapes[rid] = (ny, nx)
+        return rid
+
+    def wait(self, rid: int, timeout_s: float = -1.0):
+        """(scalar flux [ny][nx], latency s, queueing s) of request ``rid``; releases it."""
+        phi = np.empty(self._shapes[rid])
+        lat, qs = _lib.assn_server_wait(self.handle, rid, timeout_s, phi)
+        del self._shapes[rid]
+        return phi, lat, qs
+
+    def stats(self) -> dict:
+        return _lib.assn_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            _lib.assn_server_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

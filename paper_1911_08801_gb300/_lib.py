@@ -35,6 +35,27 @@ _fp = C.POINTER(C.c_float)
 _vp = C.c_void_p
 _h = C.c_void_p
 
+ASSN_INIT_LINE_SOURCE, ASSN_INIT_ZERO, ASSN_INIT_STATE = 0, 1, 2
+
+
+class AssnRequest(C.Structure):
+    """assn_request (include/assn.h)."""
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double),
+                ("y1", C.c_double), ("n_polar", C.c_int), ("n_azim", C.c_int), ("sigma_as", C.c_double),
+                ("eps", C.c_double), ("kernel_kind", C.c_int), ("normalisation", C.c_int),
+                ("sigma_a", _dp), ("sigma_s", _dp), ("q", _dp), ("init_kind", C.c_int), ("delta", C.c_double),
+                ("floor_value", C.c_double), ("psi0", _fp), ("nsteps", C.c_int), ("dt", C.c_double)]
+
+
+class AssnServerStats(C.Structure):
+    """assn_server_stats (include/assn.h)."""
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "failed", "active", "queued", "max_active_seen",
+                                         "launches")] + \
+               [(n, C.c_double) for n in ("p50_latency_s", "p99_latency_s", "mean_latency_s", "busy_s", "wall_s",
+                                          "updates", "updates_per_s")] + \
+               [("budget_bytes", C.c_int64), ("peak_bytes", C.c_int64)]
+
+
 # name -> (restype, argtypes); every function declared in include/assn.h
 SIGNATURES = {
     "assn_create": (C.c_int, [C.POINTER(_h), C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -81,6 +102,13 @@ SIGNATURES = {
                                   C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "assn_batch_last_error": (C.c_char_p, [_h]),
     "assn_autotune": (C.c_int, [_h, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
+    "assn_footprint_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "assn_server_create": (C.c_int, [C.POINTER(_h), C.c_int, C.c_size_t, C.c_int, C.c_int, C.c_int]),
+    "assn_server_submit": (C.c_int, [_h, C.POINTER(AssnRequest), C.POINTER(C.c_int64)]),
+    "assn_server_wait": (C.c_int, [_h, C.c_int64, C.c_double, _dp, _dp, _dp]),
+    "assn_server_get_stats": (C.c_int, [_h, C.POINTER(AssnServerStats)]),
+    "assn_server_destroy": (C.c_int, [_h]),
+    "assn_server_last_error": (C.c_char_p, []),
     "assn_mass_noalloc": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.c_double, _vp, _vp]),
     "assn_noalloc_last_error": (C.c_char_p, []),
 }
@@ -341,6 +369,56 @@ def assn_autotune(h: int, dt: float, use_cache: bool = True) -> dict:
     t, s, ms = C.c_int(0), C.c_int(0), C.c_double(0)
     _check(lib.assn_autotune(h, dt, int(use_cache), C.byref(t), C.byref(s), C.byref(ms)), h)
     return {"tile_cells": t.value, "stages": s.value, "ms_per_step": ms.value}
+
+
+def _scheck(status: int):
+    if status != ASSN_OK:
+        raise AssnError(status, lib.assn_server_last_error().decode())
+
+
+def assn_footprint_bytes(nx: int, ny: int, Q: int, precision: int) -> int:
+    b = C.c_size_t(0)
+    st = lib.assn_footprint_bytes(nx, ny, Q, precision, C.byref(b))
+    if st != ASSN_OK:
+        raise AssnError(st, "invalid sizes")
+    return int(b.value)
+
+
+def assn_server_create(precision: int, hbm_budget_bytes: int = 0, max_active: int = 64, chunk_steps: int = 8,
+                       use_graph: bool = True) -> int:
+    s = _h()
+    _scheck(lib.assn_server_create(C.byref(s), precision, hbm_budget_bytes, max_active, chunk_steps, int(use_graph)))
+    return s.value
+
+
+def assn_server_submit(s: int, req: AssnRequest) -> int:
+    rid = C.c_int64(0)
+    _scheck(lib.assn_server_submit(s, C.byref(req), C.byref(rid)))
+    return int(rid.value)
+
+
+def assn_server_wait(s: int, rid: int, timeout_s: float, phi_out: np.ndarray | None):
+    lat, qs = C.c_double(0), C.c_double(0)
+    ptr = None
+    if phi_out is not None:
+        assert phi_out.dtype == np.float64 and phi_out.flags.c_contiguous
+        ptr = _d(phi_out)
+    _scheck(lib.assn_server_wait(s, rid, timeout_s, ptr, C.byref(lat), C.byref(qs)))
+    return lat.value, qs.value
+
+
+def assn_server_get_stats(s: int) -> dict:
+    st = AssnServerStats()
+    _scheck(lib.assn_server_get_stats(s, C.byref(st)))
+    return {name: getattr(st, name) for name, _ in AssnServerStats._fields_}
+
+
+def assn_server_destroy(s: int) -> None:
+    _scheck(lib.assn_server_destroy(s))
+
+
+def assn_server_last_error() -> str:
+    return lib.assn_server_last_error().decode()
 
 
 def assn_mass_noalloc(psi_dev: int, elem_bytes: int, w_dev: int, ncell: int, Qp: int, h: float, mass_dev: int,
