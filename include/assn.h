@@ -219,16 +219,23 @@ int assn_check_finite(assn_problem* p);
  * set_steps:  change a member's nsteps / dt for later runs.
  * remove:     drop a member (syncs the batch stream).
  * set_tiling: tile cells (0, 32, 64, 128, 256) and ring depth (0 or 2..8) for all members.
- * autotune:   time one launch of every candidate tiling on the members' current states (outputs
- *             go to scratch buffers, no state changes; syncs) and apply the fastest.  With
+ * autotune:   per class, time one launch of every candidate tiling on the members' current states
+ *             (outputs go to scratch buffers, no state changes; syncs) and apply the fastest; the
+ *             outputs describe the class with the most ordinates, *ms_per_launch sums the classes.  With
  *             use_cache != 0 a previous result for the same precision and multiset of
  *             (cells, padded Q) is reused without timing (*ms_per_launch = -1 then).
- * run:        enqueue max_i nsteps_i launches on the batch stream (ordered after each member's
- *             stream; members' streams wait for the run).  use_graph != 0 captures them once as a
- *             CUDA graph and replays it while the membership, tiling, dt and max nsteps stay
- *             the same.  Asynchronous.
+ * Members are grouped into classes by padded ordinate count (multiples of 128): each class has its
+ * own persistent launch per step and its own tile width (wide tiles for few ordinates), so a step
+ * of the batch is at most one launch per class.
+ * run:        enqueue, for each class, max nsteps of its members launches on the batch stream
+ *             (ordered after each member's stream; members' streams wait for the run).
+ *             use_graph != 0 captures them once as a CUDA graph and replays it while the
+ *             membership, tiling, dt and the classes' max nsteps stay the same.  Asynchronous.
  * sync:       wait for the batch stream; ASSN_ERR_TIMEOUT if a bounded device wait gave up.
- * info:       members, tile cells, stages, tiles per launch, launches issued (outputs may be NULL).
+ * info:       members, tile cells and stages of the class with the most ordinates, tiles per step
+ *             summed over classes, launches issued (outputs may be NULL).
+ * classes / class_info: number of classes; for class k (0 = most ordinates) its padded ordinate
+ *             count, members, tile cells, stages and tiles per launch.
  * last_error: message of the last failure on b (b == NULL: last failed create on this thread). */
 typedef struct assn_batch assn_batch;
 int assn_batch_create(assn_batch** out, void* stream);
@@ -242,6 +249,9 @@ int assn_batch_run(assn_batch* b, int use_graph);
 int assn_batch_sync(assn_batch* b);
 int assn_batch_info(assn_batch* b, int* members, int* tile_cells, int* stages, int* total_tiles,
                     int64_t* launches);
+int assn_batch_classes(assn_batch* b, int* nclass);
+int assn_batch_class_info(assn_batch* b, int k, int* ordinate_stride, int* members, int* tile_cells, int* stages,
+                          int* tiles);
 const char* assn_batch_last_error(const assn_batch* b);
 
 /* Autotune one problem's tiling for step size dt the same way (no state change; syncs) and apply

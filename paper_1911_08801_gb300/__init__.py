@@ -160,6 +160,9 @@ class Batch:
     def info(self) -> dict:
         return _lib.assn_batch_info(self.handle)
 
+    def classes(self) -> list[dict]:
+        return _lib.assn_batch_classes(self.handle)
+
     def close(self):
         if self.handle:
             _lib.assn_batch_destroy(self.handle)

@@ -100,6 +100,9 @@ SIGNATURES = {
     "assn_batch_sync": (C.c_int, [_h]),
     "assn_batch_info": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "assn_batch_classes": (C.c_int, [_h, C.POINTER(C.c_int)]),
+    "assn_batch_class_info": (C.c_int, [_h, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "assn_batch_last_error": (C.c_char_p, [_h]),
     "assn_autotune": (C.c_int, [_h, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "assn_footprint_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
@@ -359,6 +362,17 @@ def assn_batch_info(b: int) -> dict:
     _bcheck(lib.assn_batch_info(b, C.byref(m), C.byref(t), C.byref(s), C.byref(n), C.byref(L)), b)
     return {"members": m.value, "tile_cells": t.value, "stages": s.value, "total_tiles": n.value,
             "launches": L.value}
+
+
+def assn_batch_classes(b: int) -> list[dict]:
+    n = C.c_int(0)
+    _bcheck(lib.assn_batch_classes(b, C.byref(n)), b)
+    out = []
+    for k in range(n.value):
+        v = [C.c_int(0) for _ in range(5)]
+        _bcheck(lib.assn_batch_class_info(b, k, *[C.byref(x) for x in v]), b)
+        out.append(dict(zip(("ordinate_stride", "members", "tile_cells", "stages", "tiles"), [x.value for x in v])))
+    return out
 
 
 def assn_batch_last_error(b: int | None) -> str:

@@ -31,13 +31,24 @@ struct assn_batch {
         double dt;
     };
     std::vector<Member> members;
-    Tc2Plan* plan = nullptr;            // for the current membership and tiling
-    std::vector<int> targets;
-    cudaGraphExec_t graph = nullptr;    // nlaunch launches of `plan`
-    int graph_len = 0;
+    // Members grouped by ordinate blocks (Mp / 128): each class has its own plan, tile width and
+    // launch per step, so every class runs at the tile width that suits its ordinate count.
+    struct Class {
+        int Mp = 0;
+        std::vector<int> idx;           // member indices
+        Tc2Plan* plan = nullptr;
+        std::vector<int> targets;
+        int nt = 0, stages = 0;         // requested tiling (0 = automatic)
+        int nmax = 0;                   // launches per run
+    };
+    std::vector<Class> classes;
+    bool planned = false;
+    cudaGraphExec_t graph = nullptr;    // one run: every class's launches
+    std::vector<int> graph_shape;       // nmax per class the graph was captured for
     unsigned int* d_err = nullptr;
     cudaEvent_t done = nullptr;
-    int want_nt = 0, want_stages = 0;   // 0 = automatic
+    int want_nt = 0, want_stages = 0;   // 0 = automatic (per class)
+    bool tuned = false;                 // classes carry autotuned tilings
     std::string err;
     int64_t launches = 0;
 };
@@ -65,12 +76,45 @@ int bfail(assn_batch* b, int status, const char* fmt, ...) {
                          #call, cudaGetErrorString(_e));                                               \
     } while (0)
 
-void drop_plan(assn_batch* b) {
+void drop_graph(assn_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
-    b->graph_len = 0;
-    if (b->plan) tc2_plan_destroy(b->plan);
-    b->plan = nullptr;
+    b->graph_shape.clear();
+}
+
+// Forget plans (membership, dt or tiling changed); tuned tilings are kept unless `untune`.
+void drop_plan(assn_batch* b, bool untune = true) {
+    drop_graph(b);
+    for (auto& c : b->classes)
+        if (c.plan) tc2_plan_destroy(c.plan);
+    if (untune) {
+        b->classes.clear();
+        b->tuned = false;
+    } else {
+        for (auto& c : b->classes) c.plan = nullptr;
+    }
+    b->planned = false;
+}
+
+// Group members into classes by Mp (keeps tilings of existing classes).
+void group(assn_batch* b) {
+    std::vector<assn_batch::Class> old;
+    old.swap(b->classes);
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        const int Mp = b->members[i].p->tc.Mp;
+        auto it = std::find_if(b->classes.begin(), b->classes.end(), [&](const assn_batch::Class& c) { return c.Mp == Mp; });
+        if (it == b->classes.end()) {
+            assn_batch::Class c;
+            c.Mp = Mp;
+            for (auto& o : old)
+                if (o.Mp == Mp) { c.nt = o.nt; c.stages = o.stages; }
+            b->classes.push_back(c);
+            it = b->classes.end() - 1;
+        }
+        it->idx.push_back((int)i);
+    }
+    std::sort(b->classes.begin(), b->classes.end(),
+              [](const assn_batch::Class& x, const assn_batch::Class& y) { return x.Mp > y.Mp; });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -188,22 +232,35 @@ cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int
     return cudaSuccess;
 }
 
-// Builds the plan for the current membership (targets from each member's state and nsteps).
+// Builds the per-class plans for the current membership (targets from each member's state and
+// nsteps), or only refreshes the targets when the plans exist.
 int ensure_batch_plan(assn_batch* b) {
-    const int n = (int)b->members.size();
-    b->targets.resize(n);
-    for (int i = 0; i < n; ++i) b->targets[i] = b->members[i].p->cur + b->members[i].nsteps;
-    if (b->plan) {
-        BK(b, tc2_plan_set_targets(b->plan, b->targets.data(), b->stream));
-        return ASSN_OK;
+    if (!b->planned) {
+        group(b);
+        for (auto& c : b->classes) {
+            std::vector<Tc2Problem> d;
+            for (int i : c.idx) {
+                const assn_batch::Member& m = b->members[i];
+                d.push_back(problem_tc2(m.p, m.dt, m.p->cur + m.nsteps));
+            }
+            const int nt = b->want_nt ? b->want_nt : c.nt, st = b->want_stages ? b->want_stages : c.stages;
+            cudaError_t e = tc2_plan_create(&c.plan, d.data(), (int)d.size(), b->precision == ASSN_BF16X3, nt, st);
+            if (e == cudaErrorNotSupported)
+                return bfail(b, ASSN_ERR_UNSUPPORTED, "batch: tiling %d / %d not supported for Mp = %d", nt, st, c.Mp);
+            BK(b, e);
+        }
+        b->planned = true;
     }
-    std::vector<Tc2Problem> d(n);
-    for (int i = 0; i < n; ++i) d[i] = problem_tc2(b->members[i].p, b->members[i].dt, b->targets[i]);
-    cudaError_t e = tc2_plan_create(&b->plan, d.data(), n, b->precision == ASSN_BF16X3, b->want_nt, b->want_stages);
-    if (e == cudaErrorNotSupported)
-        return bfail(b, ASSN_ERR_UNSUPPORTED, "batch: tiling %d / %d not supported for these members", b->want_nt,
-                     b->want_stages);
-    BK(b, e);
+    for (auto& c : b->classes) {
+        c.targets.resize(c.idx.size());
+        c.nmax = 0;
+        for (size_t k = 0; k < c.idx.size(); ++k) {
+            const assn_batch::Member& m = b->members[c.idx[k]];
+            c.targets[k] = m.p->cur + m.nsteps;
+            c.nmax = std::max(c.nmax, m.nsteps);
+        }
+        BK(b, tc2_plan_set_targets(c.plan, c.targets.data(), b->stream));
+    }
     return ASSN_OK;
 }
 
@@ -285,7 +342,7 @@ int assn_batch_set_steps(assn_batch* b, assn_problem* p, int nsteps, double dt) 
         const int r = problem_prepare(p, dt);
         if (r) return bfail(b, r, "member: %s", p->err.c_str());
         b->members[i].dt = dt;
-        drop_plan(b);   // dt is baked into the descriptors
+        drop_plan(b, false);   // dt is baked into the descriptors
     }
     b->members[i].nsteps = nsteps;
     return ASSN_OK;
@@ -322,24 +379,34 @@ int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stag
             BK(b, cudaStreamSynchronize(m.p->stream));
         }
     }
-    std::vector<Tc2Problem> d;
-    std::vector<int> par;
-    for (auto& m : b->members) {
-        d.push_back(problem_tc2(m.p, m.dt, 1));
-        par.push_back(m.p->cur);
-    }
-    int nt = 0, st = 0;
-    float ms = 0.0f;
-    cudaError_t e = autotune(d, par, b->precision == ASSN_BF16X3, b->stream, &nt, &st, &ms, use_cache != 0);
-    if (e == cudaErrorLaunchTimeout) return bfail(b, ASSN_ERR_TIMEOUT, "autotune: a bounded device wait gave up");
-    if (e == cudaErrorNotSupported) return bfail(b, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits these members");
-    BK(b, e);
-    b->want_nt = nt;
-    b->want_stages = st;
     drop_plan(b);
-    if (tile_cells) *tile_cells = nt;
-    if (stages) *stages = st;
-    if (ms_per_launch) *ms_per_launch = ms;
+    group(b);
+    double total_ms = 0.0;
+    bool all_cached = true;
+    for (auto& c : b->classes) {
+        std::vector<Tc2Problem> d;
+        std::vector<int> par;
+        for (int i : c.idx) {
+            d.push_back(problem_tc2(b->members[i].p, b->members[i].dt, 1));
+            par.push_back(b->members[i].p->cur);
+        }
+        int nt = 0, st = 0;
+        float ms = 0.0f;
+        cudaError_t e = autotune(d, par, b->precision == ASSN_BF16X3, b->stream, &nt, &st, &ms, use_cache != 0);
+        if (e == cudaErrorLaunchTimeout) return bfail(b, ASSN_ERR_TIMEOUT, "autotune: a bounded device wait gave up");
+        if (e == cudaErrorNotSupported) return bfail(b, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits Mp = %d", c.Mp);
+        BK(b, e);
+        c.nt = nt;
+        c.stages = st;
+        if (ms >= 0.0f) { total_ms += ms; all_cached = false; }
+    }
+    b->want_nt = 0;
+    b->want_stages = 0;
+    b->tuned = true;
+    // report the class with the most ordinate blocks (the first)
+    if (tile_cells) *tile_cells = b->classes[0].nt;
+    if (stages) *stages = b->classes[0].stages;
+    if (ms_per_launch) *ms_per_launch = all_cached ? -1.0 : total_ms;
     return ASSN_OK;
 }
 
@@ -364,26 +431,36 @@ int assn_batch_run(assn_batch* b, int use_graph) {
     }
     int r = ensure_batch_plan(b);
     if (r) return r;
+    std::vector<int> shape;
+    for (auto& c : b->classes) shape.push_back(c.nmax);
+    auto enqueue = [&]() -> cudaError_t {
+        // steps of the classes interleaved, one launch per class and step
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < nmax && e == cudaSuccess; ++k)
+            for (auto& c : b->classes)
+                if (k < c.nmax && e == cudaSuccess) e = launch_step_tc2(c.plan, b->d_err, -1, b->stream);
+        return e;
+    };
+    int nlaunch = 0;
+    for (int v : shape) nlaunch += v;
     if (use_graph) {
-        if (!b->graph || b->graph_len != nmax) {
-            if (b->graph) cudaGraphExecDestroy(b->graph);
-            b->graph = nullptr;
+        if (!b->graph || b->graph_shape != shape) {
+            drop_graph(b);
             cudaGraph_t g = nullptr;
             BK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = cudaSuccess;
-            for (int i = 0; i < nmax && e == cudaSuccess; ++i) e = launch_step_tc2(b->plan, b->d_err, -1, b->stream);
+            cudaError_t e = enqueue();
             cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
             if (e == cudaSuccess) e = e2;
             if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
             if (g) cudaGraphDestroy(g);
             BK(b, e);
-            b->graph_len = nmax;
+            b->graph_shape = shape;
         }
         BK(b, cudaGraphLaunch(b->graph, b->stream));
     } else {
-        for (int i = 0; i < nmax; ++i) BK(b, launch_step_tc2(b->plan, b->d_err, -1, b->stream));
+        BK(b, enqueue());
     }
-    b->launches += nmax;
+    b->launches += nlaunch;
     BK(b, cudaEventRecord(b->done, b->stream));
     for (auto& m : b->members) {
         assn_problem* p = m.p;
@@ -418,13 +495,46 @@ int assn_batch_info(assn_batch* b, int* members, int* tile_cells, int* stages, i
         BK(b, cudaSetDevice(b->dev));
         int r = ensure_batch_plan(b);
         if (r) return r;
-        tc2_plan_describe(b->plan, &nt, &st, &cols, &sm);
-        tiles = tc2_plan_total_tiles(b->plan);
+        tc2_plan_describe(b->classes[0].plan, &nt, &st, &cols, &sm);
+        for (auto& c : b->classes) tiles += tc2_plan_total_tiles(c.plan);
     }
     if (tile_cells) *tile_cells = nt;
     if (stages) *stages = st;
     if (total_tiles) *total_tiles = tiles;
     if (launches) *launches = b->launches;
+    return ASSN_OK;
+}
+
+int assn_batch_class_info(assn_batch* b, int k, int* ordinate_stride, int* members, int* tile_cells, int* stages,
+                          int* tiles) {
+    if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    if (!b->members.empty()) {
+        BK(b, cudaSetDevice(b->dev));
+        int r = ensure_batch_plan(b);
+        if (r) return r;
+    }
+    if (k < 0 || k >= (int)b->classes.size()) return bfail(b, ASSN_ERR_ARG, "class %d of %d", k, (int)b->classes.size());
+    const assn_batch::Class& c = b->classes[k];
+    int nt = 0, st = 0, cols = 0;
+    size_t sm = 0;
+    tc2_plan_describe(c.plan, &nt, &st, &cols, &sm);
+    if (ordinate_stride) *ordinate_stride = c.Mp;
+    if (members) *members = (int)c.idx.size();
+    if (tile_cells) *tile_cells = nt;
+    if (stages) *stages = st;
+    if (tiles) *tiles = tc2_plan_total_tiles(c.plan);
+    return ASSN_OK;
+}
+
+int assn_batch_classes(assn_batch* b, int* nclass) {
+    if (!b || !nclass) return bfail(b, ASSN_ERR_ARG, "NULL argument");
+    *nclass = 0;
+    if (!b->members.empty()) {
+        BK(b, cudaSetDevice(b->dev));
+        int r = ensure_batch_plan(b);
+        if (r) return r;
+    }
+    *nclass = (int)b->classes.size();
     return ASSN_OK;
 }
 

@@ -235,3 +235,31 @@ def ensemble(seed: int = 0, count: int = 64, sides=(128, 256, 512), qs=(64, 128,
             s7 = 7 * max(1, round(side / 7))
             out.append(lattice(s7, npol, naz, beta, t_final=3.2, name=f"ens{k}_lat{s7}_Q{Q}"))
     return out
+
+
+def serving_requests(seed: int = 0, count: int = 64, sides=(64, 128, 256, 512, 1024), qs=(64, 128, 256, 512),
+                     beta_range=(0.1, 1.0), t_range=(0.5, 2.0)) -> list[Workload]:
+    """Serving workload: one solve per request, side, Q, beta and t_final drawn from a seed,
+    line source / lattice 50/50 (lattice sides rounded to a multiple of 7)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        side = int(rng.choice(sides))
+        Q = int(rng.choice(qs))
+        beta = float(rng.uniform(*beta_range))
+        t_final = float(rng.uniform(*t_range))
+        npol, naz = QUAD_ORDERS[Q]
+        if rng.uniform() < 0.5:
+            out.append(line_source(side, npol, naz, beta, t_final=t_final, name=f"req{k}_ls{side}_Q{Q}"))
+        else:
+            s7 = 7 * max(1, round(side / 7))
+            out.append(lattice(s7, npol, naz, beta, t_final=t_final, name=f"req{k}_lat{s7}_Q{Q}"))
+    return out
+
+
+def poisson_arrivals(seed: int, count: int, rate: float) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate, starting at 0."""
+    rng = np.random.default_rng(seed + 7919)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    gaps[0] = 0.0
+    return np.cumsum(gaps)

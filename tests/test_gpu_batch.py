@@ -42,6 +42,15 @@ def build(A, precision, wls):
     return probs, dts
 
 
+def launches_per_run(wls, steps):
+    """One launch per step of each class of members with the same ordinate blocks (Q padded to 128)."""
+    cls = {}
+    for wl, n in zip(wls, steps):
+        mp = (wl.Q + 127) // 128
+        cls[mp] = max(cls.get(mp, 0), n)
+    return sum(cls.values())
+
+
 def alone(A, precision, wl, nsteps, dt, tile_cells):
     p = gpu_problem(A, wl, precision)
     p.set_tiling(tile_cells=tile_cells)
@@ -62,7 +71,7 @@ def test_members_equal_alone(A, precision, use_graph):
             b.add(p, n, dt)
         b.run(use_graph=use_graph).sync()
         info = b.info()
-    assert info["members"] == 4 and info["launches"] == max(steps)
+    assert info["members"] == 4 and info["launches"] == launches_per_run(wls, steps)
     for wl, p, n, dt in zip(wls, probs, steps, dts):
         ref = alone(A, precision, wl, n, dt, info["tile_cells"])
         got = p.state()
@@ -82,7 +91,11 @@ def test_rerun_graph_reuse_and_continue(A):
             b.add(p, n, dt)
         b.run().run().sync()
         nt = b.info()["tile_cells"]
-        assert b.info()["launches"] == 2 * max(steps)
+        assert b.info()["launches"] == 2 * launches_per_run(wls, steps)
+        cls = b.classes()
+        assert [c["ordinate_stride"] for c in cls] == [512, 256, 128]
+        assert [c["members"] for c in cls] == [1, 1, 2]
+        assert all(c["tile_cells"] * c["ordinate_stride"] // 128 <= 256 for c in cls)
     probs[0].step(1, dts[0])
     for k, (wl, p, n, dt) in enumerate(zip(wls, probs, steps, dts)):
         total = 2 * n + (1 if k == 0 else 0)
