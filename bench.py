@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="tensor-core tile cells (0 = automatic)")
     ap.add_argument("--stages", type=int, default=0, help="tensor-core kernel-matrix ring depth (0 = automatic)")
     ap.add_argument("--variant", type=int, default=0, help="tensor-core kernel: 0 persistent, 1 one tile per CTA")
-    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serving"],
+    ap.add_argument("--ref-dir", default="", help="accuracy: directory of oracle scalar fluxes <workload>.npy "
+                                                  "(written by --mode oracle-phi); missing ones are computed")
+    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serving", "accuracy", "oracle-phi"],
                     help="step: one solve stepped K times; ensemble: 64 uneven solves to completion in one "
                          "batch; serving: Poisson request stream through the serving loop")
     ap.add_argument("--count", type=int, default=64, help="ensemble members / serving requests")
@@ -145,6 +147,21 @@ def make_problem(A, wl, precision, stream):
     return p
 
 
+def max_over_ranks(ms: float, dist, device: str) -> float:
+    """The slowest rank's time (every rank gets it); ``dist`` None on one process."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Units all ranks processed (independent replicas, one per rank) over the slowest rank's time."""
+    return units_per_rank_step * steps * world / (ms_max / 1e3)
+
+
 def seeded_state_f32(wl, seed=0):
     rng = np.random.default_rng(seed)
     return rng.random((wl.ny, wl.nx, wl.Q), dtype=np.float32)
@@ -194,13 +211,9 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     launches = prob.launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_per_step = ms / args.steps
-    value = units * args.steps * world / (ms / 1e3)
+    value = whole_job_rate(units, args.steps, world, ms)
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -488,6 +501,63 @@ def run_serving(args):
     }
 
 
+def oracle_phi(wl):
+    """Scalar flux of the FP64 oracle after the workload's whole run, and the seconds it took."""
+    import oracle as O
+
+    n, dt = wl.steps()
+    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
+    K = O.kernel_matrix(Om, w, wl.eps)
+    sa, ss, q = wl.materials()
+    t0 = time.perf_counter()
+    psi = O.run(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    return O.scalar_flux(psi, w), time.perf_counter() - t0
+
+
+def run_oracle_phi(args):
+    """Write the oracle's scalar flux of --workload to <ref-dir>/<workload>.npy (host only)."""
+    wl = synth.WORKLOADS[args.workload]
+    phi, sec = oracle_phi(wl)
+    os.makedirs(args.ref_dir or ".", exist_ok=True)
+    path = os.path.join(args.ref_dir or ".", wl.name + ".npy")
+    np.save(path, phi)
+    return {"mode": "oracle-phi", "workload": wl.name, "path": path, "oracle_s": sec, "cores": os.cpu_count()}
+
+
+def run_accuracy(args):
+    """Relative L2 error of the scalar flux after whole runs, each GPU precision against the FP64 oracle
+    on the same inputs: the 64^2 line source (Q = 128, t = 1), the 256^2 line source (Q = 256, t = 1) and
+    the 448^2 lattice (Q = 512, t = 3.2).  The oracle runs on the host cores (numpy FP64)."""
+    import torch
+
+    import paper_1911_08801_gb300 as A
+
+    torch.cuda.set_device(0)
+    cases = [synth.LINE_SOURCE_64, synth.LINE_SOURCE_256_ACC, synth.LATTICE_448]
+    if args.count < 3:
+        cases = cases[:max(1, args.count)]
+    out = []
+    for wl in cases:
+        n, dt = wl.steps()
+        ref = os.path.join(args.ref_dir, wl.name + ".npy") if args.ref_dir else ""
+        if ref and os.path.exists(ref):
+            phi_ref, t_oracle = np.load(ref), None
+        else:
+            phi_ref, t_oracle = oracle_phi(wl)
+        row = {"workload": wl.name, "steps": n, "dt": dt, "oracle_s": t_oracle, "rel_l2": {}}
+        for prec in ("fp64", "fp32", "bf16", "bf16x3"):
+            p = make_problem(A, wl, prec, None)
+            if wl.kind == "line_source":
+                p.init_line_source()
+            p.step(n, dt)
+            phi = p.scalar_flux()
+            p.close()
+            row["rel_l2"][prec] = float(np.linalg.norm(phi - phi_ref) / np.linalg.norm(phi_ref))
+        out.append(row)
+    return {"mode": "accuracy", "metric": "relative L2 error of the scalar flux vs the FP64 oracle",
+            "cores": os.cpu_count(), "cases": out}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -496,9 +566,12 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
+    if args.mode == "oracle-phi":
+        print(json.dumps(run_oracle_phi(args)), flush=True)
+        return
     if args.mode != "step":
         if rank == 0:
-            line = run_ensemble(args) if args.mode == "ensemble" else run_serving(args)
+            line = {"ensemble": run_ensemble, "serving": run_serving, "accuracy": run_accuracy}[args.mode](args)
             print(json.dumps(line), flush=True)
         return
     dist = None

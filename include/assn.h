@@ -123,7 +123,7 @@ int assn_set_cross_sections(assn_problem* p, const double* sigma_a, const double
                             const double* q);
 
 /* Artificial scattering strength sigma_as >= 0 (Sec. 2.3, constant in space) and kernel
- * width eps > 0 (Sec. 2.4: eps = beta/N_q in the paper; callers pass eps directly).
+ * width eps > 0 (Sec. 2.3: eps = beta/N_q in the paper; callers pass eps directly).
  * Builds K on the device in FP64 (one block per normalised line) and derives the operands
  * of the selected precision.  Requires a quadrature.  Errors: ASSN_ERR_ARG, ASSN_ERR_STATE. */
 int assn_set_artificial_scattering(assn_problem* p, double sigma_as, double eps, int kernel_kind,
@@ -224,9 +224,9 @@ int assn_check_finite(assn_problem* p);
  *             outputs describe the class with the most ordinates, *ms_per_launch sums the classes.  With
  *             use_cache != 0 a previous result for the same precision and multiset of
  *             (cells, padded Q) is reused without timing (*ms_per_launch = -1 then).
- * Members are grouped into classes by padded ordinate count (multiples of 128): each class has its
- * own persistent launch per step and its own tile width (wide tiles for few ordinates), so a step
- * of the batch is at most one launch per class.
+ * Members are grouped into classes by padded ordinate count (Q rounded up to a multiple of 64):
+ * each class has its own persistent launch per step and its own tile width (wide tiles for few
+ * ordinates), so a step of the batch is one launch per class.
  * run:        enqueue, for each class, max nsteps of its members launches on the batch stream
  *             (ordered after each member's stream; members' streams wait for the run).
  *             use_graph != 0 captures them once as a CUDA graph and replays it while the

@@ -31,10 +31,11 @@ struct assn_batch {
         double dt;
     };
     std::vector<Member> members;
-    // Members grouped by ordinate blocks (Mp / 128): each class has its own plan, tile width and
-    // launch per step, so every class runs at the tile width that suits its ordinate count.
+    // Members grouped by padded ordinate count Qp: each class has its own plan, tile width and
+    // launch per step, so every class runs at the tile width that suits its ordinate count and on
+    // the kernel instance compiled for its ordinate stride.
     struct Class {
-        int Mp = 0;
+        int Qp = 0;
         std::vector<int> idx;           // member indices
         Tc2Plan* plan = nullptr;
         std::vector<int> targets;
@@ -96,25 +97,25 @@ void drop_plan(assn_batch* b, bool untune = true) {
     b->planned = false;
 }
 
-// Group members into classes by Mp (keeps tilings of existing classes).
+// Group members into classes by Qp (keeps tilings of existing classes).
 void group(assn_batch* b) {
     std::vector<assn_batch::Class> old;
     old.swap(b->classes);
     for (size_t i = 0; i < b->members.size(); ++i) {
-        const int Mp = b->members[i].p->tc.Mp;
-        auto it = std::find_if(b->classes.begin(), b->classes.end(), [&](const assn_batch::Class& c) { return c.Mp == Mp; });
+        const int Qp = b->members[i].p->Qp;
+        auto it = std::find_if(b->classes.begin(), b->classes.end(), [&](const assn_batch::Class& c) { return c.Qp == Qp; });
         if (it == b->classes.end()) {
             assn_batch::Class c;
-            c.Mp = Mp;
+            c.Qp = Qp;
             for (auto& o : old)
-                if (o.Mp == Mp) { c.nt = o.nt; c.stages = o.stages; }
+                if (o.Qp == Qp) { c.nt = o.nt; c.stages = o.stages; }
             b->classes.push_back(c);
             it = b->classes.end() - 1;
         }
         it->idx.push_back((int)i);
     }
     std::sort(b->classes.begin(), b->classes.end(),
-              [](const assn_batch::Class& x, const assn_batch::Class& y) { return x.Mp > y.Mp; });
+              [](const assn_batch::Class& x, const assn_batch::Class& y) { return x.Qp > y.Qp; });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -246,7 +247,7 @@ int ensure_batch_plan(assn_batch* b) {
             const int nt = b->want_nt ? b->want_nt : c.nt, st = b->want_stages ? b->want_stages : c.stages;
             cudaError_t e = tc2_plan_create(&c.plan, d.data(), (int)d.size(), b->precision == ASSN_BF16X3, nt, st);
             if (e == cudaErrorNotSupported)
-                return bfail(b, ASSN_ERR_UNSUPPORTED, "batch: tiling %d / %d not supported for Mp = %d", nt, st, c.Mp);
+                return bfail(b, ASSN_ERR_UNSUPPORTED, "batch: tiling %d / %d not supported for Qp = %d", nt, st, c.Qp);
             BK(b, e);
         }
         b->planned = true;
@@ -394,7 +395,7 @@ int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stag
         float ms = 0.0f;
         cudaError_t e = autotune(d, par, b->precision == ASSN_BF16X3, b->stream, &nt, &st, &ms, use_cache != 0);
         if (e == cudaErrorLaunchTimeout) return bfail(b, ASSN_ERR_TIMEOUT, "autotune: a bounded device wait gave up");
-        if (e == cudaErrorNotSupported) return bfail(b, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits Mp = %d", c.Mp);
+        if (e == cudaErrorNotSupported) return bfail(b, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits Qp = %d", c.Qp);
         BK(b, e);
         c.nt = nt;
         c.stages = st;
@@ -518,7 +519,7 @@ int assn_batch_class_info(assn_batch* b, int k, int* ordinate_stride, int* membe
     int nt = 0, st = 0, cols = 0;
     size_t sm = 0;
     tc2_plan_describe(c.plan, &nt, &st, &cols, &sm);
-    if (ordinate_stride) *ordinate_stride = c.Mp;
+    if (ordinate_stride) *ordinate_stride = c.Qp;
     if (members) *members = (int)c.idx.size();
     if (tile_cells) *tile_cells = nt;
     if (stages) *stages = st;

@@ -23,7 +23,7 @@ FOUR_PI = 4.0 * math.pi
 def eps_from_beta(beta: float, Q: int) -> float:
     """Kernel width eps = beta * h_Q, h_Q = sqrt(4 pi / Q) the mean angular spacing.
 
-    The paper sets eps = beta / N_q (Sec. 2.4, Sec. 4.1); the workloads here
+    The paper sets eps = beta / N_q (Sec. 2.3, Sec. 4.1); the workloads here
     state beta "scaled by the ordinate spacing", read as beta * sqrt(4 pi/Q).
     """
     return float(beta) * math.sqrt(FOUR_PI / Q)

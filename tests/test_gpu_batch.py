@@ -43,10 +43,10 @@ def build(A, precision, wls):
 
 
 def launches_per_run(wls, steps):
-    """One launch per step of each class of members with the same ordinate blocks (Q padded to 128)."""
+    """One launch per step of each class of members with the same padded ordinate count."""
     cls = {}
     for wl, n in zip(wls, steps):
-        mp = (wl.Q + 127) // 128
+        mp = (wl.Q + 63) // 64
         cls[mp] = max(cls.get(mp, 0), n)
     return sum(cls.values())
 
@@ -93,8 +93,8 @@ def test_rerun_graph_reuse_and_continue(A):
         nt = b.info()["tile_cells"]
         assert b.info()["launches"] == 2 * launches_per_run(wls, steps)
         cls = b.classes()
-        assert [c["ordinate_stride"] for c in cls] == [512, 256, 128]
-        assert [c["members"] for c in cls] == [1, 1, 2]
+        assert [c["ordinate_stride"] for c in cls] == [512, 256, 128, 64]
+        assert [c["members"] for c in cls] == [1, 1, 1, 1]
         assert all(c["tile_cells"] * c["ordinate_stride"] // 128 <= 256 for c in cls)
     probs[0].step(1, dts[0])
     for k, (wl, p, n, dt) in enumerate(zip(wls, probs, steps, dts)):

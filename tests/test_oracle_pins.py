@@ -73,7 +73,7 @@ def test_quadrature_azimuths_avoid_axes():
 
 # ----------------------------------------------------------------------------- kernel (S1)
 def p_closed(eps, i):
-    """Transport coefficient p_{eps,i} = int (1-mu)^i s_eps dmu in closed form (Sec. 2.4).
+    """Transport coefficient p_{eps,i} = int (1-mu)^i s_eps dmu in closed form (Sec. 2.5).
 
     With y = (1-mu)/eps and t = y^2 the integral is
     eps^i / (sqrt(pi) Erf(2/eps)) * gamma_lower((1+i)/2, 4/eps^2).
@@ -98,7 +98,7 @@ def test_s_eps_unit_mass_and_transport_coefficients(eps):
 
 
 def test_s_eps_dirac_sequence_and_order():
-    """int s_eps f -> f(1) as eps -> 0, and p_{eps,1} = O(eps) (Sec. 2.3, 2.4)."""
+    """int s_eps f -> f(1) as eps -> 0, and p_{eps,1} = O(eps) (Sec. 2.3, 2.5)."""
     f = lambda m: math.cos(m) + m ** 3
     for eps in (1e-2, 1e-3):
         val, _ = integrate.quad(lambda m: f(m) * float(O.s_eps(m, eps)), -1, 1, points=[1 - 10 * eps, 1],
@@ -141,7 +141,7 @@ def legendre(l, x):
 def test_kernel_funk_hecke_eigenvalues(normalisation):
     """Funk-Hecke: the normalised kernel maps P_l(Omega . e) to lambda_l P_l(Omega . e) with
     lambda_l = int_{-1}^{1} s_eps(mu) P_l(mu) dmu; lambda_1 = 1 - p_1, lambda_2 = 1 - 3 p_1 + 3/2 p_2
-    (the modified-equation coefficients of Sec. 2.4).  Fine quadrature, so c_q ~ const."""
+    (the modified-equation coefficients of Sec. 2.5).  Fine quadrature, so c_q ~ const."""
     eps = 0.3
     Om, w = O.product_quadrature(32, 64)
     K = O.kernel_matrix(Om, w, eps, normalisation=normalisation)
@@ -159,7 +159,7 @@ def test_kernel_funk_hecke_eigenvalues(normalisation):
 
 
 def test_kernel_eps_to_zero_is_identity():
-    """beta -> 0: s_eps underflows off the diagonal, K = I exactly and as-S_N is S_N (Sec. 2.4)."""
+    """beta -> 0: s_eps underflows off the diagonal, K = I exactly and as-S_N is S_N (Sec. 2.3)."""
     Om, w = O.product_quadrature(8, 16)
     for kind in ("gauss", "exp"):
         K = O.kernel_matrix(Om, w, 1e-4, kind=kind)
