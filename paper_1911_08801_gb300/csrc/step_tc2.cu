@@ -72,7 +72,7 @@ namespace {
 using namespace ptx;
 
 constexpr int kEW = 4;                  // epilogue warps per TMEM lane quarter
-constexpr int kCH = 8;                  // cells per epilogue chunk
+constexpr int kCH = 8;                  // cells per epilogue chunk (double-buffered form)
 constexpr int kEpiWarps = 4 * kEW;
 constexpr int kWarps = 7 + kEpiWarps;
 constexpr int kThreads2 = kWarps * 32;
@@ -441,14 +441,19 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
         }
     } else {
         // -------------------------------------------------------------------- epilogue
-        // Chunks of kCH cells x 32 ordinates.  The flux values of the next chunk (own cells, the
-        // two x-edge cells, the upwind y-neighbours) are loaded into registers while the current
-        // one is computed.  The flux input is read-only during the launch, so these loads may run
-        // ahead of the MMA (and into the next tile).
+        // Chunks of kCHe cells x 32 ordinates.  The warp's time per chunk is set by the latency of
+        // its flux loads (own cells, the two x-edge cells, the upwind y-neighbours), so what counts
+        // is how many bytes a warp keeps in flight: the one-pass kernel loads 16-cell chunks and
+        // waits for them (one buffer); the split kernel, whose MMA work is three times longer,
+        // keeps 8-cell chunks double-buffered (the next chunk's loads in flight while the current
+        // one is computed).  The flux input is read-only during the launch, so loads may run ahead
+        // of the MMA (and into the next tile).
         const int e = warp - 7;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
         const int grp = e >> 2;                // which part (of kEW) of the tile's cells
-        constexpr int CPH = NT / (kEW * kCH);  // chunks per part of the tile and ordinate block
+        constexpr bool kOneBuf = !SPLIT && NT / kEW >= 16;
+        constexpr int kCHe = kOneBuf ? 16 : kCH;
+        constexpr int CPH = NT / (kEW * kCHe);  // chunks per part of the tile and ordinate block
 
         // Position of a chunk: global tile T of problem pid, the it-th active tile of this CTA,
         // chunk r within that tile (cpt chunks per tile).
@@ -466,37 +471,37 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
         static_assert(sizeof(TileP) <= 64, "tile parameter slot");
 
         // Flux loads of chunk r (ordinate block m = r / CPH) of a tile into registers.
-        auto load = [&](const TileP& t, int r, float (&s)[kCH], float (&u)[kCH], float& lft, float& rgt) {
+        auto load = [&](const TileP& t, int r, float (&s)[kCHe], float (&u)[kCHe], float& lft, float& rgt) {
             const int Qp = QP > 0 ? QP : t.Qp;
             const int m = r / CPH;
-            const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCH;
+            const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCHe;
             const int ncell = t.ncell, nx = t.nx;
             const int fb = t.fb0 + c0;
             const int q = m * 128 + lq * 32 + lane;
             const bool live = q < t.Q && fb < ncell;
             const float nuy = live ? __ldg(&t.ord[q].nuy) : 0.0f;
             const float* b = t.in + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
-            const bool full = fb + kCH <= ncell;
+            const bool full = fb + kCHe <= ncell;
 #pragma unroll
-            for (int i = 0; i < kCH; ++i) s[i] = (live && (full || fb + i < ncell)) ? __ldg(b + i * Qp) : 0.0f;
+            for (int i = 0; i < kCHe; ++i) s[i] = (live && (full || fb + i < ncell)) ? __ldg(b + i * Qp) : 0.0f;
             // y-neighbour of cell f: below (f - nx) for nuy > 0, above (f + nx) for nuy < 0
             const long dyo = nuy > 0.f ? -(long)nx * Qp : (long)nx * Qp;
             const float* by = b + dyo;
-            const bool yall = nuy > 0.f ? fb >= nx : fb + kCH + nx <= ncell;
+            const bool yall = nuy > 0.f ? fb >= nx : fb + kCHe + nx <= ncell;
 #pragma unroll
-            for (int i = 0; i < kCH; ++i) {
+            for (int i = 0; i < kCHe; ++i) {
                 const int f = fb + i;
                 const bool ok = live && nuy != 0.f && (yall || (nuy > 0.f ? f >= nx : f + nx < ncell));
                 u[i] = ok ? __ldg(by + i * Qp) : 0.0f;
             }
             lft = (live && fb >= 1) ? __ldg(b - Qp) : 0.0f;
-            rgt = (live && fb + kCH < ncell) ? __ldg(b + kCH * Qp) : 0.0f;
+            rgt = (live && fb + kCHe < ncell) ? __ldg(b + kCHe * Qp) : 0.0f;
         };
         // Update of chunk r of the it-th tile of this CTA (cpt chunks per tile); false on abort.
-        auto compute = [&](const TileP& t, int it, int r, int cpt, const float (&s)[kCH], const float (&u)[kCH],
+        auto compute = [&](const TileP& t, int it, int r, int cpt, const float (&s)[kCHe], const float (&u)[kCHe],
                            float lft, float rgt) -> bool {
             const int m = r / CPH;
-            const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCH;
+            const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCHe;
             const int buf = it & 1;
             if (r == 0) {
                 const uint32_t use = (uint32_t)(it >> 1);
@@ -507,9 +512,9 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 if (!go) return false;
                 tc_fence_after();
             }
-            float y[kCH];
+            float y[kCHe];
             __syncwarp();
-            tmem_ld<kCH>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0), y);
+            tmem_ld<kCHe>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0), y);
             const int Qp = QP > 0 ? QP : t.Qp;
             const int ncell = t.ncell;
             const int fb = t.fb0 + c0;
@@ -519,7 +524,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 const float4* cb = coef + buf * NT + c0;
                 if (q >= t.Q) {
 #pragma unroll
-                    for (int i = 0; i < kCH; ++i)
+                    for (int i = 0; i < kCHe; ++i)
                         if (fb + i < ncell) __stcs(po + i * Qp, 0.0f);
                 } else {
                     const float4 o4 = __ldg(reinterpret_cast<const float4*>(t.ord) + q);
@@ -528,12 +533,12 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                     const float ge = dts * o4.w;
                     const int xbit = o4.x > 0.f ? 1 : (o4.x < 0.f ? 2 : 0);
 #pragma unroll
-                    for (int i = 0; i < kCH; ++i) {
+                    for (int i = 0; i < kCHe; ++i) {
                         const float4 cf = cb[i];
                         const int bits = __float_as_int(cf.z);
                         if (!(bits & 16)) continue;
                         const float sf = s[i];
-                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < kCH - 1 ? s[i + 1] : rgt);
+                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < kCHe - 1 ? s[i + 1] : rgt);
                         upx = (bits & xbit) ? upx : 0.0f;
                         const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
                         float out = fmaf(sf, cf.x - axy, cf.y);
@@ -556,7 +561,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             return true;
         };
 
-        float s0[kCH], u0[kCH], l0 = 0.f, r0 = 0.f, s1[kCH], u1[kCH], l1 = 0.f, r1 = 0.f;
+        float s0[kCHe], u0[kCHe], l0 = 0.f, r0 = 0.f;
         if (a.one_fixed) {
             // One problem: its tiles blockIdx.x, blockIdx.x + gridDim.x, ... (all or none active);
             // chunk k of this warp is chunk k % cpt of the (k / cpt)-th of them.
@@ -571,6 +576,14 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                              QP > 0 ? QP : a.one.Qp, a.one.dts};
             };
             int it, r;
+            if constexpr (kOneBuf) {
+                for (int k = 0; k < nchunk; ++k) {
+                    const TileP t = view(k, it, r);
+                    load(t, r, s0, u0, l0, r0);
+                    if (!compute(t, it, r, cpt, s0, u0, l0, r0)) break;
+                }
+            } else {
+            float s1[kCHe], u1[kCHe], l1 = 0.f, r1 = 0.f;
             if (nchunk > 0) load(view(0, it, r), r, s0, u0, l0, r0);
             for (int k = 0; k < nchunk; k += 2) {
                 if (k + 1 < nchunk) { const TileP t = view(k + 1, it, r); load(t, r, s1, u1, l1, r1); }
@@ -578,6 +591,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 if (k + 1 >= nchunk) break;
                 if (k + 2 < nchunk) { const TileP t = view(k + 2, it, r); load(t, r, s0, u0, l0, r0); }
                 { const TileP t = view(k + 1, it, r); if (!compute(t, it, r, cpt, s1, u1, l1, r1)) break; }
+            }
             }
         } else {
             // Several problems: walk the active tiles; the tile's parameters sit in this warp's
@@ -634,6 +648,14 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             cur.cpt = 1;
             cur.T = next_tile(blockIdx.x, cur.pid);
             fill(cur);
+            if constexpr (kOneBuf) {
+                while (cur.T < total) {
+                    load(slot(cur.it), cur.r, s0, u0, l0, r0);
+                    if (!compute(slot(cur.it), cur.it, cur.r, cur.cpt, s0, u0, l0, r0)) break;
+                    advance(cur);
+                }
+            } else {
+            float s1[kCHe], u1[kCHe], l1 = 0.f, r1 = 0.f;
             if (cur.T < total) load(slot(cur.it), cur.r, s0, u0, l0, r0);
             while (cur.T < total) {
                 Pos nxt = cur;
@@ -647,6 +669,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 if (nxt.T < total) load(slot(nxt.it), nxt.r, s0, u0, l0, r0);
                 if (!compute(slot(cur.it), cur.it, cur.r, cur.cpt, s1, u1, l1, r1)) break;
                 cur = nxt;
+            }
             }
         }
     }
