@@ -178,6 +178,15 @@ int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt,
  * combination does not fit the SM. */
 int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant);
 
+/* Rings of the persistent kernel (variant 0; BF16 / BF16X3 problems): depths of the staging ring
+ * (FP32 flux chunks fed by TMA), the operand ring (BF16 chunks written by the converter warps) and
+ * the kernel-matrix ring (2..8 each; 0 = automatic), and the ordinate blocks of 128 that one
+ * kernel-matrix request brings (1, 2, 4, 8; 0 = automatic).  Results do not depend on these
+ * choices.  Selects variant 0.  get_rings reports the resolved values (any pointer may be NULL);
+ * ASSN_ERR_UNSUPPORTED at the next step / get if the rings do not fit shared memory. */
+int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix, int blocks_per_request);
+int assn_get_rings(assn_problem* p, int* staging, int* operand, int* kernel_matrix, int* blocks_per_request);
+
 /* The tiling the next step will use (resolving automatic choices): tile cells, ring stages,
  * tensor-memory columns and dynamic shared memory per CTA.  Any output pointer may be NULL. */
 int assn_get_tiling(assn_problem* p, int* tile_cells, int* stages, int* tmem_cols, int64_t* smem_bytes);
@@ -219,9 +228,10 @@ int assn_check_finite(assn_problem* p);
  * set_steps:  change a member's nsteps / dt for later runs.
  * remove:     drop a member (syncs the batch stream).
  * set_tiling: tile cells (0, 32, 64, 128, 256) and ring depth (0 or 2..8) for all members.
- * autotune:   per class, time one launch of every candidate tiling on the members' current states
- *             (outputs go to scratch buffers, no state changes; syncs) and apply the fastest; the
- *             outputs describe the class with the most ordinates, *ms_per_launch sums the classes.  With
+ * autotune:   per class, time one launch of every candidate tiling (tile widths x ring shapes) on the
+ *             members' current states (outputs go to scratch buffers, no state changes; syncs) and
+ *             apply the fastest; the outputs describe the class with the most ordinates (*stages =
+ *             its kernel-matrix ring depth), *ms_per_launch sums the classes.  With
  *             use_cache != 0 a previous result for the same precision and multiset of
  *             (cells, padded Q) is reused without timing (*ms_per_launch = -1 then).
  * Members are grouped into classes by padded ordinate count (Q rounded up to a multiple of 64):
@@ -255,7 +265,8 @@ int assn_batch_class_info(assn_batch* b, int k, int* ordinate_stride, int* membe
 const char* assn_batch_last_error(const assn_batch* b);
 
 /* Autotune one problem's tiling for step size dt the same way (no state change; syncs) and apply
- * it as assn_set_tiling(p, tile_cells, stages, 0) would.  Outputs may be NULL. */
+ * it (tile width and rings, as assn_set_tiling + assn_set_rings would); *stages receives the
+ * kernel-matrix ring depth.  Outputs may be NULL. */
 int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, int* stages, double* ms_per_step);
 
 /* ---- Serving: a request loop over whole solves (continuous batching).

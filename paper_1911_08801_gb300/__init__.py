@@ -90,6 +90,13 @@ class Problem:
     def tiling(self) -> dict:
         return _lib.assn_get_tiling(self.handle)
 
+    def set_rings(self, staging: int = 0, operand: int = 0, kernel_matrix: int = 0, blocks_per_request: int = 0):
+        _lib.assn_set_rings(self.handle, staging, operand, kernel_matrix, blocks_per_request)
+        return self
+
+    def rings(self) -> dict:
+        return _lib.assn_get_rings(self.handle)
+
     def autotune(self, dt: float, use_cache: bool = True) -> dict:
         return _lib.assn_autotune(self.handle, dt, use_cache)
 

@@ -77,6 +77,9 @@ SIGNATURES = {
     "assn_step_device": (C.c_int, [_h, _vp, _vp, C.c_double]),
     "assn_run_f32": (C.c_int, [_h, _fp, C.c_int, C.c_double, _dp]),
     "assn_set_tiling": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
+    "assn_set_rings": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "assn_get_rings": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)]),
     "assn_get_tiling": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int64)]),
     "assn_layout": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -259,6 +262,17 @@ def assn_run_f32(h: int, psi0: np.ndarray, nsteps: int, dt: float, phi_out: np.n
 
 def assn_set_tiling(h: int, tile_cells: int = 0, stages: int = 0, variant: int = 0) -> None:
     _check(lib.assn_set_tiling(h, tile_cells, stages, variant), h)
+
+
+def assn_set_rings(h: int, staging: int = 0, operand: int = 0, kernel_matrix: int = 0,
+                   blocks_per_request: int = 0) -> None:
+    _check(lib.assn_set_rings(h, staging, operand, kernel_matrix, blocks_per_request), h)
+
+
+def assn_get_rings(h: int) -> dict:
+    v = [C.c_int(0) for _ in range(4)]
+    _check(lib.assn_get_rings(h, *[C.byref(x) for x in v]), h)
+    return dict(zip(("staging", "operand", "kernel_matrix", "blocks_per_request"), [x.value for x in v]))
 
 
 def assn_get_tiling(h: int) -> dict:

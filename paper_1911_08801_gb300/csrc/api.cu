@@ -611,7 +611,7 @@ static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
         if (p->plan2) tc2_plan_destroy(p->plan2);
         p->plan2 = nullptr;
         const Tc2Problem d = problem_tc2(p, dt, 0x7fffffff);
-        e = tc2_plan_create(&p->plan2, &d, 1, p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
+        e = tc2_plan_create(&p->plan2, &d, 1, p->precision == ASSN_BF16X3, p->want_nt, p->want_rings);
         if (e == cudaSuccess) p->plan2_dt = dt;
     }
     if (e == cudaErrorNotSupported)
@@ -680,11 +680,47 @@ int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant) {
     if (variant != 0 && variant != 1) return fail(p, ASSN_ERR_ARG, "variant must be 0 or 1");
     p->want_nt = tile_cells;
     p->want_stages = stages;
+    p->want_rings = TcRings{stages, stages, stages, 0};
     p->variant = variant;
     if (p->plan) tc_plan_destroy(p->plan);
     p->plan = nullptr;
     if (p->plan2) tc2_plan_destroy(p->plan2);
     p->plan2 = nullptr;
+    return ASSN_OK;
+}
+
+int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix, int blocks_per_request) {
+    if (!p) return ASSN_ERR_ARG;
+    auto bad = [](int v) { return v != 0 && (v < 2 || v > 8); };
+    if (bad(staging) || bad(operand) || bad(kernel_matrix))
+        return fail(p, ASSN_ERR_ARG, "ring depths must be 0 or 2..8");
+    if (blocks_per_request != 0 && blocks_per_request != 1 && blocks_per_request != 2 && blocks_per_request != 4 &&
+        blocks_per_request != 8)
+        return fail(p, ASSN_ERR_ARG, "blocks_per_request must be 0, 1, 2, 4 or 8");
+    p->want_rings = TcRings{staging, operand, kernel_matrix, blocks_per_request};
+    p->variant = 0;
+    if (p->plan2) tc2_plan_destroy(p->plan2);
+    p->plan2 = nullptr;
+    return ASSN_OK;
+}
+
+int assn_get_rings(assn_problem* p, int* staging, int* operand, int* kernel_matrix, int* blocks_per_request) {
+    if (!p) return ASSN_ERR_ARG;
+    if (!p->tensor()) return fail(p, ASSN_ERR_UNSUPPORTED, "rings apply to the tensor-core precisions");
+    int r = ready(p);
+    if (r) return r;
+    r = set_device(p);
+    if (r) return r;
+    const int v = p->variant;
+    p->variant = 0;
+    r = ensure_plan(p, p->plan2_dt > 0 ? p->plan2_dt : 1.0, false);
+    p->variant = v;
+    if (r) return r;
+    const TcRings g = tc2_plan_rings(p->plan2);
+    if (staging) *staging = g.SS;
+    if (operand) *operand = g.SB;
+    if (kernel_matrix) *kernel_matrix = g.SA;
+    if (blocks_per_request) *blocks_per_request = g.MPR;
     return ASSN_OK;
 }
 

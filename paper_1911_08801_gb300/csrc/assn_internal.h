@@ -82,11 +82,17 @@ struct Tc2Problem {
     int nx, ny, Q, Qp, Mp;
     float dt, dt_sigma_as;
 };
+// Ring request of the persistent kernel: staging (FP32 flux chunks), operand (BF16 B chunks) and
+// kernel-matrix ring depths, and ordinate blocks per kernel-matrix request; 0 = automatic.
+struct TcRings {
+    int SS = 0, SB = 0, SA = 0, MPR = 0;
+};
 struct Tc2Plan;
 cudaError_t tc2_plan_create(Tc2Plan** plan, const Tc2Problem* probs, int nprob, bool split, int want_nt,
-                            int want_stages);
+                            TcRings rings);
 void tc2_plan_destroy(Tc2Plan* plan);
 void tc2_plan_describe(const Tc2Plan* plan, int* tile_cells, int* stages, int* tmem_cols, size_t* smem);
+TcRings tc2_plan_rings(const Tc2Plan* plan);
 int tc2_plan_total_tiles(const Tc2Plan* plan);
 // New step targets (one per problem, in plan order) for later launches on `s`.
 cudaError_t tc2_plan_set_targets(Tc2Plan* plan, const int* targets, cudaStream_t s);

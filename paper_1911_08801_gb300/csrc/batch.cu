@@ -39,7 +39,8 @@ struct assn_batch {
         std::vector<int> idx;           // member indices
         Tc2Plan* plan = nullptr;
         std::vector<int> targets;
-        int nt = 0, stages = 0;         // requested tiling (0 = automatic)
+        int nt = 0;                     // requested tile width (0 = automatic)
+        TcRings rings;                  // requested rings (zero fields automatic)
         int nmax = 0;                   // launches per run
     };
     std::vector<Class> classes;
@@ -48,7 +49,8 @@ struct assn_batch {
     std::vector<int> graph_shape;       // nmax per class the graph was captured for
     unsigned int* d_err = nullptr;
     cudaEvent_t done = nullptr;
-    int want_nt = 0, want_stages = 0;   // 0 = automatic (per class)
+    int want_nt = 0;                    // 0 = automatic (per class)
+    TcRings want_rings;                 // zero fields automatic (per class)
     bool tuned = false;                 // classes carry autotuned tilings
     std::string err;
     int64_t launches = 0;
@@ -108,7 +110,7 @@ void group(assn_batch* b) {
             assn_batch::Class c;
             c.Qp = Qp;
             for (auto& o : old)
-                if (o.Qp == Qp) { c.nt = o.nt; c.stages = o.stages; }
+                if (o.Qp == Qp) { c.nt = o.nt; c.rings = o.rings; }
             b->classes.push_back(c);
             it = b->classes.end() - 1;
         }
@@ -128,7 +130,7 @@ struct TuneKey {
     bool operator<(const TuneKey& o) const { return s < o.s; }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::map<TuneKey, std::pair<int, TcRings>> g_tune_cache;
 
 TuneKey tune_key(const std::vector<Tc2Problem>& probs, bool split) {
     std::vector<std::pair<int, int>> v;
@@ -144,17 +146,18 @@ TuneKey tune_key(const std::vector<Tc2Problem>& probs, bool split) {
 }
 
 // probs: descriptions of the problems as they will be stepped (buf[parity] is read); par[i] the
-// parity of problem i's current state.  Returns cudaSuccess and the best (nt, stages), or an
-// error; ms_out gets the best launch time.
+// parity of problem i's current state.  Candidates: every tile width that fits TMEM, each with the
+// automatic rings and a few other ring shapes (duplicates of an already timed layout skipped).
+// Returns cudaSuccess and the best (nt, rings), or an error; ms_out gets the best launch time.
 cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int>& par, bool split,
-                     cudaStream_t s, int* nt_out, int* stages_out, float* ms_out, bool use_cache) {
+                     cudaStream_t s, int* nt_out, TcRings* rings_out, float* ms_out, bool use_cache) {
     const TuneKey key = tune_key(probs, split);
     if (use_cache) {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             *nt_out = it->second.first;
-            *stages_out = it->second.second;
+            *rings_out = it->second.second;
             if (ms_out) *ms_out = -1.0f;
             return cudaSuccess;
         }
@@ -168,7 +171,8 @@ cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t err = cudaSuccess;
     float best = INFINITY;
-    int best_nt = 0, best_st = 0;
+    int best_nt = 0;
+    TcRings best_r;
     do {
         for (int i = 0; i < n && err == cudaSuccess; ++i)
             err = cudaMalloc(&scratch[i], (size_t)probs[i].nx * probs[i].ny * probs[i].Qp * sizeof(float));
@@ -185,13 +189,26 @@ cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int
             trial[i].counter = d_cnt + i;
             trial[i].target = 1;
         }
+        const TcRings shapes[] = {TcRings{}, TcRings{3, 3, 3, 2}, TcRings{2, 2, 0, 4}, TcRings{3, 3, 0, 4},
+                                  TcRings{2, 2, 0, 1}, TcRings{3, 3, 0, 1}};
+        std::vector<std::pair<int, TcRings>> seen;
         for (int nt = 32; nt <= 256 && err == cudaSuccess; nt *= 2) {
             if (2 * MBmax * nt > 512) break;
-            for (int st : {0, 2, 3, 4}) {
+            for (const TcRings& want : shapes) {
                 Tc2Plan* plan = nullptr;
-                cudaError_t ce = tc2_plan_create(&plan, trial.data(), n, split, nt, st);
+                cudaError_t ce = tc2_plan_create(&plan, trial.data(), n, split, nt, want);
                 if (ce == cudaErrorNotSupported) continue;
                 if (ce != cudaSuccess) { err = ce; break; }
+                const TcRings got = tc2_plan_rings(plan);
+                bool dup = false;
+                for (auto& v : seen)
+                    dup = dup || (v.first == nt && v.second.SS == got.SS && v.second.SB == got.SB &&
+                                  v.second.SA == got.SA && v.second.MPR == got.MPR);
+                if (dup) {
+                    tc2_plan_destroy(plan);
+                    continue;
+                }
+                seen.push_back({nt, got});
                 float tot = 0.0f;
                 for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
                     err = cudaMemsetAsync(d_cnt, 0, sizeof(int) * n, s);
@@ -212,7 +229,7 @@ cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int
                 if (tot / 3.0f < best) {
                     best = tot / 3.0f;
                     best_nt = nt;
-                    best_st = st;
+                    best_r = got;
                 }
             }
         }
@@ -226,10 +243,10 @@ cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int
     if (err != cudaSuccess) return err;
     if (best_nt == 0) return cudaErrorNotSupported;
     *nt_out = best_nt;
-    *stages_out = best_st;
+    *rings_out = best_r;
     if (ms_out) *ms_out = best;
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune_cache[key] = {best_nt, best_st};
+    g_tune_cache[key] = {best_nt, best_r};
     return cudaSuccess;
 }
 
@@ -244,10 +261,12 @@ int ensure_batch_plan(assn_batch* b) {
                 const assn_batch::Member& m = b->members[i];
                 d.push_back(problem_tc2(m.p, m.dt, m.p->cur + m.nsteps));
             }
-            const int nt = b->want_nt ? b->want_nt : c.nt, st = b->want_stages ? b->want_stages : c.stages;
-            cudaError_t e = tc2_plan_create(&c.plan, d.data(), (int)d.size(), b->precision == ASSN_BF16X3, nt, st);
+            const int nt = b->want_nt ? b->want_nt : c.nt;
+            const bool user = b->want_rings.SS || b->want_rings.SB || b->want_rings.SA || b->want_rings.MPR;
+            cudaError_t e = tc2_plan_create(&c.plan, d.data(), (int)d.size(), b->precision == ASSN_BF16X3, nt,
+                                            user ? b->want_rings : c.rings);
             if (e == cudaErrorNotSupported)
-                return bfail(b, ASSN_ERR_UNSUPPORTED, "batch: tiling %d / %d not supported for Qp = %d", nt, st, c.Qp);
+                return bfail(b, ASSN_ERR_UNSUPPORTED, "batch: tiling not supported for Qp = %d (tile %d)", c.Qp, nt);
             BK(b, e);
         }
         b->planned = true;
@@ -366,7 +385,7 @@ int assn_batch_set_tiling(assn_batch* b, int tile_cells, int stages) {
         return bfail(b, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64, 128 or 256");
     if (stages != 0 && (stages < 2 || stages > 8)) return bfail(b, ASSN_ERR_ARG, "stages must be 0 or 2..8");
     b->want_nt = tile_cells;
-    b->want_stages = stages;
+    b->want_rings = TcRings{stages, stages, stages, 0};
     drop_plan(b);
     return ASSN_OK;
 }
@@ -391,22 +410,23 @@ int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stag
             d.push_back(problem_tc2(b->members[i].p, b->members[i].dt, 1));
             par.push_back(b->members[i].p->cur);
         }
-        int nt = 0, st = 0;
+        int nt = 0;
+        TcRings rr;
         float ms = 0.0f;
-        cudaError_t e = autotune(d, par, b->precision == ASSN_BF16X3, b->stream, &nt, &st, &ms, use_cache != 0);
+        cudaError_t e = autotune(d, par, b->precision == ASSN_BF16X3, b->stream, &nt, &rr, &ms, use_cache != 0);
         if (e == cudaErrorLaunchTimeout) return bfail(b, ASSN_ERR_TIMEOUT, "autotune: a bounded device wait gave up");
         if (e == cudaErrorNotSupported) return bfail(b, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits Qp = %d", c.Qp);
         BK(b, e);
         c.nt = nt;
-        c.stages = st;
+        c.rings = rr;
         if (ms >= 0.0f) { total_ms += ms; all_cached = false; }
     }
     b->want_nt = 0;
-    b->want_stages = 0;
+    b->want_rings = TcRings{};
     b->tuned = true;
     // report the class with the most ordinate blocks (the first)
     if (tile_cells) *tile_cells = b->classes[0].nt;
-    if (stages) *stages = b->classes[0].stages;
+    if (stages) *stages = b->classes[0].rings.SA;
     if (ms_per_launch) *ms_per_launch = all_cached ? -1.0 : total_ms;
     return ASSN_OK;
 }
@@ -551,14 +571,18 @@ int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, in
     if (e != cudaSuccess) return problem_fail(p, ASSN_ERR_CUDA, cudaGetErrorString(e));
     std::vector<Tc2Problem> d{problem_tc2(p, dt, 1)};
     std::vector<int> par{p->cur};
-    int nt = 0, st = 0;
+    int nt = 0;
+    TcRings rr;
     float ms = 0.0f;
-    e = autotune(d, par, p->precision == ASSN_BF16X3, p->stream, &nt, &st, &ms, use_cache != 0);
+    e = autotune(d, par, p->precision == ASSN_BF16X3, p->stream, &nt, &rr, &ms, use_cache != 0);
     if (e == cudaErrorLaunchTimeout) return problem_fail(p, ASSN_ERR_TIMEOUT, "autotune: a bounded device wait gave up");
     if (e == cudaErrorNotSupported) return problem_fail(p, ASSN_ERR_UNSUPPORTED, "autotune: no tiling fits");
     if (e != cudaSuccess) return problem_fail(p, ASSN_ERR_CUDA, cudaGetErrorString(e));
-    r = assn_set_tiling(p, nt, st, 0);
+    r = assn_set_tiling(p, nt, 0, 0);
     if (r) return r;
+    r = assn_set_rings(p, rr.SS, rr.SB, rr.SA, rr.MPR);
+    if (r) return r;
+    const int st = rr.SA;
     if (tile_cells) *tile_cells = nt;
     if (stages) *stages = st;
     if (ms_per_step) *ms_per_step = ms;

@@ -52,6 +52,7 @@ struct assn_problem {
     size_t stage_elems = 0;
 
     int want_nt = 0, want_stages = 0;   // tensor-core tiling request (0 = automatic)
+    assn::TcRings want_rings;           // persistent kernel's rings (zero fields automatic)
     int* d_counter = nullptr;           // device step counter of the persistent tensor-core kernel
     int counter_host = 0;               // last value written to / advanced on d_counter
     double plan2_dt = -1.0;             // dt the persistent plan was built for

@@ -762,10 +762,11 @@ size_t smem_for(int NT, bool split, int SS, int SB, int SA, int MPRmax) {
 
 // Tile width, ring depths and request sizes for a set of problems.  Tile width: two accumulator
 // buffers of MBmax x NT columns fill the 512 TMEM columns (or the requested width); narrower when
-// the rings do not fit shared memory.  Kernel-matrix requests cover as many ordinate blocks (MPR)
-// as two stages allow; then the deepest balanced staging / B rings (up to 4), then a deeper
-// kernel-matrix ring (up to 4).
-bool choose_tiling(int MBmax, bool split, int want_nt, int want_stages, int& NT, int& SS, int& SB, int& SA,
+// the rings do not fit shared memory.  Rings: as requested (a zero field is chosen), else two
+// staging and two operand stages and as many kernel-matrix stages of two ordinate blocks per
+// request as fit (measured on the 448^2 / Q = 512 lattice: the kernel-matrix ring's depth in
+// flight matters more than the other rings' and than fewer, larger requests).
+bool choose_tiling(int MBmax, bool split, int want_nt, TcRings want, int& NT, int& SS, int& SB, int& SA,
                    int& MPRmax) {
     int nt = 512 / (2 * MBmax);
     if (nt > 256) nt = 256;
@@ -773,21 +774,21 @@ bool choose_tiling(int MBmax, bool split, int want_nt, int want_stages, int& NT,
     const size_t limit = 227 * 1024;
     while (true) {
         if (nt < 32 || (nt & (nt - 1)) || 2 * MBmax * nt > 512) return false;
-        for (int mpr = MBmax; mpr >= 1; mpr /= 2) {
+        const int ss = want.SS ? want.SS : 2, sb = want.SB ? want.SB : 2;
+        for (int mpr = want.MPR ? want.MPR : std::min(2, MBmax); mpr >= 1; mpr /= 2) {
             if (MBmax % mpr) continue;
-            if (want_stages >= 2) {
-                if (smem_for(nt, split, want_stages, want_stages, want_stages, mpr) <= limit) {
-                    NT = nt; SS = SB = SA = want_stages; MPRmax = mpr;
+            if (want.SA) {
+                if (smem_for(nt, split, ss, sb, want.SA, mpr) <= limit) {
+                    NT = nt; SS = ss; SB = sb; SA = want.SA; MPRmax = mpr;
                     return true;
                 }
-            } else if (smem_for(nt, split, 2, 2, 2, mpr) <= limit) {
-                int ss = 2, sb = 2, sa = 2;
-                for (int k = 4; k >= 3; --k)
-                    if (smem_for(nt, split, k, k, 2, mpr) <= limit) { ss = sb = k; break; }
-                while (sa < 4 && smem_for(nt, split, ss, sb, sa + 1, mpr) <= limit) ++sa;
+            } else if (smem_for(nt, split, ss, sb, 2, mpr) <= limit) {
+                int sa = 2;
+                while (sa < 8 && smem_for(nt, split, ss, sb, sa + 1, mpr) <= limit) ++sa;
                 NT = nt; SS = ss; SB = sb; SA = sa; MPRmax = mpr;
                 return true;
             }
+            if (want.MPR) break;
         }
         if (want_nt) return false;
         nt /= 2;
@@ -806,14 +807,14 @@ struct Tc2Plan {
 };
 
 cudaError_t tc2_plan_create(Tc2Plan** out, const Tc2Problem* probs, int nprob, bool split, int want_nt,
-                            int want_stages) {
+                            TcRings rings) {
     *out = nullptr;
     if (nprob < 1 || nprob > kMaxProbs) return cudaErrorNotSupported;
     int MBmax = 1;
     for (int i = 0; i < nprob; ++i) MBmax = std::max(MBmax, probs[i].Mp / 128);
     Tc2Plan* p = new Tc2Plan();
     p->split = split;
-    if (!choose_tiling(MBmax, split, want_nt, want_stages, p->NT, p->SS, p->SB, p->SA, p->MPRmax)) {
+    if (!choose_tiling(MBmax, split, want_nt, rings, p->NT, p->SS, p->SB, p->SA, p->MPRmax)) {
         delete p;
         return cudaErrorNotSupported;
     }
@@ -892,6 +893,17 @@ void tc2_plan_describe(const Tc2Plan* p, int* tile_cells, int* stages, int* tmem
 }
 
 int tc2_plan_total_tiles(const Tc2Plan* p) { return p ? p->total_tiles : 0; }
+
+TcRings tc2_plan_rings(const Tc2Plan* p) {
+    TcRings r;
+    if (p) {
+        r.SS = p->SS;
+        r.SB = p->SB;
+        r.SA = p->SA;
+        r.MPR = p->MPRmax;
+    }
+    return r;
+}
 
 cudaError_t tc2_plan_set_targets(Tc2Plan* p, const int* targets, cudaStream_t stream) {
     if (!p) return cudaErrorInvalidValue;

@@ -216,3 +216,22 @@ def test_result_independent_of_tile_width(A):
         out.append(p.state())
         p.close()
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_result_independent_of_rings(A):
+    """Ring depths and kernel-matrix request sizes change only the pipelining, not the arithmetic."""
+    wl = workloads(seed=89)[3]   # 33 x 21 cells, Q = 512 (four ordinate blocks)
+    out = []
+    dt = None
+    for rings in ((0, 0, 0, 0), (2, 2, 2, 1), (3, 3, 3, 2), (2, 3, 2, 4)):
+        p = gpu_problem(A, wl, "bf16")
+        dt = dt or 0.9 * p.max_stable_dt()
+        p.set_rings(*rings)
+        got = p.rings()
+        if rings[0]:
+            assert (got["staging"], got["operand"], got["kernel_matrix"], got["blocks_per_request"]) == rings
+        p.step(3, dt)
+        out.append(p.state())
+        p.close()
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
