@@ -365,6 +365,13 @@ int assn_mass_noalloc(const void* psi_dev, int elem_bytes, const double* w_dev, 
                       double h, double* mass_dev, void* stream);
 const char* assn_noalloc_last_error(void);
 
+/* Self-test of the failure path of the tensor-core kernels on the current device: launches one
+ * block whose bounded wait on an mbarrier that nothing completes gives up after limit_us
+ * microseconds (1 .. 1e6), records the event in a device flag and returns; the host reads the flag.
+ * Returns ASSN_ERR_TIMEOUT when the wait gave up as designed (the CUDA context stays usable),
+ * ASSN_ERR_ARG for a limit out of range, ASSN_ERR_CUDA / ASSN_ERR_OOM if the check itself failed. */
+int assn_selftest_wait_timeout(int limit_us);
+
 /* Message of the last failure on p (never NULL; "" when none).  With p == NULL, the last
  * failure of assn_create on this thread. */
 const char* assn_last_error(const assn_problem* p);

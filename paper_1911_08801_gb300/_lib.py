@@ -92,6 +92,7 @@ SIGNATURES = {
     "assn_status_string": (C.c_char_p, [C.c_int]),
     "assn_launch_count": (C.c_int64, [_h]),
     "assn_abi_version": (C.c_int, []),
+    "assn_selftest_wait_timeout": (C.c_int, [C.c_int]),
     "assn_batch_create": (C.c_int, [C.POINTER(_h), _vp]),
     "assn_batch_destroy": (C.c_int, [_h]),
     "assn_batch_add": (C.c_int, [_h, _h, C.c_int, C.c_double]),
@@ -463,3 +464,8 @@ def assn_noalloc_last_error() -> str:
 
 def assn_abi_version() -> int:
     return int(lib.assn_abi_version())
+
+
+def assn_selftest_wait_timeout(limit_us: int) -> int:
+    """Status of the bounded-wait self-test (ASSN_ERR_TIMEOUT when the failure path works)."""
+    return int(lib.assn_selftest_wait_timeout(limit_us))

@@ -512,42 +512,49 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 if (!go) return false;
                 tc_fence_after();
             }
-            float y[kCHe];
-            __syncwarp();
-            tmem_ld<kCHe>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0), y);
+            // accumulator columns are read 8 at a time: fewer live registers than the whole chunk,
+            // which keeps the several-problem loop (per-tile parameters in registers) from spilling
+            constexpr int kY = 8;
+            const uint32_t tcol = tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0);
             const int Qp = QP > 0 ? QP : t.Qp;
             const int ncell = t.ncell;
             const int fb = t.fb0 + c0;
             const int q = m * 128 + lq * 32 + lane;
-            if (fb < ncell && q < Qp) {
-                float* po = t.out + (size_t)fb * Qp + q;
-                const float4* cb = coef + buf * NT + c0;
-                if (q >= t.Q) {
+            const bool live = fb < ncell && q < Qp;
+            const bool pad = q >= t.Q;
+            float* po = t.out + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
+            const float4* cb = coef + buf * NT + c0;
+            const float4 o4 = live ? __ldg(reinterpret_cast<const float4*>(t.ord) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float ax = fabsf(o4.x), ay = fabsf(o4.y), axy = ax + ay;
+            const float dts = t.dts;
+            const float ge = dts * o4.w;
+            const int xbit = o4.x > 0.f ? 1 : (o4.x < 0.f ? 2 : 0);
 #pragma unroll
-                    for (int i = 0; i < kCHe; ++i)
+            for (int h = 0; h < kCHe; h += kY) {
+                float y[kY];
+                __syncwarp();
+                tmem_ld<kY>(tcol + (uint32_t)h, y);
+                if (!live) continue;
+#pragma unroll
+                for (int j = 0; j < kY; ++j) {
+                    const int i = h + j;
+                    if (pad) {
                         if (fb + i < ncell) __stcs(po + i * Qp, 0.0f);
-                } else {
-                    const float4 o4 = __ldg(reinterpret_cast<const float4*>(t.ord) + q);
-                    const float ax = fabsf(o4.x), ay = fabsf(o4.y), axy = ax + ay;
-                    const float dts = t.dts;
-                    const float ge = dts * o4.w;
-                    const int xbit = o4.x > 0.f ? 1 : (o4.x < 0.f ? 2 : 0);
-#pragma unroll
-                    for (int i = 0; i < kCHe; ++i) {
-                        const float4 cf = cb[i];
-                        const int bits = __float_as_int(cf.z);
-                        if (!(bits & 16)) continue;
-                        const float sf = s[i];
-                        float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < kCHe - 1 ? s[i + 1] : rgt);
-                        upx = (bits & xbit) ? upx : 0.0f;
-                        const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
-                        float out = fmaf(sf, cf.x - axy, cf.y);
-                        out = fmaf(ax, upx, out);
-                        out = fmaf(ay, u[i], out);
-                        out = fmaf(dts, y[i], out);
-                        out = fmaf(-ge, st, out);
-                        __stcs(po + i * Qp, out);
+                        continue;
                     }
+                    const float4 cf = cb[i];
+                    const int bits = __float_as_int(cf.z);
+                    if (!(bits & 16)) continue;
+                    const float sf = s[i];
+                    float upx = xbit == 1 ? (i > 0 ? s[i - 1] : lft) : (i < kCHe - 1 ? s[i + 1] : rgt);
+                    upx = (bits & xbit) ? upx : 0.0f;
+                    const float st = SPLIT ? sf : __bfloat162float(__float2bfloat16_rn(sf));
+                    float out = fmaf(sf, cf.x - axy, cf.y);
+                    out = fmaf(ax, upx, out);
+                    out = fmaf(ay, u[i], out);
+                    out = fmaf(dts, y[j], out);
+                    out = fmaf(-ge, st, out);
+                    __stcs(po + i * Qp, out);
                 }
             }
             if (r == cpt - 1) {

@@ -60,22 +60,28 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
     return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete, for at most kWaitNs.  On expiry (or when
+// Wait for the phase with the given parity to complete, for at most limit_ns.  On expiry (or when
 // another thread of the CTA already gave up) raises *abort_flag, ORs `code` into *err and returns
 // false.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                       unsigned int* err, unsigned int code) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned int* err, unsigned int code, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(err, code);
             return false;
         }
     }
+}
+
+// The kernels' wait: limit kWaitNs, out of line (the fast path stays inline at the call sites).
+static __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned int* err, unsigned int code) {
+    return mbar_wait_for(bar, parity, abort_flag, err, code, kWaitNs);
 }
 
 __device__ __forceinline__ void fence_barrier_init() {
