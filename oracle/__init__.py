@@ -11,6 +11,10 @@ Parity status: every function is pinned by the ``-m "not gpu"`` tests in
 cases (quadrature exactness, kernel normalisation and transport moments,
 Funk-Hecke eigenvalues of the kernel matrix, exact upwind shifts and binomial
 spreading, discrete decay laws, the discrete mass balance, the eps -> 0 limit,
-and the symmetries of the line source).
+and the symmetries of the line source).  The Heun + minmod functions (the paper's
+explicit scheme, Sec. 3.1) are pinned by the minmod definition, exactness of the
+limited fluxes on monotone quadratics, constant-state and periodic conservation,
+no new extrema on an advected step, the exact RK2 amplification factor on decay,
+and a second-order convergence rate on a smooth periodic profile.
 """
 from .assn_oracle import *  # noqa: F401,F403

@@ -20,6 +20,7 @@ import numpy as np
 __all__ = [
     "product_quadrature", "s_eps", "s_exp", "kernel_matrix", "scalar_flux",
     "transport", "step", "run", "mass", "step_at_cells",
+    "minmod", "transport_minmod", "rhs", "step_heun", "run_heun",
 ]
 
 
@@ -144,6 +145,88 @@ def step(psi, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float, dt: f
     art = psi @ np.asarray(K, dtype=np.float64).T                 # sum_p K_qp psi_p
     T = transport(psi, Omega, h, bc)
     return psi - dt * T - dt * (sa + ss + sigma_as) * psi + dt * (ss * phys + sigma_as * art + src)
+
+
+# --------------------------------------------------------------------------- the paper's explicit scheme
+# Sec. 3.1 names it only: Heun's method in time with a minmod slope limiter in space.  Read here as
+# the usual second-order MUSCL finite-volume scheme: per axis, slopes Delta_i = minmod(psi_i -
+# psi_{i-1}, psi_{i+1} - psi_i), upwind face values psi_i + Delta_i/2 (Omega > 0) or
+# psi_{i+1} - Delta_{i+1}/2 (Omega < 0), and Heun (the two-stage strong-stability-preserving
+# Runge-Kutta method) in time.
+
+
+def minmod(a, b):
+    """0 where a and b differ in sign (or either is 0), else the one of smaller magnitude."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.where(a * b > 0.0, np.where(np.abs(a) < np.abs(b), a, b), 0.0)
+
+
+def _axis_flux_divergence(psi, om, h: float, axis: int, bc: str):
+    """d/dx_axis of om * psi by limited upwind fluxes; psi [ny][nx][Q], om [Q]."""
+    n = psi.shape[axis]
+    if bc == "periodic":
+        ext = np.concatenate([np.take(psi, [n - 2, n - 1], axis=axis, mode="wrap"), psi,
+                              np.take(psi, [0, 1], axis=axis, mode="wrap")], axis=axis)
+    else:   # vacuum: two zero ghost cells on each side
+        shape = list(psi.shape)
+        shape[axis] = 2
+        z = np.zeros(shape)
+        ext = np.concatenate([z, psi, z], axis=axis)
+    # ext index e = i + 2; slopes of cells i = -1 .. n (e = 1 .. n + 2)
+    def sl(lo, hi):
+        return np.take(ext, range(lo, hi), axis=axis)
+    d = minmod(sl(1, n + 3) - sl(0, n + 2), sl(2, n + 4) - sl(1, n + 3))      # cells -1 .. n
+    cell = sl(1, n + 3)                                                          # psi of cells -1 .. n
+    left_state = cell + 0.5 * d          # face value on the left side of face (i + 1/2), i = -1 .. n
+    right_state = cell - 0.5 * d         # face value on the right side of face (i - 1/2), i = -1 .. n
+    # faces f = i + 1/2 for i = -1 .. n - 1: upwind side is cell i for om > 0, cell i + 1 for om < 0
+    fl = np.take(left_state, range(0, n + 1), axis=axis)
+    fr = np.take(right_state, range(1, n + 2), axis=axis)
+    flux = np.where(om > 0, om * fl, np.where(om < 0, om * fr, 0.0))           # n + 1 faces
+    return (np.take(flux, range(1, n + 1), axis=axis) - np.take(flux, range(0, n), axis=axis)) / h
+
+
+def transport_minmod(psi, Omega, h: float, bc: str = "vacuum"):
+    """Omega . grad psi by second-order upwind fluxes with minmod-limited slopes (Sec. 3.1).
+    Vacuum boundaries: zero inflow ghost cells (two per side); "periodic" for tests."""
+    psi = np.asarray(psi, dtype=np.float64)
+    ox = np.asarray(Omega)[:, 0]
+    oy = np.asarray(Omega)[:, 1]
+    return _axis_flux_divergence(psi, ox, h, 1, bc) + _axis_flux_divergence(psi, oy, h, 0, bc)
+
+
+def rhs(psi, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float, bc: str = "vacuum",
+        second_order: bool = True):
+    """Right-hand side of the as-S_N equations (Sec. 3.2) for a time integrator:
+    -[Omega . grad psi] - (sigma_a + sigma_s + sigma_as) psi + sigma_s Phi/sum w + sigma_as K psi + q."""
+    psi = np.asarray(psi, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    sa = np.asarray(sigma_a, dtype=np.float64)[..., None]
+    ss = np.asarray(sigma_s, dtype=np.float64)[..., None]
+    src = np.asarray(q, dtype=np.float64)[..., None]
+    phys = (scalar_flux(psi, w) / w.sum())[..., None]
+    art = psi @ np.asarray(K, dtype=np.float64).T
+    T = transport_minmod(psi, Omega, h, bc) if second_order else transport(psi, Omega, h, bc)
+    return -T - (sa + ss + sigma_as) * psi + ss * phys + sigma_as * art + src
+
+
+def step_heun(psi, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float, dt: float,
+              bc: str = "vacuum"):
+    """One step of Heun's method (Sec. 3.1): psi* = psi + dt L(psi),
+    psi^{n+1} = psi/2 + (psi* + dt L(psi*))/2, with the limited second-order transport."""
+    psi = np.asarray(psi, dtype=np.float64)
+    args = (K, Omega, w, sigma_a, sigma_s, q, sigma_as, h, bc)
+    star = psi + dt * rhs(psi, *args)
+    return 0.5 * psi + 0.5 * (star + dt * rhs(star, *args))
+
+
+def run_heun(psi0, nsteps: int, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float,
+             dt: float, bc: str = "vacuum"):
+    psi = np.array(psi0, dtype=np.float64, copy=True)
+    for _ in range(nsteps):
+        psi = step_heun(psi, K, Omega, w, sigma_a, sigma_s, q, sigma_as, h, dt, bc)
+    return psi
 
 
 def run(psi0, nsteps: int, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float,
