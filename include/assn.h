@@ -83,6 +83,14 @@ typedef enum { ASSN_NORM_COLUMN = 0, ASSN_NORM_ROW = 1 } assn_normalisation;
 
 typedef enum { ASSN_BC_VACUUM = 0 } assn_boundary;
 
+/* Time and space discretisation of assn_step.
+ *   ASSN_SCHEME_EULER_UPWIND  forward Euler with first-order upwind transport (the default)
+ *   ASSN_SCHEME_HEUN_MINMOD   the paper's explicit scheme (Sec. 3.1): Heun's method (two stages,
+ *                             psi* = psi + dt L(psi), psi^{n+1} = (psi + psi* + dt L(psi*))/2)
+ *                             with second-order upwind fluxes from minmod-limited slopes (two zero
+ *                             ghost cells per vacuum side); FP32 / FP64 problems only. */
+typedef enum { ASSN_SCHEME_EULER_UPWIND = 0, ASSN_SCHEME_HEUN_MINMOD = 1 } assn_scheme;
+
 typedef struct assn_problem assn_problem;
 
 /* Maximum ordinate count and grid side accepted by assn_create / set_quadrature. */
@@ -148,9 +156,17 @@ int assn_get_state_f32(assn_problem* p, float* psi_host);
  * psi_q(x) = max{floor, exp(-|x|^2/(4 delta)) / (4 pi delta)} at cell centres for every q. */
 int assn_init_line_source(assn_problem* p, double delta, double floor_value);
 
-/* Largest dt for which the explicit step keeps every coefficient of the update
- * non-negative (positivity): dt * (max_q [(|Omega_x,q| + |Omega_y,q|)/h + sigma_as (1 - K_qq)]
- * + max_cells [sigma_a + sigma_s]) <= 1.  Requires quadrature, cross sections and K. */
+/* Scheme of later assn_step calls (an assn_scheme).  ASSN_ERR_ARG for an unknown scheme; a
+ * tensor-core problem with ASSN_SCHEME_HEUN_MINMOD fails at assn_step with ASSN_ERR_UNSUPPORTED,
+ * and so do batches and assn_step_device with that scheme. */
+int assn_set_scheme(assn_problem* p, int scheme);
+int assn_get_scheme(const assn_problem* p, int* scheme);
+
+/* Largest admissible dt for the problem's scheme.  Forward Euler: the explicit step keeps every
+ * coefficient of the update non-negative (positivity): dt * (max_q [(|Omega_x,q| + |Omega_y,q|)/h
+ * + sigma_as (1 - K_qq)] + max_cells [sigma_a + sigma_s]) <= 1.  Heun + minmod: dt max_q
+ * max(|Omega_x,q|, |Omega_y,q|)/h <= 1 and dt (sigma_as max_q (1 - K_qq) + max_cells [sigma_a +
+ * sigma_s]) <= 1.  Requires quadrature, cross sections and K. */
 int assn_max_stable_dt(assn_problem* p, double* dt_out);
 
 /* Advance nsteps explicit steps of size dt on the problem's stream (asynchronous; the

@@ -67,6 +67,14 @@ class Problem:
         return self
 
     # -- stepping and diagnostics
+    def set_scheme(self, scheme="euler"):
+        """"euler" (forward Euler, first-order upwind) or "heun" (Heun + minmod, FP32 / FP64)."""
+        _lib.assn_set_scheme(self.handle, _lib.SCHEMES[scheme] if isinstance(scheme, str) else int(scheme))
+        return self
+
+    def scheme(self) -> int:
+        return _lib.assn_get_scheme(self.handle)
+
     def max_stable_dt(self) -> float:
         return _lib.assn_max_stable_dt(self.handle)
 

@@ -27,6 +27,8 @@ ASSN_ERR_UNSUPPORTED = -8
 ASSN_FP64, ASSN_FP32, ASSN_BF16, ASSN_BF16X3 = 0, 1, 2, 3
 ASSN_KERNEL_GAUSS, ASSN_KERNEL_EXP = 0, 1
 ASSN_NORM_COLUMN, ASSN_NORM_ROW = 0, 1
+ASSN_SCHEME_EULER_UPWIND, ASSN_SCHEME_HEUN_MINMOD = 0, 1
+SCHEMES = {"euler": ASSN_SCHEME_EULER_UPWIND, "heun": ASSN_SCHEME_HEUN_MINMOD}
 
 PRECISIONS = {"fp64": ASSN_FP64, "fp32": ASSN_FP32, "bf16": ASSN_BF16, "bf16x3": ASSN_BF16X3}
 
@@ -74,6 +76,8 @@ SIGNATURES = {
     "assn_init_line_source": (C.c_int, [_h, C.c_double, C.c_double]),
     "assn_max_stable_dt": (C.c_int, [_h, _dp]),
     "assn_step": (C.c_int, [_h, C.c_int, C.c_double]),
+    "assn_set_scheme": (C.c_int, [_h, C.c_int]),
+    "assn_get_scheme": (C.c_int, [_h, C.POINTER(C.c_int)]),
     "assn_step_device": (C.c_int, [_h, _vp, _vp, C.c_double]),
     "assn_run_f32": (C.c_int, [_h, _fp, C.c_int, C.c_double, _dp]),
     "assn_set_tiling": (C.c_int, [_h, C.c_int, C.c_int, C.c_int]),
@@ -248,6 +252,16 @@ def assn_max_stable_dt(h: int) -> float:
 
 def assn_step(h: int, nsteps: int, dt: float) -> None:
     _check(lib.assn_step(h, nsteps, dt), h)
+
+
+def assn_set_scheme(h: int, scheme: int) -> None:
+    _check(lib.assn_set_scheme(h, scheme), h)
+
+
+def assn_get_scheme(h: int) -> int:
+    v = C.c_int(0)
+    _check(lib.assn_get_scheme(h, C.byref(v)), h)
+    return v.value
 
 
 def assn_step_device(h: int, psi_in_dev: int, psi_out_dev: int, dt: float) -> None:

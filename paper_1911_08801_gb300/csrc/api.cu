@@ -156,6 +156,18 @@ int upload_ord(assn_problem* p, double dt) {
 // coefficients are non-negative): 1 - dt (|Omega_x| + |Omega_y|)/h - dt sigma_as e_q
 // - dt (sigma_a + sigma_s) >= 0, maximised over ordinates and cells separately.
 double max_stable_dt(const assn_problem* p) {
+    if (p->scheme == ASSN_SCHEME_HEUN_MINMOD) {
+        // per-axis CFL number <= 1 (the paper runs this scheme at dt/dx = 0.95) and the
+        // collision / artificial-scattering rate times dt <= 1
+        double vdir = 0, emax = 0, smax = 0;
+        for (int q = 0; q < p->Q; ++q) {
+            vdir = std::max(vdir, std::max(fabs(p->omega[3 * q]), fabs(p->omega[3 * q + 1])) / p->h);
+            emax = std::max(emax, p->e[q]);
+        }
+        for (size_t c = 0; c < p->ncell(); ++c) smax = std::max(smax, p->sa[c] + p->ss[c]);
+        const double rate = std::max(vdir, p->sigma_as * emax + smax);
+        return rate > 0 ? 1.0 / rate : INFINITY;
+    }
     double vmax = 0;
     for (int q = 0; q < p->Q; ++q)
         vmax = std::max(vmax, (fabs(p->omega[3 * q]) + fabs(p->omega[3 * q + 1])) / p->h + p->sigma_as * p->e[q]);
@@ -647,9 +659,59 @@ int assn::problem_prepare(assn_problem* p, double dt) {
 
 extern "C" {
 
+int assn_set_scheme(assn_problem* p, int scheme) {
+    if (!p) return ASSN_ERR_ARG;
+    if (scheme != ASSN_SCHEME_EULER_UPWIND && scheme != ASSN_SCHEME_HEUN_MINMOD)
+        return fail(p, ASSN_ERR_ARG, "unknown scheme %d", scheme);
+    p->scheme = scheme;
+    return ASSN_OK;
+}
+
+int assn_get_scheme(const assn_problem* p, int* scheme) {
+    if (!p || !scheme) return ASSN_ERR_ARG;
+    *scheme = p->scheme;
+    return ASSN_OK;
+}
+
+// One Heun step (two stages) on the CUDA-core paths; the state stays in buffer cur.
+static int heun_step(assn_problem* p, double dt) {
+    void* a = p->d_psi[p->cur];
+    void* b = p->d_psi[p->cur ^ 1];
+    if (p->precision == ASSN_FP64) {
+        StepArgs<double, OrdD, CellD> s1{(const double*)a, (double*)b, (const OrdD*)p->d_ord, (const CellD*)p->d_cell,
+                                         p->d_KT64, p->nx, p->ny, p->Q, p->Qp, dt, dt * p->sigma_as};
+        CK(p, launch_stage_simt_f64(s1, nullptr, 0.0, 1.0, p->stream));
+        StepArgs<double, OrdD, CellD> s2 = s1;
+        s2.psi = (const double*)b;
+        s2.psi_out = (double*)a;
+        CK(p, launch_stage_simt_f64(s2, (const double*)a, 0.5, 0.5, p->stream));
+    } else {
+        StepArgs<float, OrdF, CellF> s1{(const float*)a, (float*)b, (const OrdF*)p->d_ord, (const CellF*)p->d_cell,
+                                        p->d_KT32, p->nx, p->ny, p->Q, p->Qp, (float)dt, (float)(dt * p->sigma_as)};
+        CK(p, launch_stage_simt_f32(s1, nullptr, 0.0f, 1.0f, p->stream));
+        StepArgs<float, OrdF, CellF> s2 = s1;
+        s2.psi = (const float*)b;
+        s2.psi_out = (float*)a;
+        CK(p, launch_stage_simt_f32(s2, (const float*)a, 0.5f, 0.5f, p->stream));
+    }
+    p->launches += 2;
+    return ASSN_OK;
+}
+
 int assn_step(assn_problem* p, int nsteps, double dt) {
     if (!p) return ASSN_ERR_ARG;
     if (nsteps < 0) return fail(p, ASSN_ERR_ARG, "nsteps < 0");
+    if (p->scheme == ASSN_SCHEME_HEUN_MINMOD) {
+        if (p->tensor())
+            return fail(p, ASSN_ERR_UNSUPPORTED, "the Heun + minmod scheme runs on the FP32 / FP64 paths");
+        int r = assn::problem_prepare(p, dt);
+        if (r) return r;
+        for (int n = 0; n < nsteps; ++n) {
+            r = heun_step(p, dt);
+            if (r) return r;
+        }
+        return ASSN_OK;
+    }
     int r = prepare_step(p, dt);
     if (r) return r;
     for (int n = 0; n < nsteps; ++n) {
@@ -662,6 +724,8 @@ int assn_step(assn_problem* p, int nsteps, double dt) {
 
 int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev, double dt) {
     if (!p || !psi_in_dev || !psi_out_dev) return ASSN_ERR_ARG;
+    if (p->scheme != ASSN_SCHEME_EULER_UPWIND)
+        return fail(p, ASSN_ERR_UNSUPPORTED, "assn_step_device takes the forward-Euler upwind step only");
     if (psi_in_dev == psi_out_dev) return fail(p, ASSN_ERR_ARG, "input and output buffers must differ");
     int r = prepare_step(p, dt);
     if (r) return r;

@@ -57,6 +57,13 @@ cudaError_t launch_derive_tc(const double* K64, const double* w, int Q, int Qp, 
 
 cudaError_t launch_step_simt_f64(const StepArgs<double, OrdD, CellD>& a, cudaStream_t s);
 cudaError_t launch_step_simt_f32(const StepArgs<float, OrdF, CellF>& a, cudaStream_t s);
+// One stage of Heun's method with minmod-limited second-order upwind transport (CUDA cores):
+// psi_out = alpha keep + beta (psi + dt L(psi)); keep may be psi_out itself (each element is read
+// before it is written by the same thread) and is not read when alpha == 0.
+cudaError_t launch_stage_simt_f64(const StepArgs<double, OrdD, CellD>& a, const double* keep, double alpha,
+                                  double beta, cudaStream_t s);
+cudaError_t launch_stage_simt_f32(const StepArgs<float, OrdF, CellF>& a, const float* keep, float alpha,
+                                  float beta, cudaStream_t s);
 
 // Tensor-core step.  Returns cudaErrorNotSupported for shapes the kernel does not cover.
 struct TcPlan;

@@ -340,6 +340,8 @@ int assn_batch_add(assn_batch* b, assn_problem* p, int nsteps, double dt) {
     if (nsteps < 0) return bfail(b, ASSN_ERR_ARG, "nsteps < 0");
     if (p->precision != ASSN_BF16 && p->precision != ASSN_BF16X3)
         return bfail(b, ASSN_ERR_UNSUPPORTED, "batches step the tensor-core precisions (BF16, BF16X3) only");
+    if (p->scheme != ASSN_SCHEME_EULER_UPWIND)
+        return bfail(b, ASSN_ERR_UNSUPPORTED, "batches take the forward-Euler upwind step only");
     if (b->precision >= 0 && p->precision != b->precision)
         return bfail(b, ASSN_ERR_ARG, "all members of a batch share one precision");
     if (p->dev != b->dev) return bfail(b, ASSN_ERR_ARG, "problem lives on another device");

@@ -51,6 +51,7 @@ struct assn_problem {
     double* d_stage = nullptr;
     size_t stage_elems = 0;
 
+    int scheme = 0;                     // an assn_scheme
     int want_nt = 0, want_stages = 0;   // tensor-core tiling request (0 = automatic)
     assn::TcRings want_rings;           // persistent kernel's rings (zero fields automatic)
     int* d_counter = nullptr;           // device step counter of the persistent tensor-core kernel
