@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serving", "accuracy", "oracle-phi"],
                     help="step: one solve stepped K times; ensemble: 64 uneven solves to completion in one "
                          "batch; serving: Poisson request stream through the serving loop")
+    ap.add_argument("--scheme", default="euler", choices=["euler", "heun"],
+                    help="step mode: forward Euler + first-order upwind, or Heun + minmod (FP32 / FP64 only)")
     ap.add_argument("--count", type=int, default=64, help="ensemble members / serving requests")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate, requests/s (0 = about 70%% load)")
     ap.add_argument("--seed", type=int, default=0)
@@ -147,6 +149,23 @@ def make_problem(A, wl, precision, stream):
     return p
 
 
+# CUDA-core peaks (FMA = 2 flops) from unit counts and the 2070 MHz maximum SM clock: 152 SMs x 128
+# FP32 lanes; FP64 at 1/64 of FP32 on this part.
+ALU_PEAK_TFLOPS = {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 152 * 2 * 2 * 2.07e9 / 1e12}
+
+
+def alu_roofline(args, wl, ms_per_step: float) -> dict:
+    """Heun on CUDA cores: the dense artificial-scattering sum, 2 Qp flops per update and stage, two
+    stages per step, dominates; bound by the CUDA-core arithmetic rate."""
+    qp = (wl.Q + 63) // 64 * 64
+    flops = 4.0 * qp * wl.nx * wl.ny
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    peak = ALU_PEAK_TFLOPS[args.precision]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": "derived: SMs x lanes x 2 x 2070 MHz", "flops_per_update": 4 * qp,
+            "kernel": "stage_simt_kernel (two launches per step)"}
+
+
 def max_over_ranks(ms: float, dist, device: str) -> float:
     """The slowest rank's time (every rank gets it); ``dist`` None on one process."""
     if dist is None:
@@ -179,6 +198,9 @@ def run_ours(args, rank, world, dist):
     n_total, dt = wl.steps()
     stream = torch.cuda.Stream()
     prob = make_problem(A, wl, args.precision, stream)
+    if args.scheme == "heun":
+        prob.set_scheme("heun")
+        dt = wl.t_final / math.ceil(wl.t_final / min(0.95 * wl.h, prob.max_stable_dt()))   # dt/dx 0.95
     tiling = None
     if args.precision.startswith("bf16"):
         prob.set_tiling(args.tile, args.stages, args.variant)
@@ -236,14 +258,16 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic (seeded uniform state, analytic lattice materials)",
         "config": {"workload": wl.name, "cells": f"{wl.nx}x{wl.ny}", "Q": wl.Q, "beta": wl.beta,
                    "eps": wl.eps, "sigma_as": wl.sigma_as, "dt": dt, "precision": args.precision,
+                   "scheme": {"euler": "forward Euler, first-order upwind",
+                              "heun": "Heun, minmod-limited second-order upwind"}[args.scheme],
                    "l2": "state larger than L2 (%.0f MB per buffer)" % (units * 4 / 1e6),
                    "parallelism": f"replicas x{world}", "tiling": tiling},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": ({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": kernel_traffic(args.precision) if args.variant == 0 and args.workload == synth.LATTICE_448.name else None,
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
                      "kernel": ("step_tc2_kernel" if args.variant == 0 else "step_tc_kernel") if args.precision.startswith("bf16")
-                     else "step_simt_kernel"},
+                     else "step_simt_kernel"} if args.scheme == "euler" else alu_roofline(args, wl, ms_per_step)),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "wall_s_timed": wall,
