@@ -88,7 +88,8 @@ typedef enum { ASSN_BC_VACUUM = 0 } assn_boundary;
  *   ASSN_SCHEME_HEUN_MINMOD   the paper's explicit scheme (Sec. 3.1): Heun's method (two stages,
  *                             psi* = psi + dt L(psi), psi^{n+1} = (psi + psi* + dt L(psi*))/2)
  *                             with second-order upwind fluxes from minmod-limited slopes (two zero
- *                             ghost cells per vacuum side); FP32 / FP64 problems only. */
+ *                             ghost cells per vacuum side); all precisions (tensor-core problems on
+ *                             the persistent kernel, variant 0). */
 typedef enum { ASSN_SCHEME_EULER_UPWIND = 0, ASSN_SCHEME_HEUN_MINMOD = 1 } assn_scheme;
 
 typedef struct assn_problem assn_problem;
@@ -156,9 +157,8 @@ int assn_get_state_f32(assn_problem* p, float* psi_host);
  * psi_q(x) = max{floor, exp(-|x|^2/(4 delta)) / (4 pi delta)} at cell centres for every q. */
 int assn_init_line_source(assn_problem* p, double delta, double floor_value);
 
-/* Scheme of later assn_step calls (an assn_scheme).  ASSN_ERR_ARG for an unknown scheme; a
- * tensor-core problem with ASSN_SCHEME_HEUN_MINMOD fails at assn_step with ASSN_ERR_UNSUPPORTED,
- * and so do batches and assn_step_device with that scheme. */
+/* Scheme of later assn_step calls (an assn_scheme).  ASSN_ERR_ARG for an unknown scheme;
+ * batches and assn_step_device take ASSN_SCHEME_EULER_UPWIND only (ASSN_ERR_UNSUPPORTED). */
 int assn_set_scheme(assn_problem* p, int scheme);
 int assn_get_scheme(const assn_problem* p, int* scheme);
 

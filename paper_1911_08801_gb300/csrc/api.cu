@@ -673,10 +673,25 @@ int assn_get_scheme(const assn_problem* p, int* scheme) {
     return ASSN_OK;
 }
 
-// One Heun step (two stages) on the CUDA-core paths; the state stays in buffer cur.
+// One Heun step (two stages); the state stays in buffer cur.
 static int heun_step(assn_problem* p, double dt) {
     void* a = p->d_psi[p->cur];
     void* b = p->d_psi[p->cur ^ 1];
+    if (p->tensor()) {
+        // persistent kernel: the device step counter's parity selects the flux buffer, and each
+        // launch advances it, so stage 1 reads a and writes b, stage 2 reads b and writes a
+        if ((p->counter_host & 1) != p->cur) {
+            p->counter_host = p->cur;
+            CK(p, cudaMemcpyAsync(p->d_counter, &p->counter_host, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+        }
+        cudaError_t e = launch_heun_stage_tc2(p->plan2, p->d_flags + 1, p->cur, nullptr, 0.0f, 1.0f, p->stream);
+        if (e == cudaSuccess)
+            e = launch_heun_stage_tc2(p->plan2, p->d_flags + 1, p->cur ^ 1, (const float*)a, 0.5f, 0.5f, p->stream);
+        CK(p, e);
+        p->counter_host += 2;
+        p->launches += 2;
+        return ASSN_OK;
+    }
     if (p->precision == ASSN_FP64) {
         StepArgs<double, OrdD, CellD> s1{(const double*)a, (double*)b, (const OrdD*)p->d_ord, (const CellD*)p->d_cell,
                                          p->d_KT64, p->nx, p->ny, p->Q, p->Qp, dt, dt * p->sigma_as};
@@ -702,10 +717,14 @@ int assn_step(assn_problem* p, int nsteps, double dt) {
     if (!p) return ASSN_ERR_ARG;
     if (nsteps < 0) return fail(p, ASSN_ERR_ARG, "nsteps < 0");
     if (p->scheme == ASSN_SCHEME_HEUN_MINMOD) {
-        if (p->tensor())
-            return fail(p, ASSN_ERR_UNSUPPORTED, "the Heun + minmod scheme runs on the FP32 / FP64 paths");
         int r = assn::problem_prepare(p, dt);
         if (r) return r;
+        if (p->tensor()) {
+            if (p->variant != 0)
+                return fail(p, ASSN_ERR_UNSUPPORTED, "the Heun + minmod scheme runs on the persistent kernel (variant 0)");
+            r = ensure_plan(p, dt, false);
+            if (r) return r;
+        }
         for (int n = 0; n < nsteps; ++n) {
             r = heun_step(p, dt);
             if (r) return r;

@@ -107,6 +107,11 @@ cudaError_t tc2_plan_set_targets(Tc2Plan* plan, const int* targets, cudaStream_t
 // at launch, so the flux is read from buffer parity0 and written to parity0 ^ 1; parity0 < 0:
 // every parity comes from the device counters (batches, CUDA graphs).
 cudaError_t launch_step_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, cudaStream_t s);
+// One Heun stage with minmod-limited second-order transport on a one-problem plan: reads buffer
+// parity0, writes alpha keep + beta (psi + dt L(psi)) to buffer parity0 ^ 1 (keep may be that
+// buffer; not read when alpha == 0).
+cudaError_t launch_heun_stage_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, const float* keep, float alpha,
+                                  float beta, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_scalar_flux(const T* psi, const T* w, int ncell, int Qp, float* out_f,

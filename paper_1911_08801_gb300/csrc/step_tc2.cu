@@ -94,6 +94,8 @@ struct OneProb {
     const OrdF* ord;
     int ncell, nx, Q, Qp, MB;
     float dts;
+    const float* keep;                  // Heun stage: out = alpha keep + beta (in + dt L(in))
+    float alpha, beta;
 };
 
 struct BatchArgs {
@@ -143,6 +145,19 @@ struct Ring {
     }
 };
 
+__device__ __forceinline__ float minmod(float a, float b) {
+    return a * b > 0.0f ? (fabsf(a) < fabsf(b) ? a : b) : 0.0f;
+}
+
+// F_{i+1/2} - F_{i-1/2} in face-value units of the minmod-limited upwind scheme for one ordinate
+// along one axis, from the values at i-2 .. i+2 (zero beyond the domain): nu > 0 takes the face
+// values psi_i + D_i / 2, nu < 0 takes psi_{i+1} - D_{i+1} / 2 (D: minmod of one-sided differences).
+__device__ __forceinline__ float limited_difference(float nu, float m2, float m1, float c0, float p1, float p2) {
+    if (nu > 0.0f) return (c0 + 0.5f * minmod(c0 - m1, p1 - c0)) - (m1 + 0.5f * minmod(m1 - m2, c0 - m1));
+    if (nu < 0.0f) return (p1 - 0.5f * minmod(p1 - c0, p2 - p1)) - (c0 - 0.5f * minmod(c0 - m1, p1 - c0));
+    return 0.0f;
+}
+
 // Problem owning global tile T: the last problem whose first tile is <= T.
 __device__ __forceinline__ int find_prob(const int* tile0, int nprob, int T) {
     int lo = 0, hi = nprob - 1;
@@ -153,7 +168,9 @@ __device__ __forceinline__ int find_prob(const int* tile0, int nprob, int T) {
     return lo;
 }
 
-template <int NT, bool SPLIT, int QP>
+// HEUN: one stage of Heun's method with minmod-limited second-order upwind fluxes (the paper's
+// explicit scheme, Sec. 3.1) instead of the forward-Euler first-order step; one-problem launches only.
+template <int NT, bool SPLIT, int QP, bool HEUN = false>
 __global__ void __launch_bounds__(kThreads2, 1)
 step_tc2_kernel(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -418,7 +435,8 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             if (!WAITB(&phi_empty[buf], (use & 1u) ^ 1u, 0x400u)) break;
             if (col4 == 0) {
                 // per cell: x = 1 - dt sigma_t, y = dt (sigma_s Phi / sum w + q),
-                // z = neighbour bits (1 left, 2 right, 4 below, 8 above exist; 16 cell exists)
+                // z = neighbour bits (1 left, 2 right, 4 below, 8 above exist; 16 cell exists; 32 / 64 the cells
+                // two to the left / right exist)
                 cp_async_wait<0>();
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
@@ -429,7 +447,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                         const CellF cl = cstage[r];
                         const int yy = f / nx, xx = f - yy * nx;
                         const int bits = (xx > 0 ? 1 : 0) | (xx + 1 < nx ? 2 : 0) | (yy > 0 ? 4 : 0) |
-                                         (yy + 1 < ny ? 8 : 0) | 16;
+                                         (yy + 1 < ny ? 8 : 0) | 16 | (xx > 1 ? 32 : 0) | (xx + 2 < nx ? 64 : 0);
                         cf = make_float4(1.0f - dt * cl.sig_t, dt * (cl.sig_s_over_wsum * part[i] + cl.q),
                                          __int_as_float(bits), 0.0f);
                     }
@@ -451,8 +469,8 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
         const int e = warp - 7;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
         const int grp = e >> 2;                // which part (of kEW) of the tile's cells
-        constexpr bool kOneBuf = !SPLIT && NT / kEW >= 16;
-        constexpr int kCHe = kOneBuf ? 16 : kCH;
+        constexpr bool kOneBuf = HEUN || (!SPLIT && NT / kEW >= 16);
+        constexpr int kCHe = HEUN ? kCH : (kOneBuf ? 16 : kCH);
         constexpr int CPH = NT / (kEW * kCHe);  // chunks per part of the tile and ordinate block
 
         // Position of a chunk: global tile T of problem pid, the it-th active tile of this CTA,
@@ -568,6 +586,99 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             return true;
         };
 
+        if constexpr (HEUN) {
+            // Heun stage, one problem (host-resolved buffers): chunk of kCHe cells; x-stencil cells
+            // fb-2 .. fb+kCHe+1, y-rows two below / one below / one above (Omega_y > 0) or one below /
+            // one above / two above (Omega_y < 0).
+            const int ntl = (s_info[0] & 2) ? total : 0;
+            const int my_tiles = ntl > (int)blockIdx.x ? (ntl - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+            const int cpt = a.one.MB * CPH;
+            const int nchunk = my_tiles * cpt;
+            const int ncell = a.one.ncell, nx = a.one.nx, Qp = QP > 0 ? QP : a.one.Qp;
+            const float alpha = a.one.alpha, beta = a.one.beta;
+            for (int k = 0; k < nchunk && !*abort_flag; ++k) {
+                const int it = k / cpt, r = k - it * cpt;
+                const int m = r / CPH;
+                const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCHe;
+                const int fb = ((int)blockIdx.x + it * (int)gridDim.x) * NT + c0;
+                const int q = m * 128 + lq * 32 + lane;
+                const bool live = q < a.one.Q && fb < ncell;
+                const float4 o4 = live ? __ldg(reinterpret_cast<const float4*>(a.one.ord) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float nux = o4.x, nuy = o4.y;
+                const float* b = a.one.in + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
+                float sv[kCHe], ya[kCHe], yb[kCHe], yc[kCHe], kp[kCHe], e[4];
+                // ya: row two below (nuy > 0) or two above (nuy < 0); yb: row below; yc: row above
+                const long sy = (long)nx * Qp;
+                const long da = nuy > 0.f ? -2 * sy : 2 * sy;
+#pragma unroll
+                for (int i = 0; i < kCHe; ++i) {
+                    const int f = fb + i;
+                    const bool in = live && f < ncell;
+                    sv[i] = in ? __ldg(b + i * Qp) : 0.0f;
+                    const bool ny0 = in && nuy != 0.f;
+                    ya[i] = (ny0 && (nuy > 0.f ? f >= 2 * nx : f + 2 * nx < ncell)) ? __ldg(b + i * Qp + da) : 0.0f;
+                    yb[i] = (ny0 && f >= nx) ? __ldg(b + i * Qp - sy) : 0.0f;
+                    yc[i] = (ny0 && f + nx < ncell) ? __ldg(b + i * Qp + sy) : 0.0f;
+                    kp[i] = (in && alpha != 0.0f) ? __ldg(a.one.keep + (size_t)f * Qp + q) : 0.0f;
+                }
+                e[0] = (live && fb >= 2) ? __ldg(b - 2 * Qp) : 0.0f;
+                e[1] = (live && fb >= 1) ? __ldg(b - Qp) : 0.0f;
+                e[2] = (live && fb + kCHe < ncell) ? __ldg(b + kCHe * Qp) : 0.0f;
+                e[3] = (live && fb + kCHe + 1 < ncell) ? __ldg(b + (kCHe + 1) * Qp) : 0.0f;
+                const int buf = it & 1;
+                if (r == 0) {
+                    const uint32_t use = (uint32_t)(it >> 1);
+                    int go = 1;
+                    if (lane == 0)
+                        go = WAITB(&phi_full[buf], use & 1u, 0x1000u) && WAITB(&tm_full[buf], use & 1u, 0x2000u);
+                    go = __shfl_sync(0xffffffffu, go, 0);
+                    if (!go) break;
+                    tc_fence_after();
+                }
+                float y[kCHe];
+                __syncwarp();
+                tmem_ld<kCHe>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0), y);
+                if (fb < ncell && q < Qp) {
+                    float* po = a.one.out + (size_t)fb * Qp + q;
+                    const float4* cb = coef + buf * NT + c0;
+                    const float dts = a.one.dts, ge = dts * o4.w;
+#pragma unroll
+                    for (int i = 0; i < kCHe; ++i) {
+                        const float4 cf = cb[i];
+                        const int bits = __float_as_int(cf.z);
+                        if (!(bits & 16)) continue;
+                        if (q >= a.one.Q) {
+                            __stcs(po + i * Qp, 0.0f);
+                            continue;
+                        }
+                        auto xv = [&](int k2) -> float { return k2 < 0 ? e[k2 + 2] : (k2 < kCHe ? sv[k2] : e[k2 - kCHe + 2]); };
+                        const float xm2 = (bits & 32) ? xv(i - 2) : 0.0f;
+                        const float xm1 = (bits & 1) ? xv(i - 1) : 0.0f;
+                        const float xp1 = (bits & 2) ? xv(i + 1) : 0.0f;
+                        const float xp2 = (bits & 64) ? xv(i + 2) : 0.0f;
+                        const float c = sv[i];
+                        const float tx = limited_difference(nux, xm2, xm1, c, xp1, xp2);
+                        const float ty = nuy > 0.f ? limited_difference(nuy, ya[i], yb[i], c, yc[i], 0.0f)
+                                                   : limited_difference(nuy, 0.0f, yb[i], c, yc[i], ya[i]);
+                        const float st = SPLIT ? c : __bfloat162float(__float2bfloat16_rn(c));
+                        float adv = fmaf(c, cf.x, cf.y);
+                        adv = fmaf(-nux, tx, adv);
+                        adv = fmaf(-nuy, ty, adv);
+                        adv = fmaf(dts, y[i], adv);
+                        adv = fmaf(-ge, st, adv);
+                        __stcs(po + i * Qp, fmaf(alpha, kp[i], beta * adv));
+                    }
+                }
+                if (r == cpt - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&tm_empty[buf]);
+                        mbar_arrive(&phi_empty[buf]);
+                    }
+                }
+            }
+        } else {
         float s0[kCHe], u0[kCHe], l0 = 0.f, r0 = 0.f;
         if (a.one_fixed) {
             // One problem: its tiles blockIdx.x, blockIdx.x + gridDim.x, ... (all or none active);
@@ -678,6 +789,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 cur = nxt;
             }
             }
+        }
         }
     }
 
@@ -924,9 +1036,9 @@ cudaError_t tc2_plan_set_targets(Tc2Plan* p, const int* targets, cudaStream_t st
     return cudaMemcpyAsync(p->d_probs, p->host.data(), sizeof(ProbDesc) * p->nprob, cudaMemcpyHostToDevice, stream);
 }
 
-template <int NT, bool SPLIT, int QP>
+template <int NT, bool SPLIT, int QP, bool HEUN = false>
 static cudaError_t launch2(const Tc2Plan* p, const BatchArgs& a, cudaStream_t s) {
-    auto kern = step_tc2_kernel<NT, SPLIT, QP>;
+    auto kern = step_tc2_kernel<NT, SPLIT, QP, HEUN>;
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (r != cudaSuccess) return r;
     kern<<<p->grid, kThreads2, p->smem, s>>>(a);
@@ -957,8 +1069,35 @@ static cudaError_t dispatch(const Tc2Plan* p, const BatchArgs& a, cudaStream_t s
     }
 }
 
+template <bool SPLIT>
+static cudaError_t dispatch_heun(const Tc2Plan* p, const BatchArgs& a, cudaStream_t s) {
+    switch (p->NT) {
+        case 32: return launch2<32, SPLIT, 0, true>(p, a, s);
+        case 64: return launch2<64, SPLIT, 0, true>(p, a, s);
+        case 128: return launch2<128, SPLIT, 0, true>(p, a, s);
+        default: return launch2<256, SPLIT, 0, true>(p, a, s);
+    }
+}
+
+static BatchArgs batch_args(Tc2Plan* p, unsigned int* err_flag, int parity0);
+
+cudaError_t launch_heun_stage_tc2(Tc2Plan* p, unsigned int* err_flag, int parity0, const float* keep, float alpha,
+                                  float beta, cudaStream_t stream) {
+    if (!p || p->nprob != 1 || parity0 < 0) return cudaErrorInvalidValue;
+    BatchArgs a = batch_args(p, err_flag, parity0);
+    a.one.keep = keep;
+    a.one.alpha = alpha;
+    a.one.beta = beta;
+    return p->split ? dispatch_heun<true>(p, a, stream) : dispatch_heun<false>(p, a, stream);
+}
+
 cudaError_t launch_step_tc2(Tc2Plan* p, unsigned int* err_flag, int parity0, cudaStream_t stream) {
     if (!p) return cudaErrorInvalidValue;
+    const BatchArgs a = batch_args(p, err_flag, parity0);
+    return p->split ? dispatch<true>(p, a, stream) : dispatch<false>(p, a, stream);
+}
+
+static BatchArgs batch_args(Tc2Plan* p, unsigned int* err_flag, int parity0) {
     BatchArgs a;
     for (int i = 0; i < kParamProbs && i < p->nprob; ++i) {
         const ProbDesc& d = p->host[i];
@@ -989,7 +1128,10 @@ cudaError_t launch_step_tc2(Tc2Plan* p, unsigned int* err_flag, int parity0, cud
     a.SB = p->SB;
     a.SA = p->SA;
     a.MPRmax = p->MPRmax;
-    return p->split ? dispatch<true>(p, a, stream) : dispatch<false>(p, a, stream);
+    a.one.keep = nullptr;
+    a.one.alpha = 0.0f;
+    a.one.beta = 1.0f;
+    return a;
 }
 
 }  // namespace assn

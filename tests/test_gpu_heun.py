@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import synth
-from helpers import ensure_built, oracle_setup, rel_l2
+from helpers import RUN_TOL, ensure_built, offdiag_rowsum, oracle_setup, rel_l2, step_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,30 @@ def test_one_heun_step_matches_oracle(A, nx, ny, npol, naz, precision, tol):
     p.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("nx,ny,npol,naz", [(37, 11, 4, 8), (40, 24, 8, 16), (23, 29, 16, 32)])
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_one_heun_step_tensor_cores(A, nx, ny, npol, naz, precision):
+    """Both stages on the persistent tensor-core kernel.  Each stage errs by at most the one-step
+    bound of its precision (BF16 operands of the contraction); the second stage halves the sum of
+    the first stage's error and its own, so twice the one-step bound covers the step."""
+    wl = synth.Workload("heun", "random", nx, ny, 0.0, 0.1 * nx, 0.0, 0.1 * ny, npol, naz, 0.6, seed=nx + 5 * ny)
+    psi0 = wl.psi0()
+    p = problem(A, wl, precision, psi0)
+    dt = 0.9 * p.max_stable_dt()
+    l0 = p.launch_count()
+    p.step(1, dt)
+    assert p.launch_count() - l0 == 2
+    got = p.state()
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    ref = O.step_heun(psi0, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    scale = max(1.0, np.abs(ref).max(), np.abs(psi0).max())
+    tol = 2.0 * step_tolerance(precision, dt, wl.sigma_as, scale, offdiag_rowsum(K))
+    assert np.abs(got - ref).max() <= tol
+    p.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("bf16", RUN_TOL["bf16"]),
+                                           ("bf16x3", RUN_TOL["bf16x3"])])
 def test_line_source_at_cfl_095(A, precision, tol):
     """The 64^2 line source (Q = 128, beta = 1/8) run to t = 1 at the paper's dt/dx = 0.95."""
     wl = synth.LINE_SOURCE_64
@@ -67,9 +90,6 @@ def test_line_source_at_cfl_095(A, precision, tol):
 def test_heun_unsupported_combinations(A):
     wl = synth.Workload("heun", "random", 8, 8, 0.0, 0.8, 0.0, 0.8, 4, 8, 0.6, seed=2)
     p = problem(A, wl, "bf16", wl.psi0())
-    with pytest.raises(A.AssnError) as ei:
-        p.step(1, 0.5 * p.max_stable_dt())
-    assert ei.value.status == A._lib.ASSN_ERR_UNSUPPORTED
     with A.Batch() as b:
         with pytest.raises(A.AssnError) as ei:
             b.add(p, 1, 0.5 * p.max_stable_dt())
