@@ -166,6 +166,16 @@ def alu_roofline(args, wl, ms_per_step: float) -> dict:
             "kernel": "stage_simt_kernel (two launches per step)"}
 
 
+def heun_tc_roofline(wl, ms_per_step: float) -> dict:
+    """Heun on the tensor-core kernel: per update, stage 1 reads psi^n and writes psi*, stage 2 reads
+    psi* and psi^n and writes psi^{n+1}: 20 B of FP32 state."""
+    hbm, src = peaks()
+    achieved = 20.0 * wl.nx * wl.ny * wl.Q / (ms_per_step / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_update": 20,
+            "kernel": "step_tc2_kernel<..., HEUN> (two launches per step)"}
+
+
 def max_over_ranks(ms: float, dist, device: str) -> float:
     """The slowest rank's time (every rank gets it); ``dist`` None on one process."""
     if dist is None:
@@ -267,7 +277,9 @@ def run_ours(args, rank, world, dist):
                      "traffic": kernel_traffic(args.precision) if args.variant == 0 and args.workload == synth.LATTICE_448.name else None,
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
                      "kernel": ("step_tc2_kernel" if args.variant == 0 else "step_tc_kernel") if args.precision.startswith("bf16")
-                     else "step_simt_kernel"} if args.scheme == "euler" else alu_roofline(args, wl, ms_per_step)),
+                     else "step_simt_kernel"} if args.scheme == "euler" else
+                     (heun_tc_roofline(wl, ms_per_step) if args.precision.startswith("bf16")
+                      else alu_roofline(args, wl, ms_per_step))),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "wall_s_timed": wall,
