@@ -190,7 +190,6 @@ int install_quadrature(assn_problem* p, int Q, const double* omega, const double
     dfree(p->d_w64);
     dfree(p->d_w32);
     dfree(p->d_ord);
-    dfree(p->d_ydir);
     p->ord_dt = -1;
     p->Q = Q;
     p->Qp = (Q + 63) / 64 * 64;
@@ -207,16 +206,6 @@ int install_quadrature(assn_problem* p, int Q, const double* omega, const double
     CK(p, cudaMemcpyAsync(p->d_omega, omega, sizeof(double) * 3 * Q, cudaMemcpyHostToDevice, p->stream));
     CK(p, cudaMemcpyAsync(p->d_w64, wp.data(), sizeof(double) * p->Qp, cudaMemcpyHostToDevice, p->stream));
     CK(p, cudaMemcpyAsync(p->d_w32, wf.data(), sizeof(float) * p->Qp, cudaMemcpyHostToDevice, p->stream));
-    // Upwind y side per aligned group of 4 ordinates, taken from its first ordinate with Omega_y != 0:
-    // 1 = the cell below (Omega_y > 0), 2 = the cell above, 0 = no y transport in the group.
-    std::vector<unsigned char> yd(p->Qp / 4, 0);
-    for (int g = 0; g < p->Qp / 4; ++g)
-        for (int j = 0; j < 4 && 4 * g + j < Q; ++j) {
-            const double oy = omega[3 * (4 * g + j) + 1];
-            if (oy != 0.0) { yd[g] = oy > 0 ? 1 : 2; break; }
-        }
-    CK(p, cudaMalloc(&p->d_ydir, p->Qp / 4));
-    CK(p, cudaMemcpyAsync(p->d_ydir, yd.data(), p->Qp / 4, cudaMemcpyHostToDevice, p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     int r = alloc_state(p);
     if (r) return r;
@@ -333,7 +322,7 @@ int assn_destroy(assn_problem* p) {
     cudaSetDevice(p->dev);
     if (p->stream) cudaStreamSynchronize(p->stream);
     free_operands(p);
-    dfree(p->d_omega); dfree(p->d_w64); dfree(p->d_w32); dfree(p->d_ord); dfree(p->d_cell); dfree(p->d_ydir);
+    dfree(p->d_omega); dfree(p->d_w64); dfree(p->d_w32); dfree(p->d_ord); dfree(p->d_cell);
     dfree(p->d_psi[0]); dfree(p->d_psi[1]); dfree(p->d_partials); dfree(p->d_scalar); dfree(p->d_flags);
     dfree(p->d_counter);
     dfree(p->d_stage);

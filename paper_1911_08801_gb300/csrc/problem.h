@@ -29,7 +29,6 @@ struct assn_problem {
 
     // device memory
     double* d_omega = nullptr;
-    unsigned char* d_ydir = nullptr;   // [Qp/4] upwind y side per group of 4 ordinates (tensor-core epilogue)
     double* d_w64 = nullptr;
     float* d_w32 = nullptr;
     double* d_K64 = nullptr;
