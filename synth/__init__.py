@@ -263,3 +263,22 @@ def poisson_arrivals(seed: int, count: int, rate: float) -> np.ndarray:
     gaps = rng.exponential(1.0 / rate, size=count)
     gaps[0] = 0.0
     return np.cumsum(gaps)
+
+
+def icosahedron_order2():
+    """The paper's printed order-2 icosahedron quadrature (Appendix A): Omega [12][3], w [12].
+
+    Read from the cited fixture tests/golden/icosahedron_order2.txt (input data, not method code).
+    """
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                        "icosahedron_order2.txt")
+    rows = np.loadtxt(path, comments="#")
+    return rows[:, :3].copy(), rows[:, 3].copy()
+
+
+def parameter_study_grid():
+    """(sigma_as, beta) pairs of the coarse parameter study (Sec. 4.1: 306 configurations, explicit,
+    N_q = 12 on 50 x 50 cells).  The paper's heatmap values are unreadable; read here as 17 sigma_as
+    values 0 .. 16 times 18 beta values 0.5 .. 9 (eps = beta / N_q)."""
+    return [(float(s), float(b)) for s in np.linspace(0.0, 16.0, 17) for b in np.linspace(0.5, 9.0, 18)]
