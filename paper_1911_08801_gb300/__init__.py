@@ -235,7 +235,12 @@ class Server:
     def wait(self, rid: int, timeout_s: float = -1.0):
         """(scalar flux [ny][nx], latency s, queueing s) of request ``rid``; releases it."""
         phi = np.empty(self._shapes[rid])
-        lat, qs = _lib.assn_server_wait(self.handle, rid, timeout_s, phi)
+        try:
+            lat, qs = _lib.assn_server_wait(self.handle, rid, timeout_s, phi)
+        except AssnError as e:
+            if e.status != _lib.ASSN_ERR_TIMEOUT:   # the request is released unless still pending
+                del self._shapes[rid]
+            raise
         del self._shapes[rid]
         return phi, lat, qs
 
