@@ -59,3 +59,31 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
         _lib.assn_create(4, 4, 0.0, 1.0, 0.0, 1.0, 17)
     assert e.value.status == _lib.ASSN_ERR_ARG
     assert _lib.assn_destroy(None) is None
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/assn.h compiles as pedantic C99, and a C program links against libassn.so and calls the
+    device-free entry points (no GPU needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    inc = os.path.join(root, "include")
+    libdir = os.path.join(root, "paper_1911_08801_gb300")
+    src = tmp_path / "abi.c"
+    src.write_text('#include "assn.h"\n#include <stdio.h>\n#include <string.h>\n'
+                   'int main(void) {\n'
+                   '  if (assn_abi_version() != ASSN_ABI_VERSION) return 1;\n'
+                   '  if (strcmp(assn_status_string(ASSN_ERR_TIMEOUT), "ASSN_ERR_TIMEOUT")) return 2;\n'
+                   '  size_t b = 0;\n'
+                   '  if (assn_footprint_bytes(448, 448, 512, ASSN_BF16, &b) != ASSN_OK || b < 822083584u) return 3;\n'
+                   '  if (assn_create(NULL, 1, 1, 0, 1, 0, 1, ASSN_BF16, NULL) != ASSN_ERR_ARG) return 4;\n'
+                   '  puts("ok");\n  return 0;\n}\n')
+    exe = tmp_path / "abi"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{inc}", str(src), f"-L{libdir}",
+                        "-lassn", f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
