@@ -33,8 +33,11 @@
 //                 psi' = psi (1 - dt sigma_t - a_x - a_y) + a_x psi_upx + a_y psi_upy
 //                        + dt (sigma_s Phi / sum w + q) + dt sigma_as (D - e psi~)
 //               while the MMA of the next tile fills the other buffer.  Four warps share each
-//               TMEM lane quarter; each keeps the flux values of its next 8-cell chunk in flight
-//               (register double buffer).
+//               TMEM lane quarter; the one-pass kernel loads 16-cell chunks of flux values, the
+//               split kernel keeps its next 8-cell chunk in flight (register double buffer).
+//   Most split forward-Euler kernels with tiles of up to 128 cells run 20 warps instead of 23:
+//   the G producer is warp 1, lane 1, and warps 2-3 are the converters (epilogue 4-19), which
+//   lets each thread hold 96 registers instead of 80.
 // SPLIT (BF16X3) keeps BF16 residuals of both operands and issues hi*hi + hi*lo + lo*hi.
 // QP > 0 fixes the ordinate stride at compile time (launches whose problems share one of the
 // common strides); QP = 0 reads it per problem.
@@ -74,8 +77,6 @@ using namespace ptx;
 constexpr int kEW = 4;                  // epilogue warps per TMEM lane quarter
 constexpr int kCH = 8;                  // cells per epilogue chunk (double-buffered form)
 constexpr int kEpiWarps = 4 * kEW;
-constexpr int kWarps = 7 + kEpiWarps;
-constexpr int kThreads2 = kWarps * 32;
 constexpr int kAStage = 128 * 64 * 2;   // one [128 x 64] BF16 chunk of G
 constexpr int kMaxProbs = 1024;         // problems per launch
 constexpr int kParamProbs = 4;          // problems whose tensor maps also travel as kernel parameters
@@ -168,11 +169,27 @@ __device__ __forceinline__ int find_prob(const int* tile0, int nprob, int T) {
     return lo;
 }
 
+// Warp roles of one kernel instance.  Four converter warps, except in the split forward-Euler
+// kernels up to 128-cell tiles: there two converter warps do the work and the two TMA producers
+// share warp 1, so that the block has 20 warps and ptxas may give each thread 96 registers instead
+// of 80 (the split epilogue keeps two chunks of flux values in flight).  The 128-cell instance
+// for 64 ordinates keeps four converters: with two, its converter rows spill.
+template <int NT, bool SPLIT, int QP, bool HEUN>
+struct Roles {
+    static constexpr bool kTwo = SPLIT && !HEUN && (NT <= 64 || (NT == 128 && QP != 64));
+    static constexpr int kConv = kTwo ? 2 : 4;                             // converter warps
+    static constexpr int kConv0 = kConv == 2 ? 2 : 3;                      // first converter warp
+    static constexpr int kGWarp = kConv0 - 1, kGLane = kConv == 2 ? 1 : 0; // kernel-matrix producer
+    static constexpr int kEpi0 = kConv0 + kConv;                           // first epilogue warp
+    static constexpr int kThreads = (kEpi0 + kEpiWarps) * 32;
+};
+
 // HEUN: one stage of Heun's method with minmod-limited second-order upwind fluxes (the paper's
 // explicit scheme, Sec. 3.1) instead of the forward-Euler first-order step; one-problem launches only.
 template <int NT, bool SPLIT, int QP, bool HEUN = false>
-__global__ void __launch_bounds__(kThreads2, 1)
+__global__ void __launch_bounds__((Roles<NT, SPLIT, QP, HEUN>::kThreads), 1)
 step_tc2_kernel(const __grid_constant__ BatchArgs a) {
+    using R = Roles<NT, SPLIT, QP, HEUN>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const Layout<NT, SPLIT> L(a.SS, a.SB, a.SA, a.MPRmax);
@@ -209,13 +226,13 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
         s_info[i] = (c & 1) | (c < d.target ? 2 : 0) | (d.KC << 8) | (d.MB << 16) | (d.MPR << 24);
     }
     if (tid == 0) {
-        for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], 4); }
-        for (int s = 0; s < a.SB; ++s) { mbar_init(&bf_full[s], 4); mbar_init(&bf_empty[s], 1); }
+        for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], R::kConv); }
+        for (int s = 0; s < a.SB; ++s) { mbar_init(&bf_full[s], R::kConv); mbar_init(&bf_empty[s], 1); }
         for (int s = 0; s < a.SA; ++s) { mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tm_full[b], 1);
             mbar_init(&tm_empty[b], kEpiWarps);
-            mbar_init(&phi_full[b], 4);
+            mbar_init(&phi_full[b], R::kConv);
             mbar_init(&phi_empty[b], kEpiWarps);
         }
         *abort_flag = 0;
@@ -289,7 +306,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 if (!ok) break;
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 && (lane == 0 || R::kGWarp != 1)) {
         if (lane == 0) {
             // ---------------------------------------------------------------- flux TMA producer
             // evict-last: the epilogue re-reads these lines (own values and y-neighbours) shortly
@@ -311,8 +328,8 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 if (!ok) break;
             }
         }
-    } else if (warp == 2) {
-        if (lane == 0) {
+    } else if (warp == R::kGWarp) {
+        if (lane == R::kGLane) {
             // ---------------------------------------------------------------- kernel-matrix TMA producer
             const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
             Ring ra;
@@ -337,11 +354,12 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 if (!ok) break;
             }
         }
-    } else if (warp < 7) {
+    } else if (warp < R::kEpi0) {
         // -------------------------------------------------------------------- converters
-        constexpr int NR = NT / 8;             // rows (cells) per thread
-        const int ct = tid - 96;               // 0..127
-        const int rsub = ct >> 4;              // 0..7
+        constexpr int RS = 2 * R::kConv;       // row stride: rows handled by one column of threads
+        constexpr int NR = NT / RS;            // rows (cells) per thread
+        const int ct = tid - 32 * R::kConv0;   // 0 .. 32 kConv - 1
+        const int rsub = ct >> 4;              // 0 .. RS - 1
         const int col4 = ct & 15;              // float4 column within the 64-ordinate chunk
         // Problem fields are refetched only when the tile's problem changes; the weights of the
         // next chunk (across tile ends) and the cell constants of the tile (cp.async into this
@@ -371,7 +389,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             if (col4 == 0) {
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    const int r = rsub + 8 * i;
+                    const int r = rsub + RS * i;
                     const int f = tile * NT + r;
                     if (f < ncell) cp_async16(smem_u32(cstage + r), cellp + f, 16u);
                 }
@@ -393,7 +411,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 unsigned char* dlo = blo + rb.s * LT::kB;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    const int r = rsub + 8 * i;
+                    const int r = rsub + RS * i;
                     const float4 v = src[r * 16 + col4];
                     part[i] += w4.x * v.x + w4.y * v.y + w4.z * v.z + w4.w * v.w;
                     uint2 h;
@@ -440,7 +458,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 cp_async_wait<0>();
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    const int r = rsub + 8 * i;
+                    const int r = rsub + RS * i;
                     const int f = tile * NT + r;
                     float4 cf = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
                     if (f < ncell) {
@@ -466,7 +484,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
         // keeps 8-cell chunks double-buffered (the next chunk's loads in flight while the current
         // one is computed).  The flux input is read-only during the launch, so loads may run ahead
         // of the MMA (and into the next tile).
-        const int e = warp - 7;
+        const int e = warp - R::kEpi0;
         const int lq = warp & 3;               // TMEM lane quarter this warp may access
         const int grp = e >> 2;                // which part (of kEW) of the tile's cells
         constexpr bool kOneBuf = HEUN || (!SPLIT && NT / kEW >= 16);
@@ -1041,7 +1059,7 @@ static cudaError_t launch2(const Tc2Plan* p, const BatchArgs& a, cudaStream_t s)
     auto kern = step_tc2_kernel<NT, SPLIT, QP, HEUN>;
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (r != cudaSuccess) return r;
-    kern<<<p->grid, kThreads2, p->smem, s>>>(a);
+    kern<<<p->grid, Roles<NT, SPLIT, QP, HEUN>::kThreads, p->smem, s>>>(a);
     return cudaGetLastError();
 }
 
