@@ -15,6 +15,9 @@ and the symmetries of the line source).  The Heun + minmod functions (the paper'
 explicit scheme, Sec. 3.1) are pinned by the minmod definition, exactness of the
 limited fluxes on monotone quadratics, constant-state and periodic conservation,
 no new extrema on an advected step, the exact RK2 amplification factor on decay,
-and a second-order convergence rate on a smooth periodic profile.
+and a second-order convergence rate on a smooth periodic profile.  The icosahedron
+quadrature (Sec. 3.3) is pinned by the paper's printed order-2 table (Appendix A),
+the point count N_q = 10 (k-1)^2 + 2, the 4 pi weight sum, its symmetries, exact
+degree-5 moments on the regular base and convergence of moments on the printed one.
 """
 from .assn_oracle import *  # noqa: F401,F403

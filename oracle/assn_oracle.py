@@ -21,6 +21,7 @@ __all__ = [
     "product_quadrature", "s_eps", "s_exp", "kernel_matrix", "scalar_flux",
     "transport", "step", "run", "mass", "step_at_cells",
     "minmod", "transport_minmod", "rhs", "step_heun", "run_heun",
+    "icosahedron_quadrature",
 ]
 
 
@@ -48,6 +49,94 @@ def product_quadrature(n_polar: int, n_azim: int):
             w[q] = wgl[i] * 2.0 * math.pi / n_azim
     return Omega, w
 
+
+
+def _sphere_triangle_area(a, b, c) -> float:
+    """Area of the spherical triangle with unit-vector corners a, b, c (the tangent half-angle
+    formula of Van Oosterom and Strackee, 1983)."""
+    num = abs(float(np.dot(a, np.cross(b, c))))
+    den = 1.0 + float(np.dot(a, b) + np.dot(b, c) + np.dot(c, a))
+    return 2.0 * math.atan2(num, den)
+
+
+def icosahedron_quadrature(order: int, base: str = "printed"):
+    """Icosahedron quadrature on S^2 (Sec. 3.3; the paper prints order 2 in Appendix A).
+
+    The construction the paper describes: every face of an icosahedron is triangulated with
+    equally spaced points on its edges and the matching interior points (order k: k - 1 segments
+    per edge, so N_q = 10 (k-1)^2 + 2), the points are mapped onto the unit sphere, and a point's
+    weight is the area of the cell around it whose corners are the midpoints of the neighbouring
+    triangles (and of the edges between them): the barycentric dual cell.  One vertex sits at
+    (0, 0, 1).
+
+    Readings (the paper's text and its printed table disagree on the base solid):
+      * base "printed": the twelve base vertices are (0, +-1, +-g), (+-1, +-g, 0) and
+        (+-1, 0, +-g), g the golden ratio, joined into the 20 faces of the regular icosahedron
+        below; with this base the construction reproduces the printed order-2 points and weights.
+        base "regular": the regular icosahedron, (+-g, 0, +-1) in the last group.
+      * Both are turned about the x axis so that (0, 1, g) lands on (0, 0, 1).
+      * Midpoints are taken on the sphere: the centre of a triangle with mapped corners a, b, c is
+        (a + b + c) / |a + b + c|, the midpoint of an edge (a + b) / |a + b|; cell boundaries are
+        great-circle arcs between them.
+
+    Returns (Omega[N_q, 3], w[N_q]); the order of the points is not significant.
+    """
+    if order < 2:
+        raise ValueError("order >= 2")
+    g = (1.0 + math.sqrt(5.0)) / 2.0
+    regular, used = [], []
+    for s1 in (1.0, -1.0):
+        for s2 in (1.0, -1.0):
+            regular += [(0.0, s1, s2 * g), (s1, s2 * g, 0.0), (s1 * g, 0.0, s2)]
+            used += [(0.0, s1, s2 * g), (s1, s2 * g, 0.0),
+                     (s1, 0.0, s2 * g) if base == "printed" else (s1 * g, 0.0, s2)]
+    if base not in ("printed", "regular"):
+        raise ValueError("base is 'printed' or 'regular'")
+    R = np.array(regular)
+    V = np.array(used)
+    # faces of the regular icosahedron: triples of vertices that are pairwise one edge (2) apart
+    near = np.abs(np.linalg.norm(R[:, None, :] - R[None, :, :], axis=2) - 2.0) < 1e-9
+    faces = [(i, j, k) for i in range(12) for j in range(i + 1, 12) for k in range(j + 1, 12)
+             if near[i, j] and near[j, k] and near[i, k]]
+    assert len(faces) == 20
+    # turn about x: (0, 1, g) -> (0, 0, 1)
+    ang = math.atan2(1.0, g)
+    rot = np.array([[1.0, 0.0, 0.0],
+                    [0.0, math.cos(ang), -math.sin(ang)],
+                    [0.0, math.sin(ang), math.cos(ang)]])
+    V = V @ rot.T
+    n = order - 1
+    index, points = {}, []
+
+    def node(f, i, j):
+        # the point with i / n of the way to the face's second vertex and j / n to its third;
+        # keyed by its barycentric counts so that points on shared edges and vertices coincide
+        a, b, c = faces[f]
+        key = tuple(sorted((v, m) for v, m in ((a, n - i - j), (b, i), (c, j)) if m > 0))
+        if key not in index:
+            p = V[a] + (i / n) * (V[b] - V[a]) + (j / n) * (V[c] - V[a])
+            index[key] = len(points)
+            points.append(p / np.linalg.norm(p))
+        return index[key]
+
+    triangles = []
+    for f in range(20):
+        for i in range(n):
+            for j in range(n - i):
+                triangles.append((node(f, i, j), node(f, i + 1, j), node(f, i, j + 1)))
+                if i + j + 2 <= n:
+                    triangles.append((node(f, i + 1, j), node(f, i + 1, j + 1), node(f, i, j + 1)))
+    Omega = np.array(points)
+    w = np.zeros(len(points))
+    unit = lambda x: x / np.linalg.norm(x)
+    for t in triangles:
+        P = [Omega[v] for v in t]
+        centre = unit(P[0] + P[1] + P[2])
+        for k in range(3):
+            a, b, c = P[k], P[(k + 1) % 3], P[(k + 2) % 3]
+            w[t[k]] += (_sphere_triangle_area(a, unit(a + b), centre)
+                        + _sphere_triangle_area(a, centre, unit(a + c)))
+    return Omega, w
 
 # --------------------------------------------------------------------------- S1
 def s_eps(mu, eps: float):

@@ -184,6 +184,85 @@ def test_icosahedron_order2_table_from_paper():
     assert np.allclose(Kr.sum(1), 1.0, rtol=1e-14)
 
 
+
+def _printed_table():
+    rows = [list(map(float, l.split())) for l in open(os.path.join(HERE, "golden", "icosahedron_order2.txt"))
+            if l.strip() and not l.startswith("#")]
+    return np.array(rows)
+
+
+def _match(A, B, tol):
+    """Index m with A[i] == B[m[i]] within tol, one to one."""
+    d = np.linalg.norm(A[:, None, :] - B[None, :, :], axis=2)
+    m = d.argmin(1)
+    assert d.min(1).max() <= tol and len(set(m.tolist())) == len(A)
+    return m
+
+
+def test_icosahedron_generator_reproduces_printed_table():
+    """The construction of Sec. 3.3 on the printed base reproduces the printed order-2 points and
+    weights of Appendix A (a dropped edge-midpoint part of the dual cell moves weights by 0.04)."""
+    tab = _printed_table()
+    Om, w = O.icosahedron_quadrature(2, "printed")
+    m = _match(tab[:, :3], Om, 1e-15)
+    assert np.abs(w[m] - tab[:, 3]).max() <= 1e-14
+
+
+def test_icosahedron_regular_order2_is_the_regular_solid():
+    """On the regular base the 12 order-2 points are the vertices of a regular icosahedron (every
+    pair at angle cos = +-1/sqrt 5 or antipodal) and by symmetry each weighs 4 pi / 12."""
+    Om, w = O.icosahedron_quadrature(2, "regular")
+    G = Om @ Om.T
+    off = np.abs(G[~np.eye(12, dtype=bool)])
+    assert np.all((np.abs(off - 1 / math.sqrt(5)) < 1e-15) | (np.abs(off - 1) < 1e-15))
+    assert np.allclose(w, FOUR_PI / 12, rtol=1e-14)
+
+
+@pytest.mark.parametrize("base", ["printed", "regular"])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 7])
+def test_icosahedron_counts_and_symmetries(base, order):
+    """N_q = 10 (k-1)^2 + 2 unit points with positive weights summing to 4 pi (the dual cells tile
+    the sphere), a point at (0, 0, 1), the set closed under Omega -> -Omega with equal weights;
+    the printed base is also closed under x -> -x (as its table is)."""
+    Om, w = O.icosahedron_quadrature(order, base)
+    assert len(w) == 10 * (order - 1) ** 2 + 2
+    assert np.all(w > 0) and abs(w.sum() - FOUR_PI) < 1e-13
+    assert np.allclose(np.linalg.norm(Om, axis=1), 1.0, atol=1e-15)
+    assert np.min(np.linalg.norm(Om - [0.0, 0.0, 1.0], axis=1)) < 1e-15
+    m = _match(-Om, Om, 1e-14)
+    assert np.allclose(w[m], w, rtol=1e-12)
+    if base == "printed":
+        m = _match(Om * [-1.0, 1.0, 1.0], Om, 1e-14)
+        assert np.allclose(w[m], w, rtol=1e-12)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 6])
+def test_icosahedron_regular_integrates_degree_5_exactly(order):
+    """A rule invariant under the icosahedral group integrates every spherical harmonic of degree
+    1..5 to zero (the first invariant harmonic has degree 6), so with sum w = 4 pi all polynomial
+    moments up to degree 5 are exact: int mu^2 = 4 pi/3, mu^4 = 4 pi/5, x^2 y^2 = 4 pi/15, odd = 0."""
+    Om, w = O.icosahedron_quadrature(order, "regular")
+    x, y, z = Om.T
+    assert abs(w @ z ** 2 - FOUR_PI / 3) < 1e-13
+    assert abs(w @ x ** 2 - FOUR_PI / 3) < 1e-13
+    assert abs(w @ z ** 4 - FOUR_PI / 5) < 1e-13
+    assert abs(w @ (x ** 2 * y ** 2) - FOUR_PI / 15) < 1e-13
+    for f in (x, x * y, x * y * z, z ** 3, x ** 3 * y ** 2):
+        assert abs(w @ f) < 1e-13
+    if order == 2:
+        assert abs(w @ z ** 6 - FOUR_PI / 7) > 1e-3    # degree 6 is not exact: the check can fail
+
+
+def test_icosahedron_printed_converges_with_order():
+    """The printed base is not a regular solid, so moments are not exact, but the rule converges:
+    the error of int mu^2 falls with every order and by more than 10x from order 3 to 10."""
+    err = []
+    for k in range(2, 11):
+        Om, w = O.icosahedron_quadrature(k, "printed")
+        err.append(abs(w @ Om[:, 2] ** 2 - FOUR_PI / 3))
+    assert all(b < a for a, b in zip(err, err[1:]))
+    assert err[-1] < 0.1 * err[1]
+
 # ----------------------------------------------------------------------------- scalar flux (S3)
 def test_scalar_flux_moments():
     Om, w = O.product_quadrature(8, 16)
