@@ -16,6 +16,7 @@ time over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -55,9 +56,10 @@ def parse():
                     choices=["step", "ensemble", "serving", "accuracy", "oracle-phi", "paramstudy"],
                     help="step: one solve stepped K times; ensemble: 64 uneven solves to completion in one "
                          "batch; serving: Poisson request stream through the serving loop")
-    ap.add_argument("--scheme", default="euler", choices=["euler", "heun"],
-                    help="step mode: forward Euler + first-order upwind, or Heun + minmod (FP32 / FP64 only)")
+    ap.add_argument("--scheme", default=None, choices=["euler", "heun"],
+                    help="step mode: forward Euler + first-order upwind, or Heun + minmod (default: the workload's)")
     ap.add_argument("--count", type=int, default=64, help="ensemble members / serving requests")
+    ap.add_argument("--only", default="", help="accuracy: run only the case of this workload name")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate, requests/s (0 = about 70%% load)")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
@@ -142,12 +144,39 @@ class ClockSampler:
 
 
 def make_problem(A, wl, precision, stream):
+    """The workload's problem: its quadrature, cross sections, kernel width and normalisation, scheme."""
     p = A.Problem(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1, precision, stream=stream)
-    p.set_product_quadrature(wl.n_polar, wl.n_azim)
+    if wl.quadrature == "icosahedron":
+        p.set_icosahedron_quadrature(wl.ico_order, wl.ico_base)
+    else:
+        p.set_product_quadrature(wl.n_polar, wl.n_azim)
     sa, ss, q = wl.materials()
     p.set_cross_sections(sa, ss, q)
-    p.set_artificial_scattering(wl.sigma_as, wl.eps)
+    p.set_artificial_scattering(wl.sigma_as, wl.eps, A.ASSN_KERNEL_GAUSS,
+                                A.ASSN_NORM_ROW if wl.normalisation == "row" else A.ASSN_NORM_COLUMN)
+    if wl.scheme == "heun":
+        p.set_scheme("heun")
     return p
+
+
+def oracle_parts(wl):
+    """(Omega, w, K) of the workload in the oracle: its quadrature, kernel width and normalisation."""
+    import oracle as O
+
+    if wl.quadrature == "icosahedron":
+        Om, w = O.icosahedron_quadrature(wl.ico_order, wl.ico_base)
+    else:
+        Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
+    return Om, w, O.kernel_matrix(Om, w, wl.eps, normalisation=wl.normalisation)
+
+
+def oracle_step(scheme: str):
+    import oracle as O
+
+    return O.step_heun if scheme == "heun" else O.step
+
+
+L2_BYTES = 129 << 20     # GB300 L2
 
 
 # CUDA-core peaks (FMA = 2 flops) from unit counts and the 2070 MHz maximum SM clock: 152 SMs x 128
@@ -206,12 +235,15 @@ def run_ours(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     wl = synth.WORKLOADS[args.workload]
-    n_total, dt = wl.steps()
+    args.scheme = args.scheme or wl.scheme
     stream = torch.cuda.Stream()
     prob = make_problem(A, wl, args.precision, stream)
     if args.scheme == "heun":
+        # 0.95 of the admissible dt of the limited scheme (the literal dt/dx = 0.95 is unstable in 2D)
         prob.set_scheme("heun")
-        dt = wl.t_final / math.ceil(wl.t_final / min(0.95 * wl.h, prob.max_stable_dt()))   # dt/dx 0.95
+        dt = wl.t_final / math.ceil(wl.t_final / (0.95 * prob.max_stable_dt()))
+    else:
+        _, dt = wl.steps()
     tiling = None
     if args.precision.startswith("bf16"):
         prob.set_tiling(args.tile, args.stages, args.variant)
@@ -230,21 +262,36 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # Both state buffers in L2 (129 MB): flush L2 before every timed step (a 256 MB write on the same
+    # stream, outside the step's event pair) and sum the steps' own times.
+    state_bytes = 2 * units * (8 if args.precision == "fp64" else 4)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if state_bytes < L2_BYTES else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = prob.launch_count()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        e0.record(stream)
-        for _ in range(args.steps):
-            prob.step(1, dt)
-        e1.record(stream)
+        if flush is None:
+            e0.record(stream)
+            for _ in range(args.steps):
+                prob.step(1, dt)
+            e1.record(stream)
+        else:
+            pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                     for _ in range(args.steps)]
+            with torch.cuda.stream(stream):
+                for a, b in pairs:
+                    flush.zero_()
+                    a.record(stream)
+                    prob.step(1, dt)
+                    b.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches = prob.launch_count() - launches0
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    ms_local = e0.elapsed_time(e1) if flush is None else sum(a.elapsed_time(b) for a, b in pairs)
+    ms = max_over_ranks(ms_local, dist, "cuda")
     ms_per_step = ms / args.steps
     value = whole_job_rate(units, args.steps, world, ms)
 
@@ -266,12 +313,15 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None,
         "dtype": {"bf16": "bf16 contraction, fp32 state", "bf16x3": "bf16x3 contraction, fp32 state",
                   "fp32": "fp32", "fp64": "f64"}[args.precision],
-        "data": "synthetic (seeded uniform state, analytic lattice materials)",
+        "data": "synthetic (seeded uniform state, analytic %s materials)" % wl.kind.replace("_", "-"),
         "config": {"workload": wl.name, "cells": f"{wl.nx}x{wl.ny}", "Q": wl.Q, "beta": wl.beta,
+                   "quadrature": wl.quadrature, "normalisation": wl.normalisation,
                    "eps": wl.eps, "sigma_as": wl.sigma_as, "dt": dt, "precision": args.precision,
                    "scheme": {"euler": "forward Euler, first-order upwind",
                               "heun": "Heun, minmod-limited second-order upwind"}[args.scheme],
-                   "l2": "state larger than L2 (%.0f MB per buffer)" % (units * 4 / 1e6),
+                   "l2": ("state larger than L2 (%.0f MB per buffer)" % (state_bytes / 2e6) if flush is None else
+                          "L2 flushed before every timed step (256 MB write; state %.0f MB per buffer)"
+                          % (state_bytes / 2e6)),
                    "parallelism": f"replicas x{world}", "tiling": tiling},
         "roofline": ({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
@@ -311,6 +361,8 @@ def extras_legs(A, L, torch, wl, args, prob, psi0, stream, dt):
     # the plain FP64 GPU path on the same workload
     try:
         p64 = make_problem(A, wl, "fp64", stream)
+        if args.scheme == "heun":
+            p64.set_scheme("heun")
         p64.set_state(psi0.astype(np.float64))
         p64.step(1, dt)
         torch.cuda.synchronize()
@@ -326,54 +378,52 @@ def extras_legs(A, L, torch, wl, args, prob, psi0, stream, dt):
         p64.close()
     except Exception as e:  # pragma: no cover - report, do not hide
         out["fp64_gpu_path"] = {"error": str(e)}
-    out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.scheme, dt)
     return out
 
 
-def cpu_baseline(wl, seconds: float):
-    """The FP64 oracle as it stands, timed on the host cores on a bounded strip of the workload."""
-    import oracle as O
-
-    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
-    K = O.kernel_matrix(Om, w, wl.eps)
+def cpu_baseline(wl, seconds: float, scheme: str, dt: float):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded strip of the workload, with
+    the same scheme as the GPU line."""
+    Om, w, K = oracle_parts(wl)
+    step = oracle_step(scheme)
     sa, ss, q = wl.materials()
     rows = max(1, min(wl.ny, 8))
     rng = np.random.default_rng(0)
     psi = rng.random((rows, wl.nx, wl.Q))
-    _, dt = wl.steps()
-    O.step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
+    step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
     n = 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds or n == 0:
-        psi = O.step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
+        psi = step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
         n += 1
     el = time.perf_counter() - t0
     units = rows * wl.nx * wl.Q * n
     return {"value": units / el, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} steps of a {rows}-row strip ({rows}x{wl.nx} cells, Q={wl.Q}) of {wl.name}, numpy FP64"}
+            "sample": f"{n} {scheme} steps of a {rows}-row strip ({rows}x{wl.nx} cells, Q={wl.Q}) of {wl.name}, "
+                      "numpy FP64"}
 
 
 def run_reference(args):
     """The FP64 CPU oracle stepped on a bounded strip of the workload (the reference arm)."""
-    import oracle as O
-
     wl = synth.WORKLOADS[args.workload]
-    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
-    K = O.kernel_matrix(Om, w, wl.eps)
+    scheme = args.scheme or wl.scheme
+    step = oracle_step(scheme)
+    Om, w, K = oracle_parts(wl)
     sa, ss, q = wl.materials()
-    _, dt = wl.steps()
+    _, dt = oracle_steps(wl, scheme)
     rows = 4
     rng = np.random.default_rng(0)
     psi = rng.random((rows, wl.nx, wl.Q))
     for _ in range(args.warmup):
-        psi = O.step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
+        psi = step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        psi = O.step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
+        psi = step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
     el = time.perf_counter() - t0
     units = rows * wl.nx * wl.Q * args.steps
     value = units / el
-    sample = f"each step: a {rows}-row strip ({rows}x{wl.nx} cells, Q={wl.Q}) of {wl.name}, numpy FP64"
+    sample = f"each {scheme} step: a {rows}-row strip ({rows}x{wl.nx} cells, Q={wl.Q}) of {wl.name}, numpy FP64"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -538,16 +588,30 @@ def run_serving(args):
     }
 
 
+def oracle_steps(wl, scheme=None):
+    """(n, dt) of the workload's whole run as the oracle sees it: for Heun, 0.95 of the admissible dt
+    of the limited scheme (oracle.heun_admissible_dt)."""
+    import oracle as O
+
+    if (scheme or wl.scheme) != "heun":
+        return wl.steps()
+    Om, w, K = oracle_parts(wl)
+    sa, ss, q = wl.materials()
+    bound = O.heun_admissible_dt(Om, K, sa, ss, wl.sigma_as, wl.h)
+    n = max(1, int(math.ceil(wl.t_final / (0.95 * bound) - 1e-12)))
+    return n, wl.t_final / n
+
+
 def oracle_phi(wl):
     """Scalar flux of the FP64 oracle after the workload's whole run, and the seconds it took."""
     import oracle as O
 
-    n, dt = wl.steps()
-    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
-    K = O.kernel_matrix(Om, w, wl.eps)
+    n, dt = oracle_steps(wl)
+    Om, w, K = oracle_parts(wl)
     sa, ss, q = wl.materials()
+    run = O.run_heun if wl.scheme == "heun" else O.run
     t0 = time.perf_counter()
-    psi = O.run(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    psi = run(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
     return O.scalar_flux(psi, w), time.perf_counter() - t0
 
 
@@ -655,24 +719,31 @@ def run_paramstudy(args):
 def run_accuracy(args):
     """Relative L2 error of the scalar flux after whole runs, each GPU precision against the FP64 oracle
     on the same inputs: the 64^2 line source (Q = 128, t = 1), the 256^2 line source (Q = 256, t = 1) and
-    the 448^2 lattice (Q = 512, t = 3.2).  The oracle runs on the host cores (numpy FP64)."""
+    the 448^2 lattice (Q = 512, t = 3.2), and the paper's own explicit as-S_4 run (200^2 line source,
+    icosahedron quadrature N_q = 92, eps = beta / N_q, row normalisation, Heun + minmod at dt/dx 0.95,
+    t = 1).  The oracle runs on the host cores (numpy FP64)."""
     import torch
 
     import paper_1911_08801_gb300 as A
 
     torch.cuda.set_device(0)
-    cases = [synth.LINE_SOURCE_64, synth.LINE_SOURCE_256_ACC, synth.LATTICE_448]
-    if args.count < 3:
+    heun64 = dataclasses.replace(synth.LINE_SOURCE_64, name=synth.LINE_SOURCE_64.name + "_heun", cfl=0.95,
+                                 scheme="heun", dt_rule="bound")
+    cases = [synth.LINE_SOURCE_64, synth.LINE_SOURCE_256_ACC, synth.LATTICE_448, heun64, synth.PAPER_LINE_SOURCE_200]
+    if args.only:
+        cases = [c for c in cases if c.name == args.only]
+    elif args.count < len(cases):
         cases = cases[:max(1, args.count)]
     out = []
     for wl in cases:
-        n, dt = wl.steps()
+        n, dt = oracle_steps(wl)
         ref = os.path.join(args.ref_dir, wl.name + ".npy") if args.ref_dir else ""
         if ref and os.path.exists(ref):
             phi_ref, t_oracle = np.load(ref), None
         else:
             phi_ref, t_oracle = oracle_phi(wl)
-        row = {"workload": wl.name, "steps": n, "dt": dt, "oracle_s": t_oracle, "rel_l2": {}}
+        row = {"workload": wl.name, "scheme": wl.scheme, "quadrature": wl.quadrature, "Q": wl.Q,
+               "normalisation": wl.normalisation, "steps": n, "dt": dt, "oracle_s": t_oracle, "rel_l2": {}}
         for prec in ("fp64", "fp32", "bf16", "bf16x3"):
             p = make_problem(A, wl, prec, None)
             if wl.kind == "line_source":
@@ -682,24 +753,6 @@ def run_accuracy(args):
             p.close()
             row["rel_l2"][prec] = float(np.linalg.norm(phi - phi_ref) / np.linalg.norm(phi_ref))
         out.append(row)
-    # the paper's explicit scheme (Heun + minmod) on the 64^2 line source at dt/dx = 0.95
-    import oracle as O
-    wl = synth.LINE_SOURCE_64
-    n, dt = synth.time_grid(wl.t_final, 0.95, wl.h)
-    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
-    K = O.kernel_matrix(Om, w, wl.eps)
-    sa, ss, q = wl.materials()
-    phi_ref = O.scalar_flux(O.run_heun(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt), w)
-    row = {"workload": wl.name + " (Heun + minmod, dt/dx 0.95)", "steps": n, "dt": dt, "rel_l2": {}}
-    for prec in ("fp64", "fp32", "bf16", "bf16x3"):
-        p = make_problem(A, wl, prec, None)
-        p.set_scheme("heun")
-        p.init_line_source()
-        p.step(n, dt)
-        phi = p.scalar_flux()
-        p.close()
-        row["rel_l2"][prec] = float(np.linalg.norm(phi - phi_ref) / np.linalg.norm(phi_ref))
-    out.append(row)
     return {"mode": "accuracy", "metric": "relative L2 error of the scalar flux vs the FP64 oracle",
             "cores": os.cpu_count(), "cases": out}
 

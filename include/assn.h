@@ -122,6 +122,34 @@ int assn_set_quadrature(assn_problem* p, int Q, const double* omega, const doubl
  * w = w_GL * 2 pi / n_azim; ordinate q = i*n_azim + k.  Same effects as assn_set_quadrature. */
 int assn_set_product_quadrature(assn_problem* p, int n_polar, int n_azim);
 
+/* Icosahedron quadrature (Sec. 3.3; the paper prints the order-2 rule in Appendix A).  Order k
+ * puts k - 1 equal segments on every edge of the base solid's 20 triangular faces; the lattice
+ * points are mapped to the unit sphere and weighted by the area of their spherical barycentric
+ * dual cells (corners at the centres of the neighbouring triangles and the midpoints of the edges
+ * between them); N_q = 10 (k-1)^2 + 2, weights sum to 4 pi, one point at (0, 0, 1).
+ * ASSN_ICO_REGULAR: the regular icosahedron, vertices (0, +-1, +-g), (+-1, +-g, 0), (+-g, 0, +-1),
+ * g the golden ratio.  ASSN_ICO_PRINTED: the base solid that reproduces the printed order-2
+ * points and weights: each (+-g, 0, +-1) replaced by the (+-1, 0, +-g) with the same signs, the
+ * faces kept.  Both turned about x so that (0, 1, g) maps to (0, 0, 1). */
+typedef enum {
+    ASSN_ICO_PRINTED = 0,
+    ASSN_ICO_REGULAR = 1
+} assn_ico_base;
+
+#define ASSN_ICO_MAX_ORDER 64
+
+/* Compute the icosahedron quadrature of the given order (2 .. ASSN_ICO_MAX_ORDER) and base on
+ * the host in FP64.  Returns N_q.  With omega and w non-NULL and capacity >= N_q, also writes the
+ * directions omega[N_q*3] (x, y, z) and weights w[N_q] (caller-owned); with either NULL, only
+ * returns N_q.  Needs no problem and no device.
+ * Errors (negative return): ASSN_ERR_ARG for an order or base out of range, or capacity < N_q. */
+int assn_icosahedron_quadrature(int order, int base, double* omega, double* w, int capacity);
+
+/* Set the icosahedron quadrature of the given order and base on p (N_q <= ASSN_MAX_Q, so
+ * order <= 11).  Same effects as assn_set_quadrature.  Errors: ASSN_ERR_ARG for an order or
+ * base out of range. */
+int assn_set_icosahedron_quadrature(assn_problem* p, int order, int base);
+
 /* Copy the quadrature back: omega[Q*3], w[Q] (either may be NULL).  *Q_out receives Q. */
 int assn_get_quadrature(const assn_problem* p, int* Q_out, double* omega, double* w);
 
@@ -164,9 +192,11 @@ int assn_get_scheme(const assn_problem* p, int* scheme);
 
 /* Largest admissible dt for the problem's scheme.  Forward Euler: the explicit step keeps every
  * coefficient of the update non-negative (positivity): dt * (max_q [(|Omega_x,q| + |Omega_y,q|)/h
- * + sigma_as (1 - K_qq)] + max_cells [sigma_a + sigma_s]) <= 1.  Heun + minmod: dt max_q
- * max(|Omega_x,q|, |Omega_y,q|)/h <= 1 and dt (sigma_as max_q (1 - K_qq) + max_cells [sigma_a +
- * sigma_s]) <= 1.  Requires quadrature, cross sections and K. */
+ * + sigma_as (1 - K_qq)] + max_cells [sigma_a + sigma_s]) <= 1.  Heun + minmod: every
+ * forward-Euler stage keeps the coefficients non-negative (minmod bounds the transport factor by
+ * 3/2): dt * (max_q [3/2 (|Omega_x,q| + |Omega_y,q|)/h + sigma_as (1 - K_qq)] + max_cells [sigma_a +
+ * sigma_s]) <= 1.  K_qq is taken from the operator as stored (rounded in BF16 / BF16X3).
+ * Requires quadrature, cross sections and K. */
 int assn_max_stable_dt(assn_problem* p, double* dt_out);
 
 /* Advance nsteps explicit steps of size dt on the problem's stream (asynchronous; the

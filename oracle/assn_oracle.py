@@ -21,7 +21,7 @@ __all__ = [
     "product_quadrature", "s_eps", "s_exp", "kernel_matrix", "scalar_flux",
     "transport", "step", "run", "mass", "step_at_cells",
     "minmod", "transport_minmod", "rhs", "step_heun", "run_heun",
-    "icosahedron_quadrature",
+    "icosahedron_quadrature", "heun_admissible_dt",
 ]
 
 
@@ -72,7 +72,8 @@ def icosahedron_quadrature(order: int, base: str = "printed"):
     Readings (the paper's text and its printed table disagree on the base solid):
       * base "printed": the twelve base vertices are (0, +-1, +-g), (+-1, +-g, 0) and
         (+-1, 0, +-g), g the golden ratio, joined into the 20 faces of the regular icosahedron
-        below; with this base the construction reproduces the printed order-2 points and weights.
+        below, each (+-1, 0, +-g) in the place of the regular (+-g, 0, +-1) with the same signs;
+        with this base the construction reproduces the printed order-2 points and weights.
         base "regular": the regular icosahedron, (+-g, 0, +-1) in the last group.
       * Both are turned about the x axis so that (0, 1, g) lands on (0, 0, 1).
       * Midpoints are taken on the sphere: the centre of a triangle with mapped corners a, b, c is
@@ -316,6 +317,24 @@ def run_heun(psi0, nsteps: int, K, Omega, w, sigma_a, sigma_s, q, sigma_as: floa
     for _ in range(nsteps):
         psi = step_heun(psi, K, Omega, w, sigma_a, sigma_s, q, sigma_as, h, dt, bc)
     return psi
+
+
+def heun_admissible_dt(Omega, K, sigma_a, sigma_s, sigma_as: float, h: float) -> float:
+    """Largest dt for which every forward-Euler stage of the limited scheme (Sec. 3.1) is a
+    non-negative combination of old values, so that Heun's method, an average of such stages,
+    keeps psi >= 0 and bounded.
+
+    With minmod slopes the upwind flux difference along an axis is (psi_i - psi_{i-1}) C with
+    C = 1 + (D_i - D_{i-1}) / (2 (psi_i - psi_{i-1})) in [1/2, 3/2], so a stage multiplies psi_q by
+    1 - (dt/h) sum_axes |Omega| C - dt (sigma_a + sigma_s) - dt sigma_as (1 - K_qq) and adds non-negative
+    multiples of other values.  It stays >= 0 when
+        dt (max_q [ 3/2 (|Omega_x,q| + |Omega_y,q|) / h + sigma_as (1 - K_qq) ] + max_cells [sigma_a + sigma_s]) <= 1.
+    """
+    Om = np.asarray(Omega, dtype=np.float64)
+    K = np.asarray(K, dtype=np.float64)
+    v = 1.5 * (np.abs(Om[:, 0]) + np.abs(Om[:, 1])) / h + sigma_as * (1.0 - np.diag(K))
+    rate = v.max() + float(np.max(np.asarray(sigma_a) + np.asarray(sigma_s)))
+    return 1.0 / rate if rate > 0 else math.inf
 
 
 def run(psi0, nsteps: int, K, Omega, w, sigma_a, sigma_s, q, sigma_as: float, h: float,

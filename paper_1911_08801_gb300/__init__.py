@@ -13,7 +13,13 @@ from ._lib import (ASSN_BF16, ASSN_BF16X3, ASSN_FP32, ASSN_FP64, ASSN_KERNEL_EXP
                    ASSN_NORM_COLUMN, ASSN_NORM_ROW, PRECISIONS, AssnError)
 
 __all__ = ["Problem", "Batch", "Server", "AssnError", "PRECISIONS", "ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
-           "ASSN_KERNEL_GAUSS", "ASSN_KERNEL_EXP", "ASSN_NORM_COLUMN", "ASSN_NORM_ROW"]
+           "ASSN_KERNEL_GAUSS", "ASSN_KERNEL_EXP", "ASSN_NORM_COLUMN", "ASSN_NORM_ROW", "icosahedron_quadrature"]
+
+
+def icosahedron_quadrature(order: int, base: str = "printed"):
+    """(Omega [N_q, 3], w [N_q]) of the icosahedron quadrature of Sec. 3.3, N_q = 10 (order-1)^2 + 2,
+    computed by the library (host code, no device needed)."""
+    return _lib.assn_icosahedron_quadrature(order, _lib.ICO_BASES[base])
 
 
 class Problem:
@@ -32,6 +38,13 @@ class Problem:
     def set_product_quadrature(self, n_polar: int, n_azim: int):
         _lib.assn_set_product_quadrature(self.handle, n_polar, n_azim)
         self.Q = n_polar * n_azim
+        return self
+
+    def set_icosahedron_quadrature(self, order: int, base: str = "printed"):
+        """The icosahedron quadrature of Sec. 3.3 (N_q = 10 (order-1)^2 + 2); base "printed" reproduces
+        the paper's printed order-2 rule, "regular" builds on the regular icosahedron."""
+        _lib.assn_set_icosahedron_quadrature(self.handle, order, _lib.ICO_BASES[base])
+        self.Q = 10 * (order - 1) ** 2 + 2
         return self
 
     def set_quadrature(self, omega, w):

@@ -28,6 +28,9 @@ ASSN_FP64, ASSN_FP32, ASSN_BF16, ASSN_BF16X3 = 0, 1, 2, 3
 ASSN_KERNEL_GAUSS, ASSN_KERNEL_EXP = 0, 1
 ASSN_NORM_COLUMN, ASSN_NORM_ROW = 0, 1
 ASSN_SCHEME_EULER_UPWIND, ASSN_SCHEME_HEUN_MINMOD = 0, 1
+ASSN_ICO_PRINTED, ASSN_ICO_REGULAR = 0, 1
+ASSN_ICO_MAX_ORDER = 64
+ICO_BASES = {"printed": ASSN_ICO_PRINTED, "regular": ASSN_ICO_REGULAR}
 SCHEMES = {"euler": ASSN_SCHEME_EULER_UPWIND, "heun": ASSN_SCHEME_HEUN_MINMOD}
 
 PRECISIONS = {"fp64": ASSN_FP64, "fp32": ASSN_FP32, "bf16": ASSN_BF16, "bf16x3": ASSN_BF16X3}
@@ -66,6 +69,8 @@ SIGNATURES = {
     "assn_set_quadrature": (C.c_int, [_h, C.c_int, _dp, _dp]),
     "assn_set_product_quadrature": (C.c_int, [_h, C.c_int, C.c_int]),
     "assn_get_quadrature": (C.c_int, [_h, C.POINTER(C.c_int), _dp, _dp]),
+    "assn_icosahedron_quadrature": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.c_int]),
+    "assn_set_icosahedron_quadrature": (C.c_int, [_h, C.c_int, C.c_int]),
     "assn_set_cross_sections": (C.c_int, [_h, _dp, _dp, _dp]),
     "assn_set_artificial_scattering": (C.c_int, [_h, C.c_double, C.c_double, C.c_int, C.c_int]),
     "assn_get_kernel_matrix": (C.c_int, [_h, _dp]),
@@ -190,6 +195,23 @@ def assn_set_quadrature(h: int, omega, w) -> None:
 
 def assn_set_product_quadrature(h: int, n_polar: int, n_azim: int) -> None:
     _check(lib.assn_set_product_quadrature(h, n_polar, n_azim), h)
+
+
+def assn_icosahedron_quadrature(order: int, base: int = ASSN_ICO_PRINTED):
+    """(omega [N_q, 3], w [N_q]) of the icosahedron quadrature, computed by the library on the host."""
+    n = lib.assn_icosahedron_quadrature(order, base, None, None, 0)
+    if n < 0:
+        raise AssnError(n, f"icosahedron quadrature: order {order} or base {base} out of range")
+    om = np.empty((n, 3))
+    w = np.empty(n)
+    r = lib.assn_icosahedron_quadrature(order, base, _d(om), _d(w), n)
+    if r != n:
+        raise AssnError(r if r < 0 else ASSN_ERR_STATE, "icosahedron quadrature failed")
+    return om, w
+
+
+def assn_set_icosahedron_quadrature(h: int, order: int, base: int = ASSN_ICO_PRINTED) -> None:
+    _check(lib.assn_set_icosahedron_quadrature(h, order, base), h)
 
 
 def assn_get_quadrature(h: int):

@@ -157,15 +157,16 @@ int upload_ord(assn_problem* p, double dt) {
 // - dt (sigma_a + sigma_s) >= 0, maximised over ordinates and cells separately.
 double max_stable_dt(const assn_problem* p) {
     if (p->scheme == ASSN_SCHEME_HEUN_MINMOD) {
-        // per-axis CFL number <= 1 (the paper runs this scheme at dt/dx = 0.95) and the
-        // collision / artificial-scattering rate times dt <= 1
-        double vdir = 0, emax = 0, smax = 0;
-        for (int q = 0; q < p->Q; ++q) {
-            vdir = std::max(vdir, std::max(fabs(p->omega[3 * q]), fabs(p->omega[3 * q + 1])) / p->h);
-            emax = std::max(emax, p->e[q]);
-        }
+        // Each forward-Euler stage of Heun's method stays a non-negative combination of old values:
+        // with minmod slopes the upwind flux difference along an axis is (psi_i - psi_{i-1}) times a
+        // factor in [1/2, 3/2], so the transport term takes at most 3/2 (|Omega_x| + |Omega_y|) dt / h
+        // of psi_q.
+        double vmax = 0, smax = 0;
+        for (int q = 0; q < p->Q; ++q)
+            vmax = std::max(vmax, 1.5 * (fabs(p->omega[3 * q]) + fabs(p->omega[3 * q + 1])) / p->h +
+                                      p->sigma_as * p->e[q]);
         for (size_t c = 0; c < p->ncell(); ++c) smax = std::max(smax, p->sa[c] + p->ss[c]);
-        const double rate = std::max(vdir, p->sigma_as * emax + smax);
+        const double rate = vmax + smax;
         return rate > 0 ? 1.0 / rate : INFINITY;
     }
     double vmax = 0;

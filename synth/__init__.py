@@ -158,9 +158,18 @@ class Workload:
     t_final: float = 1.0
     seed: int = 0
     extra: dict = field(default_factory=dict)
+    quadrature: str = "product"     # "product": n_polar x n_azim; "icosahedron": order ico_order
+    ico_order: int = 0              # N_q = 10 (ico_order - 1)^2 + 2
+    ico_base: str = "printed"       # "printed" (the paper's Appendix A rule) or "regular"
+    eps_rule: str = "spacing"       # "spacing": beta sqrt(4 pi / Q); "paper": beta / N_q (Sec. 4.1)
+    normalisation: str = "column"   # kernel matrix: "column" or the paper's "row" (Sec. 3.2)
+    scheme: str = "euler"           # "euler" (first-order upwind) or "heun" (Heun + minmod)
+    dt_rule: str = "cfl"            # "cfl": dt = cfl h; "bound": dt = cfl x the scheme's admissible dt
 
     @property
     def Q(self) -> int:
+        if self.quadrature == "icosahedron":
+            return 10 * (self.ico_order - 1) ** 2 + 2
         return self.n_polar * self.n_azim
 
     @property
@@ -169,10 +178,21 @@ class Workload:
 
     @property
     def eps(self) -> float:
+        if self.eps_rule == "paper":
+            return self.beta / self.Q
         return eps_from_beta(self.beta, self.Q)
 
     def steps(self) -> tuple[int, float]:
+        if self.dt_rule != "cfl":
+            raise ValueError(f"{self.name}: dt is a fraction of the admissible dt; use steps_for(bound)")
         return time_grid(self.t_final, self.cfl, self.h)
+
+    def steps_for(self, dt_bound: float) -> tuple[int, float]:
+        """(n, dt) landing on t_final with dt <= cfl x dt_bound (dt_rule "bound") or <= cfl h."""
+        if self.dt_rule == "cfl":
+            return self.steps()
+        n = max(1, int(math.ceil(self.t_final / (self.cfl * dt_bound) - 1e-12)))
+        return n, self.t_final / n
 
     def materials(self):
         """(sigma_a, sigma_s, q_per_ordinate), each [ny][nx] float64."""
@@ -205,13 +225,41 @@ def lattice(n: int, n_polar: int, n_azim: int, beta: float, t_final: float = 3.2
                     n, n, 0.0, 7.0, 0.0, 7.0, n_polar, n_azim, beta, t_final=t_final)
 
 
+def paper_line_source(n: int = 200, order: int = 4, beta: float = 4.5, sigma_as: float = 5.0,
+                      t_final: float = 1.0, base: str = "printed", name: str | None = None) -> Workload:
+    """The paper's explicit as-S_N line source (Sec. 4.1): [-1.5, 1.5]^2, the icosahedron quadrature
+    (Sec. 3.3; order 4 gives N_q = 92), eps = beta / N_q, the row normalisation of Sec. 3.2 and Heun +
+    minmod; sigma_as = 5, beta = 4.5 as in its explicit runs.  The time step is 0.95 of the scheme's
+    admissible dt (the paper's dt/dx = 0.95 is unstable for the unsplit two-dimensional scheme)."""
+    q = 10 * (order - 1) ** 2 + 2
+    return Workload(name or f"line_source_{n}x{n}_ico{q}", "line_source", n, n, -1.5, 1.5, -1.5, 1.5, 0, 0,
+                    beta, sigma_as=sigma_as, cfl=0.95, t_final=t_final, quadrature="icosahedron",
+                    ico_order=order, ico_base=base, eps_rule="paper", normalisation="row", scheme="heun",
+                    dt_rule="bound")
+
+
+def paper_lattice(n: int = 280, order: int = 4, beta: float = 4.5, sigma_as: float = 5.0,
+                  t_final: float = 3.2, name: str | None = None) -> Workload:
+    """The paper's explicit as-S_N lattice (Sec. 4.2) with its quadrature, kernel width, normalisation
+    and scheme as in paper_line_source; 280^2 cells as in its lattice figures."""
+    q = 10 * (order - 1) ** 2 + 2
+    return Workload(name or f"lattice_{n}x{n}_ico{q}", "lattice", n, n, 0.0, 7.0, 0.0, 7.0, 0, 0, beta,
+                    sigma_as=sigma_as, cfl=0.95, t_final=t_final, quadrature="icosahedron", ico_order=order,
+                    eps_rule="paper", normalisation="row", scheme="heun", dt_rule="bound")
+
+
 # The five workloads of the measurement plan.
 LINE_SOURCE_64 = line_source(64, 8, 16, 1.0 / 8.0, name="line_source_64x64_Q128_fp64")
 LATTICE_448 = lattice(448, 16, 32, 0.5, name="lattice_448x448_Q512")
 LINE_SOURCE_2048 = line_source(2048, 16, 16, 1.0 / 8.0, name="line_source_2048x2048_Q256")
 LINE_SOURCE_256_ACC = line_source(256, 16, 16, 1.0 / 8.0, name="line_source_256x256_Q256")
 
-WORKLOADS = {w.name: w for w in (LINE_SOURCE_64, LATTICE_448, LINE_SOURCE_2048, LINE_SOURCE_256_ACC)}
+# The paper's own explicit as-S_4 runs (N_q = 92).
+PAPER_LINE_SOURCE_200 = paper_line_source(200)
+PAPER_LATTICE_280 = paper_lattice(280)
+
+WORKLOADS = {w.name: w for w in (LINE_SOURCE_64, LATTICE_448, LINE_SOURCE_2048, LINE_SOURCE_256_ACC,
+                                 PAPER_LINE_SOURCE_200, PAPER_LATTICE_280)}
 
 QUAD_ORDERS = {64: (8, 8), 128: (8, 16), 256: (16, 16), 512: (16, 32)}
 

@@ -26,28 +26,51 @@ def rel_l2(a, b) -> float:
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def gpu_problem(A, wl: synth.Workload, precision: str, psi0=None, sigma_as=None, normalisation=0, kind=0):
+def gpu_problem(A, wl: synth.Workload, precision: str, psi0=None, sigma_as=None, normalisation=None, kind=0):
+    """The workload's problem through the C ABI: its quadrature, cross sections, kernel (normalisation
+    from the workload unless given: 0 column, 1 row), scheme and initial state."""
     p = A.Problem(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1, precision)
-    p.set_product_quadrature(wl.n_polar, wl.n_azim)
+    if wl.quadrature == "icosahedron":
+        p.set_icosahedron_quadrature(wl.ico_order, wl.ico_base)
+    else:
+        p.set_product_quadrature(wl.n_polar, wl.n_azim)
     sa, ss, q = wl.materials()
     p.set_cross_sections(sa, ss, q)
+    if normalisation is None:
+        normalisation = 1 if wl.normalisation == "row" else 0
     p.set_artificial_scattering(wl.sigma_as if sigma_as is None else sigma_as, wl.eps, kind, normalisation)
+    if wl.scheme == "heun":
+        p.set_scheme("heun")
     p.set_state(wl.psi0() if psi0 is None else psi0)
     return p
 
 
-def oracle_setup(wl: synth.Workload, normalisation="column", kind="gauss"):
-    Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
-    K = O.kernel_matrix(Om, w, wl.eps, kind=kind, normalisation=normalisation)
+def oracle_setup(wl: synth.Workload, normalisation=None, kind="gauss"):
+    if wl.quadrature == "icosahedron":
+        Om, w = O.icosahedron_quadrature(wl.ico_order, wl.ico_base)
+    else:
+        Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
+    K = O.kernel_matrix(Om, w, wl.eps, kind=kind, normalisation=normalisation or wl.normalisation)
     sa, ss, q = wl.materials()
     return Om, w, K, sa, ss, q
 
 
-def oracle_run(wl: synth.Workload, nsteps: int, dt: float, psi0=None, normalisation="column", sigma_as=None):
+def run_steps(wl: synth.Workload):
+    """(n, dt) of a whole run of the workload; a fraction of the scheme's admissible dt (computed by the
+    oracle) for workloads whose dt_rule is "bound"."""
+    if wl.dt_rule != "bound":
+        return wl.steps()
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    return wl.steps_for(O.heun_admissible_dt(Om, K, sa, ss, wl.sigma_as, wl.h))
+
+
+def oracle_run(wl: synth.Workload, nsteps: int, dt: float, psi0=None, normalisation=None, sigma_as=None):
+    """nsteps of the workload's scheme in the oracle; returns (psi, w)."""
     Om, w, K, sa, ss, q = oracle_setup(wl, normalisation)
     psi = wl.psi0() if psi0 is None else psi0
     s_as = wl.sigma_as if sigma_as is None else sigma_as
-    return O.run(psi, nsteps, K, Om, w, sa, ss, q, s_as, wl.h, dt), w
+    run = O.run_heun if wl.scheme == "heun" else O.run
+    return run(psi, nsteps, K, Om, w, sa, ss, q, s_as, wl.h, dt), w
 
 
 def step_tolerance(precision: str, dt: float, sigma_as: float, scale: float, rowsum: float = 1.0) -> float:
@@ -55,10 +78,11 @@ def step_tolerance(precision: str, dt: float, sigma_as: float, scale: float, row
 
     ``scale`` bounds |psi|; ``rowsum`` bounds sum_{p != q} K_qp (above 1 for the column
     normalisation).  FP32 state arithmetic: a few ulps of the largest term (~1e-6 relative).
-    BF16 contraction: both operands rounded to nearest BF16 (relative error <= 2^-9 each), so the
-    gain sum_p G_qp psi_p is off by <= 2^-8 * rowsum * max|psi|, and the loss term uses the same
-    rounded psi (<= 2^-9 * max|psi|); both enter multiplied by dt * sigma_as.  BF16X3 carries the
-    residuals, leaving ~2^-16 relative per operand.
+    BF16 contraction: both operands rounded to nearest BF16 (8-bit significand: relative error
+    <= 2^-8 each), so the gain sum_p G_qp psi_p is off by <= (2^-7 + 2^-16) * rowsum * max|psi|; the
+    loss term e_q psi_q uses the same rounded psi and e <= 1 built from the rounded G, off by
+    <= 2^-7 * max|psi|; both enter multiplied by dt * sigma_as.  BF16X3 carries the residuals,
+    leaving 2^-16 relative per operand plus the dropped lo*lo product: 2^-14 covers gain and loss.
     """
     fp32 = 4e-6 * scale
     if precision == "fp64":
@@ -66,7 +90,7 @@ def step_tolerance(precision: str, dt: float, sigma_as: float, scale: float, row
     if precision == "fp32":
         return fp32
     if precision == "bf16":
-        return dt * sigma_as * (2.0 ** -8 * rowsum + 2.0 ** -9) * scale * 1.05 + fp32
+        return dt * sigma_as * 2.0 ** -7 * ((1.0 + 2.0 ** -9) * rowsum + 1.0) * scale + fp32
     if precision == "bf16x3":
         return dt * sigma_as * 2.0 ** -14 * (rowsum + 1.0) * scale + fp32
     raise ValueError(precision)

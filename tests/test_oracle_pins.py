@@ -547,3 +547,56 @@ def test_heun_minmod_second_order_convergence():
     r1 = err(64, False) / err(128, False)
     assert r2 > 2 ** 1.6
     assert r1 < 2 ** 1.2
+
+
+def _stage(psi, K, Om, w, sa, ss, q, sigma_as, h, dt):
+    return psi + dt * O.rhs(psi, K, Om, w, sa, ss, q, sigma_as, h)
+
+
+@pytest.mark.parametrize("pattern", ["uniform", "spikes", "checker"])
+def test_heun_stage_non_negative_at_the_admissible_dt(pattern):
+    """At the admissible dt one forward-Euler stage, and so the Heun step, maps non-negative states to
+    non-negative states (random materials, row and column normalisation)."""
+    rng = np.random.default_rng({"uniform": 1, "spikes": 2, "checker": 3}[pattern])
+    Om, w = O.product_quadrature(4, 8)
+    ny, nx = 9, 11
+    if pattern == "uniform":
+        psi = rng.random((ny, nx, len(w)))
+    elif pattern == "spikes":
+        psi = (rng.random((ny, nx, len(w))) < 0.05) * rng.random((ny, nx, len(w))) * 100.0
+    else:
+        jj, ii = np.indices((ny, nx))
+        psi = np.repeat((((ii + jj) % 2) * 3.0 + 1e-3)[..., None], len(w), axis=2)
+    sa, ss, q = synth.random_materials(5, ny, nx)
+    for norm in ("column", "row"):
+        K = O.kernel_matrix(Om, w, 0.6, normalisation=norm)
+        dt = O.heun_admissible_dt(Om, K, sa, ss, 4.0, 0.1)
+        assert _stage(psi, K, Om, w, sa, ss, q, 4.0, 0.1, dt).min() >= -1e-12 * psi.max()
+        assert O.step_heun(psi, K, Om, w, sa, ss, q, 4.0, 0.1, dt).min() >= -1e-12 * psi.max()
+
+
+def test_heun_admissible_dt_is_tight():
+    """A state built so that both limiter factors reach 3/2 at one cell for the ordinate that sets the
+    bound (no inflow, no gain: sigma_s = 0, a single non-zero ordinate): the stage leaves
+    1 - dt / dt_max there, zero at the bound and negative just above it.  A bound without the 3/2 or
+    without the artificial-scattering term fails."""
+    Om, w = O.product_quadrature(4, 8)
+    h, sigma_as = 0.1, 3.0
+    ny, nx = 8, 8
+    sa = np.full((ny, nx), 0.8)
+    ss = np.zeros((ny, nx))
+    q = np.zeros((ny, nx))
+    K = O.kernel_matrix(Om, w, 0.7, normalisation="row")
+    v = 1.5 * (np.abs(Om[:, 0]) + np.abs(Om[:, 1])) / h + sigma_as * (1.0 - np.diag(K))
+    k = int(np.argmax(v))
+    sx, sy = int(np.sign(Om[k, 0])), int(np.sign(Om[k, 1]))
+    j0, i0 = 4, 4
+    psi = np.zeros((ny, nx, len(w)))
+    psi[j0, i0, k] = 1.0
+    psi[j0, i0 + sx, k] = 2.0          # downwind in x: slope limited by the upwind difference
+    psi[j0 + sy, i0, k] = 2.0          # downwind in y
+    dt_max = O.heun_admissible_dt(Om, K, sa, ss, sigma_as, h)
+    assert abs(dt_max - 1.0 / (v[k] + 0.8)) < 1e-15
+    for f in (0.5, 1.0, 1.01):
+        out = _stage(psi, K, Om, w, sa, ss, q, sigma_as, h, f * dt_max)
+        assert abs(out[j0, i0, k] - (1.0 - f)) < 1e-12
