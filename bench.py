@@ -154,8 +154,10 @@ def make_problem(A, wl, precision, stream):
     p.set_cross_sections(sa, ss, q)
     p.set_artificial_scattering(wl.sigma_as, wl.eps, A.ASSN_KERNEL_GAUSS,
                                 A.ASSN_NORM_ROW if wl.normalisation == "row" else A.ASSN_NORM_COLUMN)
-    if wl.scheme == "heun":
-        p.set_scheme("heun")
+    if wl.scheme in ("heun", "implicit"):
+        p.set_scheme(wl.scheme)
+    if wl.scheme == "implicit":
+        p.set_implicit_params(wl.si_eps, wl.gmres_tol)
     return p
 
 
@@ -170,9 +172,16 @@ def oracle_parts(wl):
     return Om, w, O.kernel_matrix(Om, w, wl.eps, normalisation=wl.normalisation)
 
 
-def oracle_step(scheme: str):
+def oracle_step(scheme: str, wl=None):
+    """The oracle's step of the scheme as f(psi, K, Om, w, sa, ss, q, sigma_as, h, dt)."""
     import oracle as O
 
+    if scheme == "implicit":
+        def implicit(psi, K, Om, w, sa, ss, q, sigma_as, h, dt):
+            out, _, _, _ = O.implicit_step(psi, O.scalar_flux(psi, w), K, Om, w, sa, ss, q, sigma_as, h, dt,
+                                           wl.si_eps, wl.gmres_tol)
+            return out
+        return implicit
     return O.step_heun if scheme == "heun" else O.step
 
 
@@ -194,6 +203,20 @@ def alu_roofline(args, wl, ms_per_step: float) -> dict:
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "peak_source": "derived: SMs x lanes x 2 x 2070 MHz", "flops_per_update": 4 * qp,
             "kernel": "stage_simt_kernel (two launches per step)"}
+
+
+def implicit_roofline(args, wl, ms_per_step: float, stats: dict, steps: int) -> dict:
+    """Implicit sweeping-Krylov step: per source iteration every cell-ordinate value is read once (the
+    iterate, for the source) and written once (the sweep's result): 2 x elem bytes; the timed region
+    also holds the GMRES vector work, the reductions and the transport sweeps' wavefront latency."""
+    hbm, src = peaks()
+    elem = 8 if args.precision == "fp64" else 4
+    si_per_step = stats["source_iterations"] / steps
+    achieved = 2.0 * elem * wl.nx * wl.ny * wl.Q * si_per_step / (ms_per_step / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_update_per_source_iteration": 2 * elem,
+            "source_iterations_per_step": si_per_step, "gmres_iterations_per_step": stats["gmres_iterations"] / steps,
+            "sweeps_per_step": stats["sweeps"] / steps, "kernel": "sweep_kernel + si_source_kernel"}
 
 
 def heun_tc_roofline(wl, ms_per_step: float) -> dict:
@@ -236,6 +259,8 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     wl = synth.WORKLOADS[args.workload]
     args.scheme = args.scheme or wl.scheme
+    if args.scheme == "implicit" and args.precision.startswith("bf16"):
+        raise SystemExit("the implicit scheme runs in fp64 or fp32: pass --precision fp64 or fp32")
     stream = torch.cuda.Stream()
     prob = make_problem(A, wl, args.precision, stream)
     if args.scheme == "heun":
@@ -268,6 +293,7 @@ def run_ours(args, rank, world, dist):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if state_bytes < L2_BYTES else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = prob.launch_count()
+    stats0 = prob.implicit_stats() if args.scheme == "implicit" else None
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         if flush is None:
@@ -318,7 +344,9 @@ def run_ours(args, rank, world, dist):
                    "quadrature": wl.quadrature, "normalisation": wl.normalisation,
                    "eps": wl.eps, "sigma_as": wl.sigma_as, "dt": dt, "precision": args.precision,
                    "scheme": {"euler": "forward Euler, first-order upwind",
-                              "heun": "Heun, minmod-limited second-order upwind"}[args.scheme],
+                              "heun": "Heun, minmod-limited second-order upwind",
+                              "implicit": "implicit Euler, second-order upwind, sweeping-Krylov "
+                                          f"(source iteration eps {wl.si_eps}, GMRES {wl.gmres_tol})"}[args.scheme],
                    "l2": ("state larger than L2 (%.0f MB per buffer)" % (state_bytes / 2e6) if flush is None else
                           "L2 flushed before every timed step (256 MB write; state %.0f MB per buffer)"
                           % (state_bytes / 2e6)),
@@ -329,6 +357,9 @@ def run_ours(args, rank, world, dist):
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
                      "kernel": ("step_tc2_kernel" if args.variant == 0 else "step_tc_kernel") if args.precision.startswith("bf16")
                      else "step_simt_kernel"} if args.scheme == "euler" else
+                     implicit_roofline(args, wl, ms_per_step,
+                                       {k: v - stats0[k] for k, v in prob.implicit_stats().items()}, args.steps)
+                     if args.scheme == "implicit" else
                      (heun_tc_roofline(wl, ms_per_step) if args.precision.startswith("bf16")
                       else alu_roofline(args, wl, ms_per_step))),
         "gpu_launches": int(launches),
@@ -386,7 +417,7 @@ def cpu_baseline(wl, seconds: float, scheme: str, dt: float):
     """The FP64 oracle as it stands, timed on the host cores on a bounded strip of the workload, with
     the same scheme as the GPU line."""
     Om, w, K = oracle_parts(wl)
-    step = oracle_step(scheme)
+    step = oracle_step(scheme, wl)
     sa, ss, q = wl.materials()
     rows = max(1, min(wl.ny, 8))
     rng = np.random.default_rng(0)
@@ -408,7 +439,7 @@ def run_reference(args):
     """The FP64 CPU oracle stepped on a bounded strip of the workload (the reference arm)."""
     wl = synth.WORKLOADS[args.workload]
     scheme = args.scheme or wl.scheme
-    step = oracle_step(scheme)
+    step = oracle_step(scheme, wl)
     Om, w, K = oracle_parts(wl)
     sa, ss, q = wl.materials()
     _, dt = oracle_steps(wl, scheme)
@@ -609,9 +640,12 @@ def oracle_phi(wl):
     n, dt = oracle_steps(wl)
     Om, w, K = oracle_parts(wl)
     sa, ss, q = wl.materials()
-    run = O.run_heun if wl.scheme == "heun" else O.run
     t0 = time.perf_counter()
-    psi = run(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    if wl.scheme == "implicit":
+        psi = O.implicit_run(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt, wl.si_eps, wl.gmres_tol)
+    else:
+        run = O.run_heun if wl.scheme == "heun" else O.run
+        psi = run(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
     return O.scalar_flux(psi, w), time.perf_counter() - t0
 
 
@@ -729,7 +763,8 @@ def run_accuracy(args):
     torch.cuda.set_device(0)
     heun64 = dataclasses.replace(synth.LINE_SOURCE_64, name=synth.LINE_SOURCE_64.name + "_heun", cfl=0.95,
                                  scheme="heun", dt_rule="bound")
-    cases = [synth.LINE_SOURCE_64, synth.LINE_SOURCE_256_ACC, synth.LATTICE_448, heun64, synth.PAPER_LINE_SOURCE_200]
+    cases = [synth.LINE_SOURCE_64, synth.LINE_SOURCE_256_ACC, synth.LATTICE_448, heun64, synth.PAPER_LINE_SOURCE_200,
+             synth.PAPER_LINE_SOURCE_200_IMPLICIT]
     if args.only:
         cases = [c for c in cases if c.name == args.only]
     elif args.count < len(cases):
@@ -744,7 +779,7 @@ def run_accuracy(args):
             phi_ref, t_oracle = oracle_phi(wl)
         row = {"workload": wl.name, "scheme": wl.scheme, "quadrature": wl.quadrature, "Q": wl.Q,
                "normalisation": wl.normalisation, "steps": n, "dt": dt, "oracle_s": t_oracle, "rel_l2": {}}
-        for prec in ("fp64", "fp32", "bf16", "bf16x3"):
+        for prec in ("fp64", "fp32") if wl.scheme == "implicit" else ("fp64", "fp32", "bf16", "bf16x3"):
             p = make_problem(A, wl, prec, None)
             if wl.kind == "line_source":
                 p.init_line_source()

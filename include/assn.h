@@ -89,8 +89,17 @@ typedef enum { ASSN_BC_VACUUM = 0 } assn_boundary;
  *                             psi* = psi + dt L(psi), psi^{n+1} = (psi + psi* + dt L(psi*))/2)
  *                             with second-order upwind fluxes from minmod-limited slopes (two zero
  *                             ghost cells per vacuum side); all precisions (tensor-core problems on
- *                             the persistent kernel, variant 0). */
-typedef enum { ASSN_SCHEME_EULER_UPWIND = 0, ASSN_SCHEME_HEUN_MINMOD = 1 } assn_scheme;
+ *                             the persistent kernel, variant 0).
+ *   ASSN_SCHEME_IMPLICIT      the paper's implicit method (Sec. 3.4-3.5, Alg. 1-3): implicit Euler
+ *                             with the second-order upwind stencil without limiter (flux difference
+ *                             3/2 psi_j - 2 psi_{j-1} + 1/2 psi_{j-2}, x and y stencils added), solved
+ *                             by source iteration over transport sweeps inside GMRES on the scalar
+ *                             flux; FP64 and FP32 problems (CUDA cores); no step-size restriction. */
+typedef enum {
+    ASSN_SCHEME_EULER_UPWIND = 0,
+    ASSN_SCHEME_HEUN_MINMOD = 1,
+    ASSN_SCHEME_IMPLICIT = 2
+} assn_scheme;
 
 typedef struct assn_problem assn_problem;
 
@@ -190,13 +199,36 @@ int assn_init_line_source(assn_problem* p, double delta, double floor_value);
 int assn_set_scheme(assn_problem* p, int scheme);
 int assn_get_scheme(const assn_problem* p, int* scheme);
 
+/* Parameters of the implicit scheme (defaults in parentheses): the source iteration stops when
+ * ||psi^{l+1} - psi^l||_2 < si_eps (1 - T) / T, T = max_cells dt sigma_as / (1 + dt (sigma_a +
+ * sigma_s + sigma_as)) (1e-4), or after max_si iterations (1000), and for FP32 problems also when the
+ * difference stops decreasing (the rounding floor of the state); GMRES on the scalar flux, restarted
+ * every `restart` iterations (30), stops at relative residual gmres_tol (1.5e-8; for FP32 problems
+ * not below 2^-20, the rounding level of FP32 source iterations) or after max_gmres iterations
+ * (500).  Errors: ASSN_ERR_ARG for negative tolerances, restart outside 1..200 or limits < 1. */
+int assn_set_implicit_params(assn_problem* p, double si_eps, double gmres_tol, int restart, int max_si,
+                             int max_gmres);
+
+/* Totals since the problem was created: source iterations, GMRES iterations, transport sweeps of
+ * the implicit scheme (any pointer may be NULL). */
+int assn_implicit_stats(const assn_problem* p, int64_t* source_iterations, int64_t* gmres_iterations,
+                        int64_t* sweeps);
+
+/* Exactly `iterations` source iterations (Alg. 1) of the implicit scheme at step size dt, for
+ * (L - dt sigma_as K) psi = dt R: psi^{l+1} = L^{-1} dt (sigma_as K psi^l + R) from psi^0 = psi0.
+ * R, psi0, psi_out: host [ny][nx][Q] FP64 (computed in the problem's precision).  One iteration
+ * from any psi0 with sigma_as = 0 is one transport sweep.  Requires quadrature, cross sections and
+ * K; ASSN_ERR_UNSUPPORTED for BF16 / BF16X3 problems. */
+int assn_implicit_source_iteration(assn_problem* p, double dt, const double* R, const double* psi0,
+                                   int iterations, double* psi_out);
+
 /* Largest admissible dt for the problem's scheme.  Forward Euler: the explicit step keeps every
  * coefficient of the update non-negative (positivity): dt * (max_q [(|Omega_x,q| + |Omega_y,q|)/h
  * + sigma_as (1 - K_qq)] + max_cells [sigma_a + sigma_s]) <= 1.  Heun + minmod: every
  * forward-Euler stage keeps the coefficients non-negative (minmod bounds the transport factor by
  * 3/2): dt * (max_q [3/2 (|Omega_x,q| + |Omega_y,q|)/h + sigma_as (1 - K_qq)] + max_cells [sigma_a +
  * sigma_s]) <= 1.  K_qq is taken from the operator as stored (rounded in BF16 / BF16X3).
- * Requires quadrature, cross sections and K. */
+ * Implicit: infinity (no restriction).  Requires quadrature, cross sections and K. */
 int assn_max_stable_dt(assn_problem* p, double* dt_out);
 
 /* Advance nsteps explicit steps of size dt on the problem's stream (asynchronous; the

@@ -40,6 +40,19 @@ class Problem:
         self.Q = n_polar * n_azim
         return self
 
+    def set_implicit_params(self, si_eps: float = 1e-4, gmres_tol: float = 1.5e-8, restart: int = 30,
+                            max_si: int = 1000, max_gmres: int = 500):
+        """Tolerances and limits of the implicit scheme (source iteration, GMRES; Alg. 1-3)."""
+        _lib.assn_set_implicit_params(self.handle, si_eps, gmres_tol, restart, max_si, max_gmres)
+        return self
+
+    def implicit_stats(self) -> dict:
+        return _lib.assn_implicit_stats(self.handle)
+
+    def implicit_source_iteration(self, dt: float, R, psi0, iterations: int) -> np.ndarray:
+        """Exactly `iterations` source iterations for (L - dt sigma_as K) psi = dt R from psi0."""
+        return _lib.assn_implicit_source_iteration(self.handle, dt, R, psi0, iterations)
+
     def set_icosahedron_quadrature(self, order: int, base: str = "printed"):
         """The icosahedron quadrature of Sec. 3.3 (N_q = 10 (order-1)^2 + 2); base "printed" reproduces
         the paper's printed order-2 rule, "regular" builds on the regular icosahedron."""

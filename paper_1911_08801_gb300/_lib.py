@@ -27,11 +27,11 @@ ASSN_ERR_UNSUPPORTED = -8
 ASSN_FP64, ASSN_FP32, ASSN_BF16, ASSN_BF16X3 = 0, 1, 2, 3
 ASSN_KERNEL_GAUSS, ASSN_KERNEL_EXP = 0, 1
 ASSN_NORM_COLUMN, ASSN_NORM_ROW = 0, 1
-ASSN_SCHEME_EULER_UPWIND, ASSN_SCHEME_HEUN_MINMOD = 0, 1
+ASSN_SCHEME_EULER_UPWIND, ASSN_SCHEME_HEUN_MINMOD, ASSN_SCHEME_IMPLICIT = 0, 1, 2
 ASSN_ICO_PRINTED, ASSN_ICO_REGULAR = 0, 1
 ASSN_ICO_MAX_ORDER = 64
 ICO_BASES = {"printed": ASSN_ICO_PRINTED, "regular": ASSN_ICO_REGULAR}
-SCHEMES = {"euler": ASSN_SCHEME_EULER_UPWIND, "heun": ASSN_SCHEME_HEUN_MINMOD}
+SCHEMES = {"euler": ASSN_SCHEME_EULER_UPWIND, "heun": ASSN_SCHEME_HEUN_MINMOD, "implicit": ASSN_SCHEME_IMPLICIT}
 
 PRECISIONS = {"fp64": ASSN_FP64, "fp32": ASSN_FP32, "bf16": ASSN_BF16, "bf16x3": ASSN_BF16X3}
 
@@ -82,6 +82,9 @@ SIGNATURES = {
     "assn_max_stable_dt": (C.c_int, [_h, _dp]),
     "assn_step": (C.c_int, [_h, C.c_int, C.c_double]),
     "assn_set_scheme": (C.c_int, [_h, C.c_int]),
+    "assn_set_implicit_params": (C.c_int, [_h, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]),
+    "assn_implicit_stats": (C.c_int, [_h, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "assn_implicit_source_iteration": (C.c_int, [_h, C.c_double, _dp, _dp, C.c_int, _dp]),
     "assn_get_scheme": (C.c_int, [_h, C.POINTER(C.c_int)]),
     "assn_step_device": (C.c_int, [_h, _vp, _vp, C.c_double]),
     "assn_run_f32": (C.c_int, [_h, _fp, C.c_int, C.c_double, _dp]),
@@ -278,6 +281,25 @@ def assn_step(h: int, nsteps: int, dt: float) -> None:
 
 def assn_set_scheme(h: int, scheme: int) -> None:
     _check(lib.assn_set_scheme(h, scheme), h)
+
+
+def assn_set_implicit_params(h: int, si_eps: float = 1e-4, gmres_tol: float = 1.5e-8, restart: int = 30,
+                             max_si: int = 1000, max_gmres: int = 500) -> None:
+    _check(lib.assn_set_implicit_params(h, si_eps, gmres_tol, restart, max_si, max_gmres), h)
+
+
+def assn_implicit_stats(h: int) -> dict:
+    a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _check(lib.assn_implicit_stats(h, C.byref(a), C.byref(b), C.byref(c)), h)
+    return {"source_iterations": a.value, "gmres_iterations": b.value, "sweeps": c.value}
+
+
+def assn_implicit_source_iteration(h: int, dt: float, R, psi0, iterations: int) -> np.ndarray:
+    r = _contig(R)
+    p0 = _contig(psi0)
+    out = np.empty_like(r)
+    _check(lib.assn_implicit_source_iteration(h, dt, _d(r), _d(p0), iterations, _d(out)), h)
+    return out
 
 
 def assn_get_scheme(h: int) -> int:

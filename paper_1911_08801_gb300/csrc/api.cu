@@ -156,6 +156,7 @@ int upload_ord(assn_problem* p, double dt) {
 // coefficients are non-negative): 1 - dt (|Omega_x| + |Omega_y|)/h - dt sigma_as e_q
 // - dt (sigma_a + sigma_s) >= 0, maximised over ordinates and cells separately.
 double max_stable_dt(const assn_problem* p) {
+    if (p->scheme == ASSN_SCHEME_IMPLICIT) return INFINITY;   // implicit Euler: no step restriction
     if (p->scheme == ASSN_SCHEME_HEUN_MINMOD) {
         // Each forward-Euler stage of Heun's method stays a non-negative combination of old values:
         // with minmod slopes the upwind flux difference along an axis is (psi_i - psi_{i-1}) times a
@@ -327,6 +328,7 @@ int assn_destroy(assn_problem* p) {
     dfree(p->d_psi[0]); dfree(p->d_psi[1]); dfree(p->d_partials); dfree(p->d_scalar); dfree(p->d_flags);
     dfree(p->d_counter);
     dfree(p->d_stage);
+    assn::implicit_free(p->impl);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
     return ASSN_OK;
@@ -651,8 +653,10 @@ extern "C" {
 
 int assn_set_scheme(assn_problem* p, int scheme) {
     if (!p) return ASSN_ERR_ARG;
-    if (scheme != ASSN_SCHEME_EULER_UPWIND && scheme != ASSN_SCHEME_HEUN_MINMOD)
+    if (scheme != ASSN_SCHEME_EULER_UPWIND && scheme != ASSN_SCHEME_HEUN_MINMOD && scheme != ASSN_SCHEME_IMPLICIT)
         return fail(p, ASSN_ERR_ARG, "unknown scheme %d", scheme);
+    if (scheme == ASSN_SCHEME_IMPLICIT && p->tensor())
+        return fail(p, ASSN_ERR_UNSUPPORTED, "the implicit scheme runs in FP64 or FP32 (CUDA cores)");
     p->scheme = scheme;
     return ASSN_OK;
 }
@@ -706,6 +710,7 @@ static int heun_step(assn_problem* p, double dt) {
 int assn_step(assn_problem* p, int nsteps, double dt) {
     if (!p) return ASSN_ERR_ARG;
     if (nsteps < 0) return fail(p, ASSN_ERR_ARG, "nsteps < 0");
+    if (p->scheme == ASSN_SCHEME_IMPLICIT) return assn::implicit_steps(p, nsteps, dt);
     if (p->scheme == ASSN_SCHEME_HEUN_MINMOD) {
         int r = assn::problem_prepare(p, dt);
         if (r) return r;

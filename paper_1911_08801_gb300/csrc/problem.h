@@ -6,6 +6,10 @@
 
 #include "assn_internal.h"
 
+namespace assn {
+struct ImplicitWork;
+}
+
 struct assn_problem {
     int dev = 0;
     int nx = 0, ny = 0;
@@ -56,6 +60,7 @@ struct assn_problem {
     int* d_counter = nullptr;           // device step counter of the persistent tensor-core kernel
     int counter_host = 0;               // last value written to / advanced on d_counter
     double plan2_dt = -1.0;             // dt the persistent plan was built for
+    assn::ImplicitWork* impl = nullptr; // implicit scheme's work space and parameters (lazy)
 
     std::string err;
     int64_t launches = 0;
@@ -66,6 +71,11 @@ struct assn_problem {
 };
 
 namespace assn {
+
+// Frees the implicit scheme's work space (NULL is a no-op).
+void implicit_free(ImplicitWork* W);
+// nsteps implicit sweeping-Krylov steps of size dt (FP64 / FP32 problems).
+int implicit_steps(assn_problem* p, int nsteps, double dt);
 
 // Set p's error message; returns status.
 int problem_fail(assn_problem* p, int status, const char* msg);

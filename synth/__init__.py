@@ -165,6 +165,8 @@ class Workload:
     normalisation: str = "column"   # kernel matrix: "column" or the paper's "row" (Sec. 3.2)
     scheme: str = "euler"           # "euler" (first-order upwind) or "heun" (Heun + minmod)
     dt_rule: str = "cfl"            # "cfl": dt = cfl h; "bound": dt = cfl x the scheme's admissible dt
+    si_eps: float = 1e-4            # implicit scheme: source-iteration tolerance (Sec. 4.1)
+    gmres_tol: float = 1.5e-8       # implicit scheme: GMRES relative residual (Sec. 4.1)
 
     @property
     def Q(self) -> int:
@@ -238,6 +240,16 @@ def paper_line_source(n: int = 200, order: int = 4, beta: float = 4.5, sigma_as:
                     dt_rule="bound")
 
 
+def paper_line_source_implicit(n: int = 200, order: int = 4, beta: float = 4.0, sigma_as: float = 7.0,
+                               t_final: float = 1.0, name: str | None = None) -> Workload:
+    """The paper's implicit as-S_N line source (Sec. 4.1): as paper_line_source, with the implicit
+    sweeping-Krylov scheme at dt/dx = 2 and its parameters sigma_as = 7, beta = 4."""
+    q = 10 * (order - 1) ** 2 + 2
+    return Workload(name or f"line_source_{n}x{n}_ico{q}_implicit", "line_source", n, n, -1.5, 1.5, -1.5, 1.5,
+                    0, 0, beta, sigma_as=sigma_as, cfl=2.0, t_final=t_final, quadrature="icosahedron",
+                    ico_order=order, eps_rule="paper", normalisation="row", scheme="implicit")
+
+
 def paper_lattice(n: int = 280, order: int = 4, beta: float = 4.5, sigma_as: float = 5.0,
                   t_final: float = 3.2, name: str | None = None) -> Workload:
     """The paper's explicit as-S_N lattice (Sec. 4.2) with its quadrature, kernel width, normalisation
@@ -257,9 +269,10 @@ LINE_SOURCE_256_ACC = line_source(256, 16, 16, 1.0 / 8.0, name="line_source_256x
 # The paper's own explicit as-S_4 runs (N_q = 92).
 PAPER_LINE_SOURCE_200 = paper_line_source(200)
 PAPER_LATTICE_280 = paper_lattice(280)
+PAPER_LINE_SOURCE_200_IMPLICIT = paper_line_source_implicit(200)
 
 WORKLOADS = {w.name: w for w in (LINE_SOURCE_64, LATTICE_448, LINE_SOURCE_2048, LINE_SOURCE_256_ACC,
-                                 PAPER_LINE_SOURCE_200, PAPER_LATTICE_280)}
+                                 PAPER_LINE_SOURCE_200, PAPER_LATTICE_280, PAPER_LINE_SOURCE_200_IMPLICIT)}
 
 QUAD_ORDERS = {64: (8, 8), 128: (8, 16), 256: (16, 16), 512: (16, 32)}
 

@@ -39,8 +39,10 @@ def gpu_problem(A, wl: synth.Workload, precision: str, psi0=None, sigma_as=None,
     if normalisation is None:
         normalisation = 1 if wl.normalisation == "row" else 0
     p.set_artificial_scattering(wl.sigma_as if sigma_as is None else sigma_as, wl.eps, kind, normalisation)
-    if wl.scheme == "heun":
-        p.set_scheme("heun")
+    if wl.scheme in ("heun", "implicit"):
+        p.set_scheme(wl.scheme)
+    if wl.scheme == "implicit":
+        p.set_implicit_params(wl.si_eps, wl.gmres_tol)
     p.set_state(wl.psi0() if psi0 is None else psi0)
     return p
 
@@ -69,6 +71,8 @@ def oracle_run(wl: synth.Workload, nsteps: int, dt: float, psi0=None, normalisat
     Om, w, K, sa, ss, q = oracle_setup(wl, normalisation)
     psi = wl.psi0() if psi0 is None else psi0
     s_as = wl.sigma_as if sigma_as is None else sigma_as
+    if wl.scheme == "implicit":
+        return O.implicit_run(psi, nsteps, K, Om, w, sa, ss, q, s_as, wl.h, dt, wl.si_eps, wl.gmres_tol), w
     run = O.run_heun if wl.scheme == "heun" else O.run
     return run(psi, nsteps, K, Om, w, sa, ss, q, s_as, wl.h, dt), w
 
