@@ -316,6 +316,8 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     launches = prob.launch_count() - launches0
+    stats_timed = ({k: v - stats0[k] for k, v in prob.implicit_stats().items()}
+                   if args.scheme == "implicit" else None)
     ms_local = e0.elapsed_time(e1) if flush is None else sum(a.elapsed_time(b) for a, b in pairs)
     ms = max_over_ranks(ms_local, dist, "cuda")
     ms_per_step = ms / args.steps
@@ -357,8 +359,7 @@ def run_ours(args, rank, world, dist):
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
                      "kernel": ("step_tc2_kernel" if args.variant == 0 else "step_tc_kernel") if args.precision.startswith("bf16")
                      else "step_simt_kernel"} if args.scheme == "euler" else
-                     implicit_roofline(args, wl, ms_per_step,
-                                       {k: v - stats0[k] for k, v in prob.implicit_stats().items()}, args.steps)
+                     implicit_roofline(args, wl, ms_per_step, stats_timed, args.steps)
                      if args.scheme == "implicit" else
                      (heun_tc_roofline(wl, ms_per_step) if args.precision.startswith("bf16")
                       else alu_roofline(args, wl, ms_per_step))),

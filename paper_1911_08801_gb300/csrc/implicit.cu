@@ -15,11 +15,15 @@
 //
 // Kernels: si_source_kernel forms S (the artificial in-scattering contraction on CUDA cores, the
 // layout of the explicit CUDA-core step: a tile of cells of one row in shared memory, threads own
-// ordinates); sweep_kernel inverts L: one block per chunk of up to kChunk ordinates of one quadrant
+// ordinates); the sweeps invert L: one block per chunk of up to kChunk ordinates of one quadrant
 // (sign of Omega_x, Omega_y), which walks the anti-diagonals of the grid in the upwind order of that
 // quadrant -- every cell needs only its two upwind neighbours in x and y, which lie on the two
-// previous anti-diagonals -- with a block barrier between anti-diagonals.  GMRES runs on the host
-// over device vectors of one value per cell.
+// previous anti-diagonals -- with a block barrier between anti-diagonals.  sweep_rows_kernel (grids
+// up to 2048 rows) gives every row its own thread, so x-neighbours stay in registers and y-neighbours
+// come from a ring of anti-diagonals in shared memory, and it also sums the convergence norm;
+// sweep_kernel (any grid) reads all neighbours back from memory.  One ordinate per block, so a sweep
+// spreads over up to Q SMs and each block's barrier joins few warps.  GMRES runs on the host over device
+// vectors of one value per cell.
 #include <math.h>
 #include <string.h>
 
@@ -54,10 +58,12 @@ struct ImplicitWork {
 
 namespace {
 
-constexpr int kChunk = 8;          // ordinates per sweep block
-constexpr int kSweepThreads = 256;
-constexpr int kTN = 4;             // cells per source-kernel tile
+constexpr int kChunk = 1;          // ordinates per sweep block (one: the ordinates spread over the SMs)
+constexpr int kSweepThreads = 256; // general sweep kernel
+constexpr int kRowBlock = 512;     // row-per-thread sweep kernel: at most this many threads per block
+constexpr int kTN = 8;             // cells per source-kernel tile
 constexpr int kRedBlocks = 304;    // reduction partials (2 per SM)
+constexpr int kPartMax = ASSN_MAX_Q;   // partial sums held: reductions and one per sweep block
 
 int blocks_for(size_t n, int threads) {
     const size_t b = (n + threads - 1) / threads;
@@ -128,6 +134,8 @@ struct SweepArgs {
     const OrdT* ord;         // nux = dt Omega_x / h, nuy = dt Omega_y / h
     const CellT* cell;       // sig_t = sigma_a + sigma_s
     const int* chunks;       // [nchunks][kChunk]
+    const T* prev;           // nullable: the previous iterate, for sum (out - prev)^2
+    double* part;            // [nchunks] per-block sums of (out - prev)^2 (when prev is set)
     int nx, ny, Qp;
     T dt, sigma_as;
 };
@@ -166,6 +174,108 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs<T,
             }
         }
         __syncthreads();
+    }
+}
+
+// The sweep with one thread per (row of the grid, ordinate), RPT rows per thread: in the upwind-ordered
+// frame row b reaches anti-diagonal d at column u = d - b, so a thread meets its row's cells in order
+// and keeps their two upwind x-neighbours in registers; the y-neighbours, computed one and two
+// anti-diagonals earlier by the threads of rows b - 1 and b - 2, come from a three-deep ring of
+// anti-diagonals in shared memory.  The source term and stencil diagonal of a thread's cells are
+// loaded three anti-diagonals before their use.  With prev set, the block also sums (out - prev)^2.
+template <typename T, typename OrdT, typename CellT, int RPT>
+__global__ void __launch_bounds__(kRowBlock) sweep_rows_kernel(const SweepArgs<T, OrdT, CellT> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kRowBlock / 32];
+    const int nx = a.nx, ny = a.ny, Qp = a.Qp;
+    T* ring = reinterpret_cast<T*>(smem_raw);                          // [3][ny][kChunk]
+    const int k = threadIdx.x % kChunk, rt = threadIdx.x / kChunk;
+    const int nrow = blockDim.x / kChunk;                               // rows handled at once
+    const int* ch = a.chunks + blockIdx.x * kChunk;
+    const int q = ch[k];
+    const OrdT o0 = a.ord[ch[0]];
+    const int sx = o0.nux >= 0 ? 1 : -1, sy = o0.nuy >= 0 ? 1 : -1;   // the chunk's quadrant
+    T ax = 0, ay = 0;
+    if (q >= 0) {
+        const OrdT o = a.ord[q];
+        ax = o.nux >= 0 ? (T)o.nux : -(T)o.nux;
+        ay = o.nuy >= 0 ? (T)o.nuy : -(T)o.nuy;
+    }
+    const T lead = T(1.5) * (ax + ay) + T(1);
+    // Per row: the x-neighbours in registers, and four sets of the cell of anti-diagonals d .. d + 3
+    // (index, source term, sigma_a + sigma_s, previous iterate): set d % 4 is loaded when anti-diagonal
+    // d - 4 is done, three anti-diagonals before its use.  The loop is unrolled by four so the sets
+    // stay in registers.
+    using Set = struct {
+        T sn[RPT], sg[RPT], pv[RPT];
+        ptrdiff_t ix[RPT];
+    };
+    T x1[RPT], x2[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) x1[r] = x2[r] = T(0);
+    Set s0, s1, s2, s3;
+    double d2 = 0;
+    auto fetch = [&](int d, Set& z) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int b = rt + r * nrow, u = d - b;
+            z.ix[r] = -1;
+            z.sn[r] = z.pv[r] = z.sg[r] = T(0);
+            if (q >= 0 && b < ny && u >= 0 && u < nx) {
+                const int i = sx > 0 ? u : nx - 1 - u, jj = sy > 0 ? b : ny - 1 - b;
+                const size_t c = (size_t)jj * nx + i;
+                z.ix[r] = (ptrdiff_t)(c * Qp + q);
+                z.sn[r] = a.S[z.ix[r]];
+                z.sg[r] = (T)a.cell[c].sig_t;        // only loaded here: used three anti-diagonals later
+                if (a.prev) z.pv[r] = a.prev[z.ix[r]];
+            }
+        }
+    };
+    const int nd = nx + ny - 1;
+    int cs = 0;                                                         // ring slot of anti-diagonal d
+    // one anti-diagonal with the cells of set z, then z takes anti-diagonal d + 4
+    auto step = [&](int d, Set& z) {
+        const int r1 = cs == 0 ? 2 : cs - 1, r2 = cs == 2 ? 0 : cs + 1;  // slots of d - 1, d - 2
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            if (z.ix[r] < 0) continue;
+            const int b = rt + r * nrow;
+            const T y1 = b >= 1 ? ring[((size_t)r1 * ny + b - 1) * kChunk + k] : T(0);
+            const T y2 = b >= 2 ? ring[((size_t)r2 * ny + b - 2) * kChunk + k] : T(0);
+            const T den = lead + a.dt * (z.sg[r] + a.sigma_as);
+            const T v = (z.sn[r] + ax * (T(2) * x1[r] - T(0.5) * x2[r]) + ay * (T(2) * y1 - T(0.5) * y2)) / den;
+            a.out[z.ix[r]] = v;
+            ring[((size_t)cs * ny + b) * kChunk + k] = v;
+            if (a.prev) {
+                const double e = (double)v - (double)z.pv[r];
+                d2 += e * e;
+            }
+            x2[r] = x1[r];
+            x1[r] = v;
+        }
+        fetch(d + 4, z);
+        __syncthreads();
+        cs = cs == 2 ? 0 : cs + 1;
+    };
+    fetch(0, s0);
+    fetch(1, s1);
+    fetch(2, s2);
+    fetch(3, s3);
+    for (int d = 0; d < nd; d += 4) {                                   // d < nd is uniform in the block
+        step(d, s0);
+        if (d + 1 < nd) step(d + 1, s1);
+        if (d + 2 < nd) step(d + 2, s2);
+        if (d + 3 < nd) step(d + 3, s3);
+    }
+    if (a.prev) {
+        for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            a.part[blockIdx.x] = t;
+        }
     }
 }
 
@@ -262,7 +372,7 @@ int ensure_work(assn_problem* p) {
     }
     if (!W->vec) {
         ICK(p, cudaMalloc(&W->vec, 4 * ncell * sizeof(double)));
-        ICK(p, cudaMalloc(&W->d_part, kRedBlocks * sizeof(double)));
+        ICK(p, cudaMalloc(&W->d_part, kPartMax * sizeof(double)));
         ICK(p, cudaMalloc(&W->d_red, sizeof(double)));
         ICK(p, cudaMallocHost(&W->h_red, sizeof(double)));
     }
@@ -311,9 +421,9 @@ double lipschitz(assn_problem* p, double dt) {
     return W->lip;
 }
 
-int read_sum(assn_problem* p, double* out) {
+int read_sum(assn_problem* p, double* out, int nparts = kRedBlocks) {
     ImplicitWork* W = p->impl;
-    finish_sum<<<1, 256, 0, p->stream>>>(W->d_part, kRedBlocks, W->d_red);
+    finish_sum<<<1, 256, 0, p->stream>>>(W->d_part, nparts, W->d_red);
     ICK(p, cudaGetLastError());
     ++p->launches;
     ICK(p, cudaMemcpyAsync(W->h_red, W->d_red, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
@@ -369,17 +479,39 @@ int source_iteration(assn_problem* p, double dt, const Rhs& R, const void* psi0,
         ICK(p, cudaFuncSetAttribute(si_source_kernel<T, Ord, Cell>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
     const size_t n = p->ncell() * p->Qp;
+    // row-per-thread sweep (rows per thread RPT) where its ring of three anti-diagonals fits
+    const int ny = p->ny;
+    const int rpt = ny <= kRowBlock ? 1 : ny <= 2 * kRowBlock ? 2 : ny <= 4 * kRowBlock ? 4 : 0;
+    const int row_threads = rpt ? ((ny + rpt - 1) / rpt * kChunk + 31) / 32 * 32 : 0;
+    const size_t ring = (size_t)3 * ny * kChunk * sizeof(T);
+    const bool rows = rpt > 0 && ring <= 200 * 1024;
+    if (rows && ring > 48 * 1024) {
+        auto set = [&](const void* f) { return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring); };
+        cudaError_t e = rpt == 1 ? set((const void*)sweep_rows_kernel<T, Ord, Cell, 1>)
+                      : rpt == 2 ? set((const void*)sweep_rows_kernel<T, Ord, Cell, 2>)
+                                 : set((const void*)sweep_rows_kernel<T, Ord, Cell, 4>);
+        ICK(p, e);
+    }
     W->last_si_converged = 1;
     double prev_d2 = INFINITY;
     while (true) {
         SourceArgs<T, Ord, Cell> sa{(const T*)cur, (T*)W->buf[2], KT, (const Ord*)p->d_ord, (const Cell*)p->d_cell,
                                     R.phi, R.old ? (const T*)p->d_psi[p->cur] : nullptr, (const T*)R.rarr, R.withq,
                                     p->nx, p->ny, p->Q, p->Qp, (T)dt, (T)p->sigma_as};
-        si_source_kernel<T, Ord, Cell><<<sgrid, 256, smem, p->stream>>>(sa);
+        si_source_kernel<T, Ord, Cell><<<sgrid, std::min(256, (p->Q + 31) / 32 * 32), smem, p->stream>>>(sa);
         ICK(p, cudaGetLastError());
+        const bool norm = fixed <= 0 && Tl > 0.0;                // the stopping rule needs the difference
         SweepArgs<T, Ord, Cell> sw{(const T*)W->buf[2], (T*)W->buf[out], (const Ord*)p->d_ord, (const Cell*)p->d_cell,
-                                   W->d_chunks, p->nx, p->ny, p->Qp, (T)dt, (T)p->sigma_as};
-        sweep_kernel<T, Ord, Cell><<<W->nchunks, kSweepThreads, 0, p->stream>>>(sw);
+                                   W->d_chunks, rows && norm ? (const T*)cur : nullptr, W->d_part,
+                                   p->nx, p->ny, p->Qp, (T)dt, (T)p->sigma_as};
+        if (rows) {
+            const dim3 g(W->nchunks), b(row_threads);
+            if (rpt == 1) sweep_rows_kernel<T, Ord, Cell, 1><<<g, b, ring, p->stream>>>(sw);
+            else if (rpt == 2) sweep_rows_kernel<T, Ord, Cell, 2><<<g, b, ring, p->stream>>>(sw);
+            else sweep_rows_kernel<T, Ord, Cell, 4><<<g, b, ring, p->stream>>>(sw);
+        } else {
+            sweep_kernel<T, Ord, Cell><<<W->nchunks, kSweepThreads, 0, p->stream>>>(sw);
+        }
         ICK(p, cudaGetLastError());
         p->launches += 2;
         ++it;
@@ -392,11 +524,15 @@ int source_iteration(assn_problem* p, double dt, const Rhs& R, const void* psi0,
             continue;
         }
         if (Tl == 0.0) break;                      // no artificial scattering: one sweep is exact
-        sqdiff_partials<T><<<kRedBlocks, 256, 0, p->stream>>>((const T*)cur, (const T*)prev, n, W->d_part);
-        ICK(p, cudaGetLastError());
-        ++p->launches;
+        int nparts = W->nchunks;
+        if (!rows) {
+            sqdiff_partials<T><<<kRedBlocks, 256, 0, p->stream>>>((const T*)cur, (const T*)prev, n, W->d_part);
+            ICK(p, cudaGetLastError());
+            ++p->launches;
+            nparts = kRedBlocks;
+        }
         double d2 = 0;
-        int r = read_sum(p, &d2);
+        int r = read_sum(p, &d2, nparts);
         if (r) return r;
         if (sqrt(d2) < tol) break;
         // FP32 state: once the difference stops falling the iterates only differ by rounding

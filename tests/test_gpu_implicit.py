@@ -45,8 +45,10 @@ def make(A, precision, nx, ny, sigma_as, seed, norm=0):
 TOL = {"fp64": 1e-12, "fp32": 2e-5}
 
 
-# ragged grids, a single row and column, tiny grids; dt/h = 2 (the paper's implicit CFL number)
-@pytest.mark.parametrize("nx,ny", [(37, 11), (1, 9), (13, 1), (2, 2), (64, 48)])
+# ragged grids, a single row and column, tiny grids, and tall grids that take 1, 2 and 4 rows per thread of
+# the row sweep or (beyond 2048 rows) the general sweep; dt/h = 2 (the paper's implicit CFL number)
+@pytest.mark.parametrize("nx,ny", [(37, 11), (1, 9), (13, 1), (2, 2), (64, 48), (5, 300), (3, 1000), (2, 1500),
+                                   (2, 2100)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_one_sweep_matches_oracle(A, nx, ny, precision):
     p, Om, w, K, sa, ss, q = make(A, precision, nx, ny, 0.0, nx + ny)
@@ -97,6 +99,41 @@ def test_step_equals_the_assembled_system(A):
     st = p.implicit_stats()
     assert st["gmres_iterations"] > 1 and st["sweeps"] >= st["source_iterations"] > st["gmres_iterations"]
     p.close()
+
+
+TALL = (3, 300)
+
+
+@pytest.fixture(scope="module")
+def tall_ref():
+    """The oracle's implicit step (tolerances 1e-13) on a 3 x 300 grid, Q = 8, sigma_as = 5, dt/h = 2."""
+    nx, ny = TALL
+    Om, w = O.product_quadrature(2, 4)
+    sa, ss, q = synth.random_materials(4, ny, nx)
+    K = O.kernel_matrix(Om, w, 0.6)
+    psi_old = np.random.default_rng(8).random((ny, nx, len(w)))
+    ref, _, _, _ = O.implicit_step(psi_old, O.scalar_flux(psi_old, w), K, Om, w, sa, ss, q, 5.0, 0.1, 0.2,
+                                   1e-13, 1e-13)
+    return Om, w, sa, ss, q, psi_old, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_on_a_tall_grid(A, tall_ref, precision):
+    """A whole implicit step on a tall grid (the row sweep, whose blocks also sum the source iteration's
+    convergence norm) against the oracle's step."""
+    Om, w, sa, ss, q, psi_old, ref = tall_ref
+    nx, ny = TALL
+    p = A.Problem(nx, ny, 0.0, 0.3, 0.0, 30.0, precision)
+    p.set_quadrature(Om, w)
+    p.set_cross_sections(sa, ss, q)
+    p.set_artificial_scattering(5.0, 0.6, 0, 0)
+    p.set_scheme("implicit")
+    p.set_implicit_params(1e-12, 1e-12)
+    p.set_state(psi_old)
+    p.step(1, 0.2)
+    got = p.state()
+    p.close()
+    assert np.abs(got - ref).max() <= (1e-9 if precision == "fp64" else 1e-5) * np.abs(ref).max()
 
 
 def paper_small(n=24, **kw):
