@@ -77,6 +77,27 @@ def test_fixed_source_iterations_match_oracle(A, precision, norm):
     p.close()
 
 
+def test_fixed_source_iterations_many_ordinates(A):
+    """Q = 512 in FP64: the largest ordinate tiles of the source kernel and 512 sweep blocks."""
+    nx, ny = 9, 7
+    Om, w = O.product_quadrature(16, 32)
+    p = A.Problem(nx, ny, 0.0, 0.9, 0.0, 0.7, "fp64")
+    p.set_quadrature(Om, w)
+    sa, ss, q = synth.random_materials(6, ny, nx)
+    p.set_cross_sections(sa, ss, q)
+    p.set_artificial_scattering(5.0, 0.3, 0, 0)
+    p.set_scheme("implicit")
+    rng = np.random.default_rng(6)
+    R = rng.random((ny, nx, len(w)))
+    psi0 = rng.random((ny, nx, len(w)))
+    got = p.implicit_source_iteration(0.2, R, psi0, 2)
+    p.close()
+    K = O.kernel_matrix(Om, w, 0.3)
+    T = O.source_iteration_lipschitz(sa, ss, 5.0, 0.2)
+    ref, _ = O.source_iteration(psi0, R, K, Om, sa + ss + 5.0, 5.0, 0.1, 0.2, 0.0, T, fixed=2)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_step_equals_the_assembled_system(A):
     """One implicit step with tight tolerances equals the implicit system solved directly."""
     nx, ny = 6, 5
