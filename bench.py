@@ -459,7 +459,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded uniform state, analytic lattice materials)",
+            "data": "synthetic (seeded uniform state, analytic %s materials)" % wl.kind.replace("_", "-"),
             "config": {"workload": wl.name, "cells": f"{wl.nx}x{wl.ny}", "Q": wl.Q, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
