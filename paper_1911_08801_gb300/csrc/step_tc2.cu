@@ -35,7 +35,8 @@
 //               while the MMA of the next tile fills the other buffer.  Four warps share each
 //               TMEM lane quarter; the one-pass kernel loads 16-cell chunks of flux values, the
 //               split kernel keeps its next 8-cell chunk in flight (register double buffer).
-//   Most split forward-Euler kernels with tiles of up to 128 cells run 20 warps instead of 23:
+//   Most split forward-Euler kernels and the Heun kernels with tiles of up to 128 cells run 20 warps
+//   instead of 23:
 //   the G producer is warp 1, lane 1, and warps 2-3 are the converters (epilogue 4-19), which
 //   lets each thread hold 96 registers instead of 80.
 // SPLIT (BF16X3) keeps BF16 residuals of both operands and issues hi*hi + hi*lo + lo*hi.
@@ -170,13 +171,14 @@ __device__ __forceinline__ int find_prob(const int* tile0, int nprob, int T) {
 }
 
 // Warp roles of one kernel instance.  Four converter warps, except in the split forward-Euler
-// kernels up to 128-cell tiles: there two converter warps do the work and the two TMA producers
-// share warp 1, so that the block has 20 warps and ptxas may give each thread 96 registers instead
-// of 80 (the split epilogue keeps two chunks of flux values in flight).  The 128-cell instance
-// for 64 ordinates keeps four converters: with two, its converter rows spill.
+// kernels up to 128-cell tiles and the Heun kernels up to 128-cell tiles: there two converter warps do
+// the work and the two TMA producers share warp 1, so that the block has 20 warps and ptxas may give
+// each thread 96 registers instead of 80 (the split epilogue keeps two chunks of flux values in
+// flight; the Heun epilogue holds the limited stencil of a chunk).  The 128-cell split instance for
+// 64 ordinates keeps four converters: with two, its converter rows spill.
 template <int NT, bool SPLIT, int QP, bool HEUN>
 struct Roles {
-    static constexpr bool kTwo = SPLIT && !HEUN && (NT <= 64 || (NT == 128 && QP != 64));
+    static constexpr bool kTwo = (SPLIT && !HEUN && (NT <= 64 || (NT == 128 && QP != 64))) || (HEUN && NT <= 128);
     static constexpr int kConv = kTwo ? 2 : 4;                             // converter warps
     static constexpr int kConv0 = kConv == 2 ? 2 : 3;                      // first converter warp
     static constexpr int kGWarp = kConv0 - 1, kGLane = kConv == 2 ? 1 : 0; // kernel-matrix producer
