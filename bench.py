@@ -765,7 +765,7 @@ def run_accuracy(args):
     heun64 = dataclasses.replace(synth.LINE_SOURCE_64, name=synth.LINE_SOURCE_64.name + "_heun", cfl=0.95,
                                  scheme="heun", dt_rule="bound")
     cases = [synth.LINE_SOURCE_64, synth.LINE_SOURCE_256_ACC, synth.LATTICE_448, heun64, synth.PAPER_LINE_SOURCE_200,
-             synth.PAPER_LINE_SOURCE_200_IMPLICIT]
+             synth.PAPER_LINE_SOURCE_200_IMPLICIT, synth.PAPER_LATTICE_280, synth.PAPER_LATTICE_280_IMPLICIT]
     if args.only:
         cases = [c for c in cases if c.name == args.only]
     elif args.count < len(cases):

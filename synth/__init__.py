@@ -260,6 +260,16 @@ def paper_lattice(n: int = 280, order: int = 4, beta: float = 4.5, sigma_as: flo
                     eps_rule="paper", normalisation="row", scheme="heun", dt_rule="bound")
 
 
+def paper_lattice_implicit(n: int = 280, order: int = 4, beta: float = 4.0, sigma_as: float = 7.0,
+                           t_final: float = 3.2, name: str | None = None) -> Workload:
+    """The paper's implicit as-S_N lattice (Sec. 4.2): as paper_lattice, with the implicit sweeping-Krylov
+    scheme at dt/dx = 2 and its implicit parameters sigma_as = 7, beta = 4."""
+    q = 10 * (order - 1) ** 2 + 2
+    return Workload(name or f"lattice_{n}x{n}_ico{q}_implicit", "lattice", n, n, 0.0, 7.0, 0.0, 7.0, 0, 0, beta,
+                    sigma_as=sigma_as, cfl=2.0, t_final=t_final, quadrature="icosahedron", ico_order=order,
+                    eps_rule="paper", normalisation="row", scheme="implicit")
+
+
 # The five workloads of the measurement plan.
 LINE_SOURCE_64 = line_source(64, 8, 16, 1.0 / 8.0, name="line_source_64x64_Q128_fp64")
 LATTICE_448 = lattice(448, 16, 32, 0.5, name="lattice_448x448_Q512")
@@ -270,9 +280,11 @@ LINE_SOURCE_256_ACC = line_source(256, 16, 16, 1.0 / 8.0, name="line_source_256x
 PAPER_LINE_SOURCE_200 = paper_line_source(200)
 PAPER_LATTICE_280 = paper_lattice(280)
 PAPER_LINE_SOURCE_200_IMPLICIT = paper_line_source_implicit(200)
+PAPER_LATTICE_280_IMPLICIT = paper_lattice_implicit(280)
 
 WORKLOADS = {w.name: w for w in (LINE_SOURCE_64, LATTICE_448, LINE_SOURCE_2048, LINE_SOURCE_256_ACC,
-                                 PAPER_LINE_SOURCE_200, PAPER_LATTICE_280, PAPER_LINE_SOURCE_200_IMPLICIT)}
+                                 PAPER_LINE_SOURCE_200, PAPER_LATTICE_280, PAPER_LINE_SOURCE_200_IMPLICIT,
+                                 PAPER_LATTICE_280_IMPLICIT)}
 
 QUAD_ORDERS = {64: (8, 8), 128: (8, 16), 256: (16, 16), 512: (16, 32)}
 

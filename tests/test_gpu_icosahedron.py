@@ -99,6 +99,21 @@ def test_paper_line_source_64(A, precision):
         assert np.abs(phi - phi[:, ::-1]).max() <= 1e-12 * np.abs(phi).max()
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_paper_lattice_28(A, precision):
+    """The paper's explicit as-S_4 lattice (Sec. 4.2: absorbers, source block, N_q = 92, row
+    normalisation, Heun + minmod) on a 28^2 grid (4 cells per block), run to t = 3.2."""
+    wl = synth.paper_lattice(28)
+    n, dt = run_steps(wl)
+    p = gpu_problem(A, wl, precision)
+    p.step(n, dt)
+    phi = p.scalar_flux()
+    p.close()
+    ref, w = oracle_run(wl, n, dt)
+    assert rel_l2(phi, ref @ w) <= RUN_TOL[precision]
+    assert phi.min() >= 0.0
+
+
 @pytest.fixture(scope="module")
 def oracle_200():
     """The oracle's scalar flux after the first 12 steps of the paper's 200^2 as-S_4 run."""

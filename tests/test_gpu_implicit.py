@@ -190,6 +190,27 @@ def test_paper_implicit_line_source_run(A, converged_24, precision):
     assert st["gmres_iterations"] >= n and st["source_iterations"] > st["gmres_iterations"]
 
 
+@pytest.fixture(scope="module")
+def converged_lattice_28():
+    """The oracle's converged run (tolerances 1e-10) of the paper's implicit as-S_4 lattice on 28^2 cells
+    (4 cells per block), dt/dx = 2, the first two steps (t = 1; the source iteration's contraction
+    factor is about 0.7 here, so converged steps are costly for the oracle)."""
+    wl = dataclasses.replace(synth.paper_lattice_implicit(28, t_final=1.0), si_eps=1e-10, gmres_tol=1e-10)
+    n, dt = wl.steps()
+    ref, w = oracle_run(wl, n, dt)
+    return wl, n, dt, ref @ w
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_paper_implicit_lattice_run(A, converged_lattice_28, precision):
+    wl, n, dt, phi_ref = converged_lattice_28
+    p = gpu_problem(A, wl, precision)
+    p.step(n, dt)
+    phi = p.scalar_flux()
+    p.close()
+    assert rel_l2(phi, phi_ref) <= IMPLICIT_RUN_TOL[precision]
+
+
 def test_paper_tolerances_give_the_tolerance_level(A, converged_24):
     """With the paper's own tolerances (source iteration 1e-4, GMRES 1.5e-8) the result stays within
     about the solver tolerance of the converged solution."""
