@@ -71,6 +71,17 @@ int blocks_for(size_t n, int threads) {
 }
 
 // ------------------------------------------------------------------------------------- kernels
+template <typename T> struct Vec4 { T x, y, z, w; };
+__device__ __forceinline__ Vec4<float> load_vec4(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Vec4<double> load_vec4(const double* p) {
+    const double2 u = *reinterpret_cast<const double2*>(p);
+    const double2 v = *reinterpret_cast<const double2*>(p + 2);
+    return {u.x, u.y, v.x, v.y};
+}
+
 template <typename T, typename OrdT, typename CellT>
 struct SourceArgs {
     const T* psi;            // iterate psi^l [ncell][Qp]
@@ -104,10 +115,15 @@ __global__ void __launch_bounds__(256) si_source_kernel(const SourceArgs<T, OrdT
 #pragma unroll
         for (int c = 0; c < kTN; ++c) acc[c] = 0;
         if (a.sigma_as != T(0)) {
-            for (int p = 0; p < Qp; ++p) {
-                const T k = a.KT[(size_t)p * Qp + q];
+            // four ordinates p at a time: one 16-byte (FP32) or two (FP64) shared loads per cell
+            for (int p = 0; p < Qp; p += 4) {
+                const T k0 = a.KT[(size_t)(p + 0) * Qp + q], k1 = a.KT[(size_t)(p + 1) * Qp + q];
+                const T k2 = a.KT[(size_t)(p + 2) * Qp + q], k3 = a.KT[(size_t)(p + 3) * Qp + q];
 #pragma unroll
-                for (int c = 0; c < kTN; ++c) acc[c] += k * ps[c * Qp + p];
+                for (int c = 0; c < kTN; ++c) {
+                    const Vec4<T> v = load_vec4(ps + c * Qp + p);
+                    acc[c] += k0 * v.x + k1 * v.y + k2 * v.z + k3 * v.w;
+                }
             }
         }
         const T kqq = T(1) - a.ord[q].e;
