@@ -19,6 +19,9 @@ and a second-order convergence rate on a smooth periodic profile.  The icosahedr
 quadrature (Sec. 3.3) is pinned by the paper's printed order-2 table (Appendix A),
 the point count N_q = 10 (k-1)^2 + 2, the 4 pi weight sum, its symmetries, exact
 degree-5 moments on the regular base and convergence of moments on the printed one.
+The admissible time step of the limited scheme (heun_admissible_dt) is pinned by
+positivity of a stage at the bound and by a constructed state that reaches zero
+exactly there and goes negative just above it.
 The implicit step (``oracle.implicit``, Sec. 3.4-3.5) is pinned by the printed
 symmetric part of the second-order upwind operator (Appendix B), sweeps that invert
 the streaming operator, the exact implicit-Euler decay of an isotropic state, the
