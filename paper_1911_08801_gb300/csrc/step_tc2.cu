@@ -154,10 +154,15 @@ __device__ __forceinline__ float minmod(float a, float b) {
 // F_{i+1/2} - F_{i-1/2} in face-value units of the minmod-limited upwind scheme for one ordinate
 // along one axis, from the values at i-2 .. i+2 (zero beyond the domain): nu > 0 takes the face
 // values psi_i + D_i / 2, nu < 0 takes psi_{i+1} - D_{i+1} / 2 (D: minmod of one-sided differences).
+// The lanes of a warp are ordinates of both signs, so both forms are computed from the three slopes
+// and one is selected (no divergent branch).
 __device__ __forceinline__ float limited_difference(float nu, float m2, float m1, float c0, float p1, float p2) {
-    if (nu > 0.0f) return (c0 + 0.5f * minmod(c0 - m1, p1 - c0)) - (m1 + 0.5f * minmod(m1 - m2, c0 - m1));
-    if (nu < 0.0f) return (p1 - 0.5f * minmod(p1 - c0, p2 - p1)) - (c0 - 0.5f * minmod(c0 - m1, p1 - c0));
-    return 0.0f;
+    const float dm = minmod(m1 - m2, c0 - m1);   // D_{i-1}
+    const float d0 = minmod(c0 - m1, p1 - c0);   // D_i
+    const float dp = minmod(p1 - c0, p2 - p1);   // D_{i+1}
+    const float pos = (c0 - m1) + 0.5f * (d0 - dm);
+    const float neg = (p1 - c0) - 0.5f * (dp - d0);
+    return nu > 0.0f ? pos : (nu < 0.0f ? neg : 0.0f);
 }
 
 // Problem owning global tile T: the last problem whose first tile is <= T.
@@ -678,8 +683,8 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                         const float xp2 = (bits & 64) ? xv(i + 2) : 0.0f;
                         const float c = sv[i];
                         const float tx = limited_difference(nux, xm2, xm1, c, xp1, xp2);
-                        const float ty = nuy > 0.f ? limited_difference(nuy, ya[i], yb[i], c, yc[i], 0.0f)
-                                                   : limited_difference(nuy, 0.0f, yb[i], c, yc[i], ya[i]);
+                        const bool up = nuy > 0.f;   // ya is two rows upwind: below for up, above otherwise
+                        const float ty = limited_difference(nuy, up ? ya[i] : 0.0f, yb[i], c, yc[i], up ? 0.0f : ya[i]);
                         const float st = SPLIT ? c : __bfloat162float(__float2bfloat16_rn(c));
                         float adv = fmaf(c, cf.x, cf.y);
                         adv = fmaf(-nux, tx, adv);
