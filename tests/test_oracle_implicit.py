@@ -110,3 +110,29 @@ def test_sweeping_krylov_step_equals_the_assembled_system(norm):
     assert np.abs(psi - ref).max() < 1e-10 * np.abs(ref).max()
     assert np.abs(phi - O.scalar_flux(ref, w)).max() < 1e-10 * np.abs(phi).max()
     assert its > 1 and si > its
+
+
+@pytest.mark.parametrize("dt,norm", [(0.05, "column"), (0.2, "row"), (0.5, "column"), (0.5, "row")])
+def test_source_iteration_stopping_rule_bounds_the_error(dt, norm):
+    """Alg. 1's a-posteriori rule with the contraction estimate T of R26: when the iteration stops, the
+    iterate is within eps (L2 over all values) of the exact solution of (L - dt sigma_as K) psi = dt R,
+    from dt/h = 0.5 to 5 (T from 0.25 to 0.73)."""
+    rng = np.random.default_rng(int(dt * 100))
+    Om, w = O.product_quadrature(2, 4)
+    K = O.kernel_matrix(Om, w, 0.7, normalisation=norm)
+    ny, nx, Q = 5, 6, len(w)
+    sa, ss, _ = synth.random_materials(11, ny, nx)
+    sig_as, h = 7.0, 0.1
+    sig = sa + ss + sig_as
+    R = rng.random((ny, nx, Q))
+    T = O.source_iteration_lipschitz(sa, ss, sig_as, dt)
+
+    def op(v):
+        p = v.reshape(ny, nx, Q)
+        return (O.streaming_apply(p, Om, h, dt, sig) - dt * sig_as * (p @ K.T)).ravel()
+    A = np.column_stack([op(e) for e in np.eye(ny * nx * Q)])
+    ref = np.linalg.solve(A, dt * R.ravel()).reshape(ny, nx, Q)
+    for eps in (1e-3, 1e-6):
+        psi, it = O.source_iteration(np.zeros_like(R), R, K, Om, sig, sig_as, h, dt, eps, T)
+        assert it > 1
+        assert np.linalg.norm(psi - ref) <= eps
