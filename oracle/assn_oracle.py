@@ -59,7 +59,7 @@ def _sphere_triangle_area(a, b, c) -> float:
     return 2.0 * math.atan2(num, den)
 
 
-def icosahedron_quadrature(order: int, base: str = "printed"):
+def icosahedron_quadrature(order: int, base: str = "printed", midpoints: str = "sphere"):
     """Icosahedron quadrature on S^2 (Sec. 3.3; the paper prints order 2 in Appendix A).
 
     The construction the paper describes: every face of an icosahedron is triangulated with
@@ -76,9 +76,10 @@ def icosahedron_quadrature(order: int, base: str = "printed"):
         with this base the construction reproduces the printed order-2 points and weights.
         base "regular": the regular icosahedron, (+-g, 0, +-1) in the last group.
       * Both are turned about the x axis so that (0, 1, g) lands on (0, 0, 1).
-      * Midpoints are taken on the sphere: the centre of a triangle with mapped corners a, b, c is
-        (a + b + c) / |a + b + c|, the midpoint of an edge (a + b) / |a + b|; cell boundaries are
-        great-circle arcs between them.
+      * midpoints "sphere": the centre of a triangle with mapped corners a, b, c is
+        (a + b + c) / |a + b + c|, the midpoint of an edge (a + b) / |a + b|; midpoints "flat": the
+        cell is drawn on the flat face and then mapped, so the centre and midpoints are those of the
+        flat points, mapped (the two agree at order 2).  Cell boundaries are great-circle arcs.
 
     Returns (Omega[N_q, 3], w[N_q]); the order of the points is not significant.
     """
@@ -106,8 +107,10 @@ def icosahedron_quadrature(order: int, base: str = "printed"):
                     [0.0, math.cos(ang), -math.sin(ang)],
                     [0.0, math.sin(ang), math.cos(ang)]])
     V = V @ rot.T
+    if midpoints not in ("sphere", "flat"):
+        raise ValueError("midpoints is 'sphere' or 'flat'")
     n = order - 1
-    index, points = {}, []
+    index, points, flat = {}, [], []
 
     def node(f, i, j):
         # the point with i / n of the way to the face's second vertex and j / n to its third;
@@ -118,6 +121,7 @@ def icosahedron_quadrature(order: int, base: str = "printed"):
             p = V[a] + (i / n) * (V[b] - V[a]) + (j / n) * (V[c] - V[a])
             index[key] = len(points)
             points.append(p / np.linalg.norm(p))
+            flat.append(p)
         return index[key]
 
     triangles = []
@@ -130,13 +134,15 @@ def icosahedron_quadrature(order: int, base: str = "printed"):
     Omega = np.array(points)
     w = np.zeros(len(points))
     unit = lambda x: x / np.linalg.norm(x)
+    M = Omega if midpoints == "sphere" else np.array(flat)     # the points midpoints are taken from
     for t in triangles:
-        P = [Omega[v] for v in t]
+        P = [M[v] for v in t]
         centre = unit(P[0] + P[1] + P[2])
         for k in range(3):
             a, b, c = P[k], P[(k + 1) % 3], P[(k + 2) % 3]
-            w[t[k]] += (_sphere_triangle_area(a, unit(a + b), centre)
-                        + _sphere_triangle_area(a, centre, unit(a + c)))
+            node_k = Omega[t[k]]
+            w[t[k]] += (_sphere_triangle_area(node_k, unit(a + b), centre)
+                        + _sphere_triangle_area(node_k, centre, unit(a + c)))
     return Omega, w
 
 # --------------------------------------------------------------------------- S1

@@ -199,11 +199,13 @@ def _match(A, B, tol):
     return m
 
 
-def test_icosahedron_generator_reproduces_printed_table():
+@pytest.mark.parametrize("midpoints", ["sphere", "flat"])
+def test_icosahedron_generator_reproduces_printed_table(midpoints):
     """The construction of Sec. 3.3 on the printed base reproduces the printed order-2 points and
-    weights of Appendix A (a dropped edge-midpoint part of the dual cell moves weights by 0.04)."""
+    weights of Appendix A, under both midpoint readings (a dropped edge-midpoint part of the dual cell
+    moves weights by 0.04)."""
     tab = _printed_table()
-    Om, w = O.icosahedron_quadrature(2, "printed")
+    Om, w = O.icosahedron_quadrature(2, "printed", midpoints)
     m = _match(tab[:, :3], Om, 1e-15)
     assert np.abs(w[m] - tab[:, 3]).max() <= 1e-14
 
@@ -218,13 +220,14 @@ def test_icosahedron_regular_order2_is_the_regular_solid():
     assert np.allclose(w, FOUR_PI / 12, rtol=1e-14)
 
 
+@pytest.mark.parametrize("midpoints", ["sphere", "flat"])
 @pytest.mark.parametrize("base", ["printed", "regular"])
 @pytest.mark.parametrize("order", [2, 3, 4, 5, 7])
-def test_icosahedron_counts_and_symmetries(base, order):
+def test_icosahedron_counts_and_symmetries(base, order, midpoints):
     """N_q = 10 (k-1)^2 + 2 unit points with positive weights summing to 4 pi (the dual cells tile
     the sphere), a point at (0, 0, 1), the set closed under Omega -> -Omega with equal weights;
     the printed base is also closed under x -> -x (as its table is)."""
-    Om, w = O.icosahedron_quadrature(order, base)
+    Om, w = O.icosahedron_quadrature(order, base, midpoints)
     assert len(w) == 10 * (order - 1) ** 2 + 2
     assert np.all(w > 0) and abs(w.sum() - FOUR_PI) < 1e-13
     assert np.allclose(np.linalg.norm(Om, axis=1), 1.0, atol=1e-15)
@@ -236,12 +239,13 @@ def test_icosahedron_counts_and_symmetries(base, order):
         assert np.allclose(w[m], w, rtol=1e-12)
 
 
+@pytest.mark.parametrize("midpoints", ["sphere", "flat"])
 @pytest.mark.parametrize("order", [2, 3, 4, 6])
-def test_icosahedron_regular_integrates_degree_5_exactly(order):
+def test_icosahedron_regular_integrates_degree_5_exactly(order, midpoints):
     """A rule invariant under the icosahedral group integrates every spherical harmonic of degree
     1..5 to zero (the first invariant harmonic has degree 6), so with sum w = 4 pi all polynomial
     moments up to degree 5 are exact: int mu^2 = 4 pi/3, mu^4 = 4 pi/5, x^2 y^2 = 4 pi/15, odd = 0."""
-    Om, w = O.icosahedron_quadrature(order, "regular")
+    Om, w = O.icosahedron_quadrature(order, "regular", midpoints)
     x, y, z = Om.T
     assert abs(w @ z ** 2 - FOUR_PI / 3) < 1e-13
     assert abs(w @ x ** 2 - FOUR_PI / 3) < 1e-13
@@ -251,6 +255,18 @@ def test_icosahedron_regular_integrates_degree_5_exactly(order):
         assert abs(w @ f) < 1e-13
     if order == 2:
         assert abs(w @ z ** 6 - FOUR_PI / 7) > 1e-3    # degree 6 is not exact: the check can fail
+
+
+def test_icosahedron_midpoint_readings_agree_only_at_order_2():
+    """The two readings of the dual cell (midpoints of the mapped points or of the flat lattice) share
+    the points and agree at order 2, where the flat and mapped points coincide; from order 3 on the
+    weights differ by more than 5 % of the largest."""
+    for order in (2, 3, 4):
+        Oa, wa = O.icosahedron_quadrature(order, "printed", "sphere")
+        Ob, wb = O.icosahedron_quadrature(order, "printed", "flat")
+        assert np.array_equal(Oa, Ob)
+        d = np.abs(wa - wb).max() / wa.max()
+        assert (d < 1e-14) if order == 2 else (d > 0.05)
 
 
 def test_icosahedron_printed_converges_with_order():
