@@ -147,7 +147,7 @@ def make_problem(A, wl, precision, stream):
     """The workload's problem: its quadrature, cross sections, kernel width and normalisation, scheme."""
     p = A.Problem(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1, precision, stream=stream)
     if wl.quadrature == "icosahedron":
-        p.set_icosahedron_quadrature(wl.ico_order, wl.ico_base)
+        p.set_icosahedron_quadrature(wl.ico_order, wl.ico_base, wl.ico_midpoints)
     else:
         p.set_product_quadrature(wl.n_polar, wl.n_azim)
     sa, ss, q = wl.materials()
@@ -166,7 +166,7 @@ def oracle_parts(wl):
     import oracle as O
 
     if wl.quadrature == "icosahedron":
-        Om, w = O.icosahedron_quadrature(wl.ico_order, wl.ico_base)
+        Om, w = O.icosahedron_quadrature(wl.ico_order, wl.ico_base, wl.ico_midpoints)
     else:
         Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
     return Om, w, O.kernel_matrix(Om, w, wl.eps, normalisation=wl.normalisation)

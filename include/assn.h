@@ -139,10 +139,14 @@ int assn_set_product_quadrature(assn_problem* p, int n_polar, int n_azim);
  * ASSN_ICO_REGULAR: the regular icosahedron, vertices (0, +-1, +-g), (+-1, +-g, 0), (+-g, 0, +-1),
  * g the golden ratio.  ASSN_ICO_PRINTED: the base solid that reproduces the printed order-2
  * points and weights: each (+-g, 0, +-1) replaced by the (+-1, 0, +-g) with the same signs, the
- * faces kept.  Both turned about x so that (0, 1, g) maps to (0, 0, 1). */
+ * faces kept.  Both turned about x so that (0, 1, g) maps to (0, 0, 1).  The dual cell's centres and
+ * midpoints are those of the mapped points; with the ASSN_ICO_FLAT_MIDPOINTS flag those of the flat
+ * lattice, mapped (the cell drawn on the flat face).  The two agree at order 2 (the printed rule) and
+ * differ from order 3 on. */
 typedef enum {
     ASSN_ICO_PRINTED = 0,
-    ASSN_ICO_REGULAR = 1
+    ASSN_ICO_REGULAR = 1,
+    ASSN_ICO_FLAT_MIDPOINTS = 2   /* flag, OR with a base: the dual cell's midpoints from the flat lattice */
 } assn_ico_base;
 
 #define ASSN_ICO_MAX_ORDER 64

@@ -16,10 +16,11 @@ __all__ = ["Problem", "Batch", "Server", "AssnError", "PRECISIONS", "ASSN_FP64",
            "ASSN_KERNEL_GAUSS", "ASSN_KERNEL_EXP", "ASSN_NORM_COLUMN", "ASSN_NORM_ROW", "icosahedron_quadrature"]
 
 
-def icosahedron_quadrature(order: int, base: str = "printed"):
+def icosahedron_quadrature(order: int, base: str = "printed", midpoints: str = "sphere"):
     """(Omega [N_q, 3], w [N_q]) of the icosahedron quadrature of Sec. 3.3, N_q = 10 (order-1)^2 + 2,
-    computed by the library (host code, no device needed)."""
-    return _lib.assn_icosahedron_quadrature(order, _lib.ICO_BASES[base])
+    computed by the library (host code, no device needed); midpoints "sphere" or "flat" selects the
+    reading of the dual cell."""
+    return _lib.assn_icosahedron_quadrature(order, _lib.ICO_BASES[base] | _lib.ICO_MIDPOINTS[midpoints])
 
 
 class Problem:
@@ -53,10 +54,12 @@ class Problem:
         """Exactly `iterations` source iterations for (L - dt sigma_as K) psi = dt R from psi0."""
         return _lib.assn_implicit_source_iteration(self.handle, dt, R, psi0, iterations)
 
-    def set_icosahedron_quadrature(self, order: int, base: str = "printed"):
+    def set_icosahedron_quadrature(self, order: int, base: str = "printed", midpoints: str = "sphere"):
         """The icosahedron quadrature of Sec. 3.3 (N_q = 10 (order-1)^2 + 2); base "printed" reproduces
-        the paper's printed order-2 rule, "regular" builds on the regular icosahedron."""
-        _lib.assn_set_icosahedron_quadrature(self.handle, order, _lib.ICO_BASES[base])
+        the paper's printed order-2 rule, "regular" builds on the regular icosahedron; midpoints
+        "sphere" or "flat" selects the reading of the dual cell (they agree at order 2)."""
+        _lib.assn_set_icosahedron_quadrature(self.handle, order,
+                                             _lib.ICO_BASES[base] | _lib.ICO_MIDPOINTS[midpoints])
         self.Q = 10 * (order - 1) ** 2 + 2
         return self
 

@@ -4,7 +4,8 @@
 // edge; the lattice points are mapped to the sphere by central projection, and each point is
 // weighted by the area of its spherical barycentric dual cell -- the region bounded by great-circle
 // arcs through the centres of its neighbouring triangles and the midpoints of the edges between
-// them, both taken from the mapped points.  N_q = 10 (k-1)^2 + 2.
+// them, taken from the mapped points (or, with ASSN_ICO_FLAT_MIDPOINTS, from the flat lattice: the cell
+// drawn on the flat face and mapped; the two agree at order 2).  N_q = 10 (k-1)^2 + 2.
 //
 // Base solid: twelve vertices joined as the 20 faces of the regular icosahedron.
 // ASSN_ICO_REGULAR is the regular icosahedron (0, +-1, +-g), (+-1, +-g, 0), (+-g, 0, +-1) with
@@ -68,7 +69,8 @@ struct Lattice {
 
 extern "C" int assn_icosahedron_quadrature(int order, int base, double* omega, double* w, int capacity) {
     if (order < 2 || order > ASSN_ICO_MAX_ORDER) return ASSN_ERR_ARG;
-    if (base != ASSN_ICO_PRINTED && base != ASSN_ICO_REGULAR) return ASSN_ERR_ARG;
+    if ((base & ~(ASSN_ICO_REGULAR | ASSN_ICO_FLAT_MIDPOINTS)) != 0) return ASSN_ERR_ARG;
+    const bool regular = (base & ASSN_ICO_REGULAR) != 0, flat_mid = (base & ASSN_ICO_FLAT_MIDPOINTS) != 0;
     Lattice L;
     L.n = order - 1;
     const int N = L.count();
@@ -85,7 +87,7 @@ extern "C" int assn_icosahedron_quadrature(int order, int base, double* omega, d
             if (group == 1) reg[m] = vert[m] = {a, b, 0.0};
             if (group == 2) {
                 reg[m] = {b, 0.0, a};   // (+-g, 0, +-1); the printed base puts (+-1, 0, +-g), same signs, here
-                vert[m] = base == ASSN_ICO_REGULAR ? reg[m] : V3{b / g, 0.0, a * g};
+                vert[m] = regular ? reg[m] : V3{b / g, 0.0, a * g};
             }
         }
     // joins of the regular icosahedron: vertex pairs at distance 2
@@ -116,27 +118,30 @@ extern "C" int assn_icosahedron_quadrature(int order, int base, double* omega, d
     for (auto& v : vert) v = {v.x, ca * v.y - sa * v.z, sa * v.y + ca * v.z};
 
     const int n = L.n;
-    std::vector<V3> P(N);
-    for (int i = 0; i < 12; ++i) P[i] = unit(vert[i]);
+    std::vector<V3> F(N);                               // the flat lattice points
+    for (int i = 0; i < 12; ++i) F[i] = vert[i];
     for (int e = 0; e < 30; ++e)
         for (int t = 1; t < n; ++t) {
             const V3 a = vert[L.edge_end[e][0]], b = vert[L.edge_end[e][1]];
-            P[12 + e * (n - 1) + t - 1] = unit(a + ((double)t / n) * (b - a));
+            F[12 + e * (n - 1) + t - 1] = a + ((double)t / n) * (b - a);
         }
     for (int f = 0; f < 20; ++f)
         for (int cb = 1; cb < n; ++cb)
             for (int cc = 1; cb + cc < n; ++cc) {
                 const V3 a = vert[L.face[f][0]], b = vert[L.face[f][1]], c = vert[L.face[f][2]];
-                P[L.node(f, n - cb - cc, cb, cc)] = unit(a + ((double)cb / n) * (b - a) + ((double)cc / n) * (c - a));
+                F[L.node(f, n - cb - cc, cb, cc)] = a + ((double)cb / n) * (b - a) + ((double)cc / n) * (c - a);
             }
+    std::vector<V3> P(N);                               // mapped to the sphere
+    for (int i = 0; i < N; ++i) P[i] = unit(F[i]);
+    const std::vector<V3>& M = flat_mid ? F : P;        // the points the cells' midpoints come from
 
     std::vector<double> W(N, 0.0);
     auto add_triangle = [&](int i0, int i1, int i2) {
         const int id[3] = {i0, i1, i2};
-        const V3 c = unit(P[i0] + P[i1] + P[i2]);
+        const V3 c = unit(M[i0] + M[i1] + M[i2]);
         for (int k = 0; k < 3; ++k) {
-            const V3 a = P[id[k]], b = P[id[(k + 1) % 3]], d = P[id[(k + 2) % 3]];
-            W[id[k]] += sphere_area(a, unit(a + b), c) + sphere_area(a, c, unit(a + d));
+            const V3 a = M[id[k]], b = M[id[(k + 1) % 3]], d = M[id[(k + 2) % 3]];
+            W[id[k]] += sphere_area(P[id[k]], unit(a + b), c) + sphere_area(P[id[k]], c, unit(a + d));
         }
     };
     for (int f = 0; f < 20; ++f)
@@ -161,7 +166,7 @@ extern "C" int assn_set_icosahedron_quadrature(assn_problem* p, int order, int b
     if (!p) return ASSN_ERR_ARG;
     if (order < 2 || 10 * (order - 1) * (order - 1) + 2 > ASSN_MAX_Q)
         return assn::problem_fail(p, ASSN_ERR_ARG, "icosahedron order out of range (2 .. 11 for Q <= 1024)");
-    if (base != ASSN_ICO_PRINTED && base != ASSN_ICO_REGULAR)
+    if ((base & ~(ASSN_ICO_REGULAR | ASSN_ICO_FLAT_MIDPOINTS)) != 0)
         return assn::problem_fail(p, ASSN_ERR_ARG, "unknown icosahedron base");
     const int N = 10 * (order - 1) * (order - 1) + 2;
     std::vector<double> om(3 * (size_t)N), w(N);

@@ -161,6 +161,7 @@ class Workload:
     quadrature: str = "product"     # "product": n_polar x n_azim; "icosahedron": order ico_order
     ico_order: int = 0              # N_q = 10 (ico_order - 1)^2 + 2
     ico_base: str = "printed"       # "printed" (the paper's Appendix A rule) or "regular"
+    ico_midpoints: str = "sphere"   # dual-cell midpoints of the mapped ("sphere") or flat ("flat") points
     eps_rule: str = "spacing"       # "spacing": beta sqrt(4 pi / Q); "paper": beta / N_q (Sec. 4.1)
     normalisation: str = "column"   # kernel matrix: "column" or the paper's "row" (Sec. 3.2)
     scheme: str = "euler"           # "euler" (first-order upwind) or "heun" (Heun + minmod)

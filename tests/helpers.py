@@ -31,7 +31,7 @@ def gpu_problem(A, wl: synth.Workload, precision: str, psi0=None, sigma_as=None,
     from the workload unless given: 0 column, 1 row), scheme and initial state."""
     p = A.Problem(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1, precision)
     if wl.quadrature == "icosahedron":
-        p.set_icosahedron_quadrature(wl.ico_order, wl.ico_base)
+        p.set_icosahedron_quadrature(wl.ico_order, wl.ico_base, wl.ico_midpoints)
     else:
         p.set_product_quadrature(wl.n_polar, wl.n_azim)
     sa, ss, q = wl.materials()
@@ -49,7 +49,7 @@ def gpu_problem(A, wl: synth.Workload, precision: str, psi0=None, sigma_as=None,
 
 def oracle_setup(wl: synth.Workload, normalisation=None, kind="gauss"):
     if wl.quadrature == "icosahedron":
-        Om, w = O.icosahedron_quadrature(wl.ico_order, wl.ico_base)
+        Om, w = O.icosahedron_quadrature(wl.ico_order, wl.ico_base, wl.ico_midpoints)
     else:
         Om, w = O.product_quadrature(wl.n_polar, wl.n_azim)
     K = O.kernel_matrix(Om, w, wl.eps, kind=kind, normalisation=normalisation or wl.normalisation)

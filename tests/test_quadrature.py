@@ -26,11 +26,12 @@ def match(A_pts, B_pts, tol):
     return m
 
 
+@pytest.mark.parametrize("midpoints", ["sphere", "flat"])
 @pytest.mark.parametrize("base", ["printed", "regular"])
 @pytest.mark.parametrize("order", list(range(2, 12)))
-def test_library_matches_oracle(A, base, order):
-    om, w = A.icosahedron_quadrature(order, base)
-    ref_om, ref_w = O.icosahedron_quadrature(order, base)
+def test_library_matches_oracle(A, base, order, midpoints):
+    om, w = A.icosahedron_quadrature(order, base, midpoints)
+    ref_om, ref_w = O.icosahedron_quadrature(order, base, midpoints)
     assert om.shape == ref_om.shape == (10 * (order - 1) ** 2 + 2, 3)
     m = match(om, ref_om, 1e-14)
     assert np.abs(w - ref_w[m]).max() <= 1e-14 * max(1.0, ref_w.max())
@@ -56,7 +57,7 @@ def test_high_order_counts(A):
 
 def test_rejects_out_of_range(A):
     from paper_1911_08801_gb300 import _lib
-    for order, base in ((1, 0), (0, 0), (65, 0), (2, 2), (2, -1)):
+    for order, base in ((1, 0), (0, 0), (65, 0), (2, 4), (2, -1), (3, 7)):
         assert _lib.lib.assn_icosahedron_quadrature(order, base, None, None, 0) == _lib.ASSN_ERR_ARG
     om = np.empty((12, 3))
     w = np.empty(12)
