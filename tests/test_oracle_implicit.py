@@ -136,3 +136,23 @@ def test_source_iteration_stopping_rule_bounds_the_error(dt, norm):
         psi, it = O.source_iteration(np.zeros_like(R), R, K, Om, sig, sig_as, h, dt, eps, T)
         assert it > 1
         assert np.linalg.norm(psi - ref) <= eps
+
+
+def test_steady_state_is_second_order_in_the_interior():
+    """One implicit step with dt -> infinity gives the discrete steady state of Omega d psi/dx + psi = 1 on
+    [0, 1] with vacuum inflow (one ordinate along x, sigma_a = q = 1); the exact cell averages are
+    1 - (e^{-x_l} - e^{-x_r}) / h.  Away from the inflow the error falls 4x per halving of h (second
+    order; the zero inflow ghosts leave a first-order error in the first cell only)."""
+    def interior_error(n):
+        h = 1.0 / n
+        Om = np.array([[1.0, 0.0, 0.0]])
+        w = np.array([FOUR_PI])
+        K = np.eye(1)
+        sa, ss, q = np.ones((1, n)), np.zeros((1, n)), np.ones((1, n))
+        psi, _, _, _ = O.implicit_step(np.zeros((1, n, 1)), np.zeros((1, n)), K, Om, w, sa, ss, q, 0.0, h, 1e9,
+                                       1e-14, 1e-14)
+        xl = np.arange(n) * h
+        exact = 1.0 - (np.exp(-xl) - np.exp(-(xl + h))) / h
+        return np.abs(psi[0, :, 0] - exact)[n // 2:].max()
+    e64, e128 = interior_error(64), interior_error(128)
+    assert 3.8 < e64 / e128 < 4.2
