@@ -49,19 +49,23 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile", type=int, default=0, help="tensor-core tile cells (0 = automatic)")
     ap.add_argument("--stages", type=int, default=0, help="tensor-core kernel-matrix ring depth (0 = automatic)")
-    ap.add_argument("--variant", type=int, default=0, help="tensor-core kernel: 0 persistent, 1 one tile per CTA")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="tensor-core kernel: 0 persistent, 1 one tile per CTA, 2 paired-SM (cta_group::2)")
     ap.add_argument("--ref-dir", default="", help="accuracy: directory of oracle scalar fluxes <workload>.npy "
                                                   "(written by --mode oracle-phi); missing ones are computed")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "ensemble", "serving", "accuracy", "oracle-phi", "paramstudy"],
+                    choices=["step", "ensemble", "serving", "accuracy", "oracle-phi", "paramstudy", "oracle-time"],
                     help="step: one solve stepped K times; ensemble: 64 uneven solves to completion in one "
                          "batch; serving: Poisson request stream through the serving loop")
     ap.add_argument("--scheme", default=None, choices=["euler", "heun"],
                     help="step mode: forward Euler + first-order upwind, or Heun + minmod (default: the workload's)")
     ap.add_argument("--count", type=int, default=64, help="ensemble members / serving requests")
+    ap.add_argument("--one-launch", action="store_true",
+                    help="ensemble: every member in one launch per step (else one launch per ordinate class)")
     ap.add_argument("--only", default="", help="accuracy: run only the case of this workload name")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate, requests/s (0 = about 70%% load)")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--dt", type=float, default=0.0, help="oracle-time: the step size to time the oracle at")
     return ap.parse_args()
 
 
@@ -357,8 +361,8 @@ def run_ours(args, rank, world, dist):
                      "frac": achieved / hbm,
                      "traffic": kernel_traffic(args.precision) if args.variant == 0 and args.workload == synth.LATTICE_448.name else None,
                      "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
-                     "kernel": ("step_tc2_kernel" if args.variant == 0 else "step_tc_kernel") if args.precision.startswith("bf16")
-                     else "step_simt_kernel"} if args.scheme == "euler" else
+                     "kernel": {0: "step_tc2_kernel", 1: "step_tc_kernel", 2: "step_tc3_kernel"}[args.variant]
+                     if args.precision.startswith("bf16") else "step_simt_kernel"} if args.scheme == "euler" else
                      implicit_roofline(args, wl, ms_per_step, stats_timed, args.steps)
                      if args.scheme == "implicit" else
                      (heun_tc_roofline(wl, ms_per_step) if args.precision.startswith("bf16")
@@ -414,26 +418,55 @@ def extras_legs(A, L, torch, wl, args, prob, psi0, stream, dt):
     return out
 
 
-def cpu_baseline(wl, seconds: float, scheme: str, dt: float):
-    """The FP64 oracle as it stands, timed on the host cores on a bounded strip of the workload, with
-    the same scheme as the GPU line."""
+def time_oracle(wl, seconds: float, scheme: str, dt: float, rows: int = 8):
+    """Steps of the FP64 oracle on a bounded strip of the workload for about `seconds`: (updates/s,
+    steps, rows, cores used).  Cores used = the process's CPU seconds over the wall seconds of the
+    timed loop (numpy runs element-wise work on one thread; only the BLAS product may use more)."""
     Om, w, K = oracle_parts(wl)
     step = oracle_step(scheme, wl)
     sa, ss, q = wl.materials()
-    rows = max(1, min(wl.ny, 8))
+    rows = max(1, min(wl.ny, rows))
     rng = np.random.default_rng(0)
     psi = rng.random((rows, wl.nx, wl.Q))
     step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
     n = 0
+    c0 = time.process_time()
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds or n == 0:
         psi = step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
         n += 1
     el = time.perf_counter() - t0
-    units = rows * wl.nx * wl.Q * n
-    return {"value": units / el, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} {scheme} steps of a {rows}-row strip ({rows}x{wl.nx} cells, Q={wl.Q}) of {wl.name}, "
-                      "numpy FP64"}
+    cpu = time.process_time() - c0
+    return rows * wl.nx * wl.Q * n / el, n, rows, cpu / el
+
+
+def cpu_baseline(wl, seconds: float, scheme: str, dt: float):
+    """The FP64 oracle as it stands, timed on the host cores on a bounded strip of the workload, with
+    the same scheme as the GPU line; then once more in a child process with every BLAS / OpenMP pool
+    held to one thread (the one-core figure)."""
+    value, n, rows, cores = time_oracle(wl, seconds, scheme, dt)
+    out = {"value": value, "unit": "updates/s", "cores": round(cores, 2), "cores_available": os.cpu_count(),
+           "kind": "oracle",
+           "sample": f"{n} {scheme} steps of a {rows}-row strip ({rows}x{wl.nx} cells, Q={wl.Q}) of {wl.name}, "
+                     "numpy FP64; cores = CPU seconds per wall second of the timed loop"}
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--mode", "oracle-time", "--workload", wl.name,
+                            "--scheme", scheme, "--dt", repr(dt), "--cpu-seconds", repr(seconds)],
+                           env=env, capture_output=True, text=True, timeout=10 * seconds + 120)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        out["one_core"] = {"value": one["value"], "unit": "updates/s", "cores": round(one["cores"], 2),
+                           "sample": f"{one['steps']} steps of the same strip, BLAS and OpenMP pools at one thread"}
+    except Exception as e:  # pragma: no cover - report, do not hide
+        out["one_core"] = {"error": str(e)[-300:]}
+    return out
+
+
+def run_oracle_time(args):
+    wl = synth.WORKLOADS[args.workload]
+    value, n, rows, cores = time_oracle(wl, args.cpu_seconds, args.scheme or wl.scheme, args.dt)
+    return {"mode": "oracle-time", "value": value, "steps": n, "rows": rows, "cores": cores}
 
 
 def run_reference(args):
@@ -449,10 +482,12 @@ def run_reference(args):
     psi = rng.random((rows, wl.nx, wl.Q))
     for _ in range(args.warmup):
         psi = step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
+    c0 = time.process_time()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         psi = step(psi, K, Om, w, sa[:rows], ss[:rows], q[:rows], wl.sigma_as, wl.h, dt)
     el = time.perf_counter() - t0
+    cores = (time.process_time() - c0) / el
     units = rows * wl.nx * wl.Q * args.steps
     value = units / el
     sample = f"each {scheme} step: a {rows}-row strip ({rows}x{wl.nx} cells, Q={wl.Q}) of {wl.name}, numpy FP64"
@@ -461,8 +496,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded uniform state, analytic %s materials)" % wl.kind.replace("_", "-"),
             "config": {"workload": wl.name, "cells": f"{wl.nx}x{wl.ny}", "Q": wl.Q, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": round(cores, 2),
+                             "cores_available": os.cpu_count(), "kind": "oracle",
+                             "sample": sample + "; cores = CPU seconds per wall second of the timed loop"},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -501,6 +537,7 @@ def run_ensemble(args):
     nmax = max(n for n, _ in plan)
     bs = torch.cuda.Stream()
     b = A.Batch(stream=bs)
+    b.set_grouping(args.one_launch)
     for p, (n, dt) in zip(probs, plan):
         b.add(p, min(n, args.warmup), dt)
     tune = b.autotune(use_cache=False)
@@ -508,6 +545,7 @@ def run_ensemble(args):
     for p, (n, dt) in zip(probs, plan):
         b.set_steps(p, n, dt)
     b.run().sync()                       # capture + warm the full-length graph
+    launches0 = b.info()["launches"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
@@ -518,6 +556,8 @@ def run_ensemble(args):
         b.sync()
         wall = time.perf_counter() - t0
     ms_graph = e0.elapsed_time(e1)
+    launches = b.info()["launches"] - launches0
+    nclass = len(b.classes())
     e0.record(bs)
     b.run(use_graph=False)
     e1.record(bs)
@@ -543,7 +583,8 @@ def run_ensemble(args):
         "dtype": f"{prec} contraction, fp32 state",
         "data": "synthetic (seeded ensemble: line source / lattice, uneven sides, Q and beta)",
         "config": {"workload": f"ensemble_{args.count}_seed{args.seed}", "members": args.count,
-                   "updates_total": updates, "launches": nmax,
+                   "updates_total": updates, "launches": launches, "classes": nclass,
+                   "grouping": "one launch per step" if args.one_launch else "one launch per ordinate class and step",
                    "state_bytes_per_buffer": sum(wl.nx * wl.ny * ((wl.Q + 63) // 64 * 64) * 4 for wl in wls),
                    "tiling": {"tile_cells": info["tile_cells"], "stages": info["stages"],
                               "total_tiles": info["total_tiles"], "autotune_ms_per_launch": tune["ms_per_launch"]},
@@ -552,7 +593,7 @@ def run_ensemble(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_update": 8,
                      "kernel": "step_tc2_kernel (batched)"},
-        "gpu_launches": nmax,
+        "gpu_launches": launches,
         "clocks": clk.summary(),
         "batched_no_graph": {"value": updates / (ms_nograph / 1e3), "ms": ms_nograph},
         "sequential_alone": {"value": updates / (ms_seq / 1e3), "ms": ms_seq,
@@ -662,11 +703,12 @@ def run_oracle_phi(args):
 
 def run_paramstudy(args):
     """The paper's coarse parameter study (Sec. 4.1) as one batch: 306 (sigma_as, beta) line-source
-    solves with the printed 12-point icosahedron quadrature (Appendix A), eps = beta / 12, on 50 x 50
-    cells to t = 1, forward Euler at dt = min(0.5 h, 0.95 x positivity bound).  The error of each is
-    the L2 error of Phi against a reference -- the semi-analytic solution the paper uses is not
-    available, so a Q = 512 (16 x 32) plain S_N solve on the same grid stands in -- divided by the
-    error without artificial scattering, as in the paper's heatmap."""
+    solves with the printed 12-point icosahedron quadrature (Appendix A), eps = beta / 12 and the row
+    normalisation of Sec. 3.2, on 50 x 50 cells to t = 1, in the paper's explicit scheme (Sec. 3.1,
+    Heun + minmod) at 0.95 of its admissible dt.  The error of each is the L2 error of Phi against a
+    reference -- the semi-analytic solution the paper uses is not available, so a Q = 512 (16 x 32)
+    plain S_N solve of the same scheme on the same grid stands in -- divided by the error without
+    artificial scattering, as in the paper's heatmap."""
     import torch
 
     import paper_1911_08801_gb300 as A
@@ -674,13 +716,12 @@ def run_paramstudy(args):
     torch.cuda.set_device(0)
     n_side, t_final = 50, 1.0
     x0, x1 = -1.5, 1.5
-    h = (x1 - x0) / n_side
     sa, ss, q = synth.line_source_materials(n_side, n_side)
     Om, w = synth.icosahedron_order2()
     prec = args.precision if args.precision.startswith("bf16") else "bf16"
 
     def schedule_dt(p):
-        dt0 = min(0.5 * h, 0.95 * p.max_stable_dt())
+        dt0 = 0.95 * p.max_stable_dt()
         n = max(1, int(math.ceil(t_final / dt0 - 1e-12)))
         return n, t_final / n
 
@@ -691,7 +732,8 @@ def run_paramstudy(args):
         else:
             p.set_product_quadrature(*quad)
         p.set_cross_sections(sa, ss, q)
-        p.set_artificial_scattering(sigma_as, eps)
+        p.set_artificial_scattering(sigma_as, eps, 0, 1)
+        p.set_scheme("heun")
         p.init_line_source()
         return p
 
@@ -743,8 +785,9 @@ def run_paramstudy(args):
     return {"mode": "paramstudy", "metric": METRIC, "value": updates / (ms / 1e3), "unit": "updates/s",
             "dtype": f"{prec} contraction, fp32 state", "data": "synthetic line source (Sec. 4.1)",
             "config": {"workload": "parameter_study_306_line_source_50x50_Nq12", "members": len(grid),
+                       "scheme": "Heun + minmod at 0.95 of the admissible dt", "normalisation": "row",
                        "updates_total": updates, "launches": int(info["launches"]), "ms_batched": ms,
-                       "reference": "Q = 512 (16 x 32) plain S_N, BF16X3, same grid and time span"},
+                       "reference": "Q = 512 (16 x 32) plain S_N, Heun + minmod, BF16X3, same grid and time span"},
             "sequential_alone": {"value": updates / (ms_seq / 1e3), "ms": ms_seq},
             "best": {"sigma_as": grid[k][0], "beta": grid[k][1], "normalized_error": errs[k]},
             "at_sigma_as_5_beta_4.5": errs[at] if at is not None else None,
@@ -803,6 +846,9 @@ def main():
         return
     if args.mode == "oracle-phi":
         print(json.dumps(run_oracle_phi(args)), flush=True)
+        return
+    if args.mode == "oracle-time":
+        print(json.dumps(run_oracle_time(args)), flush=True)
         return
     if args.mode != "step":
         if rank == 0:

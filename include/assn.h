@@ -254,17 +254,20 @@ int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt,
 
 /* Tensor-core kernel and tiling (BF16 / BF16X3 problems).  variant 0 (default): persistent
  * warp-specialised kernel, one CTA per SM, TMA-fed rings and two TMEM accumulator buffers;
- * variant 1: one tile per CTA (simpler, slower).  tile_cells: cells per tile (32, 64, 128 or 256;
+ * variant 1: one tile per CTA (simpler, slower); variant 2: paired-SM kernel, a cluster of two
+ * CTAs sharing each M = 256 contraction (cta_group::2) over 2D tiles of 16 x 8 (512 ordinates) or
+ * 16 x 16 cells (256), forward Euler in BF16 with 193..256 or 449..512 ordinates (else
+ * ASSN_ERR_UNSUPPORTED at the next step; tile_cells is fixed by the ordinate count).  tile_cells: cells per tile (32, 64, 128 or 256;
  * 0 = automatic).  stages: ring depth (2..8; 0 = automatic).  Takes effect at the next step; the
  * results do not depend on these choices.  ASSN_ERR_UNSUPPORTED at the next step if the
  * combination does not fit the SM. */
 int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant);
 
-/* Rings of the persistent kernel (variant 0; BF16 / BF16X3 problems): depths of the staging ring
- * (FP32 flux chunks fed by TMA), the operand ring (BF16 chunks written by the converter warps) and
- * the kernel-matrix ring (2..8 each; 0 = automatic), and the ordinate blocks of 128 that one
- * kernel-matrix request brings (1, 2, 4, 8; 0 = automatic).  Results do not depend on these
- * choices.  Selects variant 0.  get_rings reports the resolved values (any pointer may be NULL);
+/* Rings of the persistent kernels (variants 0 and 2; BF16 / BF16X3 problems): depths of the staging
+ * ring (FP32 flux chunks fed by TMA), the operand ring (BF16 chunks written by the converter warps)
+ * and the kernel-matrix ring (2..8 each; 0 = automatic), and the ordinate blocks of 128 that one
+ * kernel-matrix request brings (1, 2, 4, 8; 0 = automatic; variant 0 only).  Results do not depend
+ * on these choices.  Selects variant 0 unless variant 2 is set.  get_rings reports the resolved values (any pointer may be NULL);
  * ASSN_ERR_UNSUPPORTED at the next step / get if the rings do not fit shared memory. */
 int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix, int blocks_per_request);
 int assn_get_rings(assn_problem* p, int* staging, int* operand, int* kernel_matrix, int* blocks_per_request);
@@ -295,8 +298,10 @@ int assn_check_finite(assn_problem* p);
 /* ---- Batches: several problems stepped by one persistent launch per step.
  * The members may differ in grid size, quadrature (ordinate count), kernel width eps, cross
  * sections and dt; they share the device and one tensor-core precision (ASSN_BF16 or
- * ASSN_BF16X3).  Each launch applies the same explicit step as assn_step (Sec. 3.2, forward Euler
- * of the as-S_N equations) to every member that still has steps left; a member's step count is
+ * ASSN_BF16X3) and one explicit scheme (assn_set_scheme: forward-Euler upwind, or the paper's Heun +
+ * minmod of Sec. 3.1).  Each launch applies the same explicit step as assn_step (Sec. 3.2, forward
+ * Euler of the as-S_N equations; for Heun + minmod one of the two stages of a Heun step, so a step
+ * is two launches) to every member that still has steps left; a member's step count is
  * kept on the device, so members finish at their own counts within one run.  After
  * assn_batch_run each member is exactly as if assn_step(p, nsteps, dt) had been called on it
  * (bitwise, at the same tiling).  Members stay owned by the caller and must outlive their
@@ -305,8 +310,9 @@ int assn_check_finite(assn_problem* p);
  * create:     stream = a cudaStream_t or NULL (library stream).  Errors: ASSN_ERR_CUDA / OOM.
  * add:        add p, to be advanced nsteps >= 0 steps of size dt per run.  Checks p is complete
  *             and dt admissible (as assn_step).  Errors: ASSN_ERR_ARG (NULL, duplicate, other
- *             device, mixed precision, more than 1024 members), ASSN_ERR_UNSUPPORTED (not a
- *             tensor-core precision), or p's own error (ASSN_ERR_STATE, ASSN_ERR_UNSTABLE).
+ *             device, mixed precision or scheme, more than 1024 members), ASSN_ERR_UNSUPPORTED (not a
+ *             tensor-core precision, the implicit scheme), or p's own error
+ *             (ASSN_ERR_STATE, ASSN_ERR_UNSTABLE).
  * set_steps:  change a member's nsteps / dt for later runs.
  * remove:     drop a member (syncs the batch stream).
  * set_tiling: tile cells (0, 32, 64, 128, 256) and ring depth (0 or 2..8) for all members.
@@ -319,7 +325,8 @@ int assn_check_finite(assn_problem* p);
  * Members are grouped into classes by padded ordinate count (Q rounded up to a multiple of 64):
  * each class has its own persistent launch per step and its own tile width (wide tiles for few
  * ordinates), so a step of the batch is one launch per class.
- * run:        enqueue, for each class, max nsteps of its members launches on the batch stream
+ * run:        enqueue, for each class, max nsteps of its members launches (twice that for Heun +
+ *             minmod) on the batch stream
  *             (ordered after each member's stream; members' streams wait for the run).
  *             use_graph != 0 captures them once as a CUDA graph and replays it while the
  *             membership, tiling, dt and the classes' max nsteps stay the same.  Asynchronous.
@@ -336,6 +343,13 @@ int assn_batch_add(assn_batch* b, assn_problem* p, int nsteps, double dt);
 int assn_batch_set_steps(assn_batch* b, assn_problem* p, int nsteps, double dt);
 int assn_batch_remove(assn_batch* b, assn_problem* p);
 int assn_batch_set_tiling(assn_batch* b, int tile_cells, int stages);
+/* Grouping of the members into launches: one_launch = 0 (default) one class, and one persistent
+ * launch per step, for each padded ordinate count, each at the tile width that suits it;
+ * one_launch = 1 every member in a single class, so each step (Heun: stage) of the whole batch is
+ * one launch, with ordinate strides read per member and the tile width of the largest ordinate
+ * count.  Results are the same either way (bitwise, at equal tile widths).  ASSN_ERR_ARG for
+ * other values. */
+int assn_batch_set_grouping(assn_batch* b, int one_launch);
 int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stages, double* ms_per_launch);
 int assn_batch_run(assn_batch* b, int use_graph);
 int assn_batch_sync(assn_batch* b);
@@ -425,9 +439,11 @@ int assn_server_destroy(assn_server* s);
 const char* assn_server_last_error(void);
 
 /* ---- Allocation-free total mass (the paper has no counterpart; this serves library users).
- * Some callers cannot allocate device memory during a call: code between the begin and end of a
- * CUDA stream capture, real-time loops that forbid allocator calls, or hosts that run the library
- * under a foreign memory pool.  assn_mass_noalloc computes h^2 sum_cells sum_q w_q psi_q of a
+ * Some callers cannot allocate device memory during a call: real-time loops whose latency budget
+ * rules out allocator calls (cudaMalloc may block and synchronise the device), and hosts that run
+ * the library inside a memory pool they manage and account for themselves, handing it only the
+ * buffers they own.  The paper has no counterpart; this is a service of the library.
+ * assn_mass_noalloc computes h^2 sum_cells sum_q w_q psi_q of a
  * caller-owned device state without allocating anything: its partial sums go to a fixed
  * file-scope device array of ASSN_NOALLOC_MASS_MAX_BLOCKS doubles (128 KB), one per 256 cells,
  * which every device that loads the library holds until process exit.

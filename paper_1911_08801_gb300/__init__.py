@@ -190,6 +190,11 @@ class Batch:
         _lib.assn_batch_set_tiling(self.handle, tile_cells, stages)
         return self
 
+    def set_grouping(self, one_launch: bool = False):
+        """one_launch: every member in one persistent launch per step (else one per ordinate class)."""
+        _lib.assn_batch_set_grouping(self.handle, one_launch)
+        return self
+
     def autotune(self, use_cache: bool = True) -> dict:
         return _lib.assn_batch_autotune(self.handle, use_cache)
 

@@ -112,6 +112,7 @@ SIGNATURES = {
     "assn_batch_set_steps": (C.c_int, [_h, _h, C.c_int, C.c_double]),
     "assn_batch_remove": (C.c_int, [_h, _h]),
     "assn_batch_set_tiling": (C.c_int, [_h, C.c_int, C.c_int]),
+    "assn_batch_set_grouping": (C.c_int, [_h, C.c_int]),
     "assn_batch_autotune": (C.c_int, [_h, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "assn_batch_run": (C.c_int, [_h, C.c_int]),
     "assn_batch_sync": (C.c_int, [_h]),
@@ -414,6 +415,10 @@ def assn_batch_remove(b: int, p: int) -> None:
 
 def assn_batch_set_tiling(b: int, tile_cells: int = 0, stages: int = 0) -> None:
     _bcheck(lib.assn_batch_set_tiling(b, tile_cells, stages), b)
+
+
+def assn_batch_set_grouping(b: int, one_launch: bool) -> None:
+    _bcheck(lib.assn_batch_set_grouping(b, int(one_launch)), b)
 
 
 def assn_batch_autotune(b: int, use_cache: bool = True) -> dict:

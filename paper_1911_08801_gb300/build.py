@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libassn.so")
-SOURCES = ["api.cu", "batch.cu", "serve.cu", "selftest.cu", "kbuild.cu", "step_simt.cu", "step_tc.cu", "step_tc2.cu", "misc.cu", "noalloc.cu",
+SOURCES = ["api.cu", "batch.cu", "serve.cu", "selftest.cu", "kbuild.cu", "step_simt.cu", "step_tc.cu", "step_tc2.cu", "step_tc3.cu",
+           "misc.cu", "noalloc.cu",
            "quadrature.cu", "implicit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

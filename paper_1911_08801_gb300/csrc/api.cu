@@ -94,6 +94,8 @@ void free_operands(assn_problem* p) {
     p->plan = nullptr;
     if (p->plan2) tc2_plan_destroy(p->plan2);
     p->plan2 = nullptr;
+    if (p->plan3) tc3_plan_destroy(p->plan3);
+    p->plan3 = nullptr;
     p->have_K = false;
 }
 
@@ -122,7 +124,8 @@ int check_flags(assn_problem* p) {
     CK(p, cudaStreamSynchronize(p->stream));
     if (f[1]) {
         CK(p, cudaMemsetAsync(p->d_flags + 1, 0, sizeof(unsigned int), p->stream));
-        return fail(p, ASSN_ERR_TIMEOUT, "tensor-core step: a bounded device wait gave up (flag 0x%x)", f[1]);
+        return fail(p, ASSN_ERR_TIMEOUT, "tensor-core step: a bounded device wait gave up (flag 0x%x)%s", f[1],
+                    (f[1] & 0x80000000u) ? "; work in flight did not drain, treat the CUDA context as suspect" : "");
     }
     return ASSN_OK;
 }
@@ -586,7 +589,10 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
         } else {
             const bool own = in == p->d_psi[p->cur] && out == p->d_psi[p->cur ^ 1];
             cudaError_t e;
-            if (p->variant == 0 && own) {
+            if (p->variant == 2 && own) {
+                e = launch_step_tc3(p->plan3, p->cur, (const OrdF*)p->d_ord, (const CellF*)p->d_cell, p->d_w32,
+                                    (float)dt, (float)(dt * p->sigma_as), p->d_flags + 1, p->stream);
+            } else if (p->variant == 0 && own) {
                 // the persistent kernel takes its buffer parity from the device step counter
                 if ((p->counter_host & 1) != p->cur) {
                     p->counter_host = p->cur;
@@ -617,6 +623,13 @@ static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
         const Tc2Problem d = problem_tc2(p, dt, 0x7fffffff);
         e = tc2_plan_create(&p->plan2, &d, 1, p->precision == ASSN_BF16X3, p->want_nt, p->want_rings);
         if (e == cudaSuccess) p->plan2_dt = dt;
+    }
+    if (e == cudaSuccess && p->variant == 2 && !p->plan3) {
+        if (!tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision == ASSN_BF16X3))
+            return fail(p, ASSN_ERR_UNSUPPORTED,
+                        "paired-SM step (variant 2): BF16 with 193..256 or 449..512 ordinates only (Q = %d)", p->Q);
+        e = tc3_plan_create(&p->plan3, (const float*)p->d_psi[0], (const float*)p->d_psi[1], p->tc.G_hi, p->Q, p->Qp,
+                            p->tc.Mp, p->nx, p->ny, p->want_rings);
     }
     if (e == cudaErrorNotSupported)
         return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: Q = %d with tile %d / stages %d not supported", p->Q,
@@ -755,7 +768,7 @@ int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant) {
     if (tile_cells != 0 && tile_cells != 32 && tile_cells != 64 && tile_cells != 128 && tile_cells != 256)
         return fail(p, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64, 128 or 256");
     if (stages != 0 && (stages < 2 || stages > 8)) return fail(p, ASSN_ERR_ARG, "stages must be 0 or 2..8");
-    if (variant != 0 && variant != 1) return fail(p, ASSN_ERR_ARG, "variant must be 0 or 1");
+    if (variant < 0 || variant > 2) return fail(p, ASSN_ERR_ARG, "variant must be 0, 1 or 2");
     p->want_nt = tile_cells;
     p->want_stages = stages;
     p->want_rings = TcRings{stages, stages, stages, 0};
@@ -764,6 +777,8 @@ int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant) {
     p->plan = nullptr;
     if (p->plan2) tc2_plan_destroy(p->plan2);
     p->plan2 = nullptr;
+    if (p->plan3) tc3_plan_destroy(p->plan3);
+    p->plan3 = nullptr;
     return ASSN_OK;
 }
 
@@ -776,9 +791,11 @@ int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix,
         blocks_per_request != 8)
         return fail(p, ASSN_ERR_ARG, "blocks_per_request must be 0, 1, 2, 4 or 8");
     p->want_rings = TcRings{staging, operand, kernel_matrix, blocks_per_request};
-    p->variant = 0;
+    if (p->variant == 1) p->variant = 0;
     if (p->plan2) tc2_plan_destroy(p->plan2);
     p->plan2 = nullptr;
+    if (p->plan3) tc3_plan_destroy(p->plan3);
+    p->plan3 = nullptr;
     return ASSN_OK;
 }
 
@@ -812,8 +829,14 @@ int assn_get_tiling(assn_problem* p, int* tile_cells, int* stages, int* tmem_col
     r = ensure_plan(p, p->plan2_dt > 0 ? p->plan2_dt : 1.0, false);
     if (r) return r;
     size_t sm = 0;
-    if (p->variant == 1) tc_plan_describe(p->plan, tile_cells, stages, tmem_cols, &sm);
-    else tc2_plan_describe(p->plan2, tile_cells, stages, tmem_cols, &sm);
+    if (p->variant == 1) {
+        tc_plan_describe(p->plan, tile_cells, stages, tmem_cols, &sm);
+    } else if (p->variant == 2) {
+        tc3_plan_describe(p->plan3, tile_cells, stages, nullptr, &sm);
+        if (tmem_cols) *tmem_cols = 512;
+    } else {
+        tc2_plan_describe(p->plan2, tile_cells, stages, tmem_cols, &sm);
+    }
     if (smem_bytes) *smem_bytes = (int64_t)sm;
     return ASSN_OK;
 }

@@ -107,11 +107,27 @@ cudaError_t tc2_plan_set_targets(Tc2Plan* plan, const int* targets, cudaStream_t
 // at launch, so the flux is read from buffer parity0 and written to parity0 ^ 1; parity0 < 0:
 // every parity comes from the device counters (batches, CUDA graphs).
 cudaError_t launch_step_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, cudaStream_t s);
-// One Heun stage with minmod-limited second-order transport on a one-problem plan: reads buffer
-// parity0, writes alpha keep + beta (psi + dt L(psi)) to buffer parity0 ^ 1 (keep may be that
-// buffer; not read when alpha == 0).
+// One Heun stage with minmod-limited second-order transport.  parity0 >= 0 (one-problem plan): reads
+// buffer parity0, writes alpha keep + beta (psi + dt L(psi)) to buffer parity0 ^ 1 (keep may be that
+// buffer; not read when alpha == 0).  parity0 < 0 (any plan): every problem's buffers and stage come
+// from its device counter (stage 2 when the counter's parity differs from its target's, keeping psi^n
+// from the buffer it writes); keep, alpha and beta are ignored.
 cudaError_t launch_heun_stage_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, const float* keep, float alpha,
                                   float beta, cudaStream_t s);
+
+// Paired-SM tensor-core step (variant 2): one problem, forward Euler, BF16, padded ordinate count
+// 256 or 512 (equal to the kernel-matrix rows).  A cluster of two CTAs shares each M = 256 MMA;
+// the flux buffers and G are bound at plan creation, dt at launch.
+struct Tc3Plan;
+bool tc3_supported(int Q, int Qp, int Mp, bool split);
+cudaError_t tc3_plan_create(Tc3Plan** plan, const float* buf0, const float* buf1, const __nv_bfloat16* G, int Q,
+                            int Qp, int Mp, int nx, int ny, TcRings want);
+void tc3_plan_destroy(Tc3Plan* plan);
+// tile cells, kernel-matrix ring depth, CTA pairs launched, dynamic shared memory per CTA
+void tc3_plan_describe(const Tc3Plan* plan, int* tile_cells, int* stages, int* pairs, size_t* smem);
+// Reads buffer `parity`, writes buffer parity ^ 1.
+cudaError_t launch_step_tc3(const Tc3Plan* plan, int parity, const OrdF* ord, const CellF* cell, const float* w,
+                            float dt, float dt_sigma_as, unsigned int* err_flag, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_scalar_flux(const T* psi, const T* w, int ncell, int Qp, float* out_f,

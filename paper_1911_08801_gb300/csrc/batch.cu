@@ -3,9 +3,11 @@
 //
 // Every launch advances each member whose device step counter is below its target by one
 // explicit step (Sec. 3: upwind transport, collision and isotropic scattering, and the
-// artificial-scattering contraction of Sec. 3.2 in one pass); members that reached their
-// target are skipped on the device, so a run of max(nsteps) launches, captured once as a
-// graph, completes every member at its own step count with no host round trip in between.
+// artificial-scattering contraction of Sec. 3.2 in one pass) or, for a batch of the paper's
+// explicit scheme (Sec. 3.1, Heun + minmod), by one of the two stages of a Heun step; members that
+// reached their target are skipped on the device, so a run of max(launches per member) launches,
+// captured once as a graph, completes every member at its own step count with no host round trip
+// in between.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -23,6 +25,7 @@ using namespace assn;
 struct assn_batch {
     int dev = 0;
     int precision = -1;                 // of the members (BF16 or BF16X3)
+    int scheme = -1;                    // of the members (forward-Euler upwind or Heun + minmod)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     struct Member {
@@ -50,6 +53,7 @@ struct assn_batch {
     unsigned int* d_err = nullptr;
     cudaEvent_t done = nullptr;
     int want_nt = 0;                    // 0 = automatic (per class)
+    int grouping = 0;                   // 0: one class per padded ordinate count; 1: one class
     TcRings want_rings;                 // zero fields automatic (per class)
     bool tuned = false;                 // classes carry autotuned tilings
     std::string err;
@@ -79,6 +83,9 @@ int bfail(assn_batch* b, int status, const char* fmt, ...) {
                          #call, cudaGetErrorString(_e));                                               \
     } while (0)
 
+// Launches per time step of the batch's scheme (a Heun step is two stage launches).
+int launches_per_step(const assn_batch* b) { return b->scheme == ASSN_SCHEME_HEUN_MINMOD ? 2 : 1; }
+
 void drop_graph(assn_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -99,12 +106,15 @@ void drop_plan(assn_batch* b, bool untune = true) {
     b->planned = false;
 }
 
-// Group members into classes by Qp (keeps tilings of existing classes).
+// Group members into classes by Qp, or all into one class keyed by the largest Qp (keeps tilings
+// of existing classes).
 void group(assn_batch* b) {
     std::vector<assn_batch::Class> old;
     old.swap(b->classes);
+    int qmax = 0;
+    for (auto& m : b->members) qmax = std::max(qmax, m.p->Qp);
     for (size_t i = 0; i < b->members.size(); ++i) {
-        const int Qp = b->members[i].p->Qp;
+        const int Qp = b->grouping ? qmax : b->members[i].p->Qp;
         auto it = std::find_if(b->classes.begin(), b->classes.end(), [&](const assn_batch::Class& c) { return c.Qp == Qp; });
         if (it == b->classes.end()) {
             assn_batch::Class c;
@@ -259,7 +269,7 @@ int ensure_batch_plan(assn_batch* b) {
             std::vector<Tc2Problem> d;
             for (int i : c.idx) {
                 const assn_batch::Member& m = b->members[i];
-                d.push_back(problem_tc2(m.p, m.dt, m.p->cur + m.nsteps));
+                d.push_back(problem_tc2(m.p, m.dt, m.p->cur + launches_per_step(b) * m.nsteps));
             }
             const int nt = b->want_nt ? b->want_nt : c.nt;
             const bool user = b->want_rings.SS || b->want_rings.SB || b->want_rings.SA || b->want_rings.MPR;
@@ -276,8 +286,8 @@ int ensure_batch_plan(assn_batch* b) {
         c.nmax = 0;
         for (size_t k = 0; k < c.idx.size(); ++k) {
             const assn_batch::Member& m = b->members[c.idx[k]];
-            c.targets[k] = m.p->cur + m.nsteps;
-            c.nmax = std::max(c.nmax, m.nsteps);
+            c.targets[k] = m.p->cur + launches_per_step(b) * m.nsteps;
+            c.nmax = std::max(c.nmax, launches_per_step(b) * m.nsteps);
         }
         BK(b, tc2_plan_set_targets(c.plan, c.targets.data(), b->stream));
     }
@@ -340,16 +350,19 @@ int assn_batch_add(assn_batch* b, assn_problem* p, int nsteps, double dt) {
     if (nsteps < 0) return bfail(b, ASSN_ERR_ARG, "nsteps < 0");
     if (p->precision != ASSN_BF16 && p->precision != ASSN_BF16X3)
         return bfail(b, ASSN_ERR_UNSUPPORTED, "batches step the tensor-core precisions (BF16, BF16X3) only");
-    if (p->scheme != ASSN_SCHEME_EULER_UPWIND)
-        return bfail(b, ASSN_ERR_UNSUPPORTED, "batches take the forward-Euler upwind step only");
+    if (p->scheme != ASSN_SCHEME_EULER_UPWIND && p->scheme != ASSN_SCHEME_HEUN_MINMOD)
+        return bfail(b, ASSN_ERR_UNSUPPORTED, "batches take the explicit schemes (forward-Euler upwind, Heun + minmod)");
     if (b->precision >= 0 && p->precision != b->precision)
         return bfail(b, ASSN_ERR_ARG, "all members of a batch share one precision");
+    if (b->scheme >= 0 && p->scheme != b->scheme)
+        return bfail(b, ASSN_ERR_ARG, "all members of a batch share one scheme");
     if (p->dev != b->dev) return bfail(b, ASSN_ERR_ARG, "problem lives on another device");
     if (index_of(b, p) >= 0) return bfail(b, ASSN_ERR_ARG, "problem is already a member");
     if ((int)b->members.size() >= 1024) return bfail(b, ASSN_ERR_ARG, "a batch holds at most 1024 problems");
     const int r = problem_prepare(p, dt);
     if (r) return bfail(b, r, "member: %s", p->err.c_str());
     b->precision = p->precision;
+    b->scheme = p->scheme;
     b->members.push_back({p, nsteps, dt});
     drop_plan(b);
     return ASSN_OK;
@@ -376,7 +389,7 @@ int assn_batch_remove(assn_batch* b, assn_problem* p) {
     if (i < 0) return bfail(b, ASSN_ERR_ARG, "problem is not a member");
     BK(b, cudaStreamSynchronize(b->stream));
     b->members.erase(b->members.begin() + i);
-    if (b->members.empty()) b->precision = -1;
+    if (b->members.empty()) b->precision = b->scheme = -1;
     drop_plan(b);
     return ASSN_OK;
 }
@@ -389,6 +402,16 @@ int assn_batch_set_tiling(assn_batch* b, int tile_cells, int stages) {
     b->want_nt = tile_cells;
     b->want_rings = TcRings{stages, stages, stages, 0};
     drop_plan(b);
+    return ASSN_OK;
+}
+
+int assn_batch_set_grouping(assn_batch* b, int one_launch) {
+    if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    if (one_launch != 0 && one_launch != 1) return bfail(b, ASSN_ERR_ARG, "one_launch must be 0 or 1");
+    if (one_launch != b->grouping) {
+        b->grouping = one_launch;
+        drop_plan(b);
+    }
     return ASSN_OK;
 }
 
@@ -437,8 +460,9 @@ int assn_batch_run(assn_batch* b, int use_graph) {
     if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
     if (b->members.empty()) return ASSN_OK;
     BK(b, cudaSetDevice(b->dev));
+    const int lps = launches_per_step(b);
     int nmax = 0;
-    for (auto& m : b->members) nmax = std::max(nmax, m.nsteps);
+    for (auto& m : b->members) nmax = std::max(nmax, lps * m.nsteps);
     if (nmax == 0) return ASSN_OK;
     // order after each member's pending work; set each device counter to the member's parity
     for (auto& m : b->members) {
@@ -457,11 +481,13 @@ int assn_batch_run(assn_batch* b, int use_graph) {
     std::vector<int> shape;
     for (auto& c : b->classes) shape.push_back(c.nmax);
     auto enqueue = [&]() -> cudaError_t {
-        // steps of the classes interleaved, one launch per class and step
+        // steps (Heun: stages) of the classes interleaved, one launch per class and step (stage)
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < nmax && e == cudaSuccess; ++k)
             for (auto& c : b->classes)
-                if (k < c.nmax && e == cudaSuccess) e = launch_step_tc2(c.plan, b->d_err, -1, b->stream);
+                if (k < c.nmax && e == cudaSuccess)
+                    e = lps == 2 ? launch_heun_stage_tc2(c.plan, b->d_err, -1, nullptr, 0.0f, 1.0f, b->stream)
+                                 : launch_step_tc2(c.plan, b->d_err, -1, b->stream);
         return e;
     };
     int nlaunch = 0;
@@ -487,9 +513,9 @@ int assn_batch_run(assn_batch* b, int use_graph) {
     BK(b, cudaEventRecord(b->done, b->stream));
     for (auto& m : b->members) {
         assn_problem* p = m.p;
-        p->counter_host = p->cur + m.nsteps;
+        p->counter_host = p->cur + lps * m.nsteps;
         p->cur = p->counter_host & 1;
-        p->launches += m.nsteps;
+        p->launches += lps * m.nsteps;
         if (p->stream != b->stream) BK(b, cudaStreamWaitEvent(p->stream, b->done, 0));
     }
     return ASSN_OK;
@@ -503,7 +529,8 @@ int assn_batch_sync(assn_batch* b) {
     BK(b, cudaMemcpy(&f, b->d_err, sizeof f, cudaMemcpyDeviceToHost));
     if (f) {
         BK(b, cudaMemset(b->d_err, 0, sizeof f));
-        return bfail(b, ASSN_ERR_TIMEOUT, "batch step: a bounded device wait gave up (flag 0x%x)", f);
+        return bfail(b, ASSN_ERR_TIMEOUT, "batch step: a bounded device wait gave up (flag 0x%x)%s", f,
+                     (f & 0x80000000u) ? "; work in flight did not drain, treat the CUDA context as suspect" : "");
     }
     return ASSN_OK;
 }

@@ -1,9 +1,10 @@
 // Total particle number of a caller-owned device state, computed without allocating any memory.
 //
-// For callers that cannot allocate device memory during the call: code running between the
-// begin and end of a CUDA stream capture, real-time loops that forbid allocator calls, or hosts
-// embedding the library under a foreign memory pool.  The reduction's partial sums live in a
-// fixed file-scope device array instead of an allocation.
+// For callers that cannot allocate device memory during the call: real-time loops whose latency
+// budget rules out allocator calls (cudaMalloc may block and synchronise the device), and hosts
+// that run the library inside a memory pool they manage themselves.  The reduction's partial sums
+// live in a fixed file-scope device array instead of an allocation; its device address is looked
+// up once per device on the first call there (so that call should come before any stream capture).
 #include <cstdio>
 #include <mutex>
 

@@ -41,6 +41,7 @@ struct assn_problem {
     assn::TcOperands tc;
     assn::TcPlan* plan = nullptr;      // one-tile-per-CTA tensor-core kernel (variant 1)
     assn::Tc2Plan* plan2 = nullptr;    // persistent warp-specialised kernel (variant 0, default)
+    assn::Tc3Plan* plan3 = nullptr;    // paired-SM kernel (variant 2)
     int variant = 0;
     double* d_e = nullptr;
     void* d_ord = nullptr;

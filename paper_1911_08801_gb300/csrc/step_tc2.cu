@@ -44,8 +44,9 @@
 // common strides); QP = 0 reads it per problem.
 //
 // Every mbarrier wait is bounded (about 1 s); on expiry the CTA records the event in err_flag,
-// all roles stop issuing, the CTA waits briefly for copies and MMAs in flight, frees its tensor
-// memory and returns.
+// all roles stop issuing, each thread that issued copies or MMAs waits (at most 20 ms, else it
+// records kErrUndrained) for its own work to land, the CTA frees its tensor memory and returns,
+// and the launch counts no step as taken.
 #include <string.h>
 
 #include <algorithm>
@@ -129,8 +130,8 @@ struct Layout {
         pinfo = tparm + kEpiWarps * 2 * 64;                      // [kMaxProbs] first tile, [kMaxProbs] info
         bars = pinfo + kMaxProbs * 8;
         bars = (bars + 7) & ~7;
-        // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2]
-        end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 8) + 16;
+        // stg_full/empty[SS], bf_full/empty[SB], a_full/empty[SA], tm_full/empty[2], phi_full/empty[2], drain
+        end = bars + 8 * (2 * SS + 2 * SB + 2 * SA + 9) + 16;
     }
 };
 
@@ -220,7 +221,8 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
     uint64_t* tm_empty = tm_full + 2;
     uint64_t* phi_full = tm_empty + 2;
     uint64_t* phi_empty = phi_full + 2;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(phi_empty + 2);
+    uint64_t* drain_bar = phi_empty + 2;   // abort path: the MMA issuer's final commit
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain_bar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -242,6 +244,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             mbar_init(&phi_full[b], R::kConv);
             mbar_init(&phi_empty[b], kEpiWarps);
         }
+        mbar_init(drain_bar, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -312,6 +315,10 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                 mma_commit(&tm_full[buf]);
                 if (!ok) break;
             }
+            if (*abort_flag) {   // every MMA this thread issued completes before TMEM is freed
+                mma_commit(drain_bar);
+                if (!mbar_drain(drain_bar, 0u, kDrainNs)) atomicOr(a.err, kErrUndrained);
+            }
         }
     } else if (warp == 1 && (lane == 0 || R::kGWarp != 1)) {
         if (lane == 0) {
@@ -319,6 +326,7 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             // evict-last: the epilogue re-reads these lines (own values and y-neighbours) shortly
             const uint64_t pol = policy_evict_last();
             Ring rs;
+            uint32_t armed = 0u, apar = 0u;   // slots armed at least once, parity of their last arming
             int pid = 0;
             for (int T = next_tile(blockIdx.x, pid); T < total; T = next_tile(T + gridDim.x, pid)) {
                 const int info = s_info[pid];
@@ -330,16 +338,23 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                     if (!WAITB(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
                     mbar_expect_tx(&stg_full[rs.s], LT::kStg);
                     tma_load_2d_hint(stg + (size_t)rs.s * NT * 64, map, &stg_full[rs.s], kc * 64, tile * NT, pol);
+                    armed |= 1u << rs.s;
+                    apar = (apar & ~(1u << rs.s)) | (rs.ph << rs.s);
                     rs.next(a.SS);
                 }
                 if (!ok) break;
             }
+            if (*abort_flag)   // copies in flight land before the staging ring is released
+                for (int s2 = 0; s2 < a.SS; ++s2)
+                    if (((armed >> s2) & 1u) && !mbar_drain(&stg_full[s2], (apar >> s2) & 1u, kDrainNs))
+                        atomicOr(a.err, kErrUndrained);
         }
     } else if (warp == R::kGWarp) {
         if (lane == R::kGLane) {
             // ---------------------------------------------------------------- kernel-matrix TMA producer
             const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
             Ring ra;
+            uint32_t armed = 0u, apar = 0u;
             int pid = 0;
             for (int T = next_tile(blockIdx.x, pid); T < total; T = next_tile(T + gridDim.x, pid)) {
                 const int info = s_info[pid];
@@ -355,11 +370,17 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                         mbar_expect_tx(&a_full[ra.s], bytes);
                         tma_load_4d_hint(dst, mhi, &a_full[ra.s], 0, 0, mg, kc, pol);
                         if (SPLIT) tma_load_4d_hint(dst + MPR * kAStage, mlo, &a_full[ra.s], 0, 0, mg, kc, pol);
+                        armed |= 1u << ra.s;
+                        apar = (apar & ~(1u << ra.s)) | (ra.ph << ra.s);
                         ra.next(a.SA);
                     }
                 }
                 if (!ok) break;
             }
+            if (*abort_flag)
+                for (int s2 = 0; s2 < a.SA; ++s2)
+                    if (((armed >> s2) & 1u) && !mbar_drain(&a_full[s2], (apar >> s2) & 1u, kDrainNs))
+                        atomicOr(a.err, kErrUndrained);
         }
     } else if (warp < R::kEpi0) {
         // -------------------------------------------------------------------- converters
@@ -508,8 +529,9 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             const float* in;
             float* out;
             const OrdF* ord;
+            const float* keep;                 // Heun stage 2: psi^n (the output buffer); else unused
             int fb0, ncell, nx, Q, Qp;
-            float dts;
+            float dts, alpha, beta;            // Heun: out = alpha keep + beta (in + dt L(in))
         };
         static_assert(sizeof(TileP) <= 64, "tile parameter slot");
 
@@ -611,100 +633,104 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             return true;
         };
 
-        if constexpr (HEUN) {
-            // Heun stage, one problem (host-resolved buffers): chunk of kCHe cells; x-stencil cells
-            // fb-2 .. fb+kCHe+1, y-rows two below / one below / one above (Omega_y > 0) or one below /
-            // one above / two above (Omega_y < 0).
-            const int ntl = (s_info[0] & 2) ? total : 0;
-            const int my_tiles = ntl > (int)blockIdx.x ? (ntl - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-            const int cpt = a.one.MB * CPH;
-            const int nchunk = my_tiles * cpt;
-            const int ncell = a.one.ncell, nx = a.one.nx, Qp = QP > 0 ? QP : a.one.Qp;
-            const float alpha = a.one.alpha, beta = a.one.beta;
-            for (int k = 0; k < nchunk && !*abort_flag; ++k) {
-                const int it = k / cpt, r = k - it * cpt;
-                const int m = r / CPH;
-                const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCHe;
-                const int fb = ((int)blockIdx.x + it * (int)gridDim.x) * NT + c0;
-                const int q = m * 128 + lq * 32 + lane;
-                const bool live = q < a.one.Q && fb < ncell;
-                const float4 o4 = live ? __ldg(reinterpret_cast<const float4*>(a.one.ord) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float nux = o4.x, nuy = o4.y;
-                const float* b = a.one.in + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
-                float sv[kCHe], ya[kCHe], yb[kCHe], yc[kCHe], kp[kCHe], e[4];
-                // ya: row two below (nuy > 0) or two above (nuy < 0); yb: row below; yc: row above
-                const long sy = (long)nx * Qp;
-                const long da = nuy > 0.f ? -2 * sy : 2 * sy;
+        // Heun stage (the paper's explicit scheme, Sec. 3.1) of chunk r of a tile: kCHe cells;
+        // x-stencil cells fb-2 .. fb+kCHe+1, y-rows two below / one below / one above (Omega_y > 0)
+        // or one below / one above / two above (Omega_y < 0); out = alpha keep + beta (in + dt L(in)).
+        auto heun_chunk = [&](const TileP& t, int it, int r, int cpt) -> bool {
+            const int m = r / CPH;
+            const int c0 = grp * (NT / kEW) + (r - m * CPH) * kCHe;
+            const int ncell = t.ncell, nx = t.nx, Qp = QP > 0 ? QP : t.Qp;
+            const int fb = t.fb0 + c0;
+            const int q = m * 128 + lq * 32 + lane;
+            const bool live = q < t.Q && fb < ncell;
+            const float alpha = t.alpha, beta = t.beta;
+            const float4 o4 = live ? __ldg(reinterpret_cast<const float4*>(t.ord) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float nux = o4.x, nuy = o4.y;
+            const float* b = t.in + (size_t)(live ? fb : 0) * Qp + (live ? q : 0);
+            float sv[kCHe], ya[kCHe], yb[kCHe], yc[kCHe], kp[kCHe], e[4];
+            // ya: row two below (nuy > 0) or two above (nuy < 0); yb: row below; yc: row above
+            const long sy = (long)nx * Qp;
+            const long da = nuy > 0.f ? -2 * sy : 2 * sy;
+#pragma unroll
+            for (int i = 0; i < kCHe; ++i) {
+                const int f = fb + i;
+                const bool in = live && f < ncell;
+                sv[i] = in ? __ldg(b + i * Qp) : 0.0f;
+                const bool ny0 = in && nuy != 0.f;
+                ya[i] = (ny0 && (nuy > 0.f ? f >= 2 * nx : f + 2 * nx < ncell)) ? __ldg(b + i * Qp + da) : 0.0f;
+                yb[i] = (ny0 && f >= nx) ? __ldg(b + i * Qp - sy) : 0.0f;
+                yc[i] = (ny0 && f + nx < ncell) ? __ldg(b + i * Qp + sy) : 0.0f;
+                kp[i] = (in && alpha != 0.0f) ? __ldg(t.keep + (size_t)f * Qp + q) : 0.0f;
+            }
+            e[0] = (live && fb >= 2) ? __ldg(b - 2 * Qp) : 0.0f;
+            e[1] = (live && fb >= 1) ? __ldg(b - Qp) : 0.0f;
+            e[2] = (live && fb + kCHe < ncell) ? __ldg(b + kCHe * Qp) : 0.0f;
+            e[3] = (live && fb + kCHe + 1 < ncell) ? __ldg(b + (kCHe + 1) * Qp) : 0.0f;
+            const int buf = it & 1;
+            if (r == 0) {
+                const uint32_t use = (uint32_t)(it >> 1);
+                int go = 1;
+                if (lane == 0)
+                    go = WAITB(&phi_full[buf], use & 1u, 0x1000u) && WAITB(&tm_full[buf], use & 1u, 0x2000u);
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (!go) return false;
+                tc_fence_after();
+            }
+            float y[kCHe];
+            __syncwarp();
+            tmem_ld<kCHe>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0), y);
+            if (fb < ncell && q < Qp) {
+                float* po = t.out + (size_t)fb * Qp + q;
+                const float4* cb = coef + buf * NT + c0;
+                const float dts = t.dts, ge = dts * o4.w;
 #pragma unroll
                 for (int i = 0; i < kCHe; ++i) {
-                    const int f = fb + i;
-                    const bool in = live && f < ncell;
-                    sv[i] = in ? __ldg(b + i * Qp) : 0.0f;
-                    const bool ny0 = in && nuy != 0.f;
-                    ya[i] = (ny0 && (nuy > 0.f ? f >= 2 * nx : f + 2 * nx < ncell)) ? __ldg(b + i * Qp + da) : 0.0f;
-                    yb[i] = (ny0 && f >= nx) ? __ldg(b + i * Qp - sy) : 0.0f;
-                    yc[i] = (ny0 && f + nx < ncell) ? __ldg(b + i * Qp + sy) : 0.0f;
-                    kp[i] = (in && alpha != 0.0f) ? __ldg(a.one.keep + (size_t)f * Qp + q) : 0.0f;
-                }
-                e[0] = (live && fb >= 2) ? __ldg(b - 2 * Qp) : 0.0f;
-                e[1] = (live && fb >= 1) ? __ldg(b - Qp) : 0.0f;
-                e[2] = (live && fb + kCHe < ncell) ? __ldg(b + kCHe * Qp) : 0.0f;
-                e[3] = (live && fb + kCHe + 1 < ncell) ? __ldg(b + (kCHe + 1) * Qp) : 0.0f;
-                const int buf = it & 1;
-                if (r == 0) {
-                    const uint32_t use = (uint32_t)(it >> 1);
-                    int go = 1;
-                    if (lane == 0)
-                        go = WAITB(&phi_full[buf], use & 1u, 0x1000u) && WAITB(&tm_full[buf], use & 1u, 0x2000u);
-                    go = __shfl_sync(0xffffffffu, go, 0);
-                    if (!go) break;
-                    tc_fence_after();
-                }
-                float y[kCHe];
-                __syncwarp();
-                tmem_ld<kCHe>(tmem_base + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (cpt / CPH) * NT + m * NT + c0), y);
-                if (fb < ncell && q < Qp) {
-                    float* po = a.one.out + (size_t)fb * Qp + q;
-                    const float4* cb = coef + buf * NT + c0;
-                    const float dts = a.one.dts, ge = dts * o4.w;
-#pragma unroll
-                    for (int i = 0; i < kCHe; ++i) {
-                        const float4 cf = cb[i];
-                        const int bits = __float_as_int(cf.z);
-                        if (!(bits & 16)) continue;
-                        if (q >= a.one.Q) {
-                            __stcs(po + i * Qp, 0.0f);
-                            continue;
-                        }
-                        auto xv = [&](int k2) -> float { return k2 < 0 ? e[k2 + 2] : (k2 < kCHe ? sv[k2] : e[k2 - kCHe + 2]); };
-                        const float xm2 = (bits & 32) ? xv(i - 2) : 0.0f;
-                        const float xm1 = (bits & 1) ? xv(i - 1) : 0.0f;
-                        const float xp1 = (bits & 2) ? xv(i + 1) : 0.0f;
-                        const float xp2 = (bits & 64) ? xv(i + 2) : 0.0f;
-                        const float c = sv[i];
-                        const float tx = limited_difference(nux, xm2, xm1, c, xp1, xp2);
-                        const bool up = nuy > 0.f;   // ya is two rows upwind: below for up, above otherwise
-                        const float ty = limited_difference(nuy, up ? ya[i] : 0.0f, yb[i], c, yc[i], up ? 0.0f : ya[i]);
-                        const float st = SPLIT ? c : __bfloat162float(__float2bfloat16_rn(c));
-                        float adv = fmaf(c, cf.x, cf.y);
-                        adv = fmaf(-nux, tx, adv);
-                        adv = fmaf(-nuy, ty, adv);
-                        adv = fmaf(dts, y[i], adv);
-                        adv = fmaf(-ge, st, adv);
-                        __stcs(po + i * Qp, fmaf(alpha, kp[i], beta * adv));
+                    const float4 cf = cb[i];
+                    const int bits = __float_as_int(cf.z);
+                    if (!(bits & 16)) continue;
+                    if (q >= t.Q) {
+                        __stcs(po + i * Qp, 0.0f);
+                        continue;
                     }
-                }
-                if (r == cpt - 1) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) {
-                        mbar_arrive(&tm_empty[buf]);
-                        mbar_arrive(&phi_empty[buf]);
-                    }
+                    auto xv = [&](int k2) -> float { return k2 < 0 ? e[k2 + 2] : (k2 < kCHe ? sv[k2] : e[k2 - kCHe + 2]); };
+                    const float xm2 = (bits & 32) ? xv(i - 2) : 0.0f;
+                    const float xm1 = (bits & 1) ? xv(i - 1) : 0.0f;
+                    const float xp1 = (bits & 2) ? xv(i + 1) : 0.0f;
+                    const float xp2 = (bits & 64) ? xv(i + 2) : 0.0f;
+                    const float c = sv[i];
+                    const float tx = limited_difference(nux, xm2, xm1, c, xp1, xp2);
+                    const bool up = nuy > 0.f;   // ya is two rows upwind: below for up, above otherwise
+                    const float ty = limited_difference(nuy, up ? ya[i] : 0.0f, yb[i], c, yc[i], up ? 0.0f : ya[i]);
+                    const float st = SPLIT ? c : __bfloat162float(__float2bfloat16_rn(c));
+                    float adv = fmaf(c, cf.x, cf.y);
+                    adv = fmaf(-nux, tx, adv);
+                    adv = fmaf(-nuy, ty, adv);
+                    adv = fmaf(dts, y[i], adv);
+                    adv = fmaf(-ge, st, adv);
+                    __stcs(po + i * Qp, fmaf(alpha, kp[i], beta * adv));
                 }
             }
-        } else {
+            if (r == cpt - 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&tm_empty[buf]);
+                    mbar_arrive(&phi_empty[buf]);
+                }
+            }
+            return true;
+        };
+        // A chunk loaded and updated in one go (Heun, and the one-buffer forward-Euler form).
         float s0[kCHe], u0[kCHe], l0 = 0.f, r0 = 0.f;
+        auto one_chunk = [&](const TileP& t, int it, int r, int cpt) -> bool {
+            if constexpr (HEUN) {
+                return heun_chunk(t, it, r, cpt);
+            } else {
+                load(t, r, s0, u0, l0, r0);
+                return compute(t, it, r, cpt, s0, u0, l0, r0);
+            }
+        };
+
         if (a.one_fixed) {
             // One problem: its tiles blockIdx.x, blockIdx.x + gridDim.x, ... (all or none active);
             // chunk k of this warp is chunk k % cpt of the (k / cpt)-th of them.
@@ -715,15 +741,14 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             auto view = [&](int k, int& it, int& r) -> TileP {
                 it = k / cpt;
                 r = k - it * cpt;
-                return TileP{a.one.in, a.one.out, a.one.ord, ((int)blockIdx.x + it * (int)gridDim.x) * NT, a.one.ncell, a.one.nx, a.one.Q,
-                             QP > 0 ? QP : a.one.Qp, a.one.dts};
+                return TileP{a.one.in, a.one.out, a.one.ord, a.one.keep, ((int)blockIdx.x + it * (int)gridDim.x) * NT,
+                             a.one.ncell, a.one.nx, a.one.Q, QP > 0 ? QP : a.one.Qp, a.one.dts, a.one.alpha, a.one.beta};
             };
             int it, r;
             if constexpr (kOneBuf) {
-                for (int k = 0; k < nchunk; ++k) {
+                for (int k = 0; k < nchunk && !*abort_flag; ++k) {
                     const TileP t = view(k, it, r);
-                    load(t, r, s0, u0, l0, r0);
-                    if (!compute(t, it, r, cpt, s0, u0, l0, r0)) break;
+                    if (!one_chunk(t, it, r, cpt)) break;
                 }
             } else {
             float s1[kCHe], u1[kCHe], l1 = 0.f, r1 = 0.f;
@@ -739,7 +764,10 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
         } else {
             // Several problems: walk the active tiles; the tile's parameters sit in this warp's
             // shared-memory slot (it & 1), rewritten from global memory only when the problem
-            // changes (else copied from the other slot or kept).
+            // changes (else copied from the other slot or kept).  A Heun launch takes each problem's
+            // stage from its step counter: a Heun step is two launches and ends on the (even
+            // distance) target, so the second stage runs when the counter's parity differs from the
+            // target's; it keeps psi^n from the buffer it writes.
             struct Pos {
                 int T, pid, it, r, cpt;
             };
@@ -770,6 +798,10 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
                             t->Q = d.Q;
                             t->Qp = QP > 0 ? QP : d.Qp;
                             t->dts = d.dt_sigma_as;
+                            const bool stage2 = HEUN && ((par ^ d.target) & 1);
+                            t->keep = stage2 ? t->out : nullptr;
+                            t->alpha = stage2 ? 0.5f : 0.0f;
+                            t->beta = stage2 ? 0.5f : 1.0f;
                         }
                     }
                     t->fb0 = (p.T - s_tile0[p.pid]) * NT;
@@ -792,9 +824,8 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             cur.T = next_tile(blockIdx.x, cur.pid);
             fill(cur);
             if constexpr (kOneBuf) {
-                while (cur.T < total) {
-                    load(slot(cur.it), cur.r, s0, u0, l0, r0);
-                    if (!compute(slot(cur.it), cur.it, cur.r, cur.cpt, s0, u0, l0, r0)) break;
+                while (cur.T < total && !*abort_flag) {
+                    if (!one_chunk(slot(cur.it), cur.it, cur.r, cur.cpt)) break;
                     advance(cur);
                 }
             } else {
@@ -815,27 +846,24 @@ step_tc2_kernel(const __grid_constant__ BatchArgs a) {
             }
             }
         }
-        }
     }
 
+    cp_async_wait<0>();   // converters: cell constants requested before an abort have landed
     __syncthreads();
-    if (*abort_flag) {
-        // let copies and MMAs already in flight land before the memory they target goes away
-        const uint64_t t0 = globaltimer();
-        while (globaltimer() - t0 < 50000ull) __nanosleep(1000);
-    }
     if (warp == 0) {
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem_base, 512);
     }
-    // The last CTA to finish advances the step counters of the problems this launch stepped.
+    // The last CTA to finish advances the step counters of the problems this launch stepped, unless
+    // a bounded wait gave up (then no step is counted as taken).
     if (tid == 0) {
         __threadfence();
         const unsigned int done = atomicAdd(a.ticket, 1u);
         if (done == gridDim.x - 1) {
             __threadfence();
-            for (int i = 0; i < nprob; ++i)
+            const bool clean = *reinterpret_cast<volatile unsigned int*>(a.err) == 0u;
+            for (int i = 0; i < nprob && clean; ++i)
                 if (s_info[i] & 2) *a.probs[i].counter += 1;
             *a.ticket = 0u;
             __threadfence();
@@ -1108,7 +1136,7 @@ static BatchArgs batch_args(Tc2Plan* p, unsigned int* err_flag, int parity0);
 
 cudaError_t launch_heun_stage_tc2(Tc2Plan* p, unsigned int* err_flag, int parity0, const float* keep, float alpha,
                                   float beta, cudaStream_t stream) {
-    if (!p || p->nprob != 1 || parity0 < 0) return cudaErrorInvalidValue;
+    if (!p || (parity0 >= 0 && p->nprob != 1)) return cudaErrorInvalidValue;
     BatchArgs a = batch_args(p, err_flag, parity0);
     a.one.keep = keep;
     a.one.alpha = alpha;

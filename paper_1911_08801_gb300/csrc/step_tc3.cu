@@ -1,0 +1,723 @@
+// Paired-SM tensor-core as-S_N step (sm_103a): one problem, forward Euler with first-order upwind
+// transport (Sec. 3.1-3.2), 256 or 512 ordinates (padded), BF16 contraction with FP32 state.
+//
+// A cluster of two CTAs on two SMs (the pair) steps one tile of TW x TH cells per round (TW = 16;
+// TH = 8 at 512 ordinates, 16 at 256; tiles row-major over the grid, pair p takes tiles p, p + P, ...).
+// The artificial in-scattering gain without its diagonal (Sec. 3.2, Eq. (as-S_N equations))
+//   D[q][c] = sum_{p != q} G_qp psi~_p(c)
+// is computed by tcgen05.mma.cta_group::2 products of M = 256 ordinates x N = TW TH cells x K = 16
+// (BF16 in, FP32 accumulate in tensor memory).  In each 256-ordinate group the even CTA holds
+// rows 0-127 of G and of the accumulator, the odd CTA rows 128-255; each CTA converts and holds
+// the operand rows of half the tile's cells (rows 0 .. TH/2-1 in the even CTA).  Each SM thus
+// loads half of G per tile and supplies half the operand bytes of every MMA.
+//
+// Roles in each CTA (20 warps):
+//   warp 0      TMEM (both CTAs allocate the pair's 512 columns collectively); lane 0 of the even
+//               CTA issues the MMAs into one of two accumulator buffers and commits to the
+//               barriers of both CTAs; lane 0 of the odd CTA forwards the completion of its own
+//               kernel-matrix copies to the even CTA.
+//   warp 1      lane 0: TMA of this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64 ordinates]
+//               chunks, into a staging ring; lane 1: TMA of this CTA's G rows ([128 x 64] BF16
+//               blocks with 128-byte swizzle, all of its 256-row groups per request).
+//   warps 2-3   converters: staging -> BF16 operand rows (K-major, swizzled) for the pair's MMA;
+//               the scalar flux Phi = sum_p w_p psi_p of this CTA's cells, and from it the cells'
+//               coefficients, written into both CTAs.
+//   warps 4-19  epilogue: warp (lane quarter lq, group g) owns 32 ordinates of one 128-row block
+//               and an 8-cell-wide strip of the tile, and walks its 8 rows in order; the upwind
+//               y-neighbour is the previous or next row of the walk (in registers), the upwind
+//               x-neighbour the next register or one edge cell per row:
+//                 psi' = psi (1 - dt sigma_t - a_x - a_y) + a_x psi_upx + a_y psi_upy
+//                        + dt (sigma_s Phi / sum w + q) + dt sigma_as (D - e psi~)
+//               Tiles away from the boundary take a branch-free path (pairs of cells per FFMA2).
+//
+// Every wait is bounded (about 1 s); on expiry the CTA records the event in err, stops issuing,
+// lets its own copies and MMAs land (bounded again), and both CTAs meet at the final cluster
+// barrier before the tensor memory is freed.
+#include <string.h>
+
+#include <algorithm>
+
+#include "assn_internal.h"
+#include "tc_ptx.h"
+
+namespace assn {
+
+namespace {
+
+using namespace ptx;
+
+constexpr int kTW = 16;                 // tile width (cells)
+constexpr int kConv3 = 2;               // converter warps
+constexpr int kEpi3 = 16;               // epilogue warps
+constexpr int kEpi0 = 4;                // first epilogue warp (a multiple of 4: lane quarter = warp & 3)
+constexpr int kThreads3 = (kEpi0 + kEpi3) * 32;
+constexpr int kABlock = 128 * 64 * 2;   // one [128 x 64] BF16 block of G
+
+struct Tc3Args {
+    CUtensorMap tm_psi;                 // input flux [ny][nx][Qp] FP32, box {64, TW, TH/2}
+    CUtensorMap tm_G;                   // G [Mp][Qp] BF16 as {64, 128, 2, MG, KC}, box {64, 128, 1, MG, 1}
+    const float* in;
+    float* out;
+    const OrdF* ord;                    // [Qp]
+    const CellF* cell;                  // [ncell]
+    const float* w;                     // [Qp]
+    unsigned int* err;
+    int nx, ny, Q, ntx, total;
+    int SS, SB, SA;
+    float dt, dts;                      // dt and dt sigma_as
+};
+
+template <int MG>
+struct L3 {
+    static constexpr int NT = 256 / MG;         // cells per tile (MMA N)
+    static constexpr int TH = NT / kTW;         // tile rows
+    static constexpr int THc = TH / 2;          // rows per CTA
+    static constexpr int NTc = NT / 2;          // cells per CTA
+    static constexpr int QP = 256 * MG;         // ordinate stride
+    static constexpr int KC = QP / 64;          // 64-ordinate chunks
+    static constexpr int kStg = NTc * 256;      // FP32 staging stage
+    static constexpr int kB = NTc * 128;        // BF16 operand stage
+    static constexpr int kA = MG * kABlock;     // G stage (all of this CTA's blocks of one chunk)
+    int stg, b, a, cx, cy, cb, cst, bars, end;
+    __host__ __device__ L3(int SS, int SB, int SA) {
+        stg = 0;
+        b = stg + SS * kStg;
+        a = b + SB * kB;
+        cx = a + SA * kA;                       // [2][NT] 1 - dt sigma_t
+        cy = cx + 2 * NT * 4;                   // [2][NT] dt (sigma_s Phi / sum w + q)
+        cb = cy + 2 * NT * 4;                   // [2][NT] neighbour bits
+        cst = cb + 2 * NT * 4;                  // [NTc] cell constants of this CTA's cells
+        bars = cst + NTc * 16;
+        // stg full/empty [SS], b full/empty [SB], a full/pair/empty [SA], tm full/empty [2],
+        // phi full/empty [2], drain
+        end = bars + 8 * (2 * SS + 2 * SB + 3 * SA + 9) + 16;
+    }
+};
+
+struct Ring3 {
+    int s = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next(int S) {
+        if (++s == S) { s = 0; ph ^= 1u; }
+    }
+};
+
+// Local-scope and cluster-scope bounded waits, fast path inline.
+#define W3(bar, parity, code) (mbar_try_wait((bar), (parity)) || mbar_wait((bar), (parity), abort_flag, a.err, (code)))
+#define W3C(bar, parity, code) \
+    (mbar_try_wait_cl((bar), (parity)) || mbar_wait_cl((bar), (parity), abort_flag, a.err, (code)))
+
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+template <int MG>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
+step_tc3_kernel(const __grid_constant__ Tc3Args a) {
+    using LT = L3<MG>;
+    constexpr int NT = LT::NT, TH = LT::TH, THc = LT::THc, NTc = LT::NTc, QP = LT::QP, KC = LT::KC;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const LT L(a.SS, a.SB, a.SA);
+    float* stg = reinterpret_cast<float*>(base + L.stg);
+    unsigned char* bring = base + L.b;
+    unsigned char* aring = base + L.a;
+    float* cx = reinterpret_cast<float*>(base + L.cx);
+    float* cy = reinterpret_cast<float*>(base + L.cy);
+    int* cb = reinterpret_cast<int*>(base + L.cb);
+    CellF* cst = reinterpret_cast<CellF*>(base + L.cst);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
+    uint64_t* stg_full = bars;
+    uint64_t* stg_empty = stg_full + a.SS;
+    uint64_t* b_full = stg_empty + a.SS;
+    uint64_t* b_empty = b_full + a.SB;
+    uint64_t* a_full = b_empty + a.SB;
+    uint64_t* a_pair = a_full + a.SA;
+    uint64_t* a_empty = a_pair + a.SA;
+    uint64_t* tm_full = a_empty + a.SA;
+    uint64_t* tm_empty = tm_full + 2;
+    uint64_t* phi_full = tm_empty + 2;
+    uint64_t* phi_empty = phi_full + 2;
+    uint64_t* drain_bar = phi_empty + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain_bar + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = cluster_ctarank();
+    const int pair = blockIdx.x >> 1, npair = gridDim.x >> 1;
+    const int total = a.total;
+
+    if (tid == 0) {
+        for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], kConv3); }
+        for (int s = 0; s < a.SB; ++s) { mbar_init(&b_full[s], 2 * kConv3); mbar_init(&b_empty[s], 1); }
+        for (int s = 0; s < a.SA; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_pair[s], 1);
+            mbar_init(&a_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tm_full[b], 1);
+            mbar_init(&tm_empty[b], 2 * kEpi3);
+            mbar_init(&phi_full[b], 2 * kConv3);
+            mbar_init(&phi_empty[b], 2 * kEpi3);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc_pair(tmem_holder, 512);
+        tc_fence_before();
+    }
+    __syncthreads();
+    cluster_sync();   // the peer's barriers are initialised and its tensor memory allocated
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0 && rank == 0) {
+            // ------------------------------------------------------------------------ MMA issuer
+            constexpr uint32_t idesc = idesc_bf16(256, NT);
+            const uint64_t a0 = sw128_desc(smem_u32(aring));
+            const uint64_t b0 = sw128_desc(smem_u32(bring));
+            Ring3 rb, ra;
+            bool ok = true;
+            for (int T = pair, it = 0; T < total && ok; T += npair, ++it) {
+                const int buf = it & 1;
+                const uint32_t use = (uint32_t)(it >> 1);
+                if (!W3C(&tm_empty[buf], (use & 1u) ^ 1u, 0x10u)) break;
+                tc_fence_after();
+                const uint32_t dbase = tmem_base + (uint32_t)(buf * MG * NT);
+                for (int kc = 0; kc < KC; ++kc) {
+                    if (!W3C(&b_full[rb.s], rb.ph, 0x20u) || !W3(&a_full[ra.s], ra.ph, 0x40u) ||
+                        !W3C(&a_pair[ra.s], ra.ph, 0x80u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t bd0 = b0 + (uint64_t)((rb.s * LT::kB) >> 4);
+                    const uint64_t ad0 = a0 + (uint64_t)((ra.s * LT::kA) >> 4);
+#pragma unroll
+                    for (int j = 0; j < MG; ++j) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_bf16_pair(dbase + (uint32_t)(j * NT), ad0 + (uint64_t)((j * kABlock) >> 4) + (uint64_t)(kk * 2),
+                                          bd0 + (uint64_t)(kk * 2), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit_pair(&a_empty[ra.s], 3);
+                    mma_commit_pair(&b_empty[rb.s], 3);
+                    ra.next(a.SA);
+                    rb.next(a.SB);
+                }
+                mma_commit_pair(&tm_full[buf], 3);
+            }
+            if (*abort_flag) {   // every MMA issued completes before the pair's tensor memory is freed
+                mma_commit_pair(drain_bar, 1);
+                if (!mbar_drain(drain_bar, 0u, kDrainNs)) atomicOr(a.err, kErrUndrained);
+            }
+        } else if (lane == 0) {
+            // ------------------------------------------- odd CTA: forward kernel-matrix completions
+            const uint32_t pair_bar0 = mapa_shared(smem_u32(a_pair), 0);
+            Ring3 ra;
+            for (int T = pair; T < total; T += npair) {
+                bool ok = true;
+                for (int kc = 0; kc < KC; ++kc) {
+                    if (!W3(&a_full[ra.s], ra.ph, 0x400u)) { ok = false; break; }
+                    mbar_arrive_cluster(pair_bar0 + 8u * (uint32_t)ra.s);
+                    ra.next(a.SA);
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ----------------------------------------------------------------- flux TMA producer
+            const uint64_t pol = policy_evict_last();   // the epilogue re-reads these lines shortly
+            Ring3 rs;
+            uint32_t armed = 0u, apar = 0u;
+            for (int T = pair; T < total; T += npair) {
+                const int ty = T / a.ntx, tx = T - ty * a.ntx;
+                bool ok = true;
+                for (int kc = 0; kc < KC; ++kc) {
+                    if (!W3(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
+                    mbar_expect_tx(&stg_full[rs.s], LT::kStg);
+                    tma_load_3d_hint(stg + (size_t)rs.s * NTc * 64, &a.tm_psi, &stg_full[rs.s], kc * 64, tx * kTW,
+                                     ty * TH + (int)rank * THc, pol);
+                    armed |= 1u << rs.s;
+                    apar = (apar & ~(1u << rs.s)) | (rs.ph << rs.s);
+                    rs.next(a.SS);
+                }
+                if (!ok) break;
+            }
+            if (*abort_flag)
+                for (int s2 = 0; s2 < a.SS; ++s2)
+                    if (((armed >> s2) & 1u) && !mbar_drain(&stg_full[s2], (apar >> s2) & 1u, kDrainNs))
+                        atomicOr(a.err, kErrUndrained);
+        } else if (lane == 1) {
+            // --------------------------------------------------------- kernel-matrix TMA producer
+            const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
+            Ring3 ra;
+            uint32_t armed = 0u, apar = 0u;
+            for (int T = pair; T < total; T += npair) {
+                bool ok = true;
+                for (int kc = 0; kc < KC; ++kc) {
+                    if (!W3C(&a_empty[ra.s], ra.ph ^ 1u, 0x2u)) { ok = false; break; }
+                    mbar_expect_tx(&a_full[ra.s], LT::kA);
+                    tma_load_5d_hint(aring + (size_t)ra.s * LT::kA, &a.tm_G, &a_full[ra.s], 0, 0, (int)rank, 0, kc, pol);
+                    armed |= 1u << ra.s;
+                    apar = (apar & ~(1u << ra.s)) | (ra.ph << ra.s);
+                    ra.next(a.SA);
+                }
+                if (!ok) break;
+            }
+            if (*abort_flag)
+                for (int s2 = 0; s2 < a.SA; ++s2)
+                    if (((armed >> s2) & 1u) && !mbar_drain(&a_full[s2], (apar >> s2) & 1u, kDrainNs))
+                        atomicOr(a.err, kErrUndrained);
+        }
+    } else if (warp < kEpi0) {
+        // ------------------------------------------------------------------------ converters
+        constexpr int RS = 2 * kConv3;       // rows (cells) advanced per step of a thread column
+        constexpr int NR = NTc / RS;         // cells per thread
+        const int ct = tid - 64;             // 0 .. 63
+        const int rsub = ct >> 4;
+        const int col4 = ct & 15;
+        const float4* wp = reinterpret_cast<const float4*>(a.w) + col4;
+        const uint32_t b_full0 = mapa_shared(smem_u32(b_full), 0);
+        const uint32_t phi_loc = mapa_shared(smem_u32(phi_full), rank);
+        const uint32_t phi_rem = mapa_shared(smem_u32(phi_full), rank ^ 1u);
+        const uint32_t cx_rem = mapa_shared(smem_u32(cx), rank ^ 1u);
+        const uint32_t cy_rem = mapa_shared(smem_u32(cy), rank ^ 1u);
+        const uint32_t cb_rem = mapa_shared(smem_u32(cb), rank ^ 1u);
+        const float dt = a.dt;
+        Ring3 rs, rb;
+        float4 wn = __ldg(wp);
+        for (int T = pair, it = 0; T < total; T += npair, ++it) {
+            const int ty = T / a.ntx, tx = T - ty * a.ntx;
+            const int xbase = tx * kTW, ybase = ty * TH + (int)rank * THc;
+            if (col4 == 0) {
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const int r = rsub + RS * i;
+                    const int xx = xbase + (r & (kTW - 1)), yy = ybase + r / kTW;
+                    if (xx < a.nx && yy < a.ny) cp_async16(smem_u32(cst + r), a.cell + (size_t)yy * a.nx + xx, 16u);
+                }
+                cp_async_commit();
+            }
+            float part[NR];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) part[i] = 0.0f;
+            bool ok = true;
+            for (int kc = 0; kc < KC; ++kc) {
+                const float4 w4 = wn;
+                wn = __ldg(wp + (kc + 1 < KC ? kc + 1 : 0) * 16);
+                if (!W3(&stg_full[rs.s], rs.ph, 0x100u) || !W3C(&b_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
+                    ok = false;
+                    break;
+                }
+                const float4* src = reinterpret_cast<const float4*>(stg + (size_t)rs.s * NTc * 64);
+                unsigned char* dst = bring + rb.s * LT::kB;
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const int r = rsub + RS * i;
+                    const float4 v = src[r * 16 + col4];
+                    part[i] += w4.x * v.x + w4.y * v.y + w4.z * v.z + w4.w * v.w;
+                    uint2 h;
+                    h.x = pack_bf16(v.x, v.y);
+                    h.y = pack_bf16(v.z, v.w);
+                    const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
+                    *reinterpret_cast<uint2*>(dst + off) = h;
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&stg_empty[rs.s]);
+                    mbar_arrive_cluster(b_full0 + 8u * (uint32_t)rb.s);
+                }
+                rs.next(a.SS);
+                rb.next(a.SB);
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                float v = part[i];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                part[i] = v;
+            }
+            const int buf = it & 1;
+            const uint32_t use = (uint32_t)(it >> 1);
+            if (!W3C(&phi_empty[buf], (use & 1u) ^ 1u, 0x800u)) break;
+            if (col4 == 0) {
+                // per cell of the pair tile: 1 - dt sigma_t, dt (sigma_s Phi / sum w + q), neighbour bits
+                // (1 left, 2 right, 4 below, 8 above exist; 16 the cell exists)
+                cp_async_wait<0>();
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const int r = rsub + RS * i;
+                    const int xx = xbase + (r & (kTW - 1)), yy = ybase + r / kTW;
+                    float fx = 1.0f, fy = 0.0f;
+                    int bits = 0;
+                    if (xx < a.nx && yy < a.ny) {
+                        const CellF cl = cst[r];
+                        fx = 1.0f - dt * cl.sig_t;
+                        fy = dt * (cl.sig_s_over_wsum * part[i] + cl.q);
+                        bits = (xx > 0 ? 1 : 0) | (xx + 1 < a.nx ? 2 : 0) | (yy > 0 ? 4 : 0) | (yy + 1 < a.ny ? 8 : 0) | 16;
+                    }
+                    const int c = buf * NT + (int)rank * NTc + r;
+                    cx[c] = fx;
+                    cy[c] = fy;
+                    cb[c] = bits;
+                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cx_rem + 4u * (uint32_t)c), "f"(fx) : "memory");
+                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cy_rem + 4u * (uint32_t)c), "f"(fy) : "memory");
+                    asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(cb_rem + 4u * (uint32_t)c), "r"(bits) : "memory");
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive_cluster(phi_loc + 8u * (uint32_t)buf);
+                mbar_arrive_cluster(phi_rem + 8u * (uint32_t)buf);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------------------ epilogue
+        const int e = warp - kEpi0;
+        const int lq = warp & 3;             // TMEM lane quarter this warp may access
+        const int g = e >> 2;                // 0..3
+        const int j = MG == 2 ? (g >> 1) : 0;                        // 256-row group
+        const int strip = MG == 2 ? (g & 1) : g;
+        const int xs = 8 * (strip & 1), ys = MG == 2 ? 0 : 8 * (strip >> 1);
+        const int q = 256 * j + 128 * (int)rank + 32 * lq + lane;   // this lane's ordinate
+        const bool qlive = q < a.Q;
+        const bool warp_pad = 256 * j + 128 * (int)rank + 32 * lq + 31 >= a.Q;   // some lanes are padding
+        const float4 o4 = qlive ? __ldg(reinterpret_cast<const float4*>(a.ord) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float ax = fabsf(o4.x), ay = fabsf(o4.y), axy = ax + ay;
+        const bool xpos = o4.x > 0.f, ypos = o4.y > 0.f;
+        const float dts = a.dts, nge = -dts * o4.w;
+        const int nx = a.nx, ny = a.ny;
+        const size_t rowstride = (size_t)nx * QP;
+        const uint32_t tm_empty0 = mapa_shared(smem_u32(tm_empty), 0);
+        const uint32_t phe_loc = mapa_shared(smem_u32(phi_empty), rank);
+        const uint32_t phe_rem = mapa_shared(smem_u32(phi_empty), rank ^ 1u);
+        const int xedge = xpos ? -1 : 8;      // column of the edge cell (relative to the strip)
+        const float2 AX = make_float2(ax, ax), AY = make_float2(ay, ay), NAXY = make_float2(-axy, -axy);
+        const float2 DTS = make_float2(dts, dts), NGE = make_float2(nge, nge);
+
+        for (int T = pair, it = 0; T < total; T += npair, ++it) {
+            const int ty = T / a.ntx, tx = T - ty * a.ntx;
+            const int x0 = tx * kTW + xs, y0 = ty * TH + ys;   // this warp's strip origin
+            const int buf = it & 1;
+            const uint32_t use = (uint32_t)(it >> 1);
+            const bool interior = !warp_pad && tx * kTW >= 1 && tx * kTW + kTW + 1 <= nx && ty * TH >= 1 &&
+                                  ty * TH + TH + 1 <= ny;
+            const float* pin = a.in + ((size_t)y0 * nx + x0) * QP + q;   // cell (x0, y0), this ordinate
+            float* pout = a.out + ((size_t)y0 * nx + x0) * QP + q;
+            const int c0 = buf * NT + ys * kTW + xs;                    // coefficient index of (x0, y0)
+            const uint32_t tcol = tmem_base + ((uint32_t)(lq * 32) << 16) +
+                                  (uint32_t)(buf * MG * NT + j * NT + ys * kTW + xs);
+            if (interior) {
+                // rows -1 .. 8 of the strip, row r at rv[r + 1]; edge cell of row r at ev[r + 1]
+                float rv[10][8], ev[10];
+                auto load_row = [&](int r) {
+                    const float* p = pin + (long)r * (long)rowstride;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) rv[r + 1][i] = __ldg(p + i * QP);
+                    ev[r + 1] = __ldg(p + xedge * QP);
+                };
+                // halo rows: the one below (Omega_y > 0) or above (Omega_y < 0) the strip
+                {
+                    const float* p = pin + (ypos ? -(long)rowstride : 8 * (long)rowstride);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float v = __ldg(p + i * QP);
+                        rv[0][i] = v;
+                        rv[9][i] = v;
+                    }
+                }
+                load_row(0);
+                load_row(1);
+                load_row(2);
+                int go = 1;
+                if (lane == 0) go = W3C(&phi_full[buf], use & 1u, 0x1000u) && W3C(&tm_full[buf], use & 1u, 0x2000u);
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (!go) break;
+                tc_fence_after();
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    if (r + 3 < 8) load_row(r + 3);
+                    float y[8];
+                    tmem_ld8(tcol + (uint32_t)(r * kTW), y);
+                    const float4* cxr = reinterpret_cast<const float4*>(cx + c0 + r * kTW);
+                    const float4* cyr = reinterpret_cast<const float4*>(cy + c0 + r * kTW);
+                    const float4 xa = cxr[0], xb = cxr[1], ya = cyr[0], yb = cyr[1];
+                    const float fxv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                    const float fyv[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                    const float* s = rv[r + 1];
+                    const float* dn = rv[r];         // row below
+                    const float* up = rv[r + 2];     // row above (the halo row for r = 7)
+                    float* po = pout + (long)r * (long)rowstride;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i0 = 2 * k, i1 = 2 * k + 1;
+                        const float ux0 = xpos ? (i0 == 0 ? ev[r + 1] : s[i0 - 1]) : s[i0 + 1];
+                        const float ux1 = xpos ? s[i1 - 1] : (i1 == 7 ? ev[r + 1] : s[i1 + 1]);
+                        const float uy0 = ypos ? dn[i0] : up[i0];
+                        const float uy1 = ypos ? dn[i1] : up[i1];
+                        const float2 S = make_float2(s[i0], s[i1]);
+                        const float2 ST = __bfloat1622float2(__floats2bfloat162_rn(s[i0], s[i1]));
+                        float2 o = __ffma2_rn(S, __fadd2_rn(make_float2(fxv[i0], fxv[i1]), NAXY),
+                                              make_float2(fyv[i0], fyv[i1]));
+                        o = __ffma2_rn(AX, make_float2(ux0, ux1), o);
+                        o = __ffma2_rn(AY, make_float2(uy0, uy1), o);
+                        o = __ffma2_rn(DTS, make_float2(y[i0], y[i1]), o);
+                        o = __ffma2_rn(NGE, ST, o);
+                        __stcs(po + i0 * QP, o.x);
+                        __stcs(po + i1 * QP, o.y);
+                    }
+                }
+            } else {
+                // boundary tiles and lanes past Q: every load and store checked against the grid,
+                // vacuum (zero) upwind values outside it, zero flux on padded ordinates
+                float cur[8], prv[8], nxt[8], edge = 0.0f;
+                auto load = [&](int r, float (&v)[8], float& ed) {
+                    const int yy = y0 + r;
+                    const bool rowok = yy >= 0 && yy < ny;
+                    const float* p = pin + (long)r * (long)rowstride;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] = (rowok && x0 + i < nx) ? __ldg(p + i * QP) : 0.0f;
+                    const int xe = x0 + xedge;
+                    ed = (rowok && xe >= 0 && xe < nx) ? __ldg(p + xedge * QP) : 0.0f;
+                };
+                float dummy;
+                load(-1, prv, dummy);
+                load(0, cur, edge);
+                float enext = 0.0f;
+                int go = 1;
+                if (lane == 0) go = W3C(&phi_full[buf], use & 1u, 0x1000u) && W3C(&tm_full[buf], use & 1u, 0x2000u);
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (!go) break;
+                tc_fence_after();
+                for (int r = 0; r < 8; ++r) {
+                    load(r + 1, nxt, enext);
+                    float y[8];
+                    tmem_ld8(tcol + (uint32_t)(r * kTW), y);
+                    const int cc = c0 + r * kTW;
+                    float* po = pout + (long)r * (long)rowstride;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int bits = cb[cc + i];
+                        if (!(bits & 16) || q >= QP) continue;
+                        if (!qlive) {
+                            __stcs(po + i * QP, 0.0f);
+                            continue;
+                        }
+                        float ux = xpos ? (i == 0 ? edge : cur[i - 1]) : (i == 7 ? edge : cur[i + 1]);
+                        ux = (bits & (xpos ? 1 : 2)) ? ux : 0.0f;
+                        float uy = ypos ? prv[i] : nxt[i];
+                        uy = (bits & (ypos ? 4 : 8)) ? uy : 0.0f;
+                        const float sf = cur[i];
+                        float out = fmaf(sf, cx[cc + i] - axy, cy[cc + i]);
+                        out = fmaf(ax, ux, out);
+                        out = fmaf(ay, uy, out);
+                        out = fmaf(dts, y[i], out);
+                        out = fmaf(nge, bf16_round(sf), out);
+                        __stcs(po + i * QP, out);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        prv[i] = cur[i];
+                        cur[i] = nxt[i];
+                    }
+                    edge = enext;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive_cluster(tm_empty0 + 8u * (uint32_t)buf);
+                mbar_arrive_cluster(phe_loc + 8u * (uint32_t)buf);
+                mbar_arrive_cluster(phe_rem + 8u * (uint32_t)buf);
+            }
+        }
+    }
+
+    cp_async_wait<0>();
+    __syncthreads();
+    cluster_sync();   // neither CTA frees its memory while the pair's MMAs or arrivals may touch it
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, 512);
+    }
+}
+
+#undef W3
+#undef W3C
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode3() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+// Flux [ny][nx][Qp] FP32 as a 3D tensor {Qp, nx, ny}, box {64 ordinates, TW cells, rows}.
+bool encode_psi3(CUtensorMap* map, const float* psi, int Qp, int nx, int ny, int rows) {
+    EncodeFn enc = get_encode3();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)Qp, (cuuint64_t)nx, (cuuint64_t)ny};
+    const cuuint64_t strides[2] = {(cuuint64_t)Qp * 4, (cuuint64_t)Qp * 4 * nx};
+    const cuuint32_t box[3] = {64, (cuuint32_t)kTW, (cuuint32_t)rows};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(psi), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// G [Mp][Qp] BF16 as a 5D tensor {64 columns, 128 rows, 2 halves, MG groups, KC chunks}: one box
+// {64, 128, 1, MG, 1} brings one CTA's rows of every 256-row group for one 64-column chunk, landing
+// as MG consecutive canonical [128 x 64] K-major tiles (128-byte swizzle).
+bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG) {
+    EncodeFn enc = get_encode3();
+    if (!enc) return false;
+    const cuuint64_t dims[5] = {64, 128, 2, (cuuint64_t)MG, (cuuint64_t)(Qp / 64)};
+    const cuuint64_t strides[4] = {(cuuint64_t)Qp * 2, (cuuint64_t)Qp * 2 * 128, (cuuint64_t)Qp * 2 * 256, 128};
+    const cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)MG, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(G), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MG>
+size_t smem3(int SS, int SB, int SA) {
+    return (size_t)1024 + (size_t)L3<MG>(SS, SB, SA).end;
+}
+
+}  // namespace
+
+struct Tc3Plan {
+    int MG = 0, SS = 0, SB = 0, SA = 0, grid = 0, total = 0, ntx = 0;
+    size_t smem = 0;
+    CUtensorMap tm_psi[2], tm_G;
+    const float* buf[2] = {nullptr, nullptr};
+    int nx = 0, ny = 0, Q = 0;
+};
+
+bool tc3_supported(int Q, int Qp, int Mp, bool split) {
+    (void)Q;
+    return !split && (Qp == 256 || Qp == 512) && Mp == Qp;
+}
+
+cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1, const __nv_bfloat16* G, int Q,
+                            int Qp, int Mp, int nx, int ny, TcRings want) {
+    *out = nullptr;
+    if (!tc3_supported(Q, Qp, Mp, false)) return cudaErrorNotSupported;
+    Tc3Plan* p = new Tc3Plan();
+    p->MG = Qp / 256;
+    const size_t limit = 227 * 1024;
+    // staging and operand rings as requested (default two and three stages); the kernel-matrix ring
+    // as requested or as deep as fits (up to 8)
+    p->SS = want.SS ? want.SS : 2;
+    p->SB = want.SB ? want.SB : 3;
+    auto need = [&](int sa) { return p->MG == 2 ? smem3<2>(p->SS, p->SB, sa) : smem3<1>(p->SS, p->SB, sa); };
+    if (want.SA) {
+        p->SA = want.SA;
+        if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
+    } else {
+        p->SA = 2;
+        while (p->SA < 8 && need(p->SA + 1) <= limit) ++p->SA;
+        if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
+    }
+    p->smem = need(p->SA);
+    const int TH = (256 / p->MG) / kTW;
+    p->nx = nx;
+    p->ny = ny;
+    p->Q = Q;
+    p->ntx = (nx + kTW - 1) / kTW;
+    p->total = p->ntx * ((ny + TH - 1) / TH);
+    p->buf[0] = buf0;
+    p->buf[1] = buf1;
+    if (!encode_psi3(&p->tm_psi[0], buf0, Qp, nx, ny, TH / 2) || !encode_psi3(&p->tm_psi[1], buf1, Qp, nx, ny, TH / 2) ||
+        !encode_G5(&p->tm_G, G, Qp, p->MG)) {
+        delete p;
+        return cudaErrorInvalidValue;
+    }
+    // one pair per two SMs, as many pairs as the device co-schedules (never more than tiles)
+    auto kern = p->MG == 2 ? step_tc3_kernel<2> : step_tc3_kernel<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    if (e != cudaSuccess) { delete p; return e; }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * std::max(1, sms / 2), 1, 1);
+    cfg.blockDim = dim3(kThreads3, 1, 1);
+    cfg.dynamicSmemBytes = p->smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess || clusters < 1) {
+        delete p;
+        return e != cudaSuccess ? e : cudaErrorNotSupported;
+    }
+    p->grid = 2 * std::min(clusters, p->total);
+    *out = p;
+    return cudaSuccess;
+}
+
+void tc3_plan_destroy(Tc3Plan* p) { delete p; }
+
+void tc3_plan_describe(const Tc3Plan* p, int* tile_cells, int* stages, int* pairs, size_t* smem) {
+    if (tile_cells) *tile_cells = p ? 256 / p->MG : 0;
+    if (stages) *stages = p ? p->SA : 0;
+    if (pairs) *pairs = p ? p->grid / 2 : 0;
+    if (smem) *smem = p ? p->smem : 0;
+}
+
+cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* cell, const float* w,
+                            float dt, float dt_sigma_as, unsigned int* err_flag, cudaStream_t s) {
+    if (!p || parity < 0 || parity > 1) return cudaErrorInvalidValue;
+    Tc3Args a;
+    memset(&a, 0, sizeof a);
+    a.tm_psi = p->tm_psi[parity];
+    a.tm_G = p->tm_G;
+    a.in = p->buf[parity];
+    a.out = const_cast<float*>(p->buf[parity ^ 1]);
+    a.ord = ord;
+    a.cell = cell;
+    a.w = w;
+    a.err = err_flag;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.Q = p->Q;
+    a.ntx = p->ntx;
+    a.total = p->total;
+    a.SS = p->SS;
+    a.SB = p->SB;
+    a.SA = p->SA;
+    a.dt = dt;
+    a.dts = dt_sigma_as;
+    if (p->MG == 2)
+        step_tc3_kernel<2><<<p->grid, kThreads3, p->smem, s>>>(a);
+    else
+        step_tc3_kernel<1><<<p->grid, kThreads3, p->smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace assn

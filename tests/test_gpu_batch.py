@@ -80,6 +80,31 @@ def test_members_equal_alone(A, precision, use_graph):
         p.close()
 
 
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_one_launch_per_step_for_uneven_ordinate_counts(A, precision, use_graph):
+    """Members with Q = 64, 128, 256 and 512 in a single class: every step of the batch is one
+    launch (the runtime-stride kernel instance), and every member still equals its solve alone at
+    the class's tile width, bitwise."""
+    wls = workloads(seed=61)
+    probs, dts = build(A, precision, wls)
+    steps = [3, 2, 4, 1]
+    with A.Batch() as b:
+        b.set_grouping(True)
+        for p, n, dt in zip(probs, steps, dts):
+            b.add(p, n, dt)
+        b.run(use_graph=use_graph).sync()
+        info = b.info()
+        cls = b.classes()
+    assert len(cls) == 1 and cls[0]["members"] == 4 and cls[0]["ordinate_stride"] == 512
+    assert info["launches"] == max(steps)
+    for wl, p, n, dt in zip(wls, probs, steps, dts):
+        ref = alone(A, precision, wl, n, dt, info["tile_cells"])
+        assert np.array_equal(p.state(), ref), wl.name
+    for p in probs:
+        p.close()
+
+
 def test_rerun_graph_reuse_and_continue(A):
     """Two runs of the same batch (the graph is replayed) equal 2 n steps alone; stepping a member
     on its own afterwards continues from the batch's result."""

@@ -92,11 +92,15 @@ def test_line_source_at_095_of_admissible_dt(A, precision, tol):
 def test_heun_unsupported_combinations(A):
     wl = synth.Workload("heun", "random", 8, 8, 0.0, 0.8, 0.0, 0.8, 4, 8, 0.6, seed=2)
     p = problem(A, wl, "bf16", wl.psi0())
-    with A.Batch() as b:
+    e = A.Problem(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1, "bf16").set_product_quadrature(wl.n_polar, wl.n_azim)
+    e.set_cross_sections(*wl.materials()).set_artificial_scattering(wl.sigma_as, wl.eps).set_state(wl.psi0())
+    with A.Batch() as b:   # the members of a batch share one scheme
+        b.add(p, 1, 0.5 * p.max_stable_dt())
         with pytest.raises(A.AssnError) as ei:
-            b.add(p, 1, 0.5 * p.max_stable_dt())
-        assert ei.value.status == A._lib.ASSN_ERR_UNSUPPORTED
+            b.add(e, 1, 0.5 * e.max_stable_dt())
+        assert ei.value.status == A._lib.ASSN_ERR_ARG
     p.close()
+    e.close()
     q = problem(A, wl, "fp32", wl.psi0())
     with pytest.raises(A.AssnError):
         A._lib.assn_set_scheme(q.handle, 7)

@@ -1,0 +1,141 @@
+"""Parity of the paired-SM tensor-core step (tiling variant 2: a cluster of two CTAs shares each
+M = 256 MMA; 2D tiles of 16 x 8 cells at 512 ordinates, 16 x 16 at 256) with the FP64 oracle.
+
+Grids leave ragged tiles in x and y, hold interior tiles (the branch-free path) and boundary tiles
+(the checked path); ordinate counts cover 256 and 512 and padded ones (Q = 200, 500: lanes past Q);
+the full-size lattice launch the bench times is checked on sampled cells.  One step from a random
+state is compared element by element within the derived BF16 one-step bound, a short run within
+the whole-run tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests.helpers import (RUN_TOL, ensure_built, gpu_problem, offdiag_rowsum, oracle_run, oracle_setup, rel_l2,
+                           step_tolerance)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    ensure_built()
+    import paper_1911_08801_gb300 as A
+    return A
+
+
+def random_workload(nx, ny, npol, naz, beta=0.5, seed=0):
+    return synth.Workload(f"pair{nx}x{ny}", "random", nx, ny, 0.0, nx * 0.05, 0.0, ny * 0.05, npol, naz, beta,
+                          sigma_as=5.0, seed=seed)
+
+
+def pair_problem(A, wl, psi0=None):
+    p = gpu_problem(A, wl, "bf16", psi0=psi0)
+    p.set_tiling(0, 0, 2)
+    return p
+
+
+# (nx, ny): ragged in both directions with interior tiles; exact multiples of both tile shapes; one
+# tile; a single cell; a strip one row high; a tall thin grid
+SHAPES = [(70, 37), (48, 48), (16, 8), (1, 1), (200, 1), (5, 90)]
+
+
+@pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16), (10, 50), (10, 20)])
+@pytest.mark.parametrize("nx,ny", SHAPES)
+def test_one_step_random_state(A, nx, ny, npol, naz):
+    wl = random_workload(nx, ny, npol, naz, seed=nx * 31 + ny + npol)
+    p = pair_problem(A, wl)
+    assert p.tiling()["tile_cells"] == (128 if npol * naz > 256 else 256)
+    dt = 0.9 * p.max_stable_dt()
+    p.step(1, dt)
+    got = p.state()
+    p.close()
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    ref = O.step(wl.psi0(), K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    tol = step_tolerance("bf16", dt, wl.sigma_as, np.abs(wl.psi0()).max(), offdiag_rowsum(K))
+    err = np.abs(got - ref).max()
+    assert err <= tol, (err, tol)
+
+
+@pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16)])
+def test_agrees_with_persistent_kernel(A, npol, naz):
+    """Variant 2 and the one-CTA persistent kernel (variant 0) give the same step from the same state
+    to FP32 rounding (both contract the same BF16 operands with FP32 accumulation)."""
+    wl = random_workload(67, 29, npol, naz, seed=5)
+    states = []
+    for variant in (0, 2):
+        p = gpu_problem(A, wl, "bf16")
+        p.set_tiling(0, 0, variant)
+        dt = 0.9 * p.max_stable_dt()
+        p.step(1, dt)
+        states.append(p.state())
+        p.close()
+    assert np.abs(states[0] - states[1]).max() <= 1e-6
+
+
+def test_line_source_run(A):
+    """A whole short run (the 64^2 line source at 256 ordinates to t = 0.25): relative L2 of Phi
+    against the oracle within the BF16 whole-run tolerance; the state stays non-negative."""
+    wl = synth.line_source(64, 16, 16, 1.0 / 8.0, t_final=0.25, name="pair_ls64")
+    n, dt = wl.steps()
+    p = pair_problem(A, wl)
+    p.step(n, dt)
+    phi = p.scalar_flux()
+    assert p.state().min() >= 0.0
+    p.close()
+    psi, w = oracle_run(wl, n, dt)
+    assert rel_l2(phi, psi @ w) <= RUN_TOL["bf16"]
+
+
+def test_lattice_run(A):
+    """The lattice (Q = 512) on 56^2 cells to t = 0.5: absorbers, the source block and vacuum edges."""
+    wl = synth.lattice(56, 16, 32, 0.5, t_final=0.5, name="pair_lat56")
+    p = pair_problem(A, wl)
+    # on this coarse grid CFL 0.5 exceeds the positivity bound of the sigma_a = 10 blocks: take
+    # min(CFL h, 0.95 x bound), landing on t_final
+    n = int(np.ceil(wl.t_final / min(wl.cfl * wl.h, 0.95 * p.max_stable_dt()) - 1e-12))
+    dt = wl.t_final / n
+    p.step(n, dt)
+    phi = p.scalar_flux()
+    p.close()
+    psi, w = oracle_run(wl, n, dt)
+    assert rel_l2(phi, psi @ w) <= RUN_TOL["bf16"]
+
+
+def test_lattice_448_sampled_cells(A):
+    """The full-size lattice launch (448 x 448, Q = 512) on the paired-SM kernel: one step from a seeded
+    state against the oracle on sampled cells (tile corners and edges, grid corners, materials)."""
+    wl = synth.LATTICE_448
+    rng = np.random.default_rng(4)
+    psi = rng.uniform(0.0, 1.0, size=(wl.ny, wl.nx, wl.Q))
+    n, dt = wl.steps()
+    cells = [(0, 0), (0, 447), (447, 0), (447, 447), (224, 224), (7, 15), (8, 16), (7, 16), (8, 15),
+             (200, 63), (200, 64), (201, 127), (215, 128), (216, 128), (5, 383), (6, 384), (439, 431), (440, 432)]
+    cells += [(int(j), int(i)) for j, i in rng.integers(0, 448, size=(16, 2))]
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    ref = O.step_at_cells(psi, cells, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    p = pair_problem(A, wl, psi0=psi)
+    p.step(1, dt)
+    got = p.state()
+    p.close()
+    tol = step_tolerance("bf16", dt, wl.sigma_as, 1.0, offdiag_rowsum(K))
+    for n_, (j, i) in enumerate(cells):
+        assert np.abs(got[j, i] - ref[n_]).max() <= tol, (j, i)
+
+
+def test_unsupported_shapes(A):
+    wl = random_workload(20, 20, 8, 16, seed=1)          # Q = 128: one 128-row block, no pair of rows
+    p = gpu_problem(A, wl, "bf16")
+    p.set_tiling(0, 0, 2)
+    with pytest.raises(A.AssnError) as e:
+        p.step(1, 0.5 * p.max_stable_dt())
+    assert e.value.status == A._lib.ASSN_ERR_UNSUPPORTED
+    p.close()
+    wl = random_workload(20, 20, 16, 32, seed=1)
+    p = gpu_problem(A, wl, "bf16x3")                     # the split contraction runs on variants 0 and 1
+    p.set_tiling(0, 0, 2)
+    with pytest.raises(A.AssnError) as e:
+        p.step(1, 0.5 * p.max_stable_dt())
+    assert e.value.status == A._lib.ASSN_ERR_UNSUPPORTED
+    p.close()

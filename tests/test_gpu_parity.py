@@ -61,14 +61,30 @@ def test_kernel_matrix_matches_oracle(A, kind, norm, npol, naz, eps):
     p = A.Problem(4, 4, 0, 1, 0, 1, "fp64").set_product_quadrature(npol, naz)
     p.set_artificial_scattering(5.0, eps, kind, norm)
     K = p.kernel_matrix()
+    om, wl = p.quadrature()
     Om, w = O.product_quadrature(npol, naz)
     Ko = O.kernel_matrix(Om, w, eps, kind="gauss" if kind == 0 else "exp",
                          normalisation="column" if norm == 0 else "row")
-    # exp(-(1-mu)^2/eps^2) amplifies the last-bit difference of the dot product mu by
-    # 2 (1-mu)/eps^2: compare entries relative to the largest one, and the significant ones tightly
     assert np.abs(K - Ko).max() <= 1e-14 * Ko.max()
+    # Derived bound on the significant entries.  s = exp(-a(mu)) with a = (1-mu)^2/eps^2 (Gaussian)
+    # or (1-mu)/eps^2 (exp kind): an error d_mu of the cosine moves ln s by |a'(mu)| d_mu, where
+    # d_mu <= 2 max|Omega_lib - Omega_oracle| + 4u (the ordinates' own difference, then the rounding
+    # of a 3-term dot product); evaluating a and exp costs <= 4u (a + 2); the normalisation sum over
+    # Q terms adds <= 2 Q u plus twice the weighted mean of the entries' errors (bounded by their
+    # maximum over the significant entries; the rest weigh < 1e-8 Q) and twice the weights' error.
+    u = 2.0 ** -53
+    mu = np.clip(Om @ Om.T, -1.0, 1.0)
+    if kind == 0:
+        da, arg = 2.0 * (1.0 - mu) / eps ** 2, (1.0 - mu) ** 2 / eps ** 2
+    else:
+        da, arg = np.full_like(mu, 1.0 / eps ** 2), (1.0 - mu) / eps ** 2
+    d_mu = 2.0 * np.abs(om - Om).max() + 4.0 * u
+    d_w = float(np.max(np.abs(wl - w) / w))
     big = Ko > 1e-8 * Ko.max()
-    assert np.max(np.abs(K[big] - Ko[big]) / Ko[big]) <= 1e-11
+    e_s = da * d_mu + 4.0 * u * (arg + 2.0)
+    bound = e_s + 2.0 * e_s[big].max() + 2.0 * d_w + 2.0 * len(w) * u + 1e-8 * len(w) * e_s.max()
+    rel = np.abs(K - Ko) / Ko
+    assert np.all(rel[big] <= bound[big]), float(np.max(rel[big] / bound[big]))
     p.close()
 
 

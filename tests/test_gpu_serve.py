@@ -85,14 +85,17 @@ def alone_phi(A, wl, nsteps, dt, precision="bf16"):
 
 @pytest.mark.parametrize("chunk,use_graph", [(4, True), (3, False)])
 def test_mix_equals_alone(A, chunk, use_graph):
-    wls = request_workloads()
+    # A long first request (tens of chunks) keeps the device busy while the rest are submitted, so
+    # the others join it in shared launches: the results below are checked in the mix, not alone.
+    wls = [synth.line_source(40, 16, 32, 0.5, t_final=2.0, name="lead")] + request_workloads()
     plan = [steps_for(A, wl) for wl in wls]
+    assert plan[0][0] >= 10 * chunk
     with A.Server("bf16", max_active=5, chunk_steps=chunk, use_graph=use_graph) as srv:
         ids = [submit(srv, wl, n, dt) for wl, (n, dt) in zip(wls, plan)]
         results = [srv.wait(i, timeout_s=120.0) for i in ids]
         st = srv.stats()
     assert st["completed"] == len(wls) and st["failed"] == 0
-    assert 1 <= st["max_active_seen"] <= 5
+    assert 2 <= st["max_active_seen"] <= 5
     assert st["p50_latency_s"] <= st["p99_latency_s"]
     assert st["updates"] == sum(wl.nx * wl.ny * wl.Q * n for wl, (n, _) in zip(wls, plan))
     for wl, (n, dt), (phi, lat, qs) in zip(wls, plan, results):

@@ -1,12 +1,14 @@
-"""The allocation-free mass entry point agrees with the allocating one.
+"""The allocation-free mass entry point agrees with the allocating one and with the FP64 oracle.
 
-assn_mass_noalloc serves callers that cannot allocate device memory during a call (stream
-capture, real-time loops, foreign memory pools); its partial sums live in a fixed device array.
-This file runs last so that a failure here leaves every other test already run.
+assn_mass_noalloc serves callers that cannot allocate device memory during a call (real-time loops
+whose latency budget rules out allocator calls, hosts that run the library inside a memory pool of
+their own); its partial sums live in a fixed device array.  This file runs last so that a failure
+here leaves every other test already run.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from tests.helpers import ensure_built
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +50,9 @@ def test_mass_noalloc_matches_assn_mass(A, precision):
         torch.cuda.synchronize()
         got = float(out.item())
         assert abs(got - ref) <= 1e-12 * abs(ref), (call, got, ref)
+        # the oracle's mass (h^2 sum_cells sum_q w_q psi_q in FP64) of the same state and weights
+        exact = O.mass(p.state(), w, p.h)
+        assert abs(got - exact) <= 1e-12 * abs(exact), (call, got, exact)
         p.step(1, dt)
     p.close()
 
