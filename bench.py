@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile", type=int, default=0, help="tensor-core tile cells (0 = automatic)")
     ap.add_argument("--stages", type=int, default=0, help="tensor-core kernel-matrix ring depth (0 = automatic)")
-    ap.add_argument("--variant", type=int, default=0,
-                    help="tensor-core kernel: 0 persistent, 1 one tile per CTA, 2 paired-SM (cta_group::2)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="tensor-core kernel: -1 automatic, 0 persistent, 1 one tile per CTA, 2 paired-SM (cta_group::2)")
     ap.add_argument("--ref-dir", default="", help="accuracy: directory of oracle scalar fluxes <workload>.npy "
                                                   "(written by --mode oracle-phi); missing ones are computed")
     ap.add_argument("--mode", default="step",
@@ -69,16 +69,22 @@ def parse():
     return ap.parse_args()
 
 
-def kernel_traffic(precision: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source still matches."""
+KERNEL_SOURCES = {"step_tc2_kernel": ("step_tc2.cu", "tc_ptx.h"), "step_tc3_kernel": ("step_tc3.cu", "tc_ptx.h")}
+
+
+def kernel_profile(kernel: str, precision: str, workload: str):
+    """The committed ncu figures of `kernel` (profiles/traffic.json) if its source still matches the
+    hash they were taken at, for this precision and workload: DRAM bytes per launch, tensor-pipe
+    active %.  None when absent or stale."""
     import hashlib
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["step_tc2_kernel"]
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         src = b"".join(open(os.path.join(ROOT, "paper_1911_08801_gb300", "csrc", f), "rb").read()
-                       for f in ("step_tc2.cu", "tc_ptx.h"))
-        if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"] or precision != d["precision"]:
+                       for f in KERNEL_SOURCES[kernel])
+        if (hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"] or precision != d["precision"]
+                or workload != d["workload"]):
             return None
-        return d["dram_bytes_per_launch"]
+        return d
     except Exception:
         return None
 
@@ -90,6 +96,14 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s): the measured burst figure, else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 class ClockSampler:
@@ -273,10 +287,11 @@ def run_ours(args, rank, world, dist):
         dt = wl.t_final / math.ceil(wl.t_final / (0.95 * prob.max_stable_dt()))
     else:
         _, dt = wl.steps()
-    tiling = None
+    tiling, variant = None, None
     if args.precision.startswith("bf16"):
         prob.set_tiling(args.tile, args.stages, args.variant)
         tiling = prob.tiling()
+        variant = prob.variant()
     psi0 = torch.from_numpy(seeded_state_f32(wl, seed=rank)).pin_memory().numpy()
     if args.precision == "fp64":
         prob.set_state(psi0.astype(np.float64))
@@ -357,12 +372,7 @@ def run_ours(args, rank, world, dist):
                           "L2 flushed before every timed step (256 MB write; state %.0f MB per buffer)"
                           % (state_bytes / 2e6)),
                    "parallelism": f"replicas x{world}", "tiling": tiling},
-        "roofline": ({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm,
-                     "traffic": kernel_traffic(args.precision) if args.variant == 0 and args.workload == synth.LATTICE_448.name else None,
-                     "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision],
-                     "kernel": {0: "step_tc2_kernel", 1: "step_tc_kernel", 2: "step_tc3_kernel"}[args.variant]
-                     if args.precision.startswith("bf16") else "step_simt_kernel"} if args.scheme == "euler" else
+        "roofline": (euler_roofline(args, wl, ms_per_step, achieved, hbm, src, variant) if args.scheme == "euler" else
                      implicit_roofline(args, wl, ms_per_step, stats_timed, args.steps)
                      if args.scheme == "implicit" else
                      (heun_tc_roofline(wl, ms_per_step) if args.precision.startswith("bf16")
@@ -374,6 +384,29 @@ def run_ours(args, rank, world, dist):
     line.update(extras)
     prob.close()
     return line
+
+
+def euler_roofline(args, wl, ms_per_step, achieved, hbm, src, variant):
+    """HBM roofline of the forward-Euler step (8 B per update in FP32 state) and, for the tensor-core
+    kernels, the dense contraction's rate against the BF16 peak beside the ceiling the HBM bound puts
+    on it (2 Qp flops per 8 B: Qp / 4 flop per byte)."""
+    kernel = ({0: "step_tc2_kernel", 1: "step_tc_kernel", 2: "step_tc3_kernel"}[variant]
+              if args.precision.startswith("bf16") else "step_simt_kernel")
+    prof = kernel_profile(kernel, args.precision, wl.name) if kernel in KERNEL_SOURCES else None
+    out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+           "traffic": prof["dram_bytes_per_launch"] if prof else None,
+           "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision], "kernel": kernel}
+    if args.precision.startswith("bf16"):
+        qp = (wl.Q + 63) // 64 * 64
+        mp = (wl.Q + 127) // 128 * 128
+        flops = 2.0 * mp * qp * wl.nx * wl.ny * (3 if args.precision == "bf16x3" else 1)
+        tf, tsrc = bf16_peak()
+        ach = flops / (ms_per_step / 1e3) / 1e12
+        out["tensor"] = {"achieved_tflops": ach, "peak_tflops": tf, "frac": ach / tf, "peak_source": f"{tsrc} bf16_tflops",
+                         "flops_per_step": flops,
+                         "ceiling_frac_at_hbm_roofline": (hbm * 1e9 / 8.0) * (flops / (wl.nx * wl.ny * wl.Q)) / (tf * 1e12),
+                         "pipe_active_pct_ncu": prof.get("tensor_pipe_active_pct") if prof else None}
+    return out
 
 
 def extras_legs(A, L, torch, wl, args, prob, psi0, stream, dt):

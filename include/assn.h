@@ -252,12 +252,13 @@ int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev,
  * [ny][nx] in FP64.  Syncs.  FP32/BF16/BF16X3 problems only (ASSN_ERR_UNSUPPORTED on FP64). */
 int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt, double* phi_host);
 
-/* Tensor-core kernel and tiling (BF16 / BF16X3 problems).  variant 0 (default): persistent
- * warp-specialised kernel, one CTA per SM, TMA-fed rings and two TMEM accumulator buffers;
- * variant 1: one tile per CTA (simpler, slower); variant 2: paired-SM kernel, a cluster of two
- * CTAs sharing each M = 256 contraction (cta_group::2) over 2D tiles of 16 x 8 (512 ordinates) or
- * 16 x 16 cells (256), forward Euler in BF16 with 193..256 or 449..512 ordinates (else
- * ASSN_ERR_UNSUPPORTED at the next step; tile_cells is fixed by the ordinate count).  tile_cells: cells per tile (32, 64, 128 or 256;
+/* Tensor-core kernel and tiling (BF16 / BF16X3 problems).  variant -1 (the initial value):
+ * automatic, variant 2 where it applies, else variant 0.  variant 0: persistent warp-specialised
+ * kernel, one CTA per SM, TMA-fed rings and two TMEM accumulator buffers; variant 1: one tile per
+ * CTA (simpler, slower); variant 2: paired-SM kernel, a cluster of two CTAs sharing each M = 256
+ * contraction (cta_group::2) over 2D tiles of 16 x 8 (512 ordinates) or 16 x 16 cells (256),
+ * forward Euler in BF16 with 193..256 or 449..512 ordinates (else ASSN_ERR_UNSUPPORTED at the next
+ * step; tile_cells is fixed by the ordinate count).  tile_cells: cells per tile (32, 64, 128 or 256;
  * 0 = automatic).  stages: ring depth (2..8; 0 = automatic).  Takes effect at the next step; the
  * results do not depend on these choices.  ASSN_ERR_UNSUPPORTED at the next step if the
  * combination does not fit the SM. */
@@ -267,7 +268,7 @@ int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant);
  * ring (FP32 flux chunks fed by TMA), the operand ring (BF16 chunks written by the converter warps)
  * and the kernel-matrix ring (2..8 each; 0 = automatic), and the ordinate blocks of 128 that one
  * kernel-matrix request brings (1, 2, 4, 8; 0 = automatic; variant 0 only).  Results do not depend
- * on these choices.  Selects variant 0 unless variant 2 is set.  get_rings reports the resolved values (any pointer may be NULL);
+ * on these choices.  Selects variant 0 unless variant 2 was set explicitly.  get_rings reports the resolved values (any pointer may be NULL);
  * ASSN_ERR_UNSUPPORTED at the next step / get if the rings do not fit shared memory. */
 int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix, int blocks_per_request);
 int assn_get_rings(assn_problem* p, int* staging, int* operand, int* kernel_matrix, int* blocks_per_request);
@@ -275,6 +276,11 @@ int assn_get_rings(assn_problem* p, int* staging, int* operand, int* kernel_matr
 /* The tiling the next step will use (resolving automatic choices): tile cells, ring stages,
  * tensor-memory columns and dynamic shared memory per CTA.  Any output pointer may be NULL. */
 int assn_get_tiling(assn_problem* p, int* tile_cells, int* stages, int* tmem_cols, int64_t* smem_bytes);
+
+/* The tensor-core variant (0, 1 or 2) the next step of p runs, resolving the automatic choice.
+ * Requires quadrature, cross sections and K (else ASSN_ERR_STATE); ASSN_ERR_UNSUPPORTED for the
+ * CUDA-core precisions. */
+int assn_get_variant(assn_problem* p, int* variant);
 
 /* Device layout of the state: *Qpad = padded ordinate stride, *elem_bytes = 4 or 8. */
 int assn_layout(const assn_problem* p, int* Qpad, int* elem_bytes);

@@ -127,6 +127,10 @@ class Problem:
     def tiling(self) -> dict:
         return _lib.assn_get_tiling(self.handle)
 
+    def variant(self) -> int:
+        """The tensor-core kernel the next step runs (0, 1 or 2; the automatic choice resolved)."""
+        return _lib.assn_get_variant(self.handle)
+
     def set_rings(self, staging: int = 0, operand: int = 0, kernel_matrix: int = 0, blocks_per_request: int = 0):
         _lib.assn_set_rings(self.handle, staging, operand, kernel_matrix, blocks_per_request)
         return self

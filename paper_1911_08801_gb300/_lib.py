@@ -95,6 +95,7 @@ SIGNATURES = {
                                  C.POINTER(C.c_int)]),
     "assn_get_tiling": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int64)]),
+    "assn_get_variant": (C.c_int, [_h, C.POINTER(C.c_int)]),
     "assn_layout": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "assn_state_device": (C.c_int, [_h, C.POINTER(_vp)]),
     "assn_scalar_flux": (C.c_int, [_h, _dp]),
@@ -340,6 +341,12 @@ def assn_get_tiling(h: int) -> dict:
     t, s, c, m = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int64(0)
     _check(lib.assn_get_tiling(h, C.byref(t), C.byref(s), C.byref(c), C.byref(m)), h)
     return {"tile_cells": t.value, "stages": s.value, "tmem_cols": c.value, "smem_bytes": m.value}
+
+
+def assn_get_variant(h: int) -> int:
+    v = C.c_int(0)
+    _check(lib.assn_get_variant(h, C.byref(v)), h)
+    return v.value
 
 
 def assn_layout(h: int):

@@ -574,6 +574,14 @@ int assn_max_stable_dt(assn_problem* p, double* dt_out) {
     return ASSN_OK;
 }
 
+// The tensor-core kernel a step of p runs: the requested variant, or (automatic, -1) the paired-SM
+// kernel where it applies (forward Euler, BF16, 193..256 or 449..512 ordinates), else variant 0.
+static int eff_variant(const assn_problem* p) {
+    if (p->variant >= 0) return p->variant;
+    return (p->scheme == ASSN_SCHEME_EULER_UPWIND &&
+            tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision == ASSN_BF16X3)) ? 2 : 0;
+}
+
 static int step_once(assn_problem* p, const void* in, void* out, double dt) {
     if (p->precision == ASSN_FP64) {
         StepArgs<double, OrdD, CellD> a{(const double*)in, (double*)out, (const OrdD*)p->d_ord,
@@ -589,10 +597,11 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
         } else {
             const bool own = in == p->d_psi[p->cur] && out == p->d_psi[p->cur ^ 1];
             cudaError_t e;
-            if (p->variant == 2 && own) {
+            const int v = eff_variant(p);
+            if (v == 2 && own) {
                 e = launch_step_tc3(p->plan3, p->cur, (const OrdF*)p->d_ord, (const CellF*)p->d_cell, p->d_w32,
                                     (float)dt, (float)(dt * p->sigma_as), p->d_flags + 1, p->stream);
-            } else if (p->variant == 0 && own) {
+            } else if (v == 0 && own) {
                 // the persistent kernel takes its buffer parity from the device step counter
                 if ((p->counter_host & 1) != p->cur) {
                     p->counter_host = p->cur;
@@ -614,17 +623,18 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
 
 static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
     cudaError_t e = cudaSuccess;
-    if ((p->variant == 1 || need_v1) && !p->plan)
+    const int v = eff_variant(p);
+    if ((v == 1 || need_v1) && !p->plan)
         e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
                            p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
-    if (e == cudaSuccess && p->variant == 0 && (!p->plan2 || p->plan2_dt != dt)) {
+    if (e == cudaSuccess && v == 0 && (!p->plan2 || p->plan2_dt != dt)) {
         if (p->plan2) tc2_plan_destroy(p->plan2);
         p->plan2 = nullptr;
         const Tc2Problem d = problem_tc2(p, dt, 0x7fffffff);
         e = tc2_plan_create(&p->plan2, &d, 1, p->precision == ASSN_BF16X3, p->want_nt, p->want_rings);
         if (e == cudaSuccess) p->plan2_dt = dt;
     }
-    if (e == cudaSuccess && p->variant == 2 && !p->plan3) {
+    if (e == cudaSuccess && v == 2 && !p->plan3) {
         if (!tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision == ASSN_BF16X3))
             return fail(p, ASSN_ERR_UNSUPPORTED,
                         "paired-SM step (variant 2): BF16 with 193..256 or 449..512 ordinates only (Q = %d)", p->Q);
@@ -728,7 +738,7 @@ int assn_step(assn_problem* p, int nsteps, double dt) {
         int r = assn::problem_prepare(p, dt);
         if (r) return r;
         if (p->tensor()) {
-            if (p->variant != 0)
+            if (eff_variant(p) != 0)
                 return fail(p, ASSN_ERR_UNSUPPORTED, "the Heun + minmod scheme runs on the persistent kernel (variant 0)");
             r = ensure_plan(p, dt, false);
             if (r) return r;
@@ -768,7 +778,7 @@ int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant) {
     if (tile_cells != 0 && tile_cells != 32 && tile_cells != 64 && tile_cells != 128 && tile_cells != 256)
         return fail(p, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64, 128 or 256");
     if (stages != 0 && (stages < 2 || stages > 8)) return fail(p, ASSN_ERR_ARG, "stages must be 0 or 2..8");
-    if (variant < 0 || variant > 2) return fail(p, ASSN_ERR_ARG, "variant must be 0, 1 or 2");
+    if (variant < -1 || variant > 2) return fail(p, ASSN_ERR_ARG, "variant must be -1 (automatic), 0, 1 or 2");
     p->want_nt = tile_cells;
     p->want_stages = stages;
     p->want_rings = TcRings{stages, stages, stages, 0};
@@ -791,7 +801,7 @@ int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix,
         blocks_per_request != 8)
         return fail(p, ASSN_ERR_ARG, "blocks_per_request must be 0, 1, 2, 4 or 8");
     p->want_rings = TcRings{staging, operand, kernel_matrix, blocks_per_request};
-    if (p->variant == 1) p->variant = 0;
+    if (p->variant != 2) p->variant = 0;
     if (p->plan2) tc2_plan_destroy(p->plan2);
     p->plan2 = nullptr;
     if (p->plan3) tc3_plan_destroy(p->plan3);
@@ -807,11 +817,12 @@ int assn_get_rings(assn_problem* p, int* staging, int* operand, int* kernel_matr
     r = set_device(p);
     if (r) return r;
     const int v = p->variant;
-    p->variant = 0;
+    const bool pair = eff_variant(p) == 2;
+    if (!pair) p->variant = 0;
     r = ensure_plan(p, p->plan2_dt > 0 ? p->plan2_dt : 1.0, false);
     p->variant = v;
     if (r) return r;
-    const TcRings g = tc2_plan_rings(p->plan2);
+    const TcRings g = pair ? tc3_plan_rings(p->plan3) : tc2_plan_rings(p->plan2);
     if (staging) *staging = g.SS;
     if (operand) *operand = g.SB;
     if (kernel_matrix) *kernel_matrix = g.SA;
@@ -829,15 +840,25 @@ int assn_get_tiling(assn_problem* p, int* tile_cells, int* stages, int* tmem_col
     r = ensure_plan(p, p->plan2_dt > 0 ? p->plan2_dt : 1.0, false);
     if (r) return r;
     size_t sm = 0;
-    if (p->variant == 1) {
+    const int v = eff_variant(p);
+    if (v == 1) {
         tc_plan_describe(p->plan, tile_cells, stages, tmem_cols, &sm);
-    } else if (p->variant == 2) {
+    } else if (v == 2) {
         tc3_plan_describe(p->plan3, tile_cells, stages, nullptr, &sm);
         if (tmem_cols) *tmem_cols = 512;
     } else {
         tc2_plan_describe(p->plan2, tile_cells, stages, tmem_cols, &sm);
     }
     if (smem_bytes) *smem_bytes = (int64_t)sm;
+    return ASSN_OK;
+}
+
+int assn_get_variant(assn_problem* p, int* variant) {
+    if (!p || !variant) return ASSN_ERR_ARG;
+    if (!p->tensor()) return fail(p, ASSN_ERR_UNSUPPORTED, "variants apply to the tensor-core precisions");
+    int r = ready(p);
+    if (r) return r;
+    *variant = eff_variant(p);
     return ASSN_OK;
 }
 

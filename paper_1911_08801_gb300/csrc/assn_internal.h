@@ -123,6 +123,7 @@ bool tc3_supported(int Q, int Qp, int Mp, bool split);
 cudaError_t tc3_plan_create(Tc3Plan** plan, const float* buf0, const float* buf1, const __nv_bfloat16* G, int Q,
                             int Qp, int Mp, int nx, int ny, TcRings want);
 void tc3_plan_destroy(Tc3Plan* plan);
+TcRings tc3_plan_rings(const Tc3Plan* plan);   // MPR = 128-row blocks per kernel-matrix request
 // tile cells, kernel-matrix ring depth, CTA pairs launched, dynamic shared memory per CTA
 void tc3_plan_describe(const Tc3Plan* plan, int* tile_cells, int* stages, int* pairs, size_t* smem);
 // Reads buffer `parity`, writes buffer parity ^ 1.

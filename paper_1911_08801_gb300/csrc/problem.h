@@ -42,7 +42,7 @@ struct assn_problem {
     assn::TcPlan* plan = nullptr;      // one-tile-per-CTA tensor-core kernel (variant 1)
     assn::Tc2Plan* plan2 = nullptr;    // persistent warp-specialised kernel (variant 0, default)
     assn::Tc3Plan* plan3 = nullptr;    // paired-SM kernel (variant 2)
-    int variant = 0;
+    int variant = -1;                  // -1: automatic (2 where it applies, else 0)
     double* d_e = nullptr;
     void* d_ord = nullptr;
     double ord_dt = -1.0;

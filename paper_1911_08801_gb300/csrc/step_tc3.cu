@@ -11,15 +11,15 @@
 // the operand rows of half the tile's cells (rows 0 .. TH/2-1 in the even CTA).  Each SM thus
 // loads half of G per tile and supplies half the operand bytes of every MMA.
 //
-// Roles in each CTA (20 warps):
+// Roles in each CTA (20 warps: 96 registers per thread):
 //   warp 0      TMEM (both CTAs allocate the pair's 512 columns collectively); lane 0 of the even
 //               CTA issues the MMAs into one of two accumulator buffers and commits to the
 //               barriers of both CTAs; lane 0 of the odd CTA forwards the completion of its own
 //               kernel-matrix copies to the even CTA.
-//   warp 1      lane 0: TMA of this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64 ordinates]
-//               chunks, into a staging ring; lane 1: TMA of this CTA's G rows ([128 x 64] BF16
-//               blocks with 128-byte swizzle, all of its 256-row groups per request).
-//   warps 2-3   converters: staging -> BF16 operand rows (K-major, swizzled) for the pair's MMA;
+//               Lanes 1 and 2: TMA of this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64
+//               ordinates] chunks, into a staging ring, and of this CTA's G rows ([128 x 64] BF16
+//               blocks with 128-byte swizzle, all of its 256-row groups and two chunks per request).
+//   warps 1-3   converters: staging -> BF16 operand rows (K-major, swizzled) for the pair's MMA;
 //               the scalar flux Phi = sum_p w_p psi_p of this CTA's cells, and from it the cells'
 //               coefficients, written into both CTAs.
 //   warps 4-19  epilogue: warp (lane quarter lq, group g) owns 32 ordinates of one 128-row block
@@ -47,15 +47,16 @@ namespace {
 using namespace ptx;
 
 constexpr int kTW = 16;                 // tile width (cells)
-constexpr int kConv3 = 2;               // converter warps
-constexpr int kEpi3 = 16;               // epilogue warps
-constexpr int kEpi0 = 4;                // first epilogue warp (a multiple of 4: lane quarter = warp & 3)
+constexpr int kConv3 = 3;               // converter warps (1 .. 3)
+constexpr int kEpi3 = 16;               // epilogue warps (4 .. 19; any four consecutive warps cover the
+                                        // four TMEM lane quarters, warp & 3)
+constexpr int kEpi0 = 1 + kConv3;       // first epilogue warp
 constexpr int kThreads3 = (kEpi0 + kEpi3) * 32;
 constexpr int kABlock = 128 * 64 * 2;   // one [128 x 64] BF16 block of G
 
 struct Tc3Args {
     CUtensorMap tm_psi;                 // input flux [ny][nx][Qp] FP32, box {64, TW, TH/2}
-    CUtensorMap tm_G;                   // G [Mp][Qp] BF16 as {64, 128, 2, MG, KC}, box {64, 128, 1, MG, 1}
+    CUtensorMap tm_G;                   // G [Mp][Qp] BF16 as {64, 128, 2, MG, KC}, box {64, 128, 1, MG, CPS}
     const float* in;
     float* out;
     const OrdF* ord;                    // [Qp]
@@ -75,22 +76,25 @@ struct L3 {
     static constexpr int NTc = NT / 2;          // cells per CTA
     static constexpr int QP = 256 * MG;         // ordinate stride
     static constexpr int KC = QP / 64;          // 64-ordinate chunks
-    static constexpr int kStg = NTc * 256;      // FP32 staging stage
-    static constexpr int kB = NTc * 128;        // BF16 operand stage
-    static constexpr int kA = MG * kABlock;     // G stage (all of this CTA's blocks of one chunk)
-    int stg, b, a, cx, cy, cb, cst, bars, end;
+    static constexpr int CPS = 2;               // chunks per operand / kernel-matrix stage (one MMA round)
+    static constexpr int KR = KC / CPS;         // MMA rounds per tile
+    static constexpr int kStg = NTc * 256;      // FP32 staging stage (one chunk)
+    static constexpr int kB = CPS * NTc * 128;  // BF16 operand stage
+    static constexpr int kA = CPS * MG * kABlock;   // G stage: this CTA's blocks of CPS chunks
+    int stg, b, a, cx, cy, cb, cst, wsm, bars, end;
     __host__ __device__ L3(int SS, int SB, int SA) {
         stg = 0;
         b = stg + SS * kStg;
         a = b + SB * kB;
-        cx = a + SA * kA;                       // [2][NT] 1 - dt sigma_t
+        cx = a + SB * kA;                       // [2][NT] 1 - dt sigma_t (kernel-matrix ring: SB stages too)
         cy = cx + 2 * NT * 4;                   // [2][NT] dt (sigma_s Phi / sum w + q)
         cb = cy + 2 * NT * 4;                   // [2][NT] neighbour bits
         cst = cb + 2 * NT * 4;                  // [NTc] cell constants of this CTA's cells
-        bars = cst + NTc * 16;
-        // stg full/empty [SS], b full/empty [SB], a full/pair/empty [SA], tm full/empty [2],
-        // phi full/empty [2], drain
-        end = bars + 8 * (2 * SS + 2 * SB + 3 * SA + 9) + 16;
+        wsm = cst + NTc * 16;                   // [QP] quadrature weights
+        bars = wsm + QP * 4;
+        // stg full/empty [SS], stage full/pair/empty [SB] (operand and kernel-matrix rings advance
+        // together, SA == SB), tm full/empty [2], phi full/empty [2], drain
+        end = bars + 8 * (2 * SS + 3 * SB + 9) + 16;
     }
 };
 
@@ -107,6 +111,7 @@ struct Ring3 {
 #define W3C(bar, parity, code) \
     (mbar_try_wait_cl((bar), (parity)) || mbar_wait_cl((bar), (parity), abort_flag, a.err, (code)))
 
+
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 template <int MG>
@@ -114,6 +119,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
 step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     using LT = L3<MG>;
     constexpr int NT = LT::NT, TH = LT::TH, THc = LT::THc, NTc = LT::NTc, QP = LT::QP, KC = LT::KC;
+    constexpr int CPS = LT::CPS, KR = LT::KR;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const LT L(a.SS, a.SB, a.SA);
@@ -124,15 +130,17 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     float* cy = reinterpret_cast<float*>(base + L.cy);
     int* cb = reinterpret_cast<int*>(base + L.cb);
     CellF* cst = reinterpret_cast<CellF*>(base + L.cst);
+    float4* wsm = reinterpret_cast<float4*>(base + L.wsm);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* stg_full = bars;
     uint64_t* stg_empty = stg_full + a.SS;
-    uint64_t* b_full = stg_empty + a.SS;
-    uint64_t* b_empty = b_full + a.SB;
-    uint64_t* a_full = b_empty + a.SB;
-    uint64_t* a_pair = a_full + a.SA;
-    uint64_t* a_empty = a_pair + a.SA;
-    uint64_t* tm_full = a_empty + a.SA;
+    // one stage of the operand ring and of the kernel-matrix ring share a barrier set: full
+    // (this CTA's converter warps arrive, the kernel-matrix copy completes its bytes), pair (the odd
+    // CTA's full, forwarded to the even CTA), empty (the pair's MMAs of the stage completed)
+    uint64_t* st_full = stg_empty + a.SS;
+    uint64_t* st_pair = st_full + a.SB;
+    uint64_t* st_empty = st_pair + a.SB;
+    uint64_t* tm_full = st_empty + a.SB;
     uint64_t* tm_empty = tm_full + 2;
     uint64_t* phi_full = tm_empty + 2;
     uint64_t* phi_empty = phi_full + 2;
@@ -147,22 +155,22 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
 
     if (tid == 0) {
         for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], kConv3); }
-        for (int s = 0; s < a.SB; ++s) { mbar_init(&b_full[s], 2 * kConv3); mbar_init(&b_empty[s], 1); }
-        for (int s = 0; s < a.SA; ++s) {
-            mbar_init(&a_full[s], 1);
-            mbar_init(&a_pair[s], 1);
-            mbar_init(&a_empty[s], 1);
+        for (int s = 0; s < a.SB; ++s) {
+            mbar_init(&st_full[s], kConv3 + 1);
+            mbar_init(&st_pair[s], 1);
+            mbar_init(&st_empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tm_full[b], 1);
             mbar_init(&tm_empty[b], 2 * kEpi3);
-            mbar_init(&phi_full[b], 2 * kConv3);
+            mbar_init(&phi_full[b], kConv3);   // + the peer's coefficient bytes (st.async)
             mbar_init(&phi_empty[b], 2 * kEpi3);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
+    for (int i = tid; i < QP / 4; i += blockDim.x) wsm[i] = __ldg(reinterpret_cast<const float4*>(a.w) + i);
     if (warp == 0) {
         tmem_alloc_pair(tmem_holder, 512);
         tc_fence_before();
@@ -178,34 +186,36 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             constexpr uint32_t idesc = idesc_bf16(256, NT);
             const uint64_t a0 = sw128_desc(smem_u32(aring));
             const uint64_t b0 = sw128_desc(smem_u32(bring));
-            Ring3 rb, ra;
+            Ring3 rq;
             bool ok = true;
             for (int T = pair, it = 0; T < total && ok; T += npair, ++it) {
                 const int buf = it & 1;
                 const uint32_t use = (uint32_t)(it >> 1);
-                if (!W3C(&tm_empty[buf], (use & 1u) ^ 1u, 0x10u)) break;
+                if (!W3(&tm_empty[buf], (use & 1u) ^ 1u, 0x10u)) break;
                 tc_fence_after();
                 const uint32_t dbase = tmem_base + (uint32_t)(buf * MG * NT);
-                for (int kc = 0; kc < KC; ++kc) {
-                    if (!W3C(&b_full[rb.s], rb.ph, 0x20u) || !W3(&a_full[ra.s], ra.ph, 0x40u) ||
-                        !W3C(&a_pair[ra.s], ra.ph, 0x80u)) {
+                for (int kr = 0; kr < KR; ++kr) {
+                    if (!W3(&st_full[rq.s], rq.ph, 0x20u) || !W3(&st_pair[rq.s], rq.ph, 0x40u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t bd0 = b0 + (uint64_t)((rb.s * LT::kB) >> 4);
-                    const uint64_t ad0 = a0 + (uint64_t)((ra.s * LT::kA) >> 4);
+                    const uint64_t bd0 = b0 + (uint64_t)((rq.s * LT::kB) >> 4);
+                    const uint64_t ad0 = a0 + (uint64_t)((rq.s * LT::kA) >> 4);
 #pragma unroll
-                    for (int j = 0; j < MG; ++j) {
+                    for (int c = 0; c < CPS; ++c) {
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma_bf16_pair(dbase + (uint32_t)(j * NT), ad0 + (uint64_t)((j * kABlock) >> 4) + (uint64_t)(kk * 2),
-                                          bd0 + (uint64_t)(kk * 2), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        for (int j = 0; j < MG; ++j) {
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16_pair(dbase + (uint32_t)(j * NT),
+                                              ad0 + (uint64_t)(((c * MG + j) * kABlock) >> 4) + (uint64_t)(kk * 2),
+                                              bd0 + (uint64_t)((c * NTc * 128) >> 4) + (uint64_t)(kk * 2), idesc,
+                                              (kr > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                        }
                     }
-                    mma_commit_pair(&a_empty[ra.s], 3);
-                    mma_commit_pair(&b_empty[rb.s], 3);
-                    ra.next(a.SA);
-                    rb.next(a.SB);
+                    mma_commit_pair(&st_empty[rq.s], 3);
+                    rq.next(a.SB);
                 }
                 mma_commit_pair(&tm_full[buf], 3);
             }
@@ -214,21 +224,22 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 if (!mbar_drain(drain_bar, 0u, kDrainNs)) atomicOr(a.err, kErrUndrained);
             }
         } else if (lane == 0) {
-            // ------------------------------------------- odd CTA: forward kernel-matrix completions
-            const uint32_t pair_bar0 = mapa_shared(smem_u32(a_pair), 0);
-            Ring3 ra;
+            // ------------------------- odd CTA: forward its operand and kernel-matrix completions
+            // (the converters and the TMA signal this CTA's barriers; the data is complete in this
+            // CTA's shared memory when they do, and this thread republishes each completion to the
+            // even CTA, whose MMAs then read it)
+            const uint32_t pair0 = mapa_shared(smem_u32(st_pair), 0);
+            Ring3 rq;
             for (int T = pair; T < total; T += npair) {
                 bool ok = true;
-                for (int kc = 0; kc < KC; ++kc) {
-                    if (!W3(&a_full[ra.s], ra.ph, 0x400u)) { ok = false; break; }
-                    mbar_arrive_cluster(pair_bar0 + 8u * (uint32_t)ra.s);
-                    ra.next(a.SA);
+                for (int kr = 0; kr < KR; ++kr) {
+                    if (!W3(&st_full[rq.s], rq.ph, 0x400u)) { ok = false; break; }
+                    mbar_arrive_remote(pair0 + 8u * (uint32_t)rq.s);
+                    rq.next(a.SB);
                 }
                 if (!ok) break;
             }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
+        } else if (lane == 1) {
             // ----------------------------------------------------------------- flux TMA producer
             const uint64_t pol = policy_evict_last();   // the epilogue re-reads these lines shortly
             Ring3 rs;
@@ -251,89 +262,94 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 for (int s2 = 0; s2 < a.SS; ++s2)
                     if (((armed >> s2) & 1u) && !mbar_drain(&stg_full[s2], (apar >> s2) & 1u, kDrainNs))
                         atomicOr(a.err, kErrUndrained);
-        } else if (lane == 1) {
+        } else if (lane == 2) {
             // --------------------------------------------------------- kernel-matrix TMA producer
             const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
-            Ring3 ra;
+            Ring3 rq;
             uint32_t armed = 0u, apar = 0u;
             for (int T = pair; T < total; T += npair) {
                 bool ok = true;
-                for (int kc = 0; kc < KC; ++kc) {
-                    if (!W3C(&a_empty[ra.s], ra.ph ^ 1u, 0x2u)) { ok = false; break; }
-                    mbar_expect_tx(&a_full[ra.s], LT::kA);
-                    tma_load_5d_hint(aring + (size_t)ra.s * LT::kA, &a.tm_G, &a_full[ra.s], 0, 0, (int)rank, 0, kc, pol);
-                    armed |= 1u << ra.s;
-                    apar = (apar & ~(1u << ra.s)) | (ra.ph << ra.s);
-                    ra.next(a.SA);
+                for (int kr = 0; kr < KR; ++kr) {
+                    if (!W3(&st_empty[rq.s], rq.ph ^ 1u, 0x2u)) { ok = false; break; }
+                    mbar_expect_tx(&st_full[rq.s], LT::kA);
+                    tma_load_5d_hint(aring + (size_t)rq.s * LT::kA, &a.tm_G, &st_full[rq.s], 0, 0, (int)rank, 0, kr * CPS,
+                                     pol);
+                    armed |= 1u << rq.s;
+                    apar = (apar & ~(1u << rq.s)) | (rq.ph << rq.s);
+                    rq.next(a.SB);
                 }
                 if (!ok) break;
             }
-            if (*abort_flag)
-                for (int s2 = 0; s2 < a.SA; ++s2)
-                    if (((armed >> s2) & 1u) && !mbar_drain(&a_full[s2], (apar >> s2) & 1u, kDrainNs))
+            if (*abort_flag)   // (the stage's phase also waits for the converters, which stop on abort)
+                for (int s2 = 0; s2 < a.SB; ++s2)
+                    if (((armed >> s2) & 1u) && !mbar_drain(&st_full[s2], (apar >> s2) & 1u, kDrainNs))
                         atomicOr(a.err, kErrUndrained);
         }
     } else if (warp < kEpi0) {
         // ------------------------------------------------------------------------ converters
+        // Thread (rsub, col4) converts float4 column col4 of the cells rsub, rsub + RS, ... of each
+        // staged chunk and owns the cell constants and coefficients of cells col4 + 16 k of its
+        // column (when there are that many).  No global memory is read inside the chunk loop
+        // (weights in shared memory, cell constants requested at the start of the tile).
         constexpr int RS = 2 * kConv3;       // rows (cells) advanced per step of a thread column
-        constexpr int NR = NTc / RS;         // cells per thread
-        const int ct = tid - 64;             // 0 .. 63
+        constexpr int NR = (NTc + RS - 1) / RS;   // cells per thread (the last step is partial)
+        constexpr int NOWN = (NR + 15) / 16; // cells whose coefficients this thread may write
+        const int ct = tid - 32;             // 0 .. 32 kConv3 - 1
         const int rsub = ct >> 4;
         const int col4 = ct & 15;
-        const float4* wp = reinterpret_cast<const float4*>(a.w) + col4;
-        const uint32_t b_full0 = mapa_shared(smem_u32(b_full), 0);
-        const uint32_t phi_loc = mapa_shared(smem_u32(phi_full), rank);
         const uint32_t phi_rem = mapa_shared(smem_u32(phi_full), rank ^ 1u);
         const uint32_t cx_rem = mapa_shared(smem_u32(cx), rank ^ 1u);
         const uint32_t cy_rem = mapa_shared(smem_u32(cy), rank ^ 1u);
         const uint32_t cb_rem = mapa_shared(smem_u32(cb), rank ^ 1u);
         const float dt = a.dt;
         Ring3 rs, rb;
-        float4 wn = __ldg(wp);
         for (int T = pair, it = 0; T < total; T += npair, ++it) {
             const int ty = T / a.ntx, tx = T - ty * a.ntx;
             const int xbase = tx * kTW, ybase = ty * TH + (int)rank * THc;
-            if (col4 == 0) {
 #pragma unroll
-                for (int i = 0; i < NR; ++i) {
-                    const int r = rsub + RS * i;
-                    const int xx = xbase + (r & (kTW - 1)), yy = ybase + r / kTW;
-                    if (xx < a.nx && yy < a.ny) cp_async16(smem_u32(cst + r), a.cell + (size_t)yy * a.nx + xx, 16u);
-                }
-                cp_async_commit();
+            for (int k = 0; k < NOWN; ++k) {
+                const int i = col4 + 16 * k;
+                const int r = rsub + RS * i;
+                const int xx = xbase + (r & (kTW - 1)), yy = ybase + r / kTW;
+                if (i < NR && r < NTc && xx < a.nx && yy < a.ny)
+                    cp_async16(smem_u32(cst + r), a.cell + (size_t)yy * a.nx + xx, 16u);
             }
+            cp_async_commit();
             float part[NR];
 #pragma unroll
             for (int i = 0; i < NR; ++i) part[i] = 0.0f;
             bool ok = true;
             for (int kc = 0; kc < KC; ++kc) {
-                const float4 w4 = wn;
-                wn = __ldg(wp + (kc + 1 < KC ? kc + 1 : 0) * 16);
-                if (!W3(&stg_full[rs.s], rs.ph, 0x100u) || !W3C(&b_empty[rb.s], rb.ph ^ 1u, 0x200u)) {
+                const int sub = kc % CPS;    // chunk within the operand stage
+                if (!W3(&stg_full[rs.s], rs.ph, 0x100u) || (sub == 0 && !W3(&st_empty[rb.s], rb.ph ^ 1u, 0x200u))) {
                     ok = false;
                     break;
                 }
+                const float4 w4 = wsm[kc * 16 + col4];
                 const float4* src = reinterpret_cast<const float4*>(stg + (size_t)rs.s * NTc * 64);
-                unsigned char* dst = bring + rb.s * LT::kB;
+                unsigned char* dst = bring + rb.s * LT::kB + sub * NTc * 128;
+                const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
                     const int r = rsub + RS * i;
+                    if (NTc % RS != 0 && r >= NTc) break;
                     const float4 v = src[r * 16 + col4];
-                    part[i] += w4.x * v.x + w4.y * v.y + w4.z * v.z + w4.w * v.w;
+                    const float2 pp = __ffma2_rn(wb, make_float2(v.z, v.w), __fmul2_rn(wa, make_float2(v.x, v.y)));
+                    part[i] += pp.x + pp.y;
                     uint2 h;
                     h.x = pack_bf16(v.x, v.y);
                     h.y = pack_bf16(v.z, v.w);
                     const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
                     *reinterpret_cast<uint2*>(dst + off) = h;
                 }
-                fence_proxy_async();
+                if (sub == CPS - 1) fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(&stg_empty[rs.s]);
-                    mbar_arrive_cluster(b_full0 + 8u * (uint32_t)rb.s);
+                    if (sub == CPS - 1) mbar_arrive(&st_full[rb.s]);
                 }
                 rs.next(a.SS);
-                rb.next(a.SB);
+                if (sub == CPS - 1) rb.next(a.SB);
             }
             if (!ok) break;
 #pragma unroll
@@ -347,36 +363,41 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             }
             const int buf = it & 1;
             const uint32_t use = (uint32_t)(it >> 1);
-            if (!W3C(&phi_empty[buf], (use & 1u) ^ 1u, 0x800u)) break;
-            if (col4 == 0) {
-                // per cell of the pair tile: 1 - dt sigma_t, dt (sigma_s Phi / sum w + q), neighbour bits
-                // (1 left, 2 right, 4 below, 8 above exist; 16 the cell exists)
-                cp_async_wait<0>();
+            if (!W3(&phi_empty[buf], (use & 1u) ^ 1u, 0x800u)) break;
+            cp_async_wait<0>();
+            // per cell of the pair tile: 1 - dt sigma_t, dt (sigma_s Phi / sum w + q), neighbour bits
+            // (1 left, 2 right, 4 below, 8 above exist; 16 the cell exists), written here and, by
+            // st.async completing on the peer's phi_full, into the peer
+            const uint32_t pbar = phi_rem + 8u * (uint32_t)buf;
 #pragma unroll
-                for (int i = 0; i < NR; ++i) {
-                    const int r = rsub + RS * i;
-                    const int xx = xbase + (r & (kTW - 1)), yy = ybase + r / kTW;
-                    float fx = 1.0f, fy = 0.0f;
-                    int bits = 0;
-                    if (xx < a.nx && yy < a.ny) {
-                        const CellF cl = cst[r];
-                        fx = 1.0f - dt * cl.sig_t;
-                        fy = dt * (cl.sig_s_over_wsum * part[i] + cl.q);
-                        bits = (xx > 0 ? 1 : 0) | (xx + 1 < a.nx ? 2 : 0) | (yy > 0 ? 4 : 0) | (yy + 1 < a.ny ? 8 : 0) | 16;
-                    }
-                    const int c = buf * NT + (int)rank * NTc + r;
-                    cx[c] = fx;
-                    cy[c] = fy;
-                    cb[c] = bits;
-                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cx_rem + 4u * (uint32_t)c), "f"(fx) : "memory");
-                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cy_rem + 4u * (uint32_t)c), "f"(fy) : "memory");
-                    asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(cb_rem + 4u * (uint32_t)c), "r"(bits) : "memory");
+            for (int k = 0; k < NOWN; ++k) {
+                const int i = col4 + 16 * k;
+                if (i >= NR || rsub + RS * i >= NTc) continue;
+                float phi = 0.0f;
+#pragma unroll
+                for (int i2 = 0; i2 < NR; ++i2) phi = i2 == i ? part[i2] : phi;
+                const int r = rsub + RS * i;
+                const int xx = xbase + (r & (kTW - 1)), yy = ybase + r / kTW;
+                float fx = 1.0f, fy = 0.0f;
+                int bits = 0;
+                if (xx < a.nx && yy < a.ny) {
+                    const CellF cl = cst[r];
+                    fx = 1.0f - dt * cl.sig_t;
+                    fy = dt * (cl.sig_s_over_wsum * phi + cl.q);
+                    bits = (xx > 0 ? 1 : 0) | (xx + 1 < a.nx ? 2 : 0) | (yy > 0 ? 4 : 0) | (yy + 1 < a.ny ? 8 : 0) | 16;
                 }
+                const int c = buf * NT + (int)rank * NTc + r;
+                cx[c] = fx;
+                cy[c] = fy;
+                cb[c] = bits;
+                st_async_b32(cx_rem + 4u * (uint32_t)c, __float_as_uint(fx), pbar);
+                st_async_b32(cy_rem + 4u * (uint32_t)c, __float_as_uint(fy), pbar);
+                st_async_b32(cb_rem + 4u * (uint32_t)c, (uint32_t)bits, pbar);
             }
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive_cluster(phi_loc + 8u * (uint32_t)buf);
-                mbar_arrive_cluster(phi_rem + 8u * (uint32_t)buf);
+                if (warp == 1) mbar_expect_tx(&phi_full[buf], (uint32_t)NTc * 12u);   // the peer's bytes
+                else mbar_arrive(&phi_full[buf]);
             }
         }
     } else {
@@ -438,7 +459,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 load_row(1);
                 load_row(2);
                 int go = 1;
-                if (lane == 0) go = W3C(&phi_full[buf], use & 1u, 0x1000u) && W3C(&tm_full[buf], use & 1u, 0x2000u);
+                if (lane == 0) go = W3C(&phi_full[buf], use & 1u, 0x1000u) && W3(&tm_full[buf], use & 1u, 0x2000u);
                 go = __shfl_sync(0xffffffffu, go, 0);
                 if (!go) break;
                 tc_fence_after();
@@ -493,7 +514,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 load(0, cur, edge);
                 float enext = 0.0f;
                 int go = 1;
-                if (lane == 0) go = W3C(&phi_full[buf], use & 1u, 0x1000u) && W3C(&tm_full[buf], use & 1u, 0x2000u);
+                if (lane == 0) go = W3C(&phi_full[buf], use & 1u, 0x1000u) && W3(&tm_full[buf], use & 1u, 0x2000u);
                 go = __shfl_sync(0xffffffffu, go, 0);
                 if (!go) break;
                 tc_fence_after();
@@ -533,10 +554,10 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive_cluster(tm_empty0 + 8u * (uint32_t)buf);
-                mbar_arrive_cluster(phe_loc + 8u * (uint32_t)buf);
-                mbar_arrive_cluster(phe_rem + 8u * (uint32_t)buf);
+            if (lane == 0) {   // this warp's accumulator columns and coefficients are read
+                mbar_arrive_remote(tm_empty0 + 8u * (uint32_t)buf);
+                mbar_arrive_remote(phe_loc + 8u * (uint32_t)buf);
+                mbar_arrive_remote(phe_rem + 8u * (uint32_t)buf);
             }
         }
     }
@@ -584,14 +605,14 @@ bool encode_psi3(CUtensorMap* map, const float* psi, int Qp, int nx, int ny, int
 }
 
 // G [Mp][Qp] BF16 as a 5D tensor {64 columns, 128 rows, 2 halves, MG groups, KC chunks}: one box
-// {64, 128, 1, MG, 1} brings one CTA's rows of every 256-row group for one 64-column chunk, landing
-// as MG consecutive canonical [128 x 64] K-major tiles (128-byte swizzle).
+// {64, 128, 1, MG, CPS} brings one CTA's rows of every 256-row group for CPS 64-column chunks, landing
+// as CPS x MG consecutive canonical [128 x 64] K-major tiles (128-byte swizzle), chunk-major.
 bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG) {
     EncodeFn enc = get_encode3();
     if (!enc) return false;
     const cuuint64_t dims[5] = {64, 128, 2, (cuuint64_t)MG, (cuuint64_t)(Qp / 64)};
     const cuuint64_t strides[4] = {(cuuint64_t)Qp * 2, (cuuint64_t)Qp * 2 * 128, (cuuint64_t)Qp * 2 * 256, 128};
-    const cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)MG, 1};
+    const cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)MG, (cuuint32_t)L3<2>::CPS};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(G), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -625,19 +646,17 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     Tc3Plan* p = new Tc3Plan();
     p->MG = Qp / 256;
     const size_t limit = 227 * 1024;
-    // staging and operand rings as requested (default two and three stages); the kernel-matrix ring
-    // as requested or as deep as fits (up to 8)
-    p->SS = want.SS ? want.SS : 2;
-    p->SB = want.SB ? want.SB : 3;
+    // rings as requested, else two operand and two kernel-matrix stages (of two chunks each) and
+    // as many staging stages as fit, up to four (measured on the 448^2 lattice at 512 ordinates: the
+    // staging depth mattered most, two stages 0.30 ms, three or four 0.24 ms)
+    // (the operand and kernel-matrix rings advance together: one depth, the operand request's, else
+    // the kernel-matrix request's)
+    p->SS = want.SS ? want.SS : 4;
+    p->SB = p->SA = want.SB ? want.SB : (want.SA ? want.SA : 2);
     auto need = [&](int sa) { return p->MG == 2 ? smem3<2>(p->SS, p->SB, sa) : smem3<1>(p->SS, p->SB, sa); };
-    if (want.SA) {
-        p->SA = want.SA;
-        if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
-    } else {
-        p->SA = 2;
-        while (p->SA < 8 && need(p->SA + 1) <= limit) ++p->SA;
-        if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
-    }
+    if (!want.SS)
+        while (p->SS > 2 && need(p->SA) > limit) --p->SS;
+    if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
     p->smem = need(p->SA);
     const int TH = (256 / p->MG) / kTW;
     p->nx = nx;
@@ -682,6 +701,17 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
 }
 
 void tc3_plan_destroy(Tc3Plan* p) { delete p; }
+
+TcRings tc3_plan_rings(const Tc3Plan* p) {
+    TcRings r;
+    if (p) {
+        r.SS = p->SS;
+        r.SB = p->SB;
+        r.SA = p->SA;
+        r.MPR = p->MG;
+    }
+    return r;
+}
 
 void tc3_plan_describe(const Tc3Plan* p, int* tile_cells, int* stages, int* pairs, size_t* smem) {
     if (tile_cells) *tile_cells = p ? 256 / p->MG : 0;

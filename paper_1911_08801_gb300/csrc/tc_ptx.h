@@ -283,7 +283,14 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
 
-// try_wait with acquire at cluster scope (barriers that collect arrivals from the peer CTA).
+// Arrive on an mbarrier given by its shared::cluster address with the default (CTA-scope release)
+// semantics: for arrivals that only report that this warp has finished reading a buffer whose
+// values it already holds, so no prior write of the thread needs to be made visible first.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+// try_wait with acquire at cluster scope (barriers whose arrivals publish the peer CTA's writes).
 __device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -296,13 +303,26 @@ __device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait at cluster scope, as mbar_wait_for (sleeping between polls), out of line.
+// The same with a suspend-time hint (the thread sleeps in hardware until the phase completes or
+// about hint_ns pass).
+__device__ __forceinline__ bool mbar_try_wait_cl_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait at cluster scope, as mbar_wait_for, out of line.
 static __device__ __noinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                                  unsigned int* err, unsigned int code) {
     const uint64_t t0 = globaltimer();
     while (true) {
-        if (mbar_try_wait_cl(bar, parity)) return true;
-        __nanosleep(64);
+        if (mbar_try_wait_cl_sleep(bar, parity, 20000u)) return true;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kWaitNs) {
             *abort_flag = 1;
@@ -316,6 +336,15 @@ static __device__ __noinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity,
 __device__ __forceinline__ void st_cluster_v4(uint32_t caddr, float4 v) {
     asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(caddr), "f"(v.x), "f"(v.y), "f"(v.z),
                  "f"(v.w)
+                 : "memory");
+}
+
+// 4-byte store into another CTA's shared memory that completes 4 transaction bytes on an mbarrier
+// of that CTA (both as shared::cluster addresses): the data is visible to whoever observes the
+// barrier's phase complete, with no fence on the storing side.
+__device__ __forceinline__ void st_async_b32(uint32_t caddr, uint32_t v, uint32_t cbar) {
+    asm volatile("st.async.weak.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(caddr), "r"(v),
+                 "r"(cbar)
                  : "memory");
 }
 
