@@ -310,7 +310,8 @@ int assn_check_finite(assn_problem* p);
  * is two launches) to every member that still has steps left; a member's step count is
  * kept on the device, so members finish at their own counts within one run.  After
  * assn_batch_run each member is exactly as if assn_step(p, nsteps, dt) had been called on it
- * (bitwise, at the same tiling).  Members stay owned by the caller and must outlive their
+ * (bitwise, with tiling variant 0 at the same tile width: batches run the persistent one-CTA
+ * kernel).  Members stay owned by the caller and must outlive their
  * membership; while in a batch they are stepped only through it.
  *
  * create:     stream = a cudaStream_t or NULL (library stream).  Errors: ASSN_ERR_CUDA / OOM.
@@ -381,7 +382,8 @@ int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, in
  * per step (the batch path, optionally as CUDA graphs); requests that arrive meanwhile join at
  * the next chunk, and finished solves return the scalar flux Phi = sum_q w_q psi_q (FP64 on the
  * host, [ny][nx]) and free their memory.  A solve's result does not depend on which other solves
- * share its launches (each is bitwise equal to assn_step on the same problem).
+ * share its launches (each is bitwise equal to assn_step on the same problem with tiling
+ * variant 0).
  *
  * Thread safety: submit, wait and stats may be called from any host threads concurrently;
  * assn_server_last_error returns the message of the calling thread's last failed server call. */

@@ -68,7 +68,7 @@ struct Tc3Args {
     float dt, dts;                      // dt and dt sigma_as
 };
 
-template <int MG>
+template <int MG, int CPS_ = 2>
 struct L3 {
     static constexpr int NT = 256 / MG;         // cells per tile (MMA N)
     static constexpr int TH = NT / kTW;         // tile rows
@@ -76,7 +76,7 @@ struct L3 {
     static constexpr int NTc = NT / 2;          // cells per CTA
     static constexpr int QP = 256 * MG;         // ordinate stride
     static constexpr int KC = QP / 64;          // 64-ordinate chunks
-    static constexpr int CPS = 2;               // chunks per operand / kernel-matrix stage (one MMA round)
+    static constexpr int CPS = CPS_;            // chunks per operand / kernel-matrix stage (one MMA round)
     static constexpr int KR = KC / CPS;         // MMA rounds per tile
     static constexpr int kStg = NTc * 256;      // FP32 staging stage (one chunk)
     static constexpr int kB = CPS * NTc * 128;  // BF16 operand stage
@@ -114,10 +114,10 @@ struct Ring3 {
 
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-template <int MG>
+template <int MG, int CPS_>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
 step_tc3_kernel(const __grid_constant__ Tc3Args a) {
-    using LT = L3<MG>;
+    using LT = L3<MG, CPS_>;
     constexpr int NT = LT::NT, TH = LT::TH, THc = LT::THc, NTc = LT::NTc, QP = LT::QP, KC = LT::KC;
     constexpr int CPS = LT::CPS, KR = LT::KR;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -329,18 +329,30 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 const float4* src = reinterpret_cast<const float4*>(stg + (size_t)rs.s * NTc * 64);
                 unsigned char* dst = bring + rb.s * LT::kB + sub * NTc * 128;
                 const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
+                // groups of up to GR rows: all shared-memory loads of a group first, then the
+                // arithmetic and the operand stores (the rows are independent, so the loads overlap)
+                constexpr int GR = NR <= 11 ? NR : 1;   // (22 rows at 256 ordinates: one at a time)
 #pragma unroll
-                for (int i = 0; i < NR; ++i) {
-                    const int r = rsub + RS * i;
-                    if (NTc % RS != 0 && r >= NTc) break;
-                    const float4 v = src[r * 16 + col4];
-                    const float2 pp = __ffma2_rn(wb, make_float2(v.z, v.w), __fmul2_rn(wa, make_float2(v.x, v.y)));
-                    part[i] += pp.x + pp.y;
-                    uint2 h;
-                    h.x = pack_bf16(v.x, v.y);
-                    h.y = pack_bf16(v.z, v.w);
-                    const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
-                    *reinterpret_cast<uint2*>(dst + off) = h;
+                for (int i0 = 0; i0 < NR; i0 += GR) {
+                    float4 v[GR];
+#pragma unroll
+                    for (int g = 0; g < GR; ++g) {
+                        const int r = rsub + RS * (i0 + g);
+                        v[g] = (i0 + g < NR && r < NTc) ? src[r * 16 + col4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int g = 0; g < GR; ++g) {
+                        const int i = i0 + g;
+                        const int r = rsub + RS * i;
+                        if (i >= NR || r >= NTc) continue;
+                        const float2 pp = __ffma2_rn(wb, make_float2(v[g].z, v[g].w), __fmul2_rn(wa, make_float2(v[g].x, v[g].y)));
+                        part[i] += pp.x + pp.y;
+                        uint2 h;
+                        h.x = pack_bf16(v[g].x, v[g].y);
+                        h.y = pack_bf16(v[g].z, v[g].w);
+                        const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
+                        *reinterpret_cast<uint2*>(dst + off) = h;
+                    }
                 }
                 if (sub == CPS - 1) fence_proxy_async();
                 __syncwarp();
@@ -607,27 +619,38 @@ bool encode_psi3(CUtensorMap* map, const float* psi, int Qp, int nx, int ny, int
 // G [Mp][Qp] BF16 as a 5D tensor {64 columns, 128 rows, 2 halves, MG groups, KC chunks}: one box
 // {64, 128, 1, MG, CPS} brings one CTA's rows of every 256-row group for CPS 64-column chunks, landing
 // as CPS x MG consecutive canonical [128 x 64] K-major tiles (128-byte swizzle), chunk-major.
-bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG) {
+bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG, int CPS) {
     EncodeFn enc = get_encode3();
     if (!enc) return false;
     const cuuint64_t dims[5] = {64, 128, 2, (cuuint64_t)MG, (cuuint64_t)(Qp / 64)};
     const cuuint64_t strides[4] = {(cuuint64_t)Qp * 2, (cuuint64_t)Qp * 2 * 128, (cuuint64_t)Qp * 2 * 256, 128};
-    const cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)MG, (cuuint32_t)L3<2>::CPS};
+    const cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)MG, (cuuint32_t)CPS};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(G), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MG>
+template <int MG, int CPS>
 size_t smem3(int SS, int SB, int SA) {
-    return (size_t)1024 + (size_t)L3<MG>(SS, SB, SA).end;
+    return (size_t)1024 + (size_t)L3<MG, CPS>(SS, SB, SA).end;
+}
+
+size_t smem3_for(int MG, int CPS, int SS, int SB) {
+    if (MG == 2) return CPS == 2 ? smem3<2, 2>(SS, SB, SB) : smem3<2, 1>(SS, SB, SB);
+    return CPS == 2 ? smem3<1, 2>(SS, SB, SB) : smem3<1, 1>(SS, SB, SB);
+}
+
+using Tc3Kernel = void (*)(Tc3Args);
+Tc3Kernel kernel3(int MG, int CPS) {
+    if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2> : step_tc3_kernel<2, 1>;
+    return CPS == 2 ? step_tc3_kernel<1, 2> : step_tc3_kernel<1, 1>;
 }
 
 }  // namespace
 
 struct Tc3Plan {
-    int MG = 0, SS = 0, SB = 0, SA = 0, grid = 0, total = 0, ntx = 0;
+    int MG = 0, CPS = 2, SS = 0, SB = 0, SA = 0, grid = 0, total = 0, ntx = 0;
     size_t smem = 0;
     CUtensorMap tm_psi[2], tm_G;
     const float* buf[2] = {nullptr, nullptr};
@@ -646,14 +669,14 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     Tc3Plan* p = new Tc3Plan();
     p->MG = Qp / 256;
     const size_t limit = 227 * 1024;
-    // rings as requested, else two operand and two kernel-matrix stages (of two chunks each) and
-    // as many staging stages as fit, up to four (measured on the 448^2 lattice at 512 ordinates: the
-    // staging depth mattered most, two stages 0.30 ms, three or four 0.24 ms)
-    // (the operand and kernel-matrix rings advance together: one depth, the operand request's, else
-    // the kernel-matrix request's)
+    // rings as requested (MPR: 64-ordinate chunks per operand / kernel-matrix stage, 1 or 2), else
+    // two chunks per stage, two operand and kernel-matrix stages, and as many staging stages as fit,
+    // up to four (measured on the 448^2 lattice at 512 ordinates: the staging depth mattered most,
+    // two stages 0.30 ms, three or four 0.24 ms; two chunks per stage cut the per-round waits)
+    p->CPS = want.MPR == 1 ? 1 : 2;
     p->SS = want.SS ? want.SS : 4;
     p->SB = p->SA = want.SB ? want.SB : (want.SA ? want.SA : 2);
-    auto need = [&](int sa) { return p->MG == 2 ? smem3<2>(p->SS, p->SB, sa) : smem3<1>(p->SS, p->SB, sa); };
+    auto need = [&](int) { return smem3_for(p->MG, p->CPS, p->SS, p->SB); };
     if (!want.SS)
         while (p->SS > 2 && need(p->SA) > limit) --p->SS;
     if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
@@ -667,12 +690,12 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     p->buf[0] = buf0;
     p->buf[1] = buf1;
     if (!encode_psi3(&p->tm_psi[0], buf0, Qp, nx, ny, TH / 2) || !encode_psi3(&p->tm_psi[1], buf1, Qp, nx, ny, TH / 2) ||
-        !encode_G5(&p->tm_G, G, Qp, p->MG)) {
+        !encode_G5(&p->tm_G, G, Qp, p->MG, p->CPS)) {
         delete p;
         return cudaErrorInvalidValue;
     }
     // one pair per two SMs, as many pairs as the device co-schedules (never more than tiles)
-    auto kern = p->MG == 2 ? step_tc3_kernel<2> : step_tc3_kernel<1>;
+    auto kern = kernel3(p->MG, p->CPS);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (e != cudaSuccess) { delete p; return e; }
     int dev = 0, sms = 0;
@@ -708,7 +731,7 @@ TcRings tc3_plan_rings(const Tc3Plan* p) {
         r.SS = p->SS;
         r.SB = p->SB;
         r.SA = p->SA;
-        r.MPR = p->MG;
+        r.MPR = p->CPS;
     }
     return r;
 }
@@ -743,10 +766,7 @@ cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const
     a.SA = p->SA;
     a.dt = dt;
     a.dts = dt_sigma_as;
-    if (p->MG == 2)
-        step_tc3_kernel<2><<<p->grid, kThreads3, p->smem, s>>>(a);
-    else
-        step_tc3_kernel<1><<<p->grid, kThreads3, p->smem, s>>>(a);
+    kernel3(p->MG, p->CPS)<<<p->grid, kThreads3, p->smem, s>>>(a);
     return cudaGetLastError();
 }
 
