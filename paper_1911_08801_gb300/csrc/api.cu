@@ -575,7 +575,7 @@ int assn_max_stable_dt(assn_problem* p, double* dt_out) {
 }
 
 // The tensor-core kernel a step of p runs: the requested variant, or (automatic, -1) the paired-SM
-// kernel where it applies (forward Euler, BF16, 193..256 or 449..512 ordinates), else variant 0.
+// kernel where it applies (forward Euler, BF16 or BF16X3, 193..256 or 449..512 ordinates), else variant 0.
 static int eff_variant(const assn_problem* p) {
     if (p->variant >= 0) return p->variant;
     return (p->scheme == ASSN_SCHEME_EULER_UPWIND &&
@@ -637,9 +637,10 @@ static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
     if (e == cudaSuccess && v == 2 && !p->plan3) {
         if (!tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision == ASSN_BF16X3))
             return fail(p, ASSN_ERR_UNSUPPORTED,
-                        "paired-SM step (variant 2): BF16 with 193..256 or 449..512 ordinates only (Q = %d)", p->Q);
-        e = tc3_plan_create(&p->plan3, (const float*)p->d_psi[0], (const float*)p->d_psi[1], p->tc.G_hi, p->Q, p->Qp,
-                            p->tc.Mp, p->nx, p->ny, p->want_rings);
+                        "paired-SM step (variant 2): 193..256 or 449..512 ordinates only (Q = %d)", p->Q);
+        e = tc3_plan_create(&p->plan3, (const float*)p->d_psi[0], (const float*)p->d_psi[1], p->tc.G_hi,
+                            p->precision == ASSN_BF16X3 ? p->tc.G_lo : nullptr, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
+                            p->want_rings);
     }
     if (e == cudaErrorNotSupported)
         return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: Q = %d with tile %d / stages %d not supported", p->Q,

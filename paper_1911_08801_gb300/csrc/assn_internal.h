@@ -115,13 +115,14 @@ cudaError_t launch_step_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, 
 cudaError_t launch_heun_stage_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, const float* keep, float alpha,
                                   float beta, cudaStream_t s);
 
-// Paired-SM tensor-core step (variant 2): one problem, forward Euler, BF16, padded ordinate count
-// 256 or 512 (equal to the kernel-matrix rows).  A cluster of two CTAs shares each M = 256 MMA;
+// Paired-SM tensor-core step (variant 2): one problem, forward Euler, BF16 or BF16X3, padded ordinate
+// count 256 or 512 (equal to the kernel-matrix rows).  A cluster of two CTAs shares each M = 256 MMA;
 // the flux buffers and G are bound at plan creation, dt at launch.
 struct Tc3Plan;
 bool tc3_supported(int Q, int Qp, int Mp, bool split);
-cudaError_t tc3_plan_create(Tc3Plan** plan, const float* buf0, const float* buf1, const __nv_bfloat16* G, int Q,
-                            int Qp, int Mp, int nx, int ny, TcRings want);
+// G_lo non-null: the split (BF16X3) contraction, hi x hi + hi x lo + lo x hi.
+cudaError_t tc3_plan_create(Tc3Plan** plan, const float* buf0, const float* buf1, const __nv_bfloat16* G,
+                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want);
 void tc3_plan_destroy(Tc3Plan* plan);
 TcRings tc3_plan_rings(const Tc3Plan* plan);   // MPR = 128-row blocks per kernel-matrix request
 // tile cells, kernel-matrix ring depth, CTA pairs launched, dynamic shared memory per CTA

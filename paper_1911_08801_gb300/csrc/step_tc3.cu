@@ -57,6 +57,7 @@ constexpr int kABlock = 128 * 64 * 2;   // one [128 x 64] BF16 block of G
 struct Tc3Args {
     CUtensorMap tm_psi;                 // input flux [ny][nx][Qp] FP32, box {64, TW, TH/2}
     CUtensorMap tm_G;                   // G [Mp][Qp] BF16 as {64, 128, 2, MG, KC}, box {64, 128, 1, MG, CPS}
+    CUtensorMap tm_Glo;                 // split contraction: the residual of G, same view
     const float* in;
     float* out;
     const OrdF* ord;                    // [Qp]
@@ -68,7 +69,7 @@ struct Tc3Args {
     float dt, dts;                      // dt and dt sigma_as
 };
 
-template <int MG, int CPS_ = 2>
+template <int MG, int CPS_ = 2, bool SPLIT = false>
 struct L3 {
     static constexpr int NT = 256 / MG;         // cells per tile (MMA N)
     static constexpr int TH = NT / kTW;         // tile rows
@@ -79,8 +80,9 @@ struct L3 {
     static constexpr int CPS = CPS_;            // chunks per operand / kernel-matrix stage (one MMA round)
     static constexpr int KR = KC / CPS;         // MMA rounds per tile
     static constexpr int kStg = NTc * 256;      // FP32 staging stage (one chunk)
-    static constexpr int kB = CPS * NTc * 128;  // BF16 operand stage
-    static constexpr int kA = CPS * MG * kABlock;   // G stage: this CTA's blocks of CPS chunks
+    static constexpr int NP = SPLIT ? 2 : 1;    // operand parts: hi [+ lo]
+    static constexpr int kB = NP * CPS * NTc * 128;     // BF16 operand stage (hi chunks, then lo chunks)
+    static constexpr int kA = NP * CPS * MG * kABlock;  // G stage: this CTA's blocks of CPS chunks (hi, then lo)
     int stg, b, a, cx, cy, cb, cst, wsm, bars, end;
     __host__ __device__ L3(int SS, int SB, int SA) {
         stg = 0;
@@ -114,10 +116,10 @@ struct Ring3 {
 
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-template <int MG, int CPS_>
+template <int MG, int CPS_, bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
 step_tc3_kernel(const __grid_constant__ Tc3Args a) {
-    using LT = L3<MG, CPS_>;
+    using LT = L3<MG, CPS_, SPLIT>;
     constexpr int NT = LT::NT, TH = LT::TH, THc = LT::THc, NTc = LT::NTc, QP = LT::QP, KC = LT::KC;
     constexpr int CPS = LT::CPS, KR = LT::KR;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -207,11 +209,16 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
 #pragma unroll
                         for (int j = 0; j < MG; ++j) {
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk)
-                                mma_bf16_pair(dbase + (uint32_t)(j * NT),
-                                              ad0 + (uint64_t)(((c * MG + j) * kABlock) >> 4) + (uint64_t)(kk * 2),
-                                              bd0 + (uint64_t)((c * NTc * 128) >> 4) + (uint64_t)(kk * 2), idesc,
-                                              (kr > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ah = ad0 + (uint64_t)(((c * MG + j) * kABlock) >> 4) + (uint64_t)(kk * 2);
+                                const uint64_t bh = bd0 + (uint64_t)((c * NTc * 128) >> 4) + (uint64_t)(kk * 2);
+                                const uint32_t dd = dbase + (uint32_t)(j * NT);
+                                mma_bf16_pair(dd, ah, bh, idesc, (kr > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                                if (SPLIT) {   // + hi x lo + lo x hi (the lo parts follow the CPS hi chunks)
+                                    mma_bf16_pair(dd, ah, bh + (uint64_t)((CPS * NTc * 128) >> 4), idesc, 1u);
+                                    mma_bf16_pair(dd, ah + (uint64_t)((CPS * MG * kABlock) >> 4), bh, idesc, 1u);
+                                }
+                            }
                         }
                     }
                     mma_commit_pair(&st_empty[rq.s], 3);
@@ -274,6 +281,9 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                     mbar_expect_tx(&st_full[rq.s], LT::kA);
                     tma_load_5d_hint(aring + (size_t)rq.s * LT::kA, &a.tm_G, &st_full[rq.s], 0, 0, (int)rank, 0, kr * CPS,
                                      pol);
+                    if (SPLIT)
+                        tma_load_5d_hint(aring + (size_t)rq.s * LT::kA + LT::kA / 2, &a.tm_Glo, &st_full[rq.s], 0, 0,
+                                         (int)rank, 0, kr * CPS, pol);
                     armed |= 1u << rq.s;
                     apar = (apar & ~(1u << rq.s)) | (rq.ph << rq.s);
                     rq.next(a.SB);
@@ -352,6 +362,14 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         h.y = pack_bf16(v[g].z, v[g].w);
                         const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
                         *reinterpret_cast<uint2*>(dst + off) = h;
+                        if (SPLIT) {   // residual of the rounding, the lo part
+                            const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.x));
+                            const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.y));
+                            uint2 l;
+                            l.x = pack_bf16(v[g].x - f0.x, v[g].y - f0.y);
+                            l.y = pack_bf16(v[g].z - f1.x, v[g].w - f1.y);
+                            *reinterpret_cast<uint2*>(dst + CPS * NTc * 128 + off) = l;
+                        }
                     }
                 }
                 if (sub == CPS - 1) fence_proxy_async();
@@ -497,7 +515,9 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         const float uy0 = ypos ? dn[i0] : up[i0];
                         const float uy1 = ypos ? dn[i1] : up[i1];
                         const float2 S = make_float2(s[i0], s[i1]);
-                        const float2 ST = __bfloat1622float2(__floats2bfloat162_rn(s[i0], s[i1]));
+                        // the operand of the generator term: psi~ as the contraction saw it (split: psi itself)
+                        const float2 ST = SPLIT ? make_float2(s[i0], s[i1])
+                                                : __bfloat1622float2(__floats2bfloat162_rn(s[i0], s[i1]));
                         float2 o = __ffma2_rn(S, __fadd2_rn(make_float2(fxv[i0], fxv[i1]), NAXY),
                                               make_float2(fyv[i0], fyv[i1]));
                         o = __ffma2_rn(AX, make_float2(ux0, ux1), o);
@@ -553,7 +573,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         out = fmaf(ax, ux, out);
                         out = fmaf(ay, uy, out);
                         out = fmaf(dts, y[i], out);
-                        out = fmaf(nge, bf16_round(sf), out);
+                        out = fmaf(nge, SPLIT ? sf : bf16_round(sf), out);
                         __stcs(po + i * QP, out);
                     }
 #pragma unroll
@@ -631,52 +651,58 @@ bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG, int CPS
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MG, int CPS>
+template <int MG, int CPS, bool SPLIT>
 size_t smem3(int SS, int SB, int SA) {
-    return (size_t)1024 + (size_t)L3<MG, CPS>(SS, SB, SA).end;
+    return (size_t)1024 + (size_t)L3<MG, CPS, SPLIT>(SS, SB, SA).end;
 }
 
-size_t smem3_for(int MG, int CPS, int SS, int SB) {
-    if (MG == 2) return CPS == 2 ? smem3<2, 2>(SS, SB, SB) : smem3<2, 1>(SS, SB, SB);
-    return CPS == 2 ? smem3<1, 2>(SS, SB, SB) : smem3<1, 1>(SS, SB, SB);
+size_t smem3_for(int MG, int CPS, bool split, int SS, int SB) {
+    if (split) return MG == 2 ? smem3<2, 1, true>(SS, SB, SB) : smem3<1, 1, true>(SS, SB, SB);
+    if (MG == 2) return CPS == 2 ? smem3<2, 2, false>(SS, SB, SB) : smem3<2, 1, false>(SS, SB, SB);
+    return CPS == 2 ? smem3<1, 2, false>(SS, SB, SB) : smem3<1, 1, false>(SS, SB, SB);
 }
 
 using Tc3Kernel = void (*)(Tc3Args);
-Tc3Kernel kernel3(int MG, int CPS) {
-    if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2> : step_tc3_kernel<2, 1>;
-    return CPS == 2 ? step_tc3_kernel<1, 2> : step_tc3_kernel<1, 1>;
+Tc3Kernel kernel3(int MG, int CPS, bool split) {
+    if (split) return MG == 2 ? step_tc3_kernel<2, 1, true> : step_tc3_kernel<1, 1, true>;
+    if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2, false> : step_tc3_kernel<2, 1, false>;
+    return CPS == 2 ? step_tc3_kernel<1, 2, false> : step_tc3_kernel<1, 1, false>;
 }
 
 }  // namespace
 
 struct Tc3Plan {
     int MG = 0, CPS = 2, SS = 0, SB = 0, SA = 0, grid = 0, total = 0, ntx = 0;
+    bool split = false;
     size_t smem = 0;
-    CUtensorMap tm_psi[2], tm_G;
+    CUtensorMap tm_psi[2], tm_G, tm_Glo;
     const float* buf[2] = {nullptr, nullptr};
     int nx = 0, ny = 0, Q = 0;
 };
 
 bool tc3_supported(int Q, int Qp, int Mp, bool split) {
     (void)Q;
-    return !split && (Qp == 256 || Qp == 512) && Mp == Qp;
+    (void)split;
+    return (Qp == 256 || Qp == 512) && Mp == Qp;
 }
 
-cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1, const __nv_bfloat16* G, int Q,
-                            int Qp, int Mp, int nx, int ny, TcRings want) {
+cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1, const __nv_bfloat16* G,
+                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want) {
     *out = nullptr;
-    if (!tc3_supported(Q, Qp, Mp, false)) return cudaErrorNotSupported;
+    const bool split = G_lo != nullptr;
+    if (!tc3_supported(Q, Qp, Mp, split)) return cudaErrorNotSupported;
     Tc3Plan* p = new Tc3Plan();
     p->MG = Qp / 256;
+    p->split = split;
     const size_t limit = 227 * 1024;
     // rings as requested (MPR: 64-ordinate chunks per operand / kernel-matrix stage, 1 or 2), else
     // two chunks per stage, two operand and kernel-matrix stages, and as many staging stages as fit,
     // up to four (measured on the 448^2 lattice at 512 ordinates: the staging depth mattered most,
     // two stages 0.30 ms, three or four 0.24 ms; two chunks per stage cut the per-round waits)
-    p->CPS = want.MPR == 1 ? 1 : 2;
+    p->CPS = (want.MPR == 1 || split) ? 1 : 2;   // split operands: one chunk per stage
     p->SS = want.SS ? want.SS : 4;
     p->SB = p->SA = want.SB ? want.SB : (want.SA ? want.SA : 2);
-    auto need = [&](int) { return smem3_for(p->MG, p->CPS, p->SS, p->SB); };
+    auto need = [&](int) { return smem3_for(p->MG, p->CPS, p->split, p->SS, p->SB); };
     if (!want.SS)
         while (p->SS > 2 && need(p->SA) > limit) --p->SS;
     if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
@@ -690,12 +716,12 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     p->buf[0] = buf0;
     p->buf[1] = buf1;
     if (!encode_psi3(&p->tm_psi[0], buf0, Qp, nx, ny, TH / 2) || !encode_psi3(&p->tm_psi[1], buf1, Qp, nx, ny, TH / 2) ||
-        !encode_G5(&p->tm_G, G, Qp, p->MG, p->CPS)) {
+        !encode_G5(&p->tm_G, G, Qp, p->MG, p->CPS) || (split && !encode_G5(&p->tm_Glo, G_lo, Qp, p->MG, p->CPS))) {
         delete p;
         return cudaErrorInvalidValue;
     }
     // one pair per two SMs, as many pairs as the device co-schedules (never more than tiles)
-    auto kern = kernel3(p->MG, p->CPS);
+    auto kern = kernel3(p->MG, p->CPS, p->split);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (e != cudaSuccess) { delete p; return e; }
     int dev = 0, sms = 0;
@@ -750,6 +776,7 @@ cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const
     memset(&a, 0, sizeof a);
     a.tm_psi = p->tm_psi[parity];
     a.tm_G = p->tm_G;
+    a.tm_Glo = p->split ? p->tm_Glo : p->tm_G;
     a.in = p->buf[parity];
     a.out = const_cast<float*>(p->buf[parity ^ 1]);
     a.ord = ord;
@@ -766,7 +793,7 @@ cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const
     a.SA = p->SA;
     a.dt = dt;
     a.dts = dt_sigma_as;
-    kernel3(p->MG, p->CPS)<<<p->grid, kThreads3, p->smem, s>>>(a);
+    kernel3(p->MG, p->CPS, p->split)<<<p->grid, kThreads3, p->smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 """Parity of the paired-SM tensor-core step (tiling variant 2: a cluster of two CTAs shares each
-M = 256 MMA; 2D tiles of 16 x 8 cells at 512 ordinates, 16 x 16 at 256) with the FP64 oracle.
+M = 256 MMA; 2D tiles of 16 x 8 cells at 512 ordinates, 16 x 16 at 256) with the FP64 oracle, in
+both tensor-core precisions (BF16 one pass; BF16X3 split operands).
 
 Grids leave ragged tiles in x and y, hold interior tiles (the branch-free path) and boundary tiles
 (the checked path); ordinate counts cover 256 and 512 and padded ones (Q = 200, 500: lanes past Q);
@@ -30,8 +31,8 @@ def random_workload(nx, ny, npol, naz, beta=0.5, seed=0):
                           sigma_as=5.0, seed=seed)
 
 
-def pair_problem(A, wl, psi0=None):
-    p = gpu_problem(A, wl, "bf16", psi0=psi0)
+def pair_problem(A, wl, psi0=None, precision="bf16"):
+    p = gpu_problem(A, wl, precision, psi0=psi0)
     p.set_tiling(0, 0, 2)
     return p
 
@@ -58,14 +59,33 @@ def test_one_step_random_state(A, nx, ny, npol, naz):
     assert err <= tol, (err, tol)
 
 
+@pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16), (10, 50)])
+@pytest.mark.parametrize("nx,ny", [(70, 37), (16, 8), (1, 1)])
+def test_split_one_step_random_state(A, nx, ny, npol, naz):
+    """The split contraction (BF16X3: hi x hi + hi x lo + lo x hi) on the paired-SM kernel, within
+    its derived one-step bound."""
+    wl = random_workload(nx, ny, npol, naz, seed=nx * 17 + ny + npol)
+    p = pair_problem(A, wl, precision="bf16x3")
+    assert p.variant() == 2
+    dt = 0.9 * p.max_stable_dt()
+    p.step(1, dt)
+    got = p.state()
+    p.close()
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    ref = O.step(wl.psi0(), K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    tol = step_tolerance("bf16x3", dt, wl.sigma_as, np.abs(wl.psi0()).max(), offdiag_rowsum(K))
+    assert np.abs(got - ref).max() <= tol
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
 @pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16)])
-def test_agrees_with_persistent_kernel(A, npol, naz):
+def test_agrees_with_persistent_kernel(A, npol, naz, precision):
     """Variant 2 and the one-CTA persistent kernel (variant 0) give the same step from the same state
     to FP32 rounding (both contract the same BF16 operands with FP32 accumulation)."""
     wl = random_workload(67, 29, npol, naz, seed=5)
     states = []
     for variant in (0, 2):
-        p = gpu_problem(A, wl, "bf16")
+        p = gpu_problem(A, wl, precision)
         p.set_tiling(0, 0, variant)
         dt = 0.9 * p.max_stable_dt()
         p.step(1, dt)
@@ -74,18 +94,19 @@ def test_agrees_with_persistent_kernel(A, npol, naz):
     assert np.abs(states[0] - states[1]).max() <= 1e-6
 
 
-def test_line_source_run(A):
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_line_source_run(A, precision):
     """A whole short run (the 64^2 line source at 256 ordinates to t = 0.25): relative L2 of Phi
-    against the oracle within the BF16 whole-run tolerance; the state stays non-negative."""
+    against the oracle within the whole-run tolerance of the precision; the state stays non-negative."""
     wl = synth.line_source(64, 16, 16, 1.0 / 8.0, t_final=0.25, name="pair_ls64")
     n, dt = wl.steps()
-    p = pair_problem(A, wl)
+    p = pair_problem(A, wl, precision=precision)
     p.step(n, dt)
     phi = p.scalar_flux()
     assert p.state().min() >= 0.0
     p.close()
     psi, w = oracle_run(wl, n, dt)
-    assert rel_l2(phi, psi @ w) <= RUN_TOL["bf16"]
+    assert rel_l2(phi, psi @ w) <= RUN_TOL[precision]
 
 
 def test_lattice_run(A):
@@ -132,10 +153,23 @@ def test_unsupported_shapes(A):
         p.step(1, 0.5 * p.max_stable_dt())
     assert e.value.status == A._lib.ASSN_ERR_UNSUPPORTED
     p.close()
-    wl = random_workload(20, 20, 16, 32, seed=1)
-    p = gpu_problem(A, wl, "bf16x3")                     # the split contraction runs on variants 0 and 1
+    wl = random_workload(20, 20, 16, 24, seed=1)         # Q = 384: three 128-row blocks
+    p = gpu_problem(A, wl, "bf16x3")
+    assert p.variant() == 0                              # the automatic choice falls back
     p.set_tiling(0, 0, 2)
     with pytest.raises(A.AssnError) as e:
         p.step(1, 0.5 * p.max_stable_dt())
     assert e.value.status == A._lib.ASSN_ERR_UNSUPPORTED
     p.close()
+
+
+def test_automatic_variant(A):
+    """The automatic choice: the paired-SM kernel for forward-Euler steps at 256 / 512 ordinates in
+    both tensor-core precisions, the one-CTA kernel for other ordinate counts and for Heun."""
+    for (npol, naz), prec, scheme, want in [((16, 32), "bf16", "euler", 2), ((16, 16), "bf16x3", "euler", 2),
+                                            ((8, 16), "bf16", "euler", 0), ((16, 32), "bf16", "heun", 0)]:
+        wl = random_workload(8, 8, npol, naz, seed=2)
+        p = gpu_problem(A, wl, prec)
+        p.set_scheme(scheme)
+        assert p.variant() == want, (npol, naz, prec, scheme)
+        p.close()
