@@ -312,6 +312,14 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
         const uint32_t cy_rem = mapa_shared(smem_u32(cy), rank ^ 1u);
         const uint32_t cb_rem = mapa_shared(smem_u32(cb), rank ^ 1u);
         const float dt = a.dt;
+        // byte offsets of this thread's operand stores in a chunk (row r = rsub + RS i, float4 column
+        // col4, canonical K-major layout with 128-byte swizzle): fixed for the whole launch
+        int offs[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int r = rsub + RS * i;
+            offs[i] = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
+        }
         Ring3 rs, rb;
         for (int T = pair, it = 0; T < total; T += npair, ++it) {
             const int ty = T / a.ntx, tx = T - ty * a.ntx;
@@ -360,7 +368,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         uint2 h;
                         h.x = pack_bf16(v[g].x, v[g].y);
                         h.y = pack_bf16(v[g].z, v[g].w);
-                        const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
+                        const int off = offs[i];
                         *reinterpret_cast<uint2*>(dst + off) = h;
                         if (SPLIT) {   // residual of the rounding, the lo part
                             const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.x));
@@ -452,6 +460,10 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
         const uint32_t phe_rem = mapa_shared(smem_u32(phi_empty), rank ^ 1u);
         const int xedge = xpos ? -1 : 8;      // column of the edge cell (relative to the strip)
         const float2 AX = make_float2(ax, ax), AY = make_float2(ay, ay), NAXY = make_float2(-axy, -axy);
+        // upwind weights by side: a_x on the lower or the upper neighbour, zero on the other (a zero
+        // weight adds an exact zero, so the sum equals taking the upwind neighbour alone)
+        const float cl = xpos ? ax : 0.0f, cr = xpos ? 0.0f : ax, cd = ypos ? ay : 0.0f, cu = ypos ? 0.0f : ay;
+        const float2 CL = make_float2(cl, cl), CR = make_float2(cr, cr), CD = make_float2(cd, cd), CU = make_float2(cu, cu);
         const float2 DTS = make_float2(dts, dts), NGE = make_float2(nge, nge);
 
         for (int T = pair, it = 0; T < total; T += npair, ++it) {
@@ -510,18 +522,21 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const int i0 = 2 * k, i1 = 2 * k + 1;
-                        const float ux0 = xpos ? (i0 == 0 ? ev[r + 1] : s[i0 - 1]) : s[i0 + 1];
-                        const float ux1 = xpos ? s[i1 - 1] : (i1 == 7 ? ev[r + 1] : s[i1 + 1]);
-                        const float uy0 = ypos ? dn[i0] : up[i0];
-                        const float uy1 = ypos ? dn[i1] : up[i1];
+                        // lower / upper x-neighbours of cells i0, i1 (the row's edge cell stands in at
+                        // the ends: it is the side the lane's ordinate looks upwind to, weighted by
+                        // cl or cr accordingly)
+                        const float xl0 = i0 == 0 ? ev[r + 1] : s[i0 - 1], xr0 = s[i0 + 1];
+                        const float xl1 = s[i1 - 1], xr1 = i1 == 7 ? ev[r + 1] : s[i1 + 1];
                         const float2 S = make_float2(s[i0], s[i1]);
                         // the operand of the generator term: psi~ as the contraction saw it (split: psi itself)
                         const float2 ST = SPLIT ? make_float2(s[i0], s[i1])
                                                 : __bfloat1622float2(__floats2bfloat162_rn(s[i0], s[i1]));
                         float2 o = __ffma2_rn(S, __fadd2_rn(make_float2(fxv[i0], fxv[i1]), NAXY),
                                               make_float2(fyv[i0], fyv[i1]));
-                        o = __ffma2_rn(AX, make_float2(ux0, ux1), o);
-                        o = __ffma2_rn(AY, make_float2(uy0, uy1), o);
+                        o = __ffma2_rn(CL, make_float2(xl0, xl1), o);
+                        o = __ffma2_rn(CR, make_float2(xr0, xr1), o);
+                        o = __ffma2_rn(CD, make_float2(dn[i0], dn[i1]), o);
+                        o = __ffma2_rn(CU, make_float2(up[i0], up[i1]), o);
                         o = __ffma2_rn(DTS, make_float2(y[i0], y[i1]), o);
                         o = __ffma2_rn(NGE, ST, o);
                         __stcs(po + i0 * QP, o.x);
