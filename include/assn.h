@@ -128,7 +128,9 @@ int assn_set_quadrature(assn_problem* p, int Q, const double* omega, const doubl
 
 /* Product quadrature: n_polar Gauss-Legendre nodes in mu (computed on the host by Newton
  * iteration on P_n) times n_azim azimuths phi_k = (k+1/2) 2 pi / n_azim; weight
- * w = w_GL * 2 pi / n_azim; ordinate q = i*n_azim + k.  Same effects as assn_set_quadrature. */
+ * w = w_GL * 2 pi / n_azim; ordinate q = k*n_polar + i (azimuth-major: the ordinates of azimuth
+ * k are consecutive, and the kernel matrix repeats under the rotation q -> q + n_polar, which the
+ * paired-SM kernel uses to keep it resident).  Same effects as assn_set_quadrature. */
 int assn_set_product_quadrature(assn_problem* p, int n_polar, int n_azim);
 
 /* Icosahedron quadrature (Sec. 3.3; the paper prints the order-2 rule in Appendix A).  Order k

@@ -31,7 +31,8 @@ def product_quadrature(n_polar: int, n_azim: int):
 
     Sec. 3.1 (quadrature rule with weights w_q, sum of weights 4 pi) and
     Sec. 4 (ordinates projected onto the x-y plane for 2D transport).
-    Ordinate q = i * n_azim + k has mu = mu_i (i-th Gauss-Legendre node),
+    Ordinate q = k * n_polar + i (azimuth-major; the numbering of the set
+    is a convention the method does not fix) has mu = mu_i (i-th Gauss-Legendre node),
     azimuth phi_k = (k + 1/2) 2 pi / n_azim, direction
     (sqrt(1-mu^2) cos phi, sqrt(1-mu^2) sin phi, mu) and weight
     w_i^GL * 2 pi / n_azim.  Returns (Omega[Q,3], w[Q]).
@@ -44,7 +45,7 @@ def product_quadrature(n_polar: int, n_azim: int):
     for i in range(n_polar):
         st = math.sqrt(max(0.0, 1.0 - mu[i] * mu[i]))
         for k in range(n_azim):
-            q = i * n_azim + k
+            q = k * n_polar + i
             Omega[q] = (st * math.cos(phi[k]), st * math.sin(phi[k]), mu[i])
             w[q] = wgl[i] * 2.0 * math.pi / n_azim
     return Omega, w

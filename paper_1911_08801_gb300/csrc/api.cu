@@ -360,11 +360,13 @@ int assn_set_product_quadrature(assn_problem* p, int n_polar, int n_azim) {
     gauss_legendre(n_polar, mu, wg);
     const int Q = n_polar * n_azim;
     std::vector<double> om(3 * Q), w(Q);
+    // azimuth-major numbering q = k n_polar + i: a rotation by 2 pi / n_azim about the z axis maps
+    // ordinate q to q + n_polar, so the kernel matrix repeats along its block diagonals
     for (int i = 0; i < n_polar; ++i) {
         const double st = sqrt(std::max(0.0, 1.0 - mu[i] * mu[i]));
         for (int k = 0; k < n_azim; ++k) {
             const double phi = (k + 0.5) * 2.0 * M_PI / n_azim;
-            const int q = i * n_azim + k;
+            const int q = k * n_polar + i;
             om[3 * q] = st * cos(phi);
             om[3 * q + 1] = st * sin(phi);
             om[3 * q + 2] = mu[i];
