@@ -269,9 +269,14 @@ int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant);
 /* Rings of the persistent kernels (variants 0 and 2; BF16 / BF16X3 problems): depths of the staging
  * ring (FP32 flux chunks fed by TMA), the operand ring (BF16 chunks written by the converter warps)
  * and the kernel-matrix ring (2..8 each; 0 = automatic), and the ordinate blocks of 128 that one
- * kernel-matrix request brings (1, 2, 4, 8; 0 = automatic; variant 0 only).  Results do not depend
- * on these choices.  Selects variant 0 unless variant 2 was set explicitly.  get_rings reports the resolved values (any pointer may be NULL);
- * ASSN_ERR_UNSUPPORTED at the next step / get if the rings do not fit shared memory. */
+ * kernel-matrix request brings (1, 2, 4, 8; 0 = automatic; variant 0 only; variant 2 reads it as
+ * 64-ordinate chunks per stage, 1 or 2).  Variant 2 with kernel_matrix = 0 keeps the kernel matrix
+ * resident in shared memory where its distinct [128 x 64] blocks fit (all of them at 256 ordinates;
+ * at 512, the 8 distinct blocks per SM of an azimuth-major product quadrature), found by reading G
+ * back once when the step is planned (a sync; not done while the stream is being captured), and
+ * get_rings then reports kernel_matrix = 0.  Results do not depend on these choices.  Selects
+ * variant 0 unless variant 2 was set explicitly.  get_rings reports the resolved values (any pointer
+ * may be NULL); ASSN_ERR_UNSUPPORTED at the next step / get if the rings do not fit shared memory. */
 int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix, int blocks_per_request);
 int assn_get_rings(assn_problem* p, int* staging, int* operand, int* kernel_matrix, int* blocks_per_request);
 

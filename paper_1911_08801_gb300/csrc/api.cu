@@ -642,7 +642,7 @@ static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
                         "paired-SM step (variant 2): 193..256 or 449..512 ordinates only (Q = %d)", p->Q);
         e = tc3_plan_create(&p->plan3, (const float*)p->d_psi[0], (const float*)p->d_psi[1], p->tc.G_hi,
                             p->precision == ASSN_BF16X3 ? p->tc.G_lo : nullptr, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
-                            p->want_rings);
+                            p->want_rings, p->stream);
     }
     if (e == cudaErrorNotSupported)
         return fail(p, ASSN_ERR_UNSUPPORTED, "tensor-core step: Q = %d with tile %d / stages %d not supported", p->Q,

@@ -120,11 +120,15 @@ cudaError_t launch_heun_stage_tc2(Tc2Plan* plan, unsigned int* err_flag, int par
 // the flux buffers and G are bound at plan creation, dt at launch.
 struct Tc3Plan;
 bool tc3_supported(int Q, int Qp, int Mp, bool split);
-// G_lo non-null: the split (BF16X3) contraction, hi x hi + hi x lo + lo x hi.
+// G_lo non-null: the split (BF16X3) contraction, hi x hi + hi x lo + lo x hi.  With no kernel-matrix
+// ring requested (want.SA == 0) and one BF16 part, G is read back on `stream` (which syncs; skipped
+// while the stream is being captured) to find its distinct blocks, which stay resident if they fit.
 cudaError_t tc3_plan_create(Tc3Plan** plan, const float* buf0, const float* buf1, const __nv_bfloat16* G,
-                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want);
+                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want,
+                            cudaStream_t stream);
 void tc3_plan_destroy(Tc3Plan* plan);
-TcRings tc3_plan_rings(const Tc3Plan* plan);   // MPR = 128-row blocks per kernel-matrix request
+// MPR = 64-ordinate chunks per stage; SA = kernel-matrix ring depth, 0 when the matrix is resident
+TcRings tc3_plan_rings(const Tc3Plan* plan);
 // tile cells, kernel-matrix ring depth, CTA pairs launched, dynamic shared memory per CTA
 void tc3_plan_describe(const Tc3Plan* plan, int* tile_cells, int* stages, int* pairs, size_t* smem);
 // Reads buffer `parity`, writes buffer parity ^ 1.

@@ -18,7 +18,8 @@
 //               kernel-matrix copies to the even CTA.
 //               Lanes 1 and 2: TMA of this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64
 //               ordinates] chunks, into a staging ring, and of this CTA's G rows ([128 x 64] BF16
-//               blocks with 128-byte swizzle, all of its 256-row groups and two chunks per request).
+//               blocks with 128-byte swizzle): its distinct blocks once (resident), or all of its
+//               256-row groups, one or two chunks per request, through a ring.
 //   warps 1-3   converters: staging -> BF16 operand rows (K-major, swizzled) for the pair's MMA;
 //               the scalar flux Phi = sum_p w_p psi_p of this CTA's cells, and from it the cells'
 //               coefficients, written into both CTAs.
@@ -36,6 +37,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "assn_internal.h"
 #include "tc_ptx.h"
@@ -64,6 +66,11 @@ struct Tc3Args {
     const CellF* cell;                  // [ncell]
     const float* w;                     // [Qp]
     unsigned int* err;
+    // resident kernel matrix (nslot > 0): the distinct [128 x 64] blocks of this CTA's rows, loaded
+    // once; 4-bit fields indexed by kc MG + j (chunk kc, group j): slots = the slot holding that
+    // block, reps = for slot s, the index kc MG + j it is loaded from
+    unsigned long long slots, reps;
+    int nslot;
     int nx, ny, Q, ntx, total;
     int SS, SB, SA;
     float dt, dts;                      // dt and dt sigma_as
@@ -84,19 +91,20 @@ struct L3 {
     static constexpr int kB = NP * CPS * NTc * 128;     // BF16 operand stage (hi chunks, then lo chunks)
     static constexpr int kA = NP * CPS * MG * kABlock;  // G stage: this CTA's blocks of CPS chunks (hi, then lo)
     int stg, b, a, cx, cy, cb, cst, wsm, bars, end;
-    __host__ __device__ L3(int SS, int SB, int SA) {
+    __host__ __device__ L3(int SS, int SB, int SA, int nslot) {
         stg = 0;
         b = stg + SS * kStg;
         a = b + SB * kB;
-        cx = a + SB * kA;                       // [2][NT] 1 - dt sigma_t (kernel-matrix ring: SB stages too)
+        // kernel matrix: nslot resident blocks, else a ring of SB stages (the operand ring's depth)
+        cx = a + (nslot > 0 ? nslot * kABlock : SB * kA);   // [2][NT] 1 - dt sigma_t
         cy = cx + 2 * NT * 4;                   // [2][NT] dt (sigma_s Phi / sum w + q)
         cb = cy + 2 * NT * 4;                   // [2][NT] neighbour bits
         cst = cb + 2 * NT * 4;                  // [NTc] cell constants of this CTA's cells
         wsm = cst + NTc * 16;                   // [QP] quadrature weights
         bars = wsm + QP * 4;
         // stg full/empty [SS], stage full/pair/empty [SB] (operand and kernel-matrix rings advance
-        // together, SA == SB), tm full/empty [2], phi full/empty [2], drain
-        end = bars + 8 * (2 * SS + 3 * SB + 9) + 16;
+        // together, SA == SB), tm full/empty [2], phi full/empty [2], drain, resident kernel matrix
+        end = bars + 8 * (2 * SS + 3 * SB + 10) + 16;
     }
 };
 
@@ -124,7 +132,8 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     constexpr int CPS = LT::CPS, KR = LT::KR;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const LT L(a.SS, a.SB, a.SA);
+    const LT L(a.SS, a.SB, a.SA, a.nslot);
+    const bool resident = a.nslot > 0;
     float* stg = reinterpret_cast<float*>(base + L.stg);
     unsigned char* bring = base + L.b;
     unsigned char* aring = base + L.a;
@@ -147,7 +156,8 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     uint64_t* phi_full = tm_empty + 2;
     uint64_t* phi_empty = phi_full + 2;
     uint64_t* drain_bar = phi_empty + 2;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain_bar + 1);
+    uint64_t* gres = drain_bar + 1;      // the resident kernel-matrix blocks have landed
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gres + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -158,7 +168,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     if (tid == 0) {
         for (int s = 0; s < a.SS; ++s) { mbar_init(&stg_full[s], 1); mbar_init(&stg_empty[s], kConv3); }
         for (int s = 0; s < a.SB; ++s) {
-            mbar_init(&st_full[s], kConv3 + 1);
+            mbar_init(&st_full[s], kConv3 + (resident ? 0 : 1));   // + the kernel-matrix copy when streamed
             mbar_init(&st_pair[s], 1);
             mbar_init(&st_empty[s], 1);
         }
@@ -169,6 +179,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             mbar_init(&phi_empty[b], 2 * kEpi3);
         }
         mbar_init(drain_bar, 1);
+        mbar_init(gres, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -189,7 +200,8 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             const uint64_t a0 = sw128_desc(smem_u32(aring));
             const uint64_t b0 = sw128_desc(smem_u32(bring));
             Ring3 rq;
-            bool ok = true;
+            bool ok = !resident || W3(gres, 0u, 0x80u);
+            tc_fence_after();
             for (int T = pair, it = 0; T < total && ok; T += npair, ++it) {
                 const int buf = it & 1;
                 const uint32_t use = (uint32_t)(it >> 1);
@@ -208,9 +220,13 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                     for (int c = 0; c < CPS; ++c) {
 #pragma unroll
                         for (int j = 0; j < MG; ++j) {
+                            // this round's block of group j: its resident slot, else its place in the stage
+                            const int blk = resident ? (int)((a.slots >> (4 * ((kr * CPS + c) * MG + j))) & 15u)
+                                                     : c * MG + j;
+                            const uint64_t ab = resident ? a0 : ad0;
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ah = ad0 + (uint64_t)(((c * MG + j) * kABlock) >> 4) + (uint64_t)(kk * 2);
+                                const uint64_t ah = ab + (uint64_t)((blk * kABlock) >> 4) + (uint64_t)(kk * 2);
                                 const uint64_t bh = bd0 + (uint64_t)((c * NTc * 128) >> 4) + (uint64_t)(kk * 2);
                                 const uint32_t dd = dbase + (uint32_t)(j * NT);
                                 mma_bf16_pair(dd, ah, bh, idesc, (kr > 0 || c > 0 || kk > 0) ? 1u : 0u);
@@ -237,7 +253,9 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             // even CTA, whose MMAs then read it)
             const uint32_t pair0 = mapa_shared(smem_u32(st_pair), 0);
             Ring3 rq;
-            for (int T = pair; T < total; T += npair) {
+            // (with a resident kernel matrix, the first completion forwarded also vouches for its blocks)
+            const bool res_ok = !resident || W3(gres, 0u, 0x4000u);
+            for (int T = pair; T < total && res_ok; T += npair) {
                 bool ok = true;
                 for (int kr = 0; kr < KR; ++kr) {
                     if (!W3(&st_full[rq.s], rq.ph, 0x400u)) { ok = false; break; }
@@ -274,7 +292,18 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
             Ring3 rq;
             uint32_t armed = 0u, apar = 0u;
-            for (int T = pair; T < total; T += npair) {
+            if (resident) {
+                // the distinct blocks of this CTA's rows, once; this thread waits (bounded) for them
+                // to land so that no copy is in flight at teardown, whatever the other roles do
+                mbar_expect_tx(gres, (uint32_t)(a.nslot * kABlock));
+                for (int sl = 0; sl < a.nslot; ++sl) {
+                    const int idx = (int)((a.reps >> (4 * sl)) & 15u);
+                    tma_load_5d_hint(aring + (size_t)sl * kABlock, &a.tm_G, gres, 0, 0, (int)rank, idx % MG, idx / MG,
+                                     pol);
+                }
+                if (!mbar_drain(gres, 0u, kDrainNs)) atomicOr(a.err, kErrUndrained);
+            }
+            for (int T = pair; T < total && !resident; T += npair) {
                 bool ok = true;
                 for (int kr = 0; kr < KR; ++kr) {
                     if (!W3(&st_empty[rq.s], rq.ph ^ 1u, 0x2u)) { ok = false; break; }
@@ -312,14 +341,16 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
         const uint32_t cy_rem = mapa_shared(smem_u32(cy), rank ^ 1u);
         const uint32_t cb_rem = mapa_shared(smem_u32(cb), rank ^ 1u);
         const float dt = a.dt;
-        // byte offsets of this thread's operand stores in a chunk (row r = rsub + RS i, float4 column
-        // col4, canonical K-major layout with 128-byte swizzle): fixed for the whole launch
-        int offs[NR];
+        // byte offset of this thread's operand store for row r (float4 column col4, canonical
+        // K-major layout with 128-byte swizzle); fixed for the whole launch, so kept in registers
+        // where a thread has few rows
+        auto store_off = [col4](int r) {
+            return (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
+        };
+        constexpr bool kKeepOffs = NR <= 11;
+        int offs[kKeepOffs ? NR : 1];
 #pragma unroll
-        for (int i = 0; i < NR; ++i) {
-            const int r = rsub + RS * i;
-            offs[i] = (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
-        }
+        for (int i = 0; i < (kKeepOffs ? NR : 1); ++i) offs[i] = store_off(rsub + RS * i);
         Ring3 rs, rb;
         for (int T = pair, it = 0; T < total; T += npair, ++it) {
             const int ty = T / a.ntx, tx = T - ty * a.ntx;
@@ -349,7 +380,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 const float2 wa = make_float2(w4.x, w4.y), wb = make_float2(w4.z, w4.w);
                 // groups of up to GR rows: all shared-memory loads of a group first, then the
                 // arithmetic and the operand stores (the rows are independent, so the loads overlap)
-                constexpr int GR = NR <= 11 ? NR : 1;   // (22 rows at 256 ordinates: one at a time)
+                constexpr int GR = NR <= 11 ? NR : 8;      // (22 rows at 256 ordinates: groups of 8)
 #pragma unroll
                 for (int i0 = 0; i0 < NR; i0 += GR) {
                     float4 v[GR];
@@ -368,7 +399,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         uint2 h;
                         h.x = pack_bf16(v[g].x, v[g].y);
                         h.y = pack_bf16(v[g].z, v[g].w);
-                        const int off = offs[i];
+                        const int off = kKeepOffs ? offs[kKeepOffs ? i : 0] : store_off(r);
                         *reinterpret_cast<uint2*>(dst + off) = h;
                         if (SPLIT) {   // residual of the rounding, the lo part
                             const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.x));
@@ -653,13 +684,14 @@ bool encode_psi3(CUtensorMap* map, const float* psi, int Qp, int nx, int ny, int
 
 // G [Mp][Qp] BF16 as a 5D tensor {64 columns, 128 rows, 2 halves, MG groups, KC chunks}: one box
 // {64, 128, 1, MG, CPS} brings one CTA's rows of every 256-row group for CPS 64-column chunks, landing
-// as CPS x MG consecutive canonical [128 x 64] K-major tiles (128-byte swizzle), chunk-major.
-bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG, int CPS) {
+// as CPS x MG consecutive canonical [128 x 64] K-major tiles (128-byte swizzle), chunk-major.  The
+// resident kernel matrix takes single blocks (MG = CPS = 1 in the box).
+bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG, int CPS, int box_mg) {
     EncodeFn enc = get_encode3();
     if (!enc) return false;
     const cuuint64_t dims[5] = {64, 128, 2, (cuuint64_t)MG, (cuuint64_t)(Qp / 64)};
     const cuuint64_t strides[4] = {(cuuint64_t)Qp * 2, (cuuint64_t)Qp * 2 * 128, (cuuint64_t)Qp * 2 * 256, 128};
-    const cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)MG, (cuuint32_t)CPS};
+    const cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)box_mg, (cuuint32_t)CPS};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(G), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -667,14 +699,48 @@ bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG, int CPS
 }
 
 template <int MG, int CPS, bool SPLIT>
-size_t smem3(int SS, int SB, int SA) {
-    return (size_t)1024 + (size_t)L3<MG, CPS, SPLIT>(SS, SB, SA).end;
+size_t smem3(int SS, int SB, int nslot) {
+    return (size_t)1024 + (size_t)L3<MG, CPS, SPLIT>(SS, SB, SB, nslot).end;
 }
 
-size_t smem3_for(int MG, int CPS, bool split, int SS, int SB) {
-    if (split) return MG == 2 ? smem3<2, 1, true>(SS, SB, SB) : smem3<1, 1, true>(SS, SB, SB);
-    if (MG == 2) return CPS == 2 ? smem3<2, 2, false>(SS, SB, SB) : smem3<2, 1, false>(SS, SB, SB);
-    return CPS == 2 ? smem3<1, 2, false>(SS, SB, SB) : smem3<1, 1, false>(SS, SB, SB);
+size_t smem3_for(int MG, int CPS, bool split, int SS, int SB, int nslot) {
+    if (split) return MG == 2 ? smem3<2, 1, true>(SS, SB, nslot) : smem3<1, 1, true>(SS, SB, nslot);
+    if (MG == 2) return CPS == 2 ? smem3<2, 2, false>(SS, SB, nslot) : smem3<2, 1, false>(SS, SB, nslot);
+    return CPS == 2 ? smem3<1, 2, false>(SS, SB, nslot) : smem3<1, 1, false>(SS, SB, nslot);
+}
+
+// The distinct [128 x 64] blocks of G that the pair's MMAs read, as (even CTA's block, odd CTA's
+// block) pairs: a block of group j and chunk kc holds rows 256 j + 128 r .. + 127 (CTA r) and
+// columns 64 kc .. 64 kc + 63.  Both CTAs address a pair through one shared-memory slot, so two
+// (j, kc) share a slot only when both CTAs' blocks are equal bit for bit.  Fills the 4-bit slot and
+// representative tables and returns the number of slots (0 if G could not be read).
+int distinct_blocks(const __nv_bfloat16* G, int Qp, int MG, cudaStream_t s, unsigned long long* slots,
+                    unsigned long long* reps) {
+    const int KC = Qp / 64;
+    std::vector<uint16_t> h((size_t)256 * MG * Qp);
+    if (cudaMemcpyAsync(h.data(), G, h.size() * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return 0;
+    auto same = [&](int a, int b) {   // block indices kc MG + j
+        const int ja = a % MG, ka = a / MG, jb = b % MG, kb = b / MG;
+        for (int r = 0; r < 256; ++r)
+            if (memcmp(&h[(size_t)(256 * ja + r) * Qp + 64 * ka], &h[(size_t)(256 * jb + r) * Qp + 64 * kb], 128))
+                return false;
+        return true;
+    };
+    int n = 0;
+    *slots = *reps = 0ull;
+    for (int idx = 0; idx < KC * MG; ++idx) {
+        int sl = -1;
+        for (int t = 0; t < n && sl < 0; ++t)
+            if (same((int)((*reps >> (4 * t)) & 15u), idx)) sl = t;
+        if (sl < 0) {
+            sl = n++;
+            *reps |= (unsigned long long)idx << (4 * sl);
+        }
+        *slots |= (unsigned long long)sl << (4 * idx);
+    }
+    return n;
 }
 
 using Tc3Kernel = void (*)(Tc3Args);
@@ -688,6 +754,8 @@ Tc3Kernel kernel3(int MG, int CPS, bool split) {
 
 struct Tc3Plan {
     int MG = 0, CPS = 2, SS = 0, SB = 0, SA = 0, grid = 0, total = 0, ntx = 0;
+    int nslot = 0;                      // resident kernel-matrix blocks (0: the kernel-matrix ring)
+    unsigned long long slots = 0, reps = 0;
     bool split = false;
     size_t smem = 0;
     CUtensorMap tm_psi[2], tm_G, tm_Glo;
@@ -702,7 +770,8 @@ bool tc3_supported(int Q, int Qp, int Mp, bool split) {
 }
 
 cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1, const __nv_bfloat16* G,
-                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want) {
+                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want,
+                            cudaStream_t stream) {
     *out = nullptr;
     const bool split = G_lo != nullptr;
     if (!tc3_supported(Q, Qp, Mp, split)) return cudaErrorNotSupported;
@@ -717,7 +786,16 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     p->CPS = (want.MPR == 1 || split) ? 1 : 2;   // split operands: one chunk per stage
     p->SS = want.SS ? want.SS : 4;
     p->SB = p->SA = want.SB ? want.SB : (want.SA ? want.SA : 2);
-    auto need = [&](int) { return smem3_for(p->MG, p->CPS, p->split, p->SS, p->SB); };
+    // the kernel matrix resident (no kernel-matrix ring requested, one BF16 part, not while the
+    // stream is being captured: the check reads G back): its distinct blocks, loaded once per
+    // launch, when they fit beside two staging stages
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (!want.SA && !split && cudaStreamIsCapturing(stream, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone) {
+        const int n = distinct_blocks(G, Qp, p->MG, stream, &p->slots, &p->reps);
+        if (n > 0 && smem3_for(p->MG, p->CPS, false, want.SS ? want.SS : 2, p->SB, n) <= limit) p->nslot = n;
+    }
+    auto need = [&](int) { return smem3_for(p->MG, p->CPS, p->split, p->SS, p->SB, p->nslot); };
     if (!want.SS)
         while (p->SS > 2 && need(p->SA) > limit) --p->SS;
     if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
@@ -731,7 +809,8 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     p->buf[0] = buf0;
     p->buf[1] = buf1;
     if (!encode_psi3(&p->tm_psi[0], buf0, Qp, nx, ny, TH / 2) || !encode_psi3(&p->tm_psi[1], buf1, Qp, nx, ny, TH / 2) ||
-        !encode_G5(&p->tm_G, G, Qp, p->MG, p->CPS) || (split && !encode_G5(&p->tm_Glo, G_lo, Qp, p->MG, p->CPS))) {
+        !encode_G5(&p->tm_G, G, Qp, p->MG, p->nslot ? 1 : p->CPS, p->nslot ? 1 : p->MG) ||
+        (split && !encode_G5(&p->tm_Glo, G_lo, Qp, p->MG, p->CPS, p->MG))) {
         delete p;
         return cudaErrorInvalidValue;
     }
@@ -771,7 +850,7 @@ TcRings tc3_plan_rings(const Tc3Plan* p) {
     if (p) {
         r.SS = p->SS;
         r.SB = p->SB;
-        r.SA = p->SA;
+        r.SA = p->nslot ? 0 : p->SA;   // 0: the kernel matrix is resident
         r.MPR = p->CPS;
     }
     return r;
@@ -806,6 +885,9 @@ cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const
     a.SS = p->SS;
     a.SB = p->SB;
     a.SA = p->SA;
+    a.nslot = p->nslot;
+    a.slots = p->slots;
+    a.reps = p->reps;
     a.dt = dt;
     a.dts = dt_sigma_as;
     kernel3(p->MG, p->CPS, p->split)<<<p->grid, kThreads3, p->smem, s>>>(a);

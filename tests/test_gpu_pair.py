@@ -173,3 +173,33 @@ def test_automatic_variant(A):
         p.set_scheme(scheme)
         assert p.variant() == want, (npol, naz, prec, scheme)
         p.close()
+
+
+@pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16)])
+def test_resident_kernel_matrix_matches_ring(A, npol, naz):
+    """With no kernel-matrix ring requested, the distinct blocks of G stay resident (at 512
+    ordinates, numbered azimuth-major, 8 of each CTA's 16 blocks are distinct; at 256 its 4 blocks
+    fit as they are); the MMAs read the same BF16 values in the same order as with the ring, so two
+    steps are bitwise equal.  A quadrature numbered so that no two blocks are equal (the product set
+    polar-major) streams G through the ring at 512 ordinates."""
+    wl = random_workload(40, 21, npol, naz, seed=9)
+    states = []
+    for kernel_matrix in (0, 2):
+        p = pair_problem(A, wl)
+        p.set_rings(0, 0, kernel_matrix, 0)
+        assert p.variant() == 2 and p.rings()["kernel_matrix"] == kernel_matrix
+        dt = 0.9 * p.max_stable_dt()
+        p.step(2, dt)
+        states.append(p.state())
+        p.close()
+    assert np.array_equal(states[0], states[1])
+    if npol * naz == 512:
+        Om, w = O.product_quadrature(npol, naz)
+        perm = np.array([k * npol + i for i in range(npol) for k in range(naz)])   # polar-major
+        p = A.Problem(8, 8, 0.0, 0.4, 0.0, 0.4, "bf16").set_quadrature(Om[perm], w[perm])
+        z = np.zeros((8, 8))
+        p.set_cross_sections(z + 1.0, z + 0.5, z)
+        p.set_artificial_scattering(5.0, wl.eps)
+        p.set_tiling(0, 0, 2)
+        assert p.rings()["kernel_matrix"] == 2
+        p.close()
