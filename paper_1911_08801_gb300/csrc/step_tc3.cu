@@ -16,11 +16,13 @@
 //               CTA issues the MMAs into one of two accumulator buffers and commits to the
 //               barriers of both CTAs; lane 0 of the odd CTA forwards the completion of its own
 //               kernel-matrix copies to the even CTA.
-//               Lanes 1 and 2: TMA of this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64
-//               ordinates] chunks, into a staging ring, and of this CTA's G rows ([128 x 64] BF16
-//               blocks with 128-byte swizzle): its distinct blocks once (resident), or all of its
-//               256-row groups, one or two chunks per request, through a ring.
-//   warps 1-3   converters: staging -> BF16 operand rows (K-major, swizzled) for the pair's MMA;
+//               Lane 2: TMA of this CTA's G rows ([128 x 64] BF16 blocks with 128-byte swizzle): its
+//               distinct blocks once (resident), or all of its 256-row groups, one or two chunks
+//               per request, through a ring.
+//   flux TMA    this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64 ordinates] chunks, into a
+//               staging ring: warp 3 at 512 ordinates (BF16), else lane 1 of warp 0.
+//   warps 1-3   converters (1-2 at 512 ordinates in BF16): staging -> BF16 operand rows (K-major,
+//               swizzled) for the pair's MMA;
 //               the scalar flux Phi = sum_p w_p psi_p of this CTA's cells, and from it the cells'
 //               coefficients, written into both CTAs.
 //   warps 4-19  epilogue: warp (lane quarter lq, group g) owns 32 ordinates of one 128-row block
@@ -49,10 +51,10 @@ namespace {
 using namespace ptx;
 
 constexpr int kTW = 16;                 // tile width (cells)
-constexpr int kConv3 = 3;               // converter warps (1 .. 3)
 constexpr int kEpi3 = 16;               // epilogue warps (4 .. 19; any four consecutive warps cover the
                                         // four TMEM lane quarters, warp & 3)
-constexpr int kEpi0 = 1 + kConv3;       // first epilogue warp
+constexpr int kEpi0 = 4;                // first epilogue warp; warps 1-3 convert, or 1-2 convert and 3
+                                        // requests the flux copies
 constexpr int kThreads3 = (kEpi0 + kEpi3) * 32;
 constexpr int kABlock = 128 * 64 * 2;   // one [128 x 64] BF16 block of G
 
@@ -128,6 +130,13 @@ template <int MG, int CPS_, bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
 step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     using LT = L3<MG, CPS_, SPLIT>;
+    // converter warps and where the flux-copy producer runs: at 512 ordinates (16-kB chunks) two
+    // converter warps keep up and the producer gets warp 3 to itself (as one lane of warp 0, beside
+    // the MMA issuer's waits, it issued each copy about a microsecond after its slot was released:
+    // 0.180 -> 0.174 ms on the 448^2 lattice); 32-kB chunks at 256 ordinates and the split
+    // operands need three converter warps (2.14 against 1.80-1.95 ms on the 2048^2 line source)
+    constexpr int kConv3 = (MG == 2 && !SPLIT) ? 2 : 3;
+    constexpr bool kProdWarp = kConv3 == 2;
     constexpr int NT = LT::NT, TH = LT::TH, THc = LT::THc, NTc = LT::NTc, QP = LT::QP, KC = LT::KC;
     constexpr int CPS = LT::CPS, KR = LT::KR;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -192,6 +201,32 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     cluster_sync();   // the peer's barriers are initialised and its tensor memory allocated
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
+
+    // flux TMA producer: this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64 ordinates]
+    // chunks, into the staging ring
+    auto flux_producer = [&]() {
+        const uint64_t pol = policy_evict_last();   // the epilogue re-reads these lines shortly
+        Ring3 rs;
+        uint32_t armed = 0u, apar = 0u;
+        for (int T = pair; T < total; T += npair) {
+            const int ty = T / a.ntx, tx = T - ty * a.ntx;
+            bool ok = true;
+            for (int kc = 0; kc < KC; ++kc) {
+                if (!W3(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
+                mbar_expect_tx(&stg_full[rs.s], LT::kStg);
+                tma_load_3d_hint(stg + (size_t)rs.s * NTc * 64, &a.tm_psi, &stg_full[rs.s], kc * 64, tx * kTW,
+                                 ty * TH + (int)rank * THc, pol);
+                armed |= 1u << rs.s;
+                apar = (apar & ~(1u << rs.s)) | (rs.ph << rs.s);
+                rs.next(a.SS);
+            }
+            if (!ok) break;
+        }
+        if (*abort_flag)
+            for (int s2 = 0; s2 < a.SS; ++s2)
+                if (((armed >> s2) & 1u) && !mbar_drain(&stg_full[s2], (apar >> s2) & 1u, kDrainNs))
+                    atomicOr(a.err, kErrUndrained);
+    };
 
     if (warp == 0) {
         if (lane == 0 && rank == 0) {
@@ -265,28 +300,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 if (!ok) break;
             }
         } else if (lane == 1) {
-            // ----------------------------------------------------------------- flux TMA producer
-            const uint64_t pol = policy_evict_last();   // the epilogue re-reads these lines shortly
-            Ring3 rs;
-            uint32_t armed = 0u, apar = 0u;
-            for (int T = pair; T < total; T += npair) {
-                const int ty = T / a.ntx, tx = T - ty * a.ntx;
-                bool ok = true;
-                for (int kc = 0; kc < KC; ++kc) {
-                    if (!W3(&stg_empty[rs.s], rs.ph ^ 1u, 0x1u)) { ok = false; break; }
-                    mbar_expect_tx(&stg_full[rs.s], LT::kStg);
-                    tma_load_3d_hint(stg + (size_t)rs.s * NTc * 64, &a.tm_psi, &stg_full[rs.s], kc * 64, tx * kTW,
-                                     ty * TH + (int)rank * THc, pol);
-                    armed |= 1u << rs.s;
-                    apar = (apar & ~(1u << rs.s)) | (rs.ph << rs.s);
-                    rs.next(a.SS);
-                }
-                if (!ok) break;
-            }
-            if (*abort_flag)
-                for (int s2 = 0; s2 < a.SS; ++s2)
-                    if (((armed >> s2) & 1u) && !mbar_drain(&stg_full[s2], (apar >> s2) & 1u, kDrainNs))
-                        atomicOr(a.err, kErrUndrained);
+            if (!kProdWarp) flux_producer();
         } else if (lane == 2) {
             // --------------------------------------------------------- kernel-matrix TMA producer
             const uint64_t pol = policy_evict_last();   // every tile re-reads G from L2
@@ -324,7 +338,9 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                     if (((armed >> s2) & 1u) && !mbar_drain(&st_full[s2], (apar >> s2) & 1u, kDrainNs))
                         atomicOr(a.err, kErrUndrained);
         }
-    } else if (warp < kEpi0) {
+    } else if (kProdWarp && warp == 1 + kConv3) {
+        if (lane == 0) flux_producer();
+    } else if (warp <= kConv3) {
         // ------------------------------------------------------------------------ converters
         // Thread (rsub, col4) converts float4 column col4 of the cells rsub, rsub + RS, ... of each
         // staged chunk and owns the cell constants and coefficients of cells col4 + 16 k of its
