@@ -53,7 +53,8 @@ typedef enum {
     ASSN_ERR_NONFINITE = -5,    /* NaN/Inf found in the state                               */
     ASSN_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up                       */
     ASSN_ERR_STATE = -7,        /* call out of order (e.g. step before quadrature is set)   */
-    ASSN_ERR_UNSUPPORTED = -8   /* size or mode not supported by the selected kernel        */
+    ASSN_ERR_UNSUPPORTED = -8,  /* size or mode not supported by the selected kernel        */
+    ASSN_ERR_CANCELLED = -9     /* a server request was cancelled (assn_server_cancel)       */
 } assn_status;
 
 /* Arithmetic of the step.  State and stencil are FP64 for ASSN_FP64 and FP32 otherwise;
@@ -308,6 +309,14 @@ int assn_mass(assn_problem* p, double* mass_out);
 /* Check the state for NaN/Inf: ASSN_OK or ASSN_ERR_NONFINITE.  Syncs. */
 int assn_check_finite(assn_problem* p);
 
+/* Out-of-bounds write check (a debugging aid; the method has no counterpart).  Each of the two
+ * state buffers sits between two 4096-byte guard regions filled with 0xA5 when the state is
+ * allocated.  Writes *guard_bytes_changed = the guard bytes that no longer hold 0xA5, and
+ * *padding_nonzero = the padded ordinates (Q <= q < Qpad, both buffers) whose bits are not all
+ * zero; both are 0 while every kernel has kept to its cells and ordinates.  Syncs.
+ * Errors: ASSN_ERR_ARG on NULL, ASSN_ERR_STATE before a quadrature is set. */
+int assn_check_guards(assn_problem* p, int64_t* guard_bytes_changed, int64_t* padding_nonzero);
+
 /* ---- Batches: several problems stepped by one persistent launch per step.
  * The members may differ in grid size, quadrature (ordinate count), kernel width eps, cross
  * sections and dt; they share the device and one tensor-core precision (ASSN_BF16 or
@@ -447,6 +456,15 @@ int assn_server_submit(assn_server* s, const assn_request* r, int64_t* id);
  * unknown id. */
 int assn_server_wait(assn_server* s, int64_t id, double timeout_s, double* phi_host, double* latency_s,
                      double* queue_s);
+
+/* Cancel request `id`.  A request still queued leaves the queue at once; one already on the device
+ * is retired at the loop's next chunk boundary (its memory freed; a solve that reaches its last step
+ * in the chunk running when the call is made completes normally instead).  assn_server_wait then
+ * returns ASSN_ERR_CANCELLED for it, and the statistics count it as failed.  The other requests'
+ * results are unaffected (each equals its own solve alone).  Errors: ASSN_ERR_ARG for an unknown id,
+ * ASSN_ERR_STATE if the request has already finished. */
+int assn_server_cancel(assn_server* s, int64_t id);
+
 int assn_server_get_stats(assn_server* s, assn_server_stats* out);
 /* Finish every queued and admitted request, stop the loop and free the server.  Results not
  * collected by assn_server_wait are dropped. */

@@ -120,6 +120,11 @@ class Problem:
     def check_finite(self):
         _lib.assn_check_finite(self.handle)
 
+    def check_guards(self) -> dict:
+        """Guard bytes around the state buffers that changed and padded ordinates that are not zero
+        (both 0 while every kernel kept to its cells and ordinates)."""
+        return _lib.assn_check_guards(self.handle)
+
     def set_tiling(self, tile_cells: int = 0, stages: int = 0, variant: int = 0):
         _lib.assn_set_tiling(self.handle, tile_cells, stages, variant)
         return self
@@ -281,6 +286,11 @@ class Server:
             raise
         del self._shapes[rid]
         return phi, lat, qs
+
+    def cancel(self, rid: int):
+        """Cancel request ``rid``: dropped from the queue, or retired at the next chunk boundary;
+        ``wait`` then raises AssnError with ASSN_ERR_CANCELLED."""
+        _lib.assn_server_cancel(self.handle, rid)
 
     def stats(self) -> dict:
         return _lib.assn_server_get_stats(self.handle)

@@ -23,6 +23,7 @@ ASSN_ERR_NONFINITE = -5
 ASSN_ERR_TIMEOUT = -6
 ASSN_ERR_STATE = -7
 ASSN_ERR_UNSUPPORTED = -8
+ASSN_ERR_CANCELLED = -9
 
 ASSN_FP64, ASSN_FP32, ASSN_BF16, ASSN_BF16X3 = 0, 1, 2, 3
 ASSN_KERNEL_GAUSS, ASSN_KERNEL_EXP = 0, 1
@@ -102,6 +103,7 @@ SIGNATURES = {
     "assn_scalar_flux_device": (C.c_int, [_h, _vp]),
     "assn_mass": (C.c_int, [_h, _dp]),
     "assn_check_finite": (C.c_int, [_h]),
+    "assn_check_guards": (C.c_int, [_h, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "assn_last_error": (C.c_char_p, [_h]),
     "assn_status_string": (C.c_char_p, [C.c_int]),
     "assn_launch_count": (C.c_int64, [_h]),
@@ -128,6 +130,7 @@ SIGNATURES = {
     "assn_server_create": (C.c_int, [C.POINTER(_h), C.c_int, C.c_size_t, C.c_int, C.c_int, C.c_int]),
     "assn_server_submit": (C.c_int, [_h, C.POINTER(AssnRequest), C.POINTER(C.c_int64)]),
     "assn_server_wait": (C.c_int, [_h, C.c_int64, C.c_double, _dp, _dp, _dp]),
+    "assn_server_cancel": (C.c_int, [_h, C.c_int64]),
     "assn_server_get_stats": (C.c_int, [_h, C.POINTER(AssnServerStats)]),
     "assn_server_destroy": (C.c_int, [_h]),
     "assn_server_last_error": (C.c_char_p, []),
@@ -381,6 +384,12 @@ def assn_check_finite(h: int) -> None:
     _check(lib.assn_check_finite(h), h)
 
 
+def assn_check_guards(h: int) -> dict:
+    g, z = C.c_int64(0), C.c_int64(0)
+    _check(lib.assn_check_guards(h, C.byref(g), C.byref(z)), h)
+    return {"guard_bytes_changed": g.value, "padding_nonzero": z.value}
+
+
 def assn_last_error(h: int | None) -> str:
     return lib.assn_last_error(h).decode()
 
@@ -515,6 +524,10 @@ def assn_server_get_stats(s: int) -> dict:
 
 def assn_server_destroy(s: int) -> None:
     _scheck(lib.assn_server_destroy(s))
+
+
+def assn_server_cancel(s: int, rid: int) -> None:
+    _scheck(lib.assn_server_cancel(s, rid))
 
 
 def assn_server_last_error() -> str:

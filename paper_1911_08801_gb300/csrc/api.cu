@@ -108,11 +108,19 @@ int ensure_stage(assn_problem* p, size_t elems) {
     return ASSN_OK;
 }
 
+constexpr size_t kStateGuard = 4096;        // bytes before and after each state buffer
+constexpr unsigned char kGuardByte = 0xA5;
+
 int alloc_state(assn_problem* p) {
+    const size_t bytes = p->ncell() * p->Qp * p->elem();
     for (int b = 0; b < 2; ++b) {
-        dfree(p->d_psi[b]);
-        CK(p, cudaMalloc(&p->d_psi[b], p->ncell() * p->Qp * p->elem()));
-        CK(p, cudaMemsetAsync(p->d_psi[b], 0, p->ncell() * p->Qp * p->elem(), p->stream));
+        dfree(p->d_psi_raw[b]);
+        p->d_psi[b] = nullptr;
+        CK(p, cudaMalloc(&p->d_psi_raw[b], bytes + 2 * kStateGuard));
+        p->d_psi[b] = p->d_psi_raw[b] + kStateGuard;
+        CK(p, cudaMemsetAsync(p->d_psi_raw[b], kGuardByte, kStateGuard, p->stream));
+        CK(p, cudaMemsetAsync(p->d_psi_raw[b] + kStateGuard + bytes, kGuardByte, kStateGuard, p->stream));
+        CK(p, cudaMemsetAsync(p->d_psi[b], 0, bytes, p->stream));
     }
     p->cur = 0;
     return ASSN_OK;
@@ -272,6 +280,7 @@ const char* assn_status_string(int s) {
         case ASSN_ERR_TIMEOUT: return "ASSN_ERR_TIMEOUT";
         case ASSN_ERR_STATE: return "ASSN_ERR_STATE";
         case ASSN_ERR_UNSUPPORTED: return "ASSN_ERR_UNSUPPORTED";
+        case ASSN_ERR_CANCELLED: return "ASSN_ERR_CANCELLED";
         default: return "ASSN_ERR_UNKNOWN";
     }
 }
@@ -328,7 +337,7 @@ int assn_destroy(assn_problem* p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     free_operands(p);
     dfree(p->d_omega); dfree(p->d_w64); dfree(p->d_w32); dfree(p->d_ord); dfree(p->d_cell);
-    dfree(p->d_psi[0]); dfree(p->d_psi[1]); dfree(p->d_partials); dfree(p->d_scalar); dfree(p->d_flags);
+    dfree(p->d_psi_raw[0]); dfree(p->d_psi_raw[1]); dfree(p->d_partials); dfree(p->d_scalar); dfree(p->d_flags);
     dfree(p->d_counter);
     dfree(p->d_stage);
     assn::implicit_free(p->impl);
@@ -941,6 +950,36 @@ int assn_check_finite(assn_problem* p) {
     CK(p, cudaMemcpyAsync(&f, p->d_flags, sizeof f, cudaMemcpyDeviceToHost, p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     if (f) return fail(p, ASSN_ERR_NONFINITE, "state holds NaN or Inf");
+    return check_flags(p);
+}
+
+int assn_check_guards(assn_problem* p, int64_t* guard_bytes_changed, int64_t* padding_nonzero) {
+    if (!p || !guard_bytes_changed || !padding_nonzero) return ASSN_ERR_ARG;
+    if (!p->d_psi_raw[0]) return fail(p, ASSN_ERR_STATE, "no state allocated");
+    int r = set_device(p);
+    if (r) return r;
+    const size_t bytes = p->ncell() * p->Qp * p->elem();
+    std::vector<unsigned char> g(4 * kStateGuard);
+    unsigned long long* d_count = reinterpret_cast<unsigned long long*>(p->d_partials);   // scratch
+    CK(p, cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), p->stream));
+    for (int b = 0; b < 2; ++b) {
+        CK(p, cudaMemcpyAsync(g.data() + (2 * b) * kStateGuard, p->d_psi_raw[b], kStateGuard, cudaMemcpyDeviceToHost,
+                              p->stream));
+        CK(p, cudaMemcpyAsync(g.data() + (2 * b + 1) * kStateGuard, p->d_psi_raw[b] + kStateGuard + bytes, kStateGuard,
+                              cudaMemcpyDeviceToHost, p->stream));
+        if (p->precision == ASSN_FP64)
+            CK(p, launch_padding_nonzero((const double*)p->d_psi[b], p->ncell(), p->Q, p->Qp, d_count, p->stream));
+        else
+            CK(p, launch_padding_nonzero((const float*)p->d_psi[b], p->ncell(), p->Q, p->Qp, d_count, p->stream));
+        p->launches++;
+    }
+    unsigned long long nz = 0;
+    CK(p, cudaMemcpyAsync(&nz, d_count, sizeof nz, cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaStreamSynchronize(p->stream));
+    int64_t bad = 0;
+    for (unsigned char c : g) bad += c != kGuardByte;
+    *guard_bytes_changed = bad;
+    *padding_nonzero = (int64_t)nz;
     return check_flags(p);
 }
 

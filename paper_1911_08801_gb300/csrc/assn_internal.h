@@ -145,6 +145,9 @@ cudaError_t launch_reduce_partials(const double* partials, int n, double* out, c
 template <typename T>
 cudaError_t launch_check_finite(const T* psi, size_t n, unsigned int* flag, cudaStream_t s);
 template <typename T>
+cudaError_t launch_padding_nonzero(const T* psi, size_t ncell, int Q, int Qp, unsigned long long* count,
+                                   cudaStream_t s);
+template <typename T>
 cudaError_t launch_init_line_source(T* psi, int nx, int ny, int Q, int Qp, double x0, double y0,
                                     double h, double delta, double floor_value, cudaStream_t s);
 template <typename T>

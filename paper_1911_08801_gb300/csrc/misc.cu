@@ -136,6 +136,35 @@ cudaError_t launch_reduce_partials(const double* partials, int n, double* out, c
 }
 
 template <typename T>
+__device__ __forceinline__ bool bits_nonzero(T v);
+template <>
+__device__ __forceinline__ bool bits_nonzero<float>(float v) { return __float_as_uint(v) != 0u; }
+template <>
+__device__ __forceinline__ bool bits_nonzero<double>(double v) { return __double_as_longlong(v) != 0ll; }
+
+// Counts the padded ordinates (Q <= q < Qp) of a state buffer whose bits are not all zero.
+template <typename T>
+__global__ void padding_nonzero_kernel(const T* psi, size_t ncell, int Q, int Qp, unsigned long long* count) {
+    const int pad = Qp - Q;
+    const size_t n = ncell * (size_t)pad;
+    unsigned long long local = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = i / (size_t)pad;
+        const int q = Q + (int)(i - c * (size_t)pad);
+        if (bits_nonzero<T>(psi[c * (size_t)Qp + q])) ++local;
+    }
+    if (local) atomicAdd(count, local);
+}
+
+template <typename T>
+cudaError_t launch_padding_nonzero(const T* psi, size_t ncell, int Q, int Qp, unsigned long long* count,
+                                   cudaStream_t s) {
+    if (Qp <= Q || ncell == 0) return cudaSuccess;
+    padding_nonzero_kernel<T><<<grid_for(ncell * (size_t)(Qp - Q), 256), 256, 0, s>>>(psi, ncell, Q, Qp, count);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_check_finite(const T* psi, size_t n, unsigned int* flag, cudaStream_t s) {
     check_finite_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(psi, n, flag);
     return cudaGetLastError();
@@ -165,6 +194,7 @@ cudaError_t launch_unpack_state(const T* src, double* dst, size_t ncell, int Q, 
     template cudaError_t launch_scalar_flux<T>(const T*, const T*, int, int, float*, double*, cudaStream_t);  \
     template cudaError_t launch_mass_partials<T>(const T*, const T*, int, int, double*, int, cudaStream_t);   \
     template cudaError_t launch_check_finite<T>(const T*, size_t, unsigned int*, cudaStream_t);              \
+    template cudaError_t launch_padding_nonzero<T>(const T*, size_t, int, int, unsigned long long*, cudaStream_t); \
     template cudaError_t launch_init_line_source<T>(T*, int, int, int, int, double, double, double, double,   \
                                                     double, cudaStream_t);                                    \
     template cudaError_t launch_pack_state<T>(const double*, T*, size_t, int, int, cudaStream_t);            \

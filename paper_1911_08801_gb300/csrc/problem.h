@@ -48,6 +48,9 @@ struct assn_problem {
     double ord_dt = -1.0;
     void* d_cell = nullptr;
     void* d_psi[2] = {nullptr, nullptr};
+    // each state buffer sits between two guard regions of kStateGuard bytes holding kGuardByte (the
+    // allocation starts at d_psi_raw[b]); assn_check_guards reads them back
+    unsigned char* d_psi_raw[2] = {nullptr, nullptr};
     int cur = 0;
     double* d_partials = nullptr;
     double* d_scalar = nullptr;

@@ -20,6 +20,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -71,6 +72,7 @@ struct assn_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request> queue;
     std::map<int64_t, Result> results;
+    std::set<int64_t> cancel;            // admitted requests to retire at the next chunk boundary
     bool stopping = false;
     int64_t next_id = 1;
 
@@ -169,6 +171,7 @@ void finish(assn_server* s, Active& a, int status, const std::string& msg) {
         ++s->failed;
     }
     s->t_last_done = now;
+    s->cancel.erase(a.req.id);
     s->results[a.req.id] = std::move(res);
     s->cv_done.notify_all();
 }
@@ -214,6 +217,24 @@ void loop_main(assn_server* s) {
                 continue;
             }
             s->active.push_back(std::move(a));
+        }
+        {   // cancelled while admitted: retire before the next chunk
+            std::vector<int64_t> drop;
+            {
+                std::lock_guard<std::mutex> g(s->mu);
+                for (const Active& a : s->active)
+                    if (s->cancel.count(a.req.id)) drop.push_back(a.req.id);
+            }
+            if (!drop.empty()) {
+                std::vector<Active> keep;
+                for (Active& a : s->active) {
+                    if (std::find(drop.begin(), drop.end(), a.req.id) != drop.end())
+                        finish(s, a, ASSN_ERR_CANCELLED, "cancelled");
+                    else
+                        keep.push_back(std::move(a));
+                }
+                s->active.swap(keep);
+            }
         }
         {
             std::lock_guard<std::mutex> g(s->mu);
@@ -266,7 +287,7 @@ int assn_footprint_bytes(int nx, int ny, int Q, int precision, size_t* bytes) {
         return ASSN_ERR_ARG;
     const size_t ncell = (size_t)nx * ny, Qp = (size_t)padq(Q), Mp = (Qp + 127) / 128 * 128;
     const size_t elem = precision == ASSN_FP64 ? 8 : 4;
-    size_t b = 2 * ncell * Qp * elem;            // ping-pong state
+    size_t b = 2 * ncell * Qp * elem + 4 * 4096; // ping-pong state and its guard regions
     b += ncell * 32 + ncell * 8;                 // cell constants, FP64 staging for the scalar flux
     b += (size_t)Q * Q * 8 + Qp * 64;            // FP64 K, per-ordinate constants
     if (precision == ASSN_FP64) b += Qp * Qp * 8;
@@ -371,6 +392,33 @@ int assn_server_wait(assn_server* s, int64_t id, double timeout_s, double* phi_h
     if (queue_s) *queue_s = res.queue_s;
     if (res.status != ASSN_OK) return sfail(s, res.status, "request %lld: %s", (long long)id, res.error.c_str());
     if (phi_host) std::copy(res.phi.begin(), res.phi.end(), phi_host);
+    return ASSN_OK;
+}
+
+int assn_server_cancel(assn_server* s, int64_t id) {
+    if (!s) return sfail(s, ASSN_ERR_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        auto it = s->results.find(id);
+        if (it == s->results.end()) return sfail(s, ASSN_ERR_ARG, "unknown request id %lld", (long long)id);
+        if (it->second.done) return sfail(s, ASSN_ERR_STATE, "request %lld has finished", (long long)id);
+        auto q = std::find_if(s->queue.begin(), s->queue.end(), [&](const Request& r) { return r.id == id; });
+        if (q == s->queue.end()) {   // admitted (or being admitted): the loop retires it
+            s->cancel.insert(id);
+            return ASSN_OK;
+        }
+        Result res;
+        res.status = ASSN_ERR_CANCELLED;
+        res.error = "cancelled before admission";
+        res.latency_s = std::chrono::duration<double>(Clock::now() - q->t_submit).count();
+        res.queue_s = res.latency_s;
+        res.done = true;
+        s->queue.erase(q);
+        ++s->failed;
+        it->second = std::move(res);
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();
     return ASSN_OK;
 }
 

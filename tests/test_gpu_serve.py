@@ -8,6 +8,7 @@ admission never exceeds the footprint budget, and failures stay with their own r
 from __future__ import annotations
 
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -155,3 +156,32 @@ def test_concurrent_submitters(A):
             t.join()
     for k, wl in enumerate(wls):
         assert np.array_equal(out[k], alone_phi(A, wl, *plan[k])), wl.name
+
+
+def test_cancel_queued_and_running(A):
+    """One request cancelled while queued and one while on the device both end with
+    ASSN_ERR_CANCELLED and leave the loop; the others' results stay equal to their solves alone."""
+    lead = synth.line_source(40, 16, 32, 0.5, t_final=10.0, name="long")   # hundreds of one-step chunks
+    n_lead, dt_lead = steps_for(A, lead)
+    others = request_workloads(seed=21, count=3)
+    plan = [steps_for(A, wl) for wl in others]
+    with A.Server("bf16", max_active=1, chunk_steps=1) as srv:   # the others queue behind the lead
+        rid = submit(srv, lead, n_lead, dt_lead)
+        ids = [submit(srv, wl, n, dt) for wl, (n, dt) in zip(others, plan)]
+        srv.cancel(ids[1])                                        # still queued
+        t0 = time.time()
+        while srv.stats()["active"] < 1 and time.time() - t0 < 60.0:
+            time.sleep(0.005)
+        srv.cancel(rid)                                           # on the device
+        for i in (rid, ids[1]):
+            with pytest.raises(A.AssnError) as ei:
+                srv.wait(i, timeout_s=120.0)
+            assert ei.value.status == A._lib.ASSN_ERR_CANCELLED
+        for k in (0, 2):
+            phi, _, _ = srv.wait(ids[k], timeout_s=120.0)
+            assert np.array_equal(phi, alone_phi(A, others[k], *plan[k])), others[k].name
+        with pytest.raises(A.AssnError) as ei:                   # collected: no longer known
+            srv.cancel(ids[0])
+        assert ei.value.status == A._lib.ASSN_ERR_ARG
+        st = srv.stats()
+    assert st["failed"] == 2 and st["completed"] == 2 and st["launches"] < n_lead
