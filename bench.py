@@ -237,14 +237,15 @@ def implicit_roofline(args, wl, ms_per_step: float, stats: dict, steps: int) -> 
             "sweeps_per_step": stats["sweeps"] / steps, "kernel": "sweep_kernel + si_source_kernel"}
 
 
-def heun_tc_roofline(wl, ms_per_step: float) -> dict:
-    """Heun on the tensor-core kernel: per update, stage 1 reads psi^n and writes psi*, stage 2 reads
+def heun_tc_roofline(wl, ms_per_step: float, variant) -> dict:
+    """Heun on a tensor-core kernel: per update, stage 1 reads psi^n and writes psi*, stage 2 reads
     psi* and psi^n and writes psi^{n+1}: 20 B of FP32 state."""
     hbm, src = peaks()
     achieved = 20.0 * wl.nx * wl.ny * wl.Q / (ms_per_step / 1e3) / 1e9
+    kernel = "step_tc3_kernel" if variant == 2 else "step_tc2_kernel"
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_update": 20,
-            "kernel": "step_tc2_kernel<..., HEUN> (two launches per step)"}
+            "kernel": f"{kernel}<..., HEUN> (two launches per step)"}
 
 
 def max_over_ranks(ms: float, dist, device: str) -> float:
@@ -375,7 +376,7 @@ def run_ours(args, rank, world, dist):
         "roofline": (euler_roofline(args, wl, ms_per_step, achieved, hbm, src, variant) if args.scheme == "euler" else
                      implicit_roofline(args, wl, ms_per_step, stats_timed, args.steps)
                      if args.scheme == "implicit" else
-                     (heun_tc_roofline(wl, ms_per_step) if args.precision.startswith("bf16")
+                     (heun_tc_roofline(wl, ms_per_step, variant) if args.precision.startswith("bf16")
                       else alu_roofline(args, wl, ms_per_step))),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

@@ -586,10 +586,11 @@ int assn_max_stable_dt(assn_problem* p, double* dt_out) {
 }
 
 // The tensor-core kernel a step of p runs: the requested variant, or (automatic, -1) the paired-SM
-// kernel where it applies (forward Euler, BF16 or BF16X3, 193..256 or 449..512 ordinates), else variant 0.
+// kernel where it applies (forward Euler or Heun, BF16 or BF16X3, 193..256 or 449..512 ordinates),
+// else variant 0.
 static int eff_variant(const assn_problem* p) {
     if (p->variant >= 0) return p->variant;
-    return (p->scheme == ASSN_SCHEME_EULER_UPWIND &&
+    return (p->scheme != ASSN_SCHEME_IMPLICIT &&
             tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision == ASSN_BF16X3)) ? 2 : 0;
 }
 
@@ -706,6 +707,19 @@ int assn_get_scheme(const assn_problem* p, int* scheme) {
 static int heun_step(assn_problem* p, double dt) {
     void* a = p->d_psi[p->cur];
     void* b = p->d_psi[p->cur ^ 1];
+    if (p->tensor() && eff_variant(p) == 2) {
+        // paired-SM kernel: stage 1 reads a and writes b; stage 2 reads b and writes a, keeping psi^n
+        // from a (each element is read there before it is overwritten, by the same thread)
+        const float fdt = (float)dt, fdts = (float)(dt * p->sigma_as);
+        cudaError_t e = launch_heun_stage_tc3(p->plan3, p->cur, (const OrdF*)p->d_ord, (const CellF*)p->d_cell,
+                                              p->d_w32, fdt, fdts, nullptr, 0.0f, 1.0f, p->d_flags + 1, p->stream);
+        if (e == cudaSuccess)
+            e = launch_heun_stage_tc3(p->plan3, p->cur ^ 1, (const OrdF*)p->d_ord, (const CellF*)p->d_cell, p->d_w32,
+                                      fdt, fdts, (const float*)a, 0.5f, 0.5f, p->d_flags + 1, p->stream);
+        CK(p, e);
+        p->launches += 2;
+        return ASSN_OK;
+    }
     if (p->tensor()) {
         // persistent kernel: the device step counter's parity selects the flux buffer, and each
         // launch advances it, so stage 1 reads a and writes b, stage 2 reads b and writes a
@@ -750,8 +764,9 @@ int assn_step(assn_problem* p, int nsteps, double dt) {
         int r = assn::problem_prepare(p, dt);
         if (r) return r;
         if (p->tensor()) {
-            if (eff_variant(p) != 0)
-                return fail(p, ASSN_ERR_UNSUPPORTED, "the Heun + minmod scheme runs on the persistent kernel (variant 0)");
+            if (eff_variant(p) == 1)
+                return fail(p, ASSN_ERR_UNSUPPORTED,
+                            "the Heun + minmod scheme runs on the persistent kernels (variants 0 and 2)");
             r = ensure_plan(p, dt, false);
             if (r) return r;
         }

@@ -39,6 +39,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "assn_internal.h"
@@ -76,6 +77,9 @@ struct Tc3Args {
     int nx, ny, Q, ntx, total;
     int SS, SB, SA;
     float dt, dts;                      // dt and dt sigma_as
+    // Heun stage (HEUN instances): out = alpha keep + beta (in + dt L(in)); keep may be out itself
+    const float* keep;
+    float alpha, beta;
 };
 
 template <int MG, int CPS_ = 2, bool SPLIT = false>
@@ -126,7 +130,15 @@ struct Ring3 {
 
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-template <int MG, int CPS_, bool SPLIT>
+// minmod of two one-sided differences: the one of smaller magnitude when they agree in sign, else 0
+__device__ __forceinline__ float minmod3(float a, float b) {
+    return a * b > 0.0f ? (fabsf(a) < fabsf(b) ? a : b) : 0.0f;
+}
+
+// HEUN: one stage of Heun's method with minmod-limited second-order upwind fluxes (Sec. 3.1):
+// out = alpha keep + beta (in + dt L(in)), L with the limited transport, collision, scattering,
+// source and the artificial gain of the stage state.
+template <int MG, int CPS_, bool SPLIT, bool HEUN = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
 step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     using LT = L3<MG, CPS_, SPLIT>;
@@ -525,7 +537,142 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
             const int c0 = buf * NT + ys * kTW + xs;                    // coefficient index of (x0, y0)
             const uint32_t tcol = tmem_base + ((uint32_t)(lq * 32) << 16) +
                                   (uint32_t)(buf * MG * NT + j * NT + ys * kTW + xs);
-            if (interior) {
+            if constexpr (HEUN) {
+                // Heun stage: the strip in two halves of 4 cells, each walked along its 8 rows.  A row
+                // is read with two cells either side (x-stencil), three rows are held ahead of the
+                // one updated (y-stencil), zero outside the grid (vacuum) and on padded ordinates.
+                // The limited differences take the lane's upwind side:
+                //   nu > 0: (psi_i - psi_{i-1}) + (D_i - D_{i-1}) / 2,
+                //   nu < 0: (psi_{i+1} - psi_i) - (D_{i+1} - D_i) / 2,   D_i = minmod(psi_i - psi_{i-1}, psi_{i+1} - psi_i),
+                // each slope computed once per row and shared by the neighbouring cells.
+                const float nux = o4.x, nuy = o4.y, alpha = a.alpha, beta = a.beta;
+                if (alpha != 0.0f && qlive) {
+                    // stage 2: psi^n of the strip (the buffer this stage overwrites) has long left L2;
+                    // ask for it while the tile's contraction runs (the walk reads it a row ahead)
+                    for (int r = 0; r < 8 && y0 + r < ny; ++r)
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (x0 + i < nx)
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(pout + (long)r * (long)rowstride + i * QP));
+                }
+                int go = 1;
+                if (lane == 0) go = W3C(&phi_full[buf], use & 1u, 0x1000u) && W3(&tm_full[buf], use & 1u, 0x2000u);
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (!go) break;
+                tc_fence_after();
+                // whole stencil (rows y0-2 .. y0+9, cells x0-2 .. x0+9) inside the grid, every lane live:
+                // the walk without bounds checks
+                const bool inside = !warp_pad && x0 >= 2 && x0 + 10 <= nx && y0 >= 2 && y0 + 10 <= ny;
+                auto walk = [&](auto checked_tag) {
+                    constexpr bool CK = decltype(checked_tag)::value;
+#pragma unroll 1
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int xh = x0 + 4 * hh;   // first cell of this half
+                    // strip row r: its 4 cells (S) or the two cells either side of them (H: xh-2, xh-1,
+                    // xh+4, xh+5), zero outside the grid and on padded ordinates; psi^n of its cells
+                    // for stage 2 (K), which is the buffer the stage writes: read a row ahead of its
+                    // use, by the thread that then overwrites it
+                    const float* base = a.in + ((size_t)y0 * nx + xh) * QP + q;   // (xh, y0), this ordinate
+                    float* obase = a.out + ((size_t)y0 * nx + xh) * QP + q;
+                    auto ld4 = [&](int r, int k0, int k1, int k2, int k3, float (&v)[4]) {
+                        const int ks[4] = {k0, k1, k2, k3};
+                        const float* p = base + (long)r * (long)rowstride;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if constexpr (CK) {
+                                const int yy = y0 + r, xx = xh + ks[i];
+                                v[i] = (qlive && yy >= 0 && yy < ny && xx >= 0 && xx < nx) ? __ldg(p + ks[i] * QP) : 0.0f;
+                            } else {
+                                v[i] = __ldg(p + ks[i] * QP);
+                            }
+                        }
+                    };
+                    auto ldS = [&](int r, float (&v)[4]) { ld4(r, 0, 1, 2, 3, v); };
+                    auto ldH = [&](int r, float (&v)[4]) { ld4(r, -2, -1, 4, 5, v); };
+                    auto ldK = [&](int r, float (&v)[4]) {
+                        const float* p = obase + (long)r * (long)rowstride;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if constexpr (CK) v[i] = (alpha != 0.0f && qlive && y0 + r < ny && xh + i < nx) ? p[i * QP] : 0.0f;
+                            else v[i] = alpha != 0.0f ? p[i * QP] : 0.0f;
+                        }
+                    };
+                    float m2S[4], m1S[4], cS[4], cH[4], p1S[4], p1H[4], p2S[4], p2H[4], kc[4];
+                    ldS(-2, m2S);
+                    ldS(-1, m1S);
+                    ldS(0, cS);
+                    ldH(0, cH);
+                    ldS(1, p1S);
+                    ldH(1, p1H);
+                    ldS(2, p2S);
+                    ldH(2, p2H);
+                    ldK(0, kc);
+                    float Dp[4], Dc[4];   // y-slopes of the row below and of the current row
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        Dp[i] = minmod3(m1S[i] - m2S[i], cS[i] - m1S[i]);
+                        Dc[i] = minmod3(cS[i] - m1S[i], p1S[i] - cS[i]);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        float p3S[4], p3H[4], kn[4];
+                        if (r < 7) {
+                            ldS(r + 3, p3S);
+                            ldK(r + 1, kn);
+                        }
+                        if (r < 6) ldH(r + 3, p3H);
+                        float y[4];
+                        tmem_ld4(tcol + (uint32_t)(r * kTW + 4 * hh), y);
+                        // the current row, cells xh-2 .. xh+5
+                        const float c[8] = {cH[0], cH[1], cS[0], cS[1], cS[2], cS[3], cH[2], cH[3]};
+                        float Dn[4], Dx[6];   // y-slopes of the row above; x-slopes at cells xh-1 .. xh+4
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) Dn[i] = minmod3(p1S[i] - cS[i], p2S[i] - p1S[i]);
+#pragma unroll
+                        for (int k = 1; k <= 6; ++k) Dx[k - 1] = minmod3(c[k] - c[k - 1], c[k + 1] - c[k]);
+                        float* po = obase + (long)r * (long)rowstride;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int k = i + 2;
+                            if constexpr (CK) {
+                                if (y0 + r >= ny || xh + i >= nx) continue;
+                                if (!qlive) {
+                                    __stcs(po + i * QP, 0.0f);
+                                    continue;
+                                }
+                            }
+                            const float cv = c[k];
+                            const float tx = nux > 0.0f ? (cv - c[k - 1]) + 0.5f * (Dx[k - 1] - Dx[k - 2])
+                                                        : (nux < 0.0f ? (c[k + 1] - cv) - 0.5f * (Dx[k] - Dx[k - 1]) : 0.0f);
+                            const float ty = nuy > 0.0f ? (cv - m1S[i]) + 0.5f * (Dc[i] - Dp[i])
+                                                        : (nuy < 0.0f ? (p1S[i] - cv) - 0.5f * (Dn[i] - Dc[i]) : 0.0f);
+                            const int ci = c0 + r * kTW + 4 * hh + i;
+                            float adv = fmaf(cv, cx[ci], cy[ci]);
+                            adv = fmaf(-nux, tx, adv);
+                            adv = fmaf(-nuy, ty, adv);
+                            adv = fmaf(dts, y[i], adv);
+                            adv = fmaf(nge, SPLIT ? cv : bf16_round(cv), adv);
+                            __stcs(po + i * QP, fmaf(alpha, kc[i], beta * adv));
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            m1S[i] = cS[i];
+                            cS[i] = p1S[i];
+                            cH[i] = p1H[i];
+                            p1S[i] = p2S[i];
+                            p1H[i] = p2H[i];
+                            if (r < 7) p2S[i] = p3S[i];
+                            if (r < 6) p2H[i] = p3H[i];
+                            Dp[i] = Dc[i];
+                            Dc[i] = Dn[i];
+                            if (r < 7) kc[i] = kn[i];
+                        }
+                    }
+                }
+                };
+                if (inside) walk(std::false_type{});
+                else walk(std::true_type{});
+            } else if (interior) {
                 // rows -1 .. 8 of the strip, row r at rv[r + 1]; edge cell of row r at ev[r + 1]
                 float rv[10][8], ev[10];
                 auto load_row = [&](int r) {
@@ -760,10 +907,14 @@ int distinct_blocks(const __nv_bfloat16* G, int Qp, int MG, cudaStream_t s, unsi
 }
 
 using Tc3Kernel = void (*)(Tc3Args);
-Tc3Kernel kernel3(int MG, int CPS, bool split) {
-    if (split) return MG == 2 ? step_tc3_kernel<2, 1, true> : step_tc3_kernel<1, 1, true>;
-    if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2, false> : step_tc3_kernel<2, 1, false>;
-    return CPS == 2 ? step_tc3_kernel<1, 2, false> : step_tc3_kernel<1, 1, false>;
+template <bool HEUN>
+Tc3Kernel kernel3_t(int MG, int CPS, bool split) {
+    if (split) return MG == 2 ? step_tc3_kernel<2, 1, true, HEUN> : step_tc3_kernel<1, 1, true, HEUN>;
+    if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2, false, HEUN> : step_tc3_kernel<2, 1, false, HEUN>;
+    return CPS == 2 ? step_tc3_kernel<1, 2, false, HEUN> : step_tc3_kernel<1, 1, false, HEUN>;
+}
+Tc3Kernel kernel3(int MG, int CPS, bool split, bool heun) {
+    return heun ? kernel3_t<true>(MG, CPS, split) : kernel3_t<false>(MG, CPS, split);
 }
 
 }  // namespace
@@ -831,8 +982,11 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
         return cudaErrorInvalidValue;
     }
     // one pair per two SMs, as many pairs as the device co-schedules (never more than tiles)
-    auto kern = kernel3(p->MG, p->CPS, p->split);
+    auto kern = kernel3(p->MG, p->CPS, p->split, false);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    if (e == cudaSuccess)   // the Heun-stage instance: same layout and shared memory
+        e = cudaFuncSetAttribute(kernel3(p->MG, p->CPS, p->split, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)p->smem);
     if (e != cudaSuccess) { delete p; return e; }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -879,8 +1033,10 @@ void tc3_plan_describe(const Tc3Plan* p, int* tile_cells, int* stages, int* pair
     if (smem) *smem = p ? p->smem : 0;
 }
 
-cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* cell, const float* w,
-                            float dt, float dt_sigma_as, unsigned int* err_flag, cudaStream_t s) {
+namespace {
+cudaError_t launch3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* cell, const float* w, float dt,
+                    float dt_sigma_as, bool heun, const float* keep, float alpha, float beta, unsigned int* err_flag,
+                    cudaStream_t s) {
     if (!p || parity < 0 || parity > 1) return cudaErrorInvalidValue;
     Tc3Args a;
     memset(&a, 0, sizeof a);
@@ -906,8 +1062,23 @@ cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const
     a.reps = p->reps;
     a.dt = dt;
     a.dts = dt_sigma_as;
-    kernel3(p->MG, p->CPS, p->split)<<<p->grid, kThreads3, p->smem, s>>>(a);
+    a.keep = keep;
+    a.alpha = alpha;
+    a.beta = beta;
+    kernel3(p->MG, p->CPS, p->split, heun)<<<p->grid, kThreads3, p->smem, s>>>(a);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_step_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* cell, const float* w,
+                            float dt, float dt_sigma_as, unsigned int* err_flag, cudaStream_t s) {
+    return launch3(p, parity, ord, cell, w, dt, dt_sigma_as, false, nullptr, 0.0f, 1.0f, err_flag, s);
+}
+
+cudaError_t launch_heun_stage_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* cell, const float* w,
+                                  float dt, float dt_sigma_as, const float* keep, float alpha, float beta,
+                                  unsigned int* err_flag, cudaStream_t s) {
+    return launch3(p, parity, ord, cell, w, dt, dt_sigma_as, true, keep, alpha, beta, err_flag, s);
 }
 
 }  // namespace assn

@@ -164,10 +164,11 @@ def test_unsupported_shapes(A):
 
 
 def test_automatic_variant(A):
-    """The automatic choice: the paired-SM kernel for forward-Euler steps at 256 / 512 ordinates in
-    both tensor-core precisions, the one-CTA kernel for other ordinate counts and for Heun."""
+    """The automatic choice: the paired-SM kernel for forward-Euler and Heun steps at 256 / 512
+    ordinates in both tensor-core precisions, the one-CTA kernel for other ordinate counts."""
     for (npol, naz), prec, scheme, want in [((16, 32), "bf16", "euler", 2), ((16, 16), "bf16x3", "euler", 2),
-                                            ((8, 16), "bf16", "euler", 0), ((16, 32), "bf16", "heun", 0)]:
+                                            ((8, 16), "bf16", "euler", 0), ((16, 32), "bf16", "heun", 2),
+                                            ((16, 16), "bf16x3", "heun", 2), ((8, 16), "bf16", "heun", 0)]:
         wl = random_workload(8, 8, npol, naz, seed=2)
         p = gpu_problem(A, wl, prec)
         p.set_scheme(scheme)
@@ -203,3 +204,67 @@ def test_resident_kernel_matrix_matches_ring(A, npol, naz):
         p.set_tiling(0, 0, 2)
         assert p.rings()["kernel_matrix"] == 2
         p.close()
+
+
+def heun_problem(A, wl, precision, psi0, variant=2):
+    p = gpu_problem(A, wl, precision, psi0=psi0)
+    p.set_scheme("heun")
+    p.set_tiling(0, 0, variant)
+    return p
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16), (10, 50), (10, 20)])
+@pytest.mark.parametrize("nx,ny", [(70, 37), (16, 8), (1, 1), (5, 90), (3, 2)])
+def test_heun_one_step(A, nx, ny, npol, naz, precision):
+    """One Heun step (Sec. 3.1: two stages, minmod-limited second-order upwind transport) on the
+    paired-SM kernel against oracle.step_heun: within twice the one-step bound of the precision (the
+    second stage halves the sum of the first stage's error and its own)."""
+    wl = random_workload(nx, ny, npol, naz, seed=nx * 13 + ny + naz)
+    psi0 = wl.psi0()
+    p = heun_problem(A, wl, precision, psi0)
+    assert p.variant() == 2
+    dt = 0.9 * p.max_stable_dt()
+    l0 = p.launch_count()
+    p.step(1, dt)
+    assert p.launch_count() - l0 == 2
+    got = p.state()
+    p.close()
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    ref = O.step_heun(psi0, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    scale = max(1.0, np.abs(ref).max(), np.abs(psi0).max())
+    tol = 2.0 * step_tolerance(precision, dt, wl.sigma_as, scale, offdiag_rowsum(K))
+    assert np.abs(got - ref).max() <= tol
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("npol,naz", [(16, 32), (10, 20)])
+def test_heun_agrees_with_persistent_kernel(A, npol, naz, precision):
+    """The paired-SM Heun stages and the one-CTA kernel's give the same two steps to FP32 rounding."""
+    wl = random_workload(53, 27, npol, naz, seed=8)
+    psi0 = wl.psi0()
+    states = []
+    for variant in (0, 2):
+        p = heun_problem(A, wl, precision, psi0, variant)
+        p.step(2, 0.9 * p.max_stable_dt())
+        states.append(p.state())
+        p.close()
+    assert np.abs(states[0] - states[1]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_heun_line_source_run(A, precision):
+    """The 64^2 line source at 256 ordinates under the paper's scheme at 0.95 of its admissible dt to
+    t = 0.25: relative L2 of Phi against oracle.run_heun within the whole-run tolerance."""
+    wl = synth.line_source(64, 16, 16, 1.0 / 8.0, t_final=0.25, name="pair_heun_ls64")
+    p = gpu_problem(A, wl, precision)
+    p.set_scheme("heun")
+    assert p.variant() == 2
+    n = int(np.ceil(wl.t_final / (0.95 * p.max_stable_dt()) - 1e-12))
+    dt = wl.t_final / n
+    p.step(n, dt)
+    phi = p.scalar_flux()
+    p.close()
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    psi = O.run_heun(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
+    assert rel_l2(phi, psi @ w) <= RUN_TOL[precision]
