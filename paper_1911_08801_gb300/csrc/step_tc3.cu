@@ -546,6 +546,8 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 //   nu < 0: (psi_{i+1} - psi_i) - (D_{i+1} - D_i) / 2,   D_i = minmod(psi_i - psi_{i-1}, psi_{i+1} - psi_i),
                 // each slope computed once per row and shared by the neighbouring cells.
                 const float nux = o4.x, nuy = o4.y, alpha = a.alpha, beta = a.beta;
+                const float2 NAX = make_float2(-fabsf(nux), -fabsf(nux)), NAY = make_float2(-fabsf(nuy), -fabsf(nuy));
+                const float2 ALPHA = make_float2(alpha, alpha), BETA = make_float2(beta, beta);
                 if (alpha != 0.0f && qlive) {
                     // stage 2: psi^n of the strip (the buffer this stage overwrites) has long left L2;
                     // ask for it while the tile's contraction runs (the walk reads it a row ahead)
@@ -607,11 +609,13 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                     ldS(2, p2S);
                     ldH(2, p2H);
                     ldK(0, kc);
-                    float Dp[4], Dc[4];   // y-slopes of the row below and of the current row
+                    // y-slope of the current row, and its difference to the slope of the row below
+                    float Dc[4], EyP[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        Dp[i] = minmod3(m1S[i] - m2S[i], cS[i] - m1S[i]);
+                        const float Dp = minmod3(m1S[i] - m2S[i], cS[i] - m1S[i]);
                         Dc[i] = minmod3(cS[i] - m1S[i], p1S[i] - cS[i]);
+                        EyP[i] = Dc[i] - Dp;
                     }
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
@@ -625,34 +629,53 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         tmem_ld4(tcol + (uint32_t)(r * kTW + 4 * hh), y);
                         // the current row, cells xh-2 .. xh+5
                         const float c[8] = {cH[0], cH[1], cS[0], cS[1], cS[2], cS[3], cH[2], cH[3]};
-                        float Dn[4], Dx[6];   // y-slopes of the row above; x-slopes at cells xh-1 .. xh+4
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) Dn[i] = minmod3(p1S[i] - cS[i], p2S[i] - p1S[i]);
-#pragma unroll
-                        for (int k = 1; k <= 6; ++k) Dx[k - 1] = minmod3(c[k] - c[k - 1], c[k + 1] - c[k]);
-                        float* po = obase + (long)r * (long)rowstride;
+                        // slopes of the row above (y) and of cells xh-1 .. xh+4 (x), and the differences
+                        // of neighbouring slopes: the limited difference on the lane's upwind side is
+                        //   (psi - psi_up) + (difference of the slopes on that side) / 2
+                        // with the sign of the velocity folded into the coefficient -|nu| (for nu < 0
+                        // it is the negated downwind form, so the product is the same number)
+                        float Dn[4], EyN[4], Dx[6], Ex[5];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const int k = i + 2;
+                            Dn[i] = minmod3(p1S[i] - cS[i], p2S[i] - p1S[i]);
+                            EyN[i] = Dn[i] - Dc[i];
+                        }
+#pragma unroll
+                        for (int k = 1; k <= 6; ++k) Dx[k - 1] = minmod3(c[k] - c[k - 1], c[k + 1] - c[k]);
+#pragma unroll
+                        for (int j = 0; j < 5; ++j) Ex[j] = Dx[j + 1] - Dx[j];
+                        float* po = obase + (long)r * (long)rowstride;
+                        const int ci = c0 + r * kTW + 4 * hh;
+                        float out[4];
+#pragma unroll
+                        for (int i = 0; i < 4; i += 2) {
+                            float txd[2], tyd[2], st[2];
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                const int k = i + u + 2;
+                                const float cv = c[k];
+                                txd[u] = (cv - (xpos ? c[k - 1] : c[k + 1])) + 0.5f * (xpos ? Ex[k - 2] : Ex[k - 1]);
+                                tyd[u] = (cv - (ypos ? m1S[i + u] : p1S[i + u])) + 0.5f * (ypos ? EyP[i + u] : EyN[i + u]);
+                                st[u] = SPLIT ? cv : bf16_round(cv);
+                            }
+                            const float2 CV = make_float2(c[i + 2], c[i + 3]);
+                            float2 adv = __ffma2_rn(CV, *reinterpret_cast<const float2*>(cx + ci + i),
+                                                    *reinterpret_cast<const float2*>(cy + ci + i));
+                            adv = __ffma2_rn(NAX, make_float2(txd[0], txd[1]), adv);
+                            adv = __ffma2_rn(NAY, make_float2(tyd[0], tyd[1]), adv);
+                            adv = __ffma2_rn(DTS, make_float2(y[i], y[i + 1]), adv);
+                            adv = __ffma2_rn(NGE, make_float2(st[0], st[1]), adv);
+                            const float2 o = __ffma2_rn(ALPHA, make_float2(kc[i], kc[i + 1]), __fmul2_rn(BETA, adv));
+                            out[i] = o.x;
+                            out[i + 1] = o.y;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
                             if constexpr (CK) {
                                 if (y0 + r >= ny || xh + i >= nx) continue;
-                                if (!qlive) {
-                                    __stcs(po + i * QP, 0.0f);
-                                    continue;
-                                }
+                                if (!qlive) out[i] = 0.0f;
                             }
-                            const float cv = c[k];
-                            const float tx = nux > 0.0f ? (cv - c[k - 1]) + 0.5f * (Dx[k - 1] - Dx[k - 2])
-                                                        : (nux < 0.0f ? (c[k + 1] - cv) - 0.5f * (Dx[k] - Dx[k - 1]) : 0.0f);
-                            const float ty = nuy > 0.0f ? (cv - m1S[i]) + 0.5f * (Dc[i] - Dp[i])
-                                                        : (nuy < 0.0f ? (p1S[i] - cv) - 0.5f * (Dn[i] - Dc[i]) : 0.0f);
-                            const int ci = c0 + r * kTW + 4 * hh + i;
-                            float adv = fmaf(cv, cx[ci], cy[ci]);
-                            adv = fmaf(-nux, tx, adv);
-                            adv = fmaf(-nuy, ty, adv);
-                            adv = fmaf(dts, y[i], adv);
-                            adv = fmaf(nge, SPLIT ? cv : bf16_round(cv), adv);
-                            __stcs(po + i * QP, fmaf(alpha, kc[i], beta * adv));
+                            __stcs(po + i * QP, out[i]);
                         }
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
@@ -663,8 +686,8 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                             p1H[i] = p2H[i];
                             if (r < 7) p2S[i] = p3S[i];
                             if (r < 6) p2H[i] = p3H[i];
-                            Dp[i] = Dc[i];
                             Dc[i] = Dn[i];
+                            EyP[i] = EyN[i];
                             if (r < 7) kc[i] = kn[i];
                         }
                     }
