@@ -132,7 +132,7 @@ int check_flags(assn_problem* p) {
     CK(p, cudaStreamSynchronize(p->stream));
     if (f[1]) {
         CK(p, cudaMemsetAsync(p->d_flags + 1, 0, sizeof(unsigned int), p->stream));
-        return fail(p, ASSN_ERR_TIMEOUT, "tensor-core step: a bounded device wait gave up (flag 0x%x)%s", f[1],
+        return fail(p, ASSN_ERR_TIMEOUT, "a bounded device wait gave up (flag 0x%x)%s", f[1],
                     (f[1] & 0x80000000u) ? "; work in flight did not drain, treat the CUDA context as suspect" : "");
     }
     return ASSN_OK;
