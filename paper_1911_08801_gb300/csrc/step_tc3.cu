@@ -20,8 +20,8 @@
 //               distinct blocks once (resident), or all of its 256-row groups, one or two chunks
 //               per request, through a ring.
 //   flux TMA    this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64 ordinates] chunks, into a
-//               staging ring: warp 3 at 512 ordinates (BF16), else lane 1 of warp 0.
-//   warps 1-3   converters (1-2 at 512 ordinates in BF16): staging -> BF16 operand rows (K-major,
+//               staging ring: warp 3 at 512 ordinates, else lane 1 of warp 0.
+//   warps 1-3   converters (1-2 at 512 ordinates): staging -> BF16 operand rows (K-major,
 //               swizzled) for the pair's MMA;
 //               the scalar flux Phi = sum_p w_p psi_p of this CTA's cells, and from it the cells'
 //               coefficients, written into both CTAs.
@@ -145,9 +145,9 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     // converter warps and where the flux-copy producer runs: at 512 ordinates (16-kB chunks) two
     // converter warps keep up and the producer gets warp 3 to itself (as one lane of warp 0, beside
     // the MMA issuer's waits, it issued each copy about a microsecond after its slot was released:
-    // 0.180 -> 0.174 ms on the 448^2 lattice); 32-kB chunks at 256 ordinates and the split
-    // operands need three converter warps (2.14 against 1.80-1.95 ms on the 2048^2 line source)
-    constexpr int kConv3 = (MG == 2 && !SPLIT) ? 2 : 3;
+    // on the 448^2 lattice 0.180 -> 0.174 ms in BF16, 0.334 -> 0.288 ms in BF16X3); the 32-kB chunks
+    // at 256 ordinates need three converter warps (2.14 against 1.80-1.95 ms on the 2048^2 line source)
+    constexpr int kConv3 = MG == 2 ? 2 : 3;
     constexpr bool kProdWarp = kConv3 == 2;
     constexpr int NT = LT::NT, TH = LT::TH, THc = LT::THc, NTc = LT::NTc, QP = LT::QP, KC = LT::KC;
     constexpr int CPS = LT::CPS, KR = LT::KR;
