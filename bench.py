@@ -424,10 +424,17 @@ def extras_legs(A, L, torch, wl, args, prob, psi0, stream, dt):
         for _ in range(reps):
             L.assn_run_f32(prob.handle, psi0, n_e2e, dt, phi)
         el = (time.perf_counter() - t0) / reps
+        # the upload alone (the same pinned buffer, the same copy), for its share of the call
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            L.assn_set_state_f32(prob.handle, psi0)
+            prob.check_finite()   # syncs the problem's stream
+        up = (time.perf_counter() - t0) / reps
         out["e2e"] = {"value": units * n_e2e / el, "unit": "updates/s",
                       "h2d_bytes_per_step": int(psi0.nbytes) // n_e2e, "d2h_bytes_per_step": int(phi.nbytes) // n_e2e,
                       "call": f"assn_run_f32: pinned host psi0 -> {n_e2e} steps -> host Phi",
-                      "ms_per_call": el * 1e3}
+                      "ms_per_call": el * 1e3, "h2d_ms_per_call": up * 1e3,
+                      "h2d_share": min(1.0, up / el), "h2d_gbs": psi0.nbytes / up / 1e9}
     # the plain FP64 GPU path on the same workload
     try:
         p64 = make_problem(A, wl, "fp64", stream)

@@ -34,10 +34,12 @@ def test_whole_job_rate_and_single_rank_max(bench):
 
 def test_heun_roofline_counts_20_bytes_per_update(bench):
     wl = synth.LATTICE_448
-    r = bench.heun_tc_roofline(wl, 2.0)
+    r = bench.heun_tc_roofline(wl, 2.0, 2)
     updates = wl.nx * wl.ny * wl.Q
     assert r["achieved"] == pytest.approx(20.0 * updates / 2e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["kernel"].startswith("step_tc3_kernel")
+    assert bench.heun_tc_roofline(wl, 2.0, 0)["kernel"].startswith("step_tc2_kernel")
 
 
 def test_implicit_roofline_counts_source_iterations(bench):
