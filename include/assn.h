@@ -90,7 +90,7 @@ typedef enum { ASSN_BC_VACUUM = 0 } assn_boundary;
  *                             psi* = psi + dt L(psi), psi^{n+1} = (psi + psi* + dt L(psi*))/2)
  *                             with second-order upwind fluxes from minmod-limited slopes (two zero
  *                             ghost cells per vacuum side); all precisions (tensor-core problems on
- *                             the persistent kernel, variant 0).
+ *                             the paired-SM kernel at 256 / 512 ordinates, else variant 0).
  *   ASSN_SCHEME_IMPLICIT      the paper's implicit method (Sec. 3.4-3.5, Alg. 1-3): implicit Euler
  *                             with the second-order upwind stencil without limiter (flux difference
  *                             3/2 psi_j - 2 psi_{j-1} + 1/2 psi_{j-2}, x and y stencils added), solved
@@ -325,10 +325,13 @@ int assn_check_guards(assn_problem* p, int64_t* guard_bytes_changed, int64_t* pa
  * Euler of the as-S_N equations; for Heun + minmod one of the two stages of a Heun step, so a step
  * is two launches) to every member that still has steps left; a member's step count is
  * kept on the device, so members finish at their own counts within one run.  After
- * assn_batch_run each member is exactly as if assn_step(p, nsteps, dt) had been called on it
- * (bitwise, with tiling variant 0 at the same tile width: batches run the persistent one-CTA
- * kernel).  Members stay owned by the caller and must outlive their
- * membership; while in a batch they are stepped only through it.
+ * assn_batch_run each member is exactly as if assn_step(p, nsteps, dt) had been called on it,
+ * bitwise.  With one class per padded ordinate count (the default grouping) a member whose steps run
+ * on the paired-SM kernel (variant 2, automatic or set) is stepped by its own launches of that
+ * kernel inside the batch's sequence (and graph); the other members run the persistent one-CTA
+ * kernel, one launch per class and step, and equal assn_step with tiling variant 0 at the class's
+ * tile width.  Members stay owned by the caller and must outlive their membership; while in a
+ * batch they are stepped only through it.
  *
  * create:     stream = a cudaStream_t or NULL (library stream).  Errors: ASSN_ERR_CUDA / OOM.
  * add:        add p, to be advanced nsteps >= 0 steps of size dt per run.  Checks p is complete
@@ -370,8 +373,8 @@ int assn_batch_set_tiling(assn_batch* b, int tile_cells, int stages);
  * launch per step, for each padded ordinate count, each at the tile width that suits it;
  * one_launch = 1 every member in a single class, so each step (Heun: stage) of the whole batch is
  * one launch, with ordinate strides read per member and the tile width of the largest ordinate
- * count.  Results are the same either way (bitwise, at equal tile widths).  ASSN_ERR_ARG for
- * other values. */
+ * count (every member on the one-CTA kernel).  Results of one-CTA members are the same either way
+ * (bitwise, at equal tile widths).  ASSN_ERR_ARG for other values. */
 int assn_batch_set_grouping(assn_batch* b, int one_launch);
 int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stages, double* ms_per_launch);
 int assn_batch_run(assn_batch* b, int use_graph);
@@ -398,8 +401,8 @@ int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, in
  * per step (the batch path, optionally as CUDA graphs); requests that arrive meanwhile join at
  * the next chunk, and finished solves return the scalar flux Phi = sum_q w_q psi_q (FP64 on the
  * host, [ny][nx]) and free their memory.  A solve's result does not depend on which other solves
- * share its launches (each is bitwise equal to assn_step on the same problem with tiling
- * variant 0).
+ * share its launches (each is bitwise equal to assn_step on the same problem with its default
+ * tiling).
  *
  * Thread safety: submit, wait and stats may be called from any host threads concurrently;
  * assn_server_last_error returns the message of the calling thread's last failed server call. */

@@ -602,6 +602,27 @@ static int eff_variant(const assn_problem* p) {
             tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision == ASSN_BF16X3)) ? 2 : 0;
 }
 
+}  // extern "C"
+
+namespace assn {
+bool problem_paired(const assn_problem* p) { return p->tensor() && eff_variant(p) == 2; }
+
+cudaError_t problem_pair_launch(assn_problem* p, double dt, int parity, int heun_stage, unsigned int* err_flag,
+                                cudaStream_t s) {
+    const float fdt = (float)dt, fdts = (float)(dt * p->sigma_as);
+    if (heun_stage < 0)
+        return launch_step_tc3(p->plan3, parity, (const OrdF*)p->d_ord, (const CellF*)p->d_cell, p->d_w32, fdt, fdts,
+                               err_flag, s);
+    if (heun_stage == 0)
+        return launch_heun_stage_tc3(p->plan3, parity, (const OrdF*)p->d_ord, (const CellF*)p->d_cell, p->d_w32, fdt,
+                                     fdts, nullptr, 0.0f, 1.0f, err_flag, s);
+    return launch_heun_stage_tc3(p->plan3, parity, (const OrdF*)p->d_ord, (const CellF*)p->d_cell, p->d_w32, fdt, fdts,
+                                 (const float*)p->d_psi[parity ^ 1], 0.5f, 0.5f, err_flag, s);
+}
+}  // namespace assn
+
+extern "C" {
+
 static int step_once(assn_problem* p, const void* in, void* out, double dt) {
     if (p->precision == ASSN_FP64) {
         StepArgs<double, OrdD, CellD> a{(const double*)in, (double*)out, (const OrdD*)p->d_ord,
@@ -668,6 +689,14 @@ static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
     CK(p, e);
     return ASSN_OK;
 }
+
+}  // extern "C"
+
+namespace assn {
+int problem_pair_plan(assn_problem* p, double dt) { return ensure_plan(p, dt, false); }
+}  // namespace assn
+
+extern "C" {
 
 static int prepare_step(assn_problem* p, double dt) {
     int r = assn::problem_prepare(p, dt);

@@ -32,6 +32,8 @@ struct assn_batch {
         assn_problem* p;
         int nsteps;
         double dt;
+        // stepped by its own paired-SM launches (the kernel its steps run alone), not in a class
+        bool paired = false;
     };
     std::vector<Member> members;
     // Members grouped by padded ordinate count Qp: each class has its own plan, tile width and
@@ -114,6 +116,10 @@ void group(assn_batch* b) {
     int qmax = 0;
     for (auto& m : b->members) qmax = std::max(qmax, m.p->Qp);
     for (size_t i = 0; i < b->members.size(); ++i) {
+        // with one class per ordinate count, a member whose steps run on the paired-SM kernel keeps
+        // it: its launches join the batch's sequence (and graph) beside the class launches
+        b->members[i].paired = !b->grouping && problem_paired(b->members[i].p);
+        if (b->members[i].paired) continue;
         const int Qp = b->grouping ? qmax : b->members[i].p->Qp;
         auto it = std::find_if(b->classes.begin(), b->classes.end(), [&](const assn_batch::Class& c) { return c.Qp == Qp; });
         if (it == b->classes.end()) {
@@ -265,6 +271,11 @@ cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int
 int ensure_batch_plan(assn_batch* b) {
     if (!b->planned) {
         group(b);
+        for (auto& m : b->members)
+            if (m.paired) {
+                const int r = problem_pair_plan(m.p, m.dt);
+                if (r) return bfail(b, r, "batch: paired-SM plan: %s", assn_last_error(m.p));
+            }
         for (auto& c : b->classes) {
             std::vector<Tc2Problem> d;
             for (int i : c.idx) {
@@ -478,20 +489,36 @@ int assn_batch_run(assn_batch* b, int use_graph) {
     }
     int r = ensure_batch_plan(b);
     if (r) return r;
-    std::vector<int> shape;
+    std::vector<int> shape;   // what a captured graph is specific to
     for (auto& c : b->classes) shape.push_back(c.nmax);
+    int nlaunch = 0;
+    for (int v : shape) nlaunch += v;
+    for (auto& m : b->members)
+        if (m.paired) {   // (the launches' buffers follow from the member's current one)
+            shape.push_back(lps * m.nsteps);
+            shape.push_back(m.p->cur);
+            nlaunch += lps * m.nsteps;
+        }
     auto enqueue = [&]() -> cudaError_t {
-        // steps (Heun: stages) of the classes interleaved, one launch per class and step (stage)
+        // steps (Heun: stages) of the classes interleaved, one launch per class and step (stage),
+        // then one per paired member and step (stage)
         cudaError_t e = cudaSuccess;
-        for (int k = 0; k < nmax && e == cudaSuccess; ++k)
+        for (int k = 0; k < nmax && e == cudaSuccess; ++k) {
             for (auto& c : b->classes)
                 if (k < c.nmax && e == cudaSuccess)
                     e = lps == 2 ? launch_heun_stage_tc2(c.plan, b->d_err, -1, nullptr, 0.0f, 1.0f, b->stream)
                                  : launch_step_tc2(c.plan, b->d_err, -1, b->stream);
+            for (auto& m : b->members) {
+                if (!m.paired || k >= lps * m.nsteps || e != cudaSuccess) continue;
+                const int cur0 = m.p->cur;
+                if (lps == 2)   // a Heun step ends in the buffer it started from
+                    e = problem_pair_launch(m.p, m.dt, (k & 1) ? cur0 ^ 1 : cur0, k & 1, b->d_err, b->stream);
+                else
+                    e = problem_pair_launch(m.p, m.dt, (cur0 + k) & 1, -1, b->d_err, b->stream);
+            }
+        }
         return e;
     };
-    int nlaunch = 0;
-    for (int v : shape) nlaunch += v;
     if (use_graph) {
         if (!b->graph || b->graph_shape != shape) {
             drop_graph(b);
@@ -516,6 +543,8 @@ int assn_batch_run(assn_batch* b, int use_graph) {
         p->counter_host = p->cur + lps * m.nsteps;
         p->cur = p->counter_host & 1;
         p->launches += lps * m.nsteps;
+        if (m.paired)   // the paired-SM kernel leaves the device step counter alone: set it
+            BK(b, cudaMemcpyAsync(p->d_counter, &p->counter_host, sizeof(int), cudaMemcpyHostToDevice, b->stream));
         if (p->stream != b->stream) BK(b, cudaStreamWaitEvent(p->stream, b->done, 0));
     }
     return ASSN_OK;

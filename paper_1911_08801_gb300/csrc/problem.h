@@ -90,5 +90,14 @@ int problem_check_flags(assn_problem* p);
 // Description of p for the persistent tensor-core kernel: buffers, constants, step counter,
 // stepped while the counter is below target.
 Tc2Problem problem_tc2(const assn_problem* p, double dt, int target);
+// True when p's steps run on the paired-SM kernel (the variant its own steps resolve to is 2).
+bool problem_paired(const assn_problem* p);
+// Creates p's paired-SM plan if missing (reads G back once: not while a stream is being captured).
+int problem_pair_plan(assn_problem* p, double dt);
+// Enqueues one launch of p's paired-SM kernel on stream s at step size dt: a forward-Euler step, or
+// a Heun stage (stage 0: psi* from buffer `parity`; stage 1: psi^{n+1} into buffer parity ^ 1 from
+// psi* in buffer `parity`, keeping psi^n there).  Errors go to err_flag.
+cudaError_t problem_pair_launch(assn_problem* p, double dt, int parity, int heun_stage, unsigned int* err_flag,
+                                cudaStream_t s);
 
 }  // namespace assn

@@ -42,18 +42,31 @@ def build(A, precision, wls):
     return probs, dts
 
 
+def paired(wl):
+    """Members whose steps run on the paired-SM kernel (256 or 512 padded ordinates): a batch steps
+    them with their own launches, not in an ordinate class."""
+    return (wl.Q + 63) // 64 * 64 in (256, 512)
+
+
 def launches_per_run(wls, steps):
-    """One launch per step of each class of members with the same padded ordinate count."""
-    cls = {}
+    """One launch per step of each class of members with the same padded ordinate count, and one per
+    step of each paired member."""
+    cls, own = {}, 0
     for wl, n in zip(wls, steps):
+        if paired(wl):
+            own += n
+            continue
         mp = (wl.Q + 63) // 64
         cls[mp] = max(cls.get(mp, 0), n)
-    return sum(cls.values())
+    return sum(cls.values()) + own
 
 
-def alone(A, precision, wl, nsteps, dt, tile_cells):
+def alone(A, precision, wl, nsteps, dt, tile_cells, in_class=False):
+    """The member's solve stepped alone: on the paired-SM kernel where it steps there in a batch,
+    else on the one-CTA kernel at the class's tile width."""
     p = gpu_problem(A, wl, precision)
-    p.set_tiling(tile_cells=tile_cells)
+    if in_class or not paired(wl):
+        p.set_tiling(tile_cells=tile_cells)
     p.step(nsteps, dt)
     s = p.state()
     p.close()
@@ -99,7 +112,7 @@ def test_one_launch_per_step_for_uneven_ordinate_counts(A, precision, use_graph)
     assert len(cls) == 1 and cls[0]["members"] == 4 and cls[0]["ordinate_stride"] == 512
     assert info["launches"] == max(steps)
     for wl, p, n, dt in zip(wls, probs, steps, dts):
-        ref = alone(A, precision, wl, n, dt, info["tile_cells"])
+        ref = alone(A, precision, wl, n, dt, info["tile_cells"], in_class=True)
         assert np.array_equal(p.state(), ref), wl.name
     for p in probs:
         p.close()
@@ -118,12 +131,13 @@ def test_rerun_graph_reuse_and_continue(A):
         nt = b.info()["tile_cells"]
         assert b.info()["launches"] == 2 * launches_per_run(wls, steps)
         cls = b.classes()
-        assert [c["ordinate_stride"] for c in cls] == [512, 256, 128, 64]
-        assert [c["members"] for c in cls] == [1, 1, 1, 1]
+        assert [c["ordinate_stride"] for c in cls] == [128, 64]   # Q = 256 and 512 step on the paired kernel
+        assert [c["members"] for c in cls] == [1, 1]
         assert all(c["tile_cells"] * c["ordinate_stride"] // 128 <= 256 for c in cls)
-    probs[0].step(1, dts[0])
+    probs[0].step(1, dts[0])   # a class member and a paired member continue on their own
+    probs[3].step(1, dts[3])
     for k, (wl, p, n, dt) in enumerate(zip(wls, probs, steps, dts)):
-        total = 2 * n + (1 if k == 0 else 0)
+        total = 2 * n + (1 if k in (0, 3) else 0)
         ref = alone(A, "bf16", wl, total, dt, nt)
         assert np.array_equal(p.state(), ref), wl.name
     for p in probs:
@@ -194,8 +208,8 @@ def test_single_problem_autotune(A):
     t = p.autotune(dt, use_cache=False)
     assert np.array_equal(p.state(), s0)
     assert p.tiling()["tile_cells"] == t["tile_cells"]
-    p.step(3, dt)
-    assert np.array_equal(p.state(), alone(A, "bf16", wl, 3, dt, t["tile_cells"]))
+    p.step(3, dt)   # (a tuned tiling selects the one-CTA kernel)
+    assert np.array_equal(p.state(), alone(A, "bf16", wl, 3, dt, t["tile_cells"], in_class=True))
     p.close()
 
 

@@ -56,7 +56,9 @@ def test_ensemble_members_one_batched_launch(A):
         for p, dt in zip(probs, dts):
             b.add(p, 1, dt)
         b.run().sync()
-        assert len(b.classes()) == 4
+        cls = b.classes()   # Q = 64 and 128 in one-CTA classes; Q = 256 and 512 on the paired-SM kernel
+        assert sorted(c["ordinate_stride"] for c in cls) == [64, 128]
+        assert sum(c["members"] for c in cls) == sum(1 for wl in wls if wl.Q < 256)
     for wl, p, psi, dt in zip(wls, probs, states, dts):
         got = p.state()
         Om, w, K, sa, ss, q = oracle_parts(wl)

@@ -69,9 +69,9 @@ def submit(srv, wl, nsteps, dt):
 
 
 def alone_phi(A, wl, nsteps, dt, precision="bf16"):
-    """The same solve stepped alone with assn_step on the kernel the server's batches run (variant 0)."""
+    """The same solve stepped alone with assn_step on its default kernel (the paired-SM kernel at 256 /
+    512 ordinates, which the server's batches launch per solve; else the one-CTA kernel)."""
     p = A.Problem(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1, precision)
-    p.set_tiling(variant=0)
     p.set_product_quadrature(wl.n_polar, wl.n_azim)
     sa, ss, q = wl.materials()
     p.set_cross_sections(sa, ss, q)
