@@ -633,7 +633,8 @@ def run_ensemble(args):
                    "wall_s": wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_update": 8,
-                     "kernel": "step_tc2_kernel (batched)"},
+                     "kernel": ("step_tc2_kernel (all members in one class)" if args.one_launch else
+                                "step_tc2_kernel per ordinate class, step_tc3_kernel per 256 / 512-ordinate member")},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "batched_no_graph": {"value": updates / (ms_nograph / 1e3), "ms": ms_nograph},
@@ -695,7 +696,7 @@ def run_serving(args):
                                       "budget_bytes", "peak_bytes")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_update": 8,
-                     "kernel": "step_tc2_kernel (batched)"},
+                     "kernel": "step_tc2_kernel per ordinate class, step_tc3_kernel per 256 / 512-ordinate solve"},
         "gpu_launches": int(st["launches"]),
         "clocks": clk.summary(),
         "wall_s_timed": wall,
