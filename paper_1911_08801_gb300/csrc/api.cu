@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "problem.h"
+#include "trace.h"
 
 using namespace assn;
 
@@ -540,6 +541,7 @@ int assn_get_state(assn_problem* p, double* psi) {
 
 int assn_set_state_f32(assn_problem* p, const float* psi) {
     if (!p || !psi) return ASSN_ERR_ARG;
+    assn::TraceRange tr("assn_set_state_f32");
     if (!p->have_quad) return fail(p, ASSN_ERR_STATE, "no quadrature set");
     if (p->precision == ASSN_FP64) return fail(p, ASSN_ERR_UNSUPPORTED, "FP32 state copy on an FP64 problem");
     int r = set_device(p);
@@ -555,6 +557,7 @@ int assn_set_state_f32(assn_problem* p, const float* psi) {
 
 int assn_get_state_f32(assn_problem* p, float* psi) {
     if (!p || !psi) return ASSN_ERR_ARG;
+    assn::TraceRange tr("assn_get_state_f32");
     if (!p->have_quad) return fail(p, ASSN_ERR_STATE, "no quadrature set");
     if (p->precision == ASSN_FP64) return fail(p, ASSN_ERR_UNSUPPORTED, "FP32 state copy on an FP64 problem");
     int r = set_device(p);
@@ -795,6 +798,7 @@ static int heun_step(assn_problem* p, double dt) {
 
 int assn_step(assn_problem* p, int nsteps, double dt) {
     if (!p) return ASSN_ERR_ARG;
+    assn::TraceRange tr("assn_step");
     if (nsteps < 0) return fail(p, ASSN_ERR_ARG, "nsteps < 0");
     if (p->scheme == ASSN_SCHEME_IMPLICIT) return assn::implicit_steps(p, nsteps, dt);
     if (p->scheme == ASSN_SCHEME_HEUN_MINMOD) {
@@ -928,6 +932,7 @@ int assn_get_variant(assn_problem* p, int* variant) {
 
 int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt, double* phi_host) {
     if (!p || !psi0_host || !phi_host) return ASSN_ERR_ARG;
+    assn::TraceRange tr("assn_run_f32");
     if (nsteps < 0) return fail(p, ASSN_ERR_ARG, "nsteps < 0");
     int r = prepare_step(p, dt);
     if (r) return r;
@@ -940,6 +945,7 @@ int assn_run_f32(assn_problem* p, const float* psi0_host, int nsteps, double dt,
 
 int assn_scalar_flux(assn_problem* p, double* phi_host) {
     if (!p || !phi_host) return ASSN_ERR_ARG;
+    assn::TraceRange tr("assn_scalar_flux");
     if (!p->have_quad) return fail(p, ASSN_ERR_STATE, "no quadrature set");
     int r = set_device(p);
     if (r) return r;

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "problem.h"
+#include "trace.h"
 
 using namespace assn;
 
@@ -469,6 +470,7 @@ int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stag
 
 int assn_batch_run(assn_batch* b, int use_graph) {
     if (!b) return bfail(b, ASSN_ERR_ARG, "batch is NULL");
+    TraceRange tr("assn_batch_run");
     if (b->members.empty()) return ASSN_OK;
     BK(b, cudaSetDevice(b->dev));
     const int lps = launches_per_step(b);

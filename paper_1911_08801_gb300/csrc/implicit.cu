@@ -33,6 +33,7 @@
 
 #include "assn.h"
 #include "problem.h"
+#include "trace.h"
 
 namespace assn {
 
@@ -712,6 +713,7 @@ void implicit_free(ImplicitWork* W) {
 }
 
 int implicit_steps(assn_problem* p, int nsteps, double dt) {
+    TraceRange tr("implicit steps");
     if (p->tensor())
         return problem_fail(p, ASSN_ERR_UNSUPPORTED, "the implicit scheme runs in FP64 or FP32 (CUDA cores)");
     int r = problem_prepare(p, dt);

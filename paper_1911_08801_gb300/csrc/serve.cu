@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "problem.h"
+#include "trace.h"
 
 using Clock = std::chrono::steady_clock;
 
@@ -195,6 +196,7 @@ void loop_main(assn_server* s) {
                 --slots;
             }
         }
+        assn::TraceRange admit_range("serving admission");
         for (Request& r : admit) {
             Active a;
             a.t_admit = Clock::now();
@@ -246,6 +248,7 @@ void loop_main(assn_server* s) {
         if (s->active.empty()) continue;
 
         // ---- one chunk of steps for every active solve
+        assn::TraceRange chunk_range("serving chunk");
         const auto t0 = Clock::now();
         int st = ASSN_OK;
         for (Active& a : s->active) {
