@@ -247,7 +247,10 @@ int assn_step(assn_problem* p, int nsteps, double dt);
 
 /* Same step, with the ordinate state supplied and returned by the caller in device memory
  * laid out as the problem's own buffers ([ny][nx][Qpad] of FP32, or FP64 for ASSN_FP64;
- * Qpad from assn_layout).  psi_in_dev and psi_out_dev must not overlap.  Asynchronous. */
+ * Qpad from assn_layout).  psi_in_dev and psi_out_dev must not overlap.  Asynchronous, on the
+ * problem's stream.  Where the problem's steps run on the paired-SM kernel (variant 2) and
+ * psi_in_dev is 16-byte aligned, the step runs there (bitwise equal to assn_step); other tensor-core
+ * problems run the one-tile-per-CTA kernel (variant 1). */
 int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev, double dt);
 
 /* One call from host data to host result: upload psi0 (FP32 [ny][nx][Q] host; pinned memory gives

@@ -834,7 +834,17 @@ int assn_step_device(assn_problem* p, const void* psi_in_dev, void* psi_out_dev,
     if (psi_in_dev == psi_out_dev) return fail(p, ASSN_ERR_ARG, "input and output buffers must differ");
     int r = prepare_step(p, dt);
     if (r) return r;
-    if (p->tensor()) {   // caller-owned buffers run on the one-tile-per-CTA kernel
+    if (p->tensor() && eff_variant(p) == 2 && !((uintptr_t)psi_in_dev & 15u) && !((uintptr_t)psi_out_dev & 3u)) {
+        // the paired-SM kernel, with a tensor map of the caller's input
+        r = ensure_plan(p, dt, false);
+        if (r) return r;
+        CK(p, launch_step_tc3_buffers(p->plan3, (const float*)psi_in_dev, (float*)psi_out_dev, (const OrdF*)p->d_ord,
+                                      (const CellF*)p->d_cell, p->d_w32, (float)dt, (float)(dt * p->sigma_as),
+                                      p->d_flags + 1, p->stream));
+        p->launches++;
+        return ASSN_OK;
+    }
+    if (p->tensor()) {   // other caller-owned buffers run on the one-tile-per-CTA kernel
         r = ensure_plan(p, dt, true);
         if (r) return r;
     }

@@ -134,6 +134,11 @@ void tc3_plan_describe(const Tc3Plan* plan, int* tile_cells, int* stages, int* p
 // Reads buffer `parity`, writes buffer parity ^ 1.
 cudaError_t launch_step_tc3(const Tc3Plan* plan, int parity, const OrdF* ord, const CellF* cell, const float* w,
                             float dt, float dt_sigma_as, unsigned int* err_flag, cudaStream_t s);
+// The forward-Euler step of launch_step_tc3 between caller-owned buffers of the plan's layout
+// ([ny][nx][Qp] FP32; in 16-byte aligned for the tensor copies, else cudaErrorInvalidValue).
+cudaError_t launch_step_tc3_buffers(const Tc3Plan* p, const float* in, float* out, const OrdF* ord,
+                                    const CellF* cell, const float* w, float dt, float dt_sigma_as,
+                                    unsigned int* err_flag, cudaStream_t s);
 // One Heun stage (Sec. 3.1) on the paired-SM kernel: reads buffer `parity`, writes buffer parity ^ 1
 // = alpha keep + beta (in + dt L(in)) with the minmod-limited second-order upwind transport.
 cudaError_t launch_heun_stage_tc3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* cell, const float* w,

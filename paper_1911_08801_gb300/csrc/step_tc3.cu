@@ -1059,7 +1059,7 @@ void tc3_plan_describe(const Tc3Plan* p, int* tile_cells, int* stages, int* pair
 namespace {
 cudaError_t launch3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* cell, const float* w, float dt,
                     float dt_sigma_as, bool heun, const float* keep, float alpha, float beta, unsigned int* err_flag,
-                    cudaStream_t s) {
+                    cudaStream_t s, const float* in_ext = nullptr, float* out_ext = nullptr) {
     if (!p || parity < 0 || parity > 1) return cudaErrorInvalidValue;
     Tc3Args a;
     memset(&a, 0, sizeof a);
@@ -1088,6 +1088,12 @@ cudaError_t launch3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* 
     a.keep = keep;
     a.alpha = alpha;
     a.beta = beta;
+    if (in_ext) {   // caller-owned buffers of the same layout: a tensor map of this input
+        if (!encode_psi3(&a.tm_psi, in_ext, 256 * p->MG, p->nx, p->ny, (256 / p->MG) / kTW / 2))
+            return cudaErrorInvalidValue;
+        a.in = in_ext;
+        a.out = out_ext;
+    }
     kernel3(p->MG, p->CPS, p->split, heun)<<<p->grid, kThreads3, p->smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -1102,6 +1108,13 @@ cudaError_t launch_heun_stage_tc3(const Tc3Plan* p, int parity, const OrdF* ord,
                                   float dt, float dt_sigma_as, const float* keep, float alpha, float beta,
                                   unsigned int* err_flag, cudaStream_t s) {
     return launch3(p, parity, ord, cell, w, dt, dt_sigma_as, true, keep, alpha, beta, err_flag, s);
+}
+
+cudaError_t launch_step_tc3_buffers(const Tc3Plan* p, const float* in, float* out, const OrdF* ord,
+                                    const CellF* cell, const float* w, float dt, float dt_sigma_as,
+                                    unsigned int* err_flag, cudaStream_t s) {
+    if (!in || !out || ((uintptr_t)in & 15u) || ((uintptr_t)out & 3u)) return cudaErrorInvalidValue;
+    return launch3(p, 0, ord, cell, w, dt, dt_sigma_as, false, nullptr, 0.0f, 1.0f, err_flag, s, in, out);
 }
 
 }  // namespace assn

@@ -268,3 +268,35 @@ def test_heun_line_source_run(A, precision):
     Om, w, K, sa, ss, q = oracle_setup(wl)
     psi = O.run_heun(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
     assert rel_l2(phi, psi @ w) <= RUN_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("npol,naz", [(16, 32), (8, 16)])
+def test_step_device_on_caller_buffers(A, npol, naz, precision):
+    """assn_step_device between caller-owned device buffers (torch tensors in the problem's padded
+    layout) against assn_step from the same state: bitwise where both run on the paired-SM kernel
+    (Q = 512); within FP32 rounding at Q = 128 (the one-tile-per-CTA kernel against the persistent
+    one)."""
+    import torch
+
+    wl = random_workload(33, 18, npol, naz, seed=3)
+    p = gpu_problem(A, wl, precision)
+    qpad, _ = p.layout()
+    dt = 0.9 * p.max_stable_dt()
+    buf = np.zeros((wl.ny, wl.nx, qpad), dtype=np.float32)
+    buf[..., :wl.Q] = wl.psi0()
+    d_in = torch.from_numpy(buf).cuda()
+    d_out = torch.full_like(d_in, -1.0)
+    torch.cuda.synchronize()
+    A._lib.assn_step_device(p.handle, d_in.data_ptr(), d_out.data_ptr(), dt)
+    p.check_finite()                       # (syncs the problem's stream, where the step ran)
+    out = d_out.cpu().numpy()
+    assert np.all(out[..., wl.Q:] == 0.0)  # padded ordinates written as zeros
+    p.step(1, dt)                          # the problem's own state is the same psi0
+    ref = p.state()
+    p.close()
+    got = out[..., :wl.Q].astype(np.float64)
+    if npol * naz == 512:
+        assert np.array_equal(got, ref)
+    else:
+        assert np.abs(got - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
