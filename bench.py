@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "cell-ordinate updates/s"
-BYTES_PER_UPDATE = {"fp64": 16, "fp32": 8, "bf16": 8, "bf16x3": 8}
+BYTES_PER_UPDATE = {"fp64": 16, "fp32": 8, "bf16": 8, "bf16x3": 8, "tf32": 8}
+TENSOR_PRECISIONS = ("bf16", "bf16x3", "tf32")
 
 
 def parse():
@@ -43,7 +44,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "fp32", "fp64"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "tf32", "fp32", "fp64"])
+    ap.add_argument("--precisions", default="",
+                    help="accuracy: comma-separated precisions to run (default fp64,fp32,bf16,bf16x3,tf32)")
     ap.add_argument("--workload", default=synth.LATTICE_448.name, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64/e2e/CPU legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -73,12 +76,13 @@ KERNEL_SOURCES = {"step_tc2_kernel": ("step_tc2.cu", "tc_ptx.h"), "step_tc3_kern
 
 
 def kernel_profile(kernel: str, precision: str, workload: str):
-    """The committed ncu figures of `kernel` (profiles/traffic.json) if its source still matches the
-    hash they were taken at, for this precision and workload: DRAM bytes per launch, tensor-pipe
-    active %.  None when absent or stale."""
+    """The committed ncu figures of `kernel` (profiles/traffic.json, under "<kernel>/<precision>" or
+    "<kernel>") if its source still matches the hash they were taken at, for this precision and
+    workload: DRAM bytes per launch, tensor-pipe active %.  None when absent or stale."""
     import hashlib
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        d = t.get(f"{kernel}/{precision}") or t[kernel]
         src = b"".join(open(os.path.join(ROOT, "paper_1911_08801_gb300", "csrc", f), "rb").read()
                        for f in KERNEL_SOURCES[kernel])
         if (hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"] or precision != d["precision"]
@@ -104,6 +108,20 @@ def bf16_peak():
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]), "measured"
     except Exception:
         return 1900.0, "fallback"
+
+
+# nominal dense TF32 / BF16 tensor rates of the part (1.1 and 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tensor_peak(precision: str):
+    """Dense tensor peak of the contraction's own operand type (TFLOP/s) and where it comes from:
+    BF16 (one pass or the three BF16 passes of BF16X3) the measured BF16 figure; TF32 that figure
+    times the nominal TF32 / BF16 ratio."""
+    tf, src = bf16_peak()
+    if precision == "tf32":
+        return tf * TF32_PER_BF16, f"{src} bf16_tflops x nominal tf32/bf16 {TF32_PER_BF16:.3f}"
+    return tf, f"{src} bf16_tflops"
 
 
 class ClockSampler:
@@ -278,7 +296,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     wl = synth.WORKLOADS[args.workload]
     args.scheme = args.scheme or wl.scheme
-    if args.scheme == "implicit" and args.precision.startswith("bf16"):
+    if args.scheme == "implicit" and args.precision in TENSOR_PRECISIONS:
         raise SystemExit("the implicit scheme runs in fp64 or fp32: pass --precision fp64 or fp32")
     stream = torch.cuda.Stream()
     prob = make_problem(A, wl, args.precision, stream)
@@ -289,7 +307,7 @@ def run_ours(args, rank, world, dist):
     else:
         _, dt = wl.steps()
     tiling, variant = None, None
-    if args.precision.startswith("bf16"):
+    if args.precision in TENSOR_PRECISIONS:
         prob.set_tiling(args.tile, args.stages, args.variant)
         tiling = prob.tiling()
         variant = prob.variant()
@@ -360,7 +378,7 @@ def run_ours(args, rank, world, dist):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"bf16": "bf16 contraction, fp32 state", "bf16x3": "bf16x3 contraction, fp32 state",
-                  "fp32": "fp32", "fp64": "f64"}[args.precision],
+                  "tf32": "tf32 contraction, fp32 state", "fp32": "fp32", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded uniform state, analytic %s materials)" % wl.kind.replace("_", "-"),
         "config": {"workload": wl.name, "cells": f"{wl.nx}x{wl.ny}", "Q": wl.Q, "beta": wl.beta,
                    "quadrature": wl.quadrature, "normalisation": wl.normalisation,
@@ -376,7 +394,7 @@ def run_ours(args, rank, world, dist):
         "roofline": (euler_roofline(args, wl, ms_per_step, achieved, hbm, src, variant) if args.scheme == "euler" else
                      implicit_roofline(args, wl, ms_per_step, stats_timed, args.steps)
                      if args.scheme == "implicit" else
-                     (heun_tc_roofline(wl, ms_per_step, variant) if args.precision.startswith("bf16")
+                     (heun_tc_roofline(wl, ms_per_step, variant) if args.precision in TENSOR_PRECISIONS
                       else alu_roofline(args, wl, ms_per_step))),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -392,18 +410,18 @@ def euler_roofline(args, wl, ms_per_step, achieved, hbm, src, variant):
     kernels, the dense contraction's rate against the BF16 peak beside the ceiling the HBM bound puts
     on it (2 Qp flops per 8 B: Qp / 4 flop per byte)."""
     kernel = ({0: "step_tc2_kernel", 1: "step_tc_kernel", 2: "step_tc3_kernel"}[variant]
-              if args.precision.startswith("bf16") else "step_simt_kernel")
+              if args.precision in TENSOR_PRECISIONS else "step_simt_kernel")
     prof = kernel_profile(kernel, args.precision, wl.name) if kernel in KERNEL_SOURCES else None
     out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
            "traffic": prof["dram_bytes_per_launch"] if prof else None,
            "peak_source": f"{src} hbm_gbs", "bytes_per_update": BYTES_PER_UPDATE[args.precision], "kernel": kernel}
-    if args.precision.startswith("bf16"):
+    if args.precision in TENSOR_PRECISIONS:
         qp = (wl.Q + 63) // 64 * 64
         mp = (wl.Q + 127) // 128 * 128
         flops = 2.0 * mp * qp * wl.nx * wl.ny * (3 if args.precision == "bf16x3" else 1)
-        tf, tsrc = bf16_peak()
+        tf, tsrc = tensor_peak(args.precision)
         ach = flops / (ms_per_step / 1e3) / 1e12
-        out["tensor"] = {"achieved_tflops": ach, "peak_tflops": tf, "frac": ach / tf, "peak_source": f"{tsrc} bf16_tflops",
+        out["tensor"] = {"achieved_tflops": ach, "peak_tflops": tf, "frac": ach / tf, "peak_source": tsrc,
                          "flops_per_step": flops,
                          "ceiling_frac_at_hbm_roofline": (hbm * 1e9 / 8.0) * (flops / (wl.nx * wl.ny * wl.Q)) / (tf * 1e12),
                          "pipe_active_pct_ncu": prof.get("tensor_pipe_active_pct") if prof else None}
@@ -419,22 +437,28 @@ def extras_legs(A, L, torch, wl, args, prob, psi0, stream, dt):
         n_e2e = 20
         phi = np.empty((wl.ny, wl.nx))
         L.assn_run_f32(prob.handle, psi0, 2, dt, phi)
-        reps = 3
-        t0 = time.perf_counter()
+        # each call timed on its own (it returns after Phi is on the host); the median of five, so
+        # that one stall of the shared host does not stand for the call, every time listed
+        reps = 5
+        calls = []
         for _ in range(reps):
+            t0 = time.perf_counter()
             L.assn_run_f32(prob.handle, psi0, n_e2e, dt, phi)
-        el = (time.perf_counter() - t0) / reps
+            calls.append(time.perf_counter() - t0)
+        el = float(np.median(calls))
         # the upload alone (the same pinned buffer, the same copy), for its share of the call
-        t0 = time.perf_counter()
+        ups = []
         for _ in range(reps):
+            t0 = time.perf_counter()
             L.assn_set_state_f32(prob.handle, psi0)
             prob.check_finite()   # syncs the problem's stream
-        up = (time.perf_counter() - t0) / reps
+            ups.append(time.perf_counter() - t0)
+        up = float(np.median(ups))
         out["e2e"] = {"value": units * n_e2e / el, "unit": "updates/s",
                       "h2d_bytes_per_step": int(psi0.nbytes) // n_e2e, "d2h_bytes_per_step": int(phi.nbytes) // n_e2e,
-                      "call": f"assn_run_f32: pinned host psi0 -> {n_e2e} steps -> host Phi",
-                      "ms_per_call": el * 1e3, "h2d_ms_per_call": up * 1e3,
-                      "h2d_share": min(1.0, up / el), "h2d_gbs": psi0.nbytes / up / 1e9}
+                      "call": f"assn_run_f32: pinned host psi0 -> {n_e2e} steps -> host Phi (median of {reps} calls)",
+                      "ms_per_call": el * 1e3, "ms_each_call": [round(c * 1e3, 3) for c in calls],
+                      "h2d_ms_per_call": up * 1e3, "h2d_share": min(1.0, up / el), "h2d_gbs": psi0.nbytes / up / 1e9}
     # the plain FP64 GPU path on the same workload
     try:
         p64 = make_problem(A, wl, "fp64", stream)
@@ -865,11 +889,21 @@ def run_accuracy(args):
             phi_ref, t_oracle = oracle_phi(wl)
         row = {"workload": wl.name, "scheme": wl.scheme, "quadrature": wl.quadrature, "Q": wl.Q,
                "normalisation": wl.normalisation, "steps": n, "dt": dt, "oracle_s": t_oracle, "rel_l2": {}}
-        for prec in ("fp64", "fp32") if wl.scheme == "implicit" else ("fp64", "fp32", "bf16", "bf16x3"):
+        wanted = args.precisions.split(",") if args.precisions else ["fp64", "fp32", "bf16", "bf16x3", "tf32"]
+        for prec in wanted:
+            if wl.scheme == "implicit" and prec in TENSOR_PRECISIONS:
+                continue
             p = make_problem(A, wl, prec, None)
             if wl.kind == "line_source":
                 p.init_line_source()
-            p.step(n, dt)
+            try:
+                p.step(n, dt)
+            except A.AssnError as e:   # TF32 runs at 256 / 512 ordinates only
+                if e.status != A._lib.ASSN_ERR_UNSUPPORTED:
+                    raise
+                row["rel_l2"][prec] = None
+                p.close()
+                continue
             phi = p.scalar_flux()
             p.close()
             row["rel_l2"][prec] = float(np.linalg.norm(phi - phi_ref) / np.linalg.norm(phi_ref))

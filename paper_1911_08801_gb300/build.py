@@ -40,7 +40,8 @@ def _newer(target: str, deps: list[str]) -> bool:
 
 def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "assn_internal.h"), os.path.join(CSRC, "problem.h"), os.path.join(CSRC, "tc_ptx.h"), os.path.join(ROOT, "include", "assn.h")]
+    headers = [os.path.join(CSRC, "assn_internal.h"), os.path.join(CSRC, "problem.h"), os.path.join(CSRC, "tc_ptx.h"), os.path.join(CSRC, "trace.h"),
+               os.path.join(ROOT, "include", "assn.h")]
     nv = nvcc()
     extra = extra or []
 

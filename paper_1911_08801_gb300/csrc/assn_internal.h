@@ -37,12 +37,20 @@ struct StepArgs {
     T dt, dt_sigma_as;
 };
 
-// Tensor-core operands of the BF16 paths.
+// Tensor-core operands of the BF16 and TF32 paths.
 struct TcOperands {
     __nv_bfloat16* G_hi = nullptr;   // [Mp][Qp] row q, column p: off-diagonal K rounded to BF16
     __nv_bfloat16* G_lo = nullptr;   // [Mp][Qp] residual K - G_hi rounded to BF16 (BF16X3 only)
+    float* G32 = nullptr;            // [Mp][Qp] off-diagonal K rounded to TF32 (ASSN_TF32 only)
     int Mp = 0;                      // Q rounded up to 128 (the MMA M dimension)
 };
+
+// FP32 -> TF32 (sign, exponent, 10 significand bits): round to nearest, ties away from zero, by
+// adding half a unit of the last kept bit to the magnitude and clearing the 13 bits below it (an
+// overflowing magnitude carries into the exponent, which is the correctly rounded result).  Finite
+// inputs; the word is what the contraction reads, its low 13 bits zero.
+__device__ __forceinline__ uint32_t tf32_bits(float v) { return (__float_as_uint(v) + 0x1000u) & 0xffffe000u; }
+__device__ __forceinline__ float tf32_round(float v) { return __uint_as_float(tf32_bits(v)); }
 
 // Launchers (each returns cudaSuccess or the launch error).
 cudaError_t launch_build_K(const double* omega, const double* w, int Q, double eps, int kind,
@@ -54,6 +62,10 @@ cudaError_t launch_derive_simt_f32(const double* K64, const double* w, int Q, in
 cudaError_t launch_derive_tc(const double* K64, const double* w, int Q, int Qp, int Mp, int norm,
                              bool split, __nv_bfloat16* G_hi, __nv_bfloat16* G_lo, double* e,
                              cudaStream_t s);
+// The TF32 operand: G32[q][p] = tf32_round((float) K_qp) off the diagonal, zero elsewhere, and the
+// generator diagonal e from those values.
+cudaError_t launch_derive_tf32(const double* K64, const double* w, int Q, int Qp, int Mp, int norm, float* G32,
+                               double* e, cudaStream_t s);
 
 cudaError_t launch_step_simt_f64(const StepArgs<double, OrdD, CellD>& a, cudaStream_t s);
 cudaError_t launch_step_simt_f32(const StepArgs<float, OrdF, CellF>& a, cudaStream_t s);
@@ -115,17 +127,18 @@ cudaError_t launch_step_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, 
 cudaError_t launch_heun_stage_tc2(Tc2Plan* plan, unsigned int* err_flag, int parity0, const float* keep, float alpha,
                                   float beta, cudaStream_t s);
 
-// Paired-SM tensor-core step (variant 2): one problem, forward Euler, BF16 or BF16X3, padded ordinate
-// count 256 or 512 (equal to the kernel-matrix rows).  A cluster of two CTAs shares each M = 256 MMA;
-// the flux buffers and G are bound at plan creation, dt at launch.
+// Paired-SM tensor-core step (variant 2): one problem, forward Euler or a Heun stage, BF16, BF16X3
+// or TF32, padded ordinate count 256 or 512 (equal to the kernel-matrix rows).  A cluster of two CTAs
+// shares each M = 256 MMA; the flux buffers and G are bound at plan creation, dt at launch.
 struct Tc3Plan;
 bool tc3_supported(int Q, int Qp, int Mp, bool split);
-// G_lo non-null: the split (BF16X3) contraction, hi x hi + hi x lo + lo x hi.  With no kernel-matrix
-// ring requested (want.SA == 0) and one BF16 part, G is read back on `stream` (which syncs; skipped
-// while the stream is being captured) to find its distinct blocks, which stay resident if they fit.
-cudaError_t tc3_plan_create(Tc3Plan** plan, const float* buf0, const float* buf1, const __nv_bfloat16* G,
-                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want,
-                            cudaStream_t stream);
+// precision: ASSN_BF16 (ops.G_hi), ASSN_BF16X3 (ops.G_hi and ops.G_lo: the split contraction
+// hi x hi + hi x lo + lo x hi) or ASSN_TF32 (ops.G32); else cudaErrorInvalidValue.  With no
+// kernel-matrix ring requested (want.SA == 0) and BF16, G is read back on `stream` (which syncs;
+// skipped while the stream is being captured) to find its distinct blocks, which stay resident if
+// they fit.
+cudaError_t tc3_plan_create(Tc3Plan** plan, const float* buf0, const float* buf1, const TcOperands& ops,
+                            int precision, int Q, int Qp, int Mp, int nx, int ny, TcRings want, cudaStream_t stream);
 void tc3_plan_destroy(Tc3Plan* plan);
 // MPR = 64-ordinate chunks per stage; SA = kernel-matrix ring depth, 0 when the matrix is resident
 TcRings tc3_plan_rings(const Tc3Plan* plan);

@@ -105,6 +105,15 @@ struct StoreBF16 {
     }
 };
 
+struct StoreTF32 {
+    float* G; int Qp;
+    __device__ double operator()(int q, int p, double v) const {
+        const float t = tf32_round((float)v);
+        G[(size_t)q * Qp + p] = t;
+        return (double)t;
+    }
+};
+
 int line_threads(int Q) { return Q >= 256 ? 256 : (Q >= 128 ? 128 : 64); }
 
 }  // namespace
@@ -138,6 +147,14 @@ cudaError_t launch_derive_tc(const double* K64, const double* w, int Q, int Qp, 
     if (r == cudaSuccess && split) r = cudaMemsetAsync(G_lo, 0, sizeof(__nv_bfloat16) * (size_t)Mp * Qp, s);
     if (r != cudaSuccess) return r;
     derive_kernel<<<Q, line_threads(Q), 0, s>>>(K64, w, Q, norm, StoreBF16{G_hi, split ? G_lo : nullptr, Qp}, e);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_derive_tf32(const double* K64, const double* w, int Q, int Qp, int Mp, int norm, float* G32,
+                               double* e, cudaStream_t s) {
+    cudaError_t r = cudaMemsetAsync(G32, 0, sizeof(float) * (size_t)Mp * Qp, s);
+    if (r != cudaSuccess) return r;
+    derive_kernel<<<Q, line_threads(Q), 0, s>>>(K64, w, Q, norm, StoreTF32{G32, Qp}, e);
     return cudaGetLastError();
 }
 

@@ -71,7 +71,7 @@ struct assn_problem {
 
     size_t ncell() const { return (size_t)nx * ny; }
     size_t elem() const { return precision == ASSN_FP64 ? 8 : 4; }
-    bool tensor() const { return precision == ASSN_BF16 || precision == ASSN_BF16X3; }
+    bool tensor() const { return precision == ASSN_BF16 || precision == ASSN_BF16X3 || precision == ASSN_TF32; }
 };
 
 namespace assn {

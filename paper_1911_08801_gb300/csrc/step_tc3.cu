@@ -1,12 +1,15 @@
 // Paired-SM tensor-core as-S_N step (sm_103a): one problem, forward Euler with first-order upwind
-// transport (Sec. 3.1-3.2), 256 or 512 ordinates (padded), BF16 contraction with FP32 state.
+// transport (Sec. 3.1-3.2), 256 or 512 ordinates (padded), FP32 state; the contraction in BF16, in
+// BF16X3 (split operands) or in TF32.
 //
 // A cluster of two CTAs on two SMs (the pair) steps one tile of TW x TH cells per round (TW = 16;
 // TH = 8 at 512 ordinates, 16 at 256; tiles row-major over the grid, pair p takes tiles p, p + P, ...).
 // The artificial in-scattering gain without its diagonal (Sec. 3.2, Eq. (as-S_N equations))
 //   D[q][c] = sum_{p != q} G_qp psi~_p(c)
 // is computed by tcgen05.mma.cta_group::2 products of M = 256 ordinates x N = TW TH cells x K = 16
-// (BF16 in, FP32 accumulate in tensor memory).  In each 256-ordinate group the even CTA holds
+// (BF16 in, FP32 accumulate in tensor memory; K = 8 in TF32, whose 64-ordinate chunk is two
+// 32-ordinate halves of 128-byte rows, laid out like the hi and lo parts of the split contraction).
+// In each 256-ordinate group the even CTA holds
 // rows 0-127 of G and of the accumulator, the odd CTA rows 128-255; each CTA converts and holds
 // the operand rows of half the tile's cells (rows 0 .. TH/2-1 in the even CTA).  Each SM thus
 // loads half of G per tile and supplies half the operand bytes of every MMA.
@@ -16,13 +19,13 @@
 //               CTA issues the MMAs into one of two accumulator buffers and commits to the
 //               barriers of both CTAs; lane 0 of the odd CTA forwards the completion of its own
 //               kernel-matrix copies to the even CTA.
-//               Lane 2: TMA of this CTA's G rows ([128 x 64] BF16 blocks with 128-byte swizzle): its
-//               distinct blocks once (resident), or all of its 256-row groups, one or two chunks
-//               per request, through a ring.
+//               Lane 2: TMA of this CTA's G rows ([128 x 64] BF16 blocks, or [128 x 32] TF32 ones,
+//               with 128-byte swizzle): its distinct BF16 blocks once (resident), or all of its
+//               256-row groups, one or two chunks per request, through a ring.
 //   flux TMA    this CTA's half tile of FP32 flux, [TW x TH/2 cells x 64 ordinates] chunks, into a
 //               staging ring: warp 3 at 512 ordinates, else lane 1 of warp 0.
-//   warps 1-3   converters (1-2 at 512 ordinates): staging -> BF16 operand rows (K-major,
-//               swizzled) for the pair's MMA;
+//   warps 1-3   converters (1-2 at 512 ordinates): staging -> BF16 (hi [+ lo]) or TF32 operand
+//               rows (K-major, swizzled) for the pair's MMA;
 //               the scalar flux Phi = sum_p w_p psi_p of this CTA's cells, and from it the cells'
 //               coefficients, written into both CTAs.
 //   warps 4-19  epilogue: warp (lane quarter lq, group g) owns 32 ordinates of one 128-row block
@@ -62,6 +65,7 @@ constexpr int kABlock = 128 * 64 * 2;   // one [128 x 64] BF16 block of G
 struct Tc3Args {
     CUtensorMap tm_psi;                 // input flux [ny][nx][Qp] FP32, box {64, TW, TH/2}
     CUtensorMap tm_G;                   // G [Mp][Qp] BF16 as {64, 128, 2, MG, KC}, box {64, 128, 1, MG, CPS}
+                                        // (TF32: {32, 128, 2, MG, 2 KC}, box {32, 128, 1, MG, 1})
     CUtensorMap tm_Glo;                 // split contraction: the residual of G, same view
     const float* in;
     float* out;
@@ -82,7 +86,10 @@ struct Tc3Args {
     float alpha, beta;
 };
 
-template <int MG, int CPS_ = 2, bool SPLIT = false>
+// Contraction precision of a kernel instance: one BF16 pass, the BF16X3 split, or one TF32 pass.
+constexpr int kPrBF16 = 0, kPrSplit = 1, kPrTF32 = 2;
+
+template <int MG, int CPS_ = 2, int PR = kPrBF16>
 struct L3 {
     static constexpr int NT = 256 / MG;         // cells per tile (MMA N)
     static constexpr int TH = NT / kTW;         // tile rows
@@ -93,9 +100,11 @@ struct L3 {
     static constexpr int CPS = CPS_;            // chunks per operand / kernel-matrix stage (one MMA round)
     static constexpr int KR = KC / CPS;         // MMA rounds per tile
     static constexpr int kStg = NTc * 256;      // FP32 staging stage (one chunk)
-    static constexpr int NP = SPLIT ? 2 : 1;    // operand parts: hi [+ lo]
-    static constexpr int kB = NP * CPS * NTc * 128;     // BF16 operand stage (hi chunks, then lo chunks)
-    static constexpr int kA = NP * CPS * MG * kABlock;  // G stage: this CTA's blocks of CPS chunks (hi, then lo)
+    // operand parts of a chunk: hi [+ lo] BF16, or the two 32-ordinate halves of a TF32 chunk (each part
+    // [rows x 128 B], so a TF32 stage has the split contraction's layout)
+    static constexpr int NP = PR == kPrBF16 ? 1 : 2;
+    static constexpr int kB = NP * CPS * NTc * 128;     // operand stage (first parts of the CPS chunks, then second)
+    static constexpr int kA = NP * CPS * MG * kABlock;  // G stage: this CTA's blocks of CPS chunks (first parts, then second)
     int stg, b, a, cx, cy, cb, cst, wsm, bars, end;
     __host__ __device__ L3(int SS, int SB, int SA, int nslot) {
         stg = 0;
@@ -135,13 +144,23 @@ __device__ __forceinline__ float minmod3(float a, float b) {
     return a * b > 0.0f ? (fabsf(a) < fabsf(b) ? a : b) : 0.0f;
 }
 
+// psi~ as the contraction sees it: rounded to BF16, itself (split: hi + lo carry it to about 2^-16),
+// or rounded to TF32
+template <int PR>
+__device__ __forceinline__ float operand_value(float v) {
+    if constexpr (PR == kPrBF16) return bf16_round(v);
+    else if constexpr (PR == kPrTF32) return tf32_round(v);
+    else return v;
+}
+
 // HEUN: one stage of Heun's method with minmod-limited second-order upwind fluxes (Sec. 3.1):
 // out = alpha keep + beta (in + dt L(in)), L with the limited transport, collision, scattering,
 // source and the artificial gain of the stage state.
-template <int MG, int CPS_, bool SPLIT, bool HEUN = false>
+template <int MG, int CPS_, int PR, bool HEUN = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
 step_tc3_kernel(const __grid_constant__ Tc3Args a) {
-    using LT = L3<MG, CPS_, SPLIT>;
+    using LT = L3<MG, CPS_, PR>;
+    constexpr bool SPLIT = PR == kPrSplit, TF = PR == kPrTF32;
     // converter warps and where the flux-copy producer runs: at 512 ordinates (16-kB chunks) two
     // converter warps keep up and the producer gets warp 3 to itself (as one lane of warp 0, beside
     // the MMA issuer's waits, it issued each copy about a microsecond after its slot was released:
@@ -243,7 +262,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     if (warp == 0) {
         if (lane == 0 && rank == 0) {
             // ------------------------------------------------------------------------ MMA issuer
-            constexpr uint32_t idesc = idesc_bf16(256, NT);
+            constexpr uint32_t idesc = TF ? idesc_tf32(256, NT) : idesc_bf16(256, NT);
             const uint64_t a0 = sw128_desc(smem_u32(aring));
             const uint64_t b0 = sw128_desc(smem_u32(bring));
             Ring3 rq;
@@ -276,10 +295,18 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                                 const uint64_t ah = ab + (uint64_t)((blk * kABlock) >> 4) + (uint64_t)(kk * 2);
                                 const uint64_t bh = bd0 + (uint64_t)((c * NTc * 128) >> 4) + (uint64_t)(kk * 2);
                                 const uint32_t dd = dbase + (uint32_t)(j * NT);
-                                mma_bf16_pair(dd, ah, bh, idesc, (kr > 0 || c > 0 || kk > 0) ? 1u : 0u);
-                                if (SPLIT) {   // + hi x lo + lo x hi (the lo parts follow the CPS hi chunks)
-                                    mma_bf16_pair(dd, ah, bh + (uint64_t)((CPS * NTc * 128) >> 4), idesc, 1u);
-                                    mma_bf16_pair(dd, ah + (uint64_t)((CPS * MG * kABlock) >> 4), bh, idesc, 1u);
+                                // (second parts of the stage: the lo parts, or the TF32 chunks' upper halves)
+                                const uint64_t bh2 = bh + (uint64_t)((CPS * NTc * 128) >> 4);
+                                const uint64_t ah2 = ah + (uint64_t)((CPS * MG * kABlock) >> 4);
+                                if constexpr (TF) {   // ordinates 8 kk .. + 7 of each 32-ordinate half
+                                    mma_tf32_pair(dd, ah, bh, idesc, (kr > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                                    mma_tf32_pair(dd, ah2, bh2, idesc, 1u);
+                                } else {
+                                    mma_bf16_pair(dd, ah, bh, idesc, (kr > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                                    if (SPLIT) {   // + hi x lo + lo x hi (the lo parts follow the CPS hi chunks)
+                                        mma_bf16_pair(dd, ah, bh2, idesc, 1u);
+                                        mma_bf16_pair(dd, ah2, bh, idesc, 1u);
+                                    }
                                 }
                             }
                         }
@@ -334,11 +361,13 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                 for (int kr = 0; kr < KR; ++kr) {
                     if (!W3(&st_empty[rq.s], rq.ph ^ 1u, 0x2u)) { ok = false; break; }
                     mbar_expect_tx(&st_full[rq.s], LT::kA);
-                    tma_load_5d_hint(aring + (size_t)rq.s * LT::kA, &a.tm_G, &st_full[rq.s], 0, 0, (int)rank, 0, kr * CPS,
+                    // TF32: G's 32-column chunks 2 kr and 2 kr + 1 (one 64-ordinate chunk per stage)
+                    const int gch = TF ? 2 * kr : kr * CPS;
+                    tma_load_5d_hint(aring + (size_t)rq.s * LT::kA, &a.tm_G, &st_full[rq.s], 0, 0, (int)rank, 0, gch,
                                      pol);
-                    if (SPLIT)
-                        tma_load_5d_hint(aring + (size_t)rq.s * LT::kA + LT::kA / 2, &a.tm_Glo, &st_full[rq.s], 0, 0,
-                                         (int)rank, 0, kr * CPS, pol);
+                    if (SPLIT || TF)
+                        tma_load_5d_hint(aring + (size_t)rq.s * LT::kA + LT::kA / 2, TF ? &a.tm_G : &a.tm_Glo,
+                                         &st_full[rq.s], 0, 0, (int)rank, 0, TF ? gch + 1 : gch, pol);
                     armed |= 1u << rq.s;
                     apar = (apar & ~(1u << rq.s)) | (rq.ph << rq.s);
                     rq.next(a.SB);
@@ -370,10 +399,14 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
         const uint32_t cb_rem = mapa_shared(smem_u32(cb), rank ^ 1u);
         const float dt = a.dt;
         // byte offset of this thread's operand store for row r (float4 column col4, canonical
-        // K-major layout with 128-byte swizzle); fixed for the whole launch, so kept in registers
-        // where a thread has few rows
+        // K-major layout with 128-byte swizzle: BF16, 8 bytes in 16-byte unit col4 / 2 of the row;
+        // TF32, the 16-byte unit col4 % 8 of the row in half col4 / 8); fixed for the whole launch,
+        // so kept in registers where a thread has few rows
         auto store_off = [col4](int r) {
-            return (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
+            if constexpr (TF)
+                return (col4 >> 3) * (CPS * NTc * 128) + (r >> 3) * 1024 + (r & 7) * 128 + (((col4 & 7) ^ (r & 7)) << 4);
+            else
+                return (r >> 3) * 1024 + (r & 7) * 128 + (((col4 >> 1) ^ (r & 7)) << 4) + ((col4 & 1) << 3);
         };
         constexpr bool kKeepOffs = NR <= 11;
         int offs[kKeepOffs ? NR : 1];
@@ -424,10 +457,15 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         if (i >= NR || r >= NTc) continue;
                         const float2 pp = __ffma2_rn(wb, make_float2(v[g].z, v[g].w), __fmul2_rn(wa, make_float2(v[g].x, v[g].y)));
                         part[i] += pp.x + pp.y;
+                        const int off = kKeepOffs ? offs[kKeepOffs ? i : 0] : store_off(r);
+                        if constexpr (TF) {
+                            *reinterpret_cast<uint4*>(dst + off) =
+                                make_uint4(tf32_bits(v[g].x), tf32_bits(v[g].y), tf32_bits(v[g].z), tf32_bits(v[g].w));
+                            continue;
+                        }
                         uint2 h;
                         h.x = pack_bf16(v[g].x, v[g].y);
                         h.y = pack_bf16(v[g].z, v[g].w);
-                        const int off = kKeepOffs ? offs[kKeepOffs ? i : 0] : store_off(r);
                         *reinterpret_cast<uint2*>(dst + off) = h;
                         if (SPLIT) {   // residual of the rounding, the lo part
                             const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.x));
@@ -656,7 +694,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                                 const float cv = c[k];
                                 txd[u] = (cv - (xpos ? c[k - 1] : c[k + 1])) + 0.5f * (xpos ? Ex[k - 2] : Ex[k - 1]);
                                 tyd[u] = (cv - (ypos ? m1S[i + u] : p1S[i + u])) + 0.5f * (ypos ? EyP[i + u] : EyN[i + u]);
-                                st[u] = SPLIT ? cv : bf16_round(cv);
+                                st[u] = operand_value<PR>(cv);
                             }
                             const float2 CV = make_float2(c[i + 2], c[i + 3]);
                             float2 adv = __ffma2_rn(CV, *reinterpret_cast<const float2*>(cx + ci + i),
@@ -746,8 +784,9 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         const float xl1 = s[i1 - 1], xr1 = i1 == 7 ? ev[r + 1] : s[i1 + 1];
                         const float2 S = make_float2(s[i0], s[i1]);
                         // the operand of the generator term: psi~ as the contraction saw it (split: psi itself)
-                        const float2 ST = SPLIT ? make_float2(s[i0], s[i1])
-                                                : __bfloat1622float2(__floats2bfloat162_rn(s[i0], s[i1]));
+                        const float2 ST = PR == kPrBF16
+                                              ? __bfloat1622float2(__floats2bfloat162_rn(s[i0], s[i1]))
+                                              : make_float2(operand_value<PR>(s[i0]), operand_value<PR>(s[i1]));
                         float2 o = __ffma2_rn(S, __fadd2_rn(make_float2(fxv[i0], fxv[i1]), NAXY),
                                               make_float2(fyv[i0], fyv[i1]));
                         o = __ffma2_rn(CL, make_float2(xl0, xl1), o);
@@ -805,7 +844,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                         out = fmaf(ax, ux, out);
                         out = fmaf(ay, uy, out);
                         out = fmaf(dts, y[i], out);
-                        out = fmaf(nge, SPLIT ? sf : bf16_round(sf), out);
+                        out = fmaf(nge, operand_value<PR>(sf), out);
                         __stcs(po + i * QP, out);
                     }
 #pragma unroll
@@ -884,15 +923,32 @@ bool encode_G5(CUtensorMap* map, const __nv_bfloat16* G, int Qp, int MG, int CPS
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MG, int CPS, bool SPLIT>
-size_t smem3(int SS, int SB, int nslot) {
-    return (size_t)1024 + (size_t)L3<MG, CPS, SPLIT>(SS, SB, SB, nslot).end;
+// G [Mp][Qp] TF32 (FP32 words) as a 5D tensor {32 columns, 128 rows, 2 halves, MG groups, Qp / 32
+// chunks}: one box {32, 128, 1, MG, 1} brings one CTA's rows of every 256-row group for one
+// 32-column chunk, landing as MG consecutive [128 x 32] K-major tiles of 128-byte rows (128-byte
+// swizzle); a 64-ordinate stage takes chunks 2 kc and 2 kc + 1.
+bool encode_G5_tf32(CUtensorMap* map, const float* G, int Qp, int MG) {
+    EncodeFn enc = get_encode3();
+    if (!enc) return false;
+    const cuuint64_t dims[5] = {32, 128, 2, (cuuint64_t)MG, (cuuint64_t)(Qp / 32)};
+    const cuuint64_t strides[4] = {(cuuint64_t)Qp * 4, (cuuint64_t)Qp * 4 * 128, (cuuint64_t)Qp * 4 * 256, 128};
+    const cuuint32_t box[5] = {32, 128, 1, (cuuint32_t)MG, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float*>(G), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t smem3_for(int MG, int CPS, bool split, int SS, int SB, int nslot) {
-    if (split) return MG == 2 ? smem3<2, 1, true>(SS, SB, nslot) : smem3<1, 1, true>(SS, SB, nslot);
-    if (MG == 2) return CPS == 2 ? smem3<2, 2, false>(SS, SB, nslot) : smem3<2, 1, false>(SS, SB, nslot);
-    return CPS == 2 ? smem3<1, 2, false>(SS, SB, nslot) : smem3<1, 1, false>(SS, SB, nslot);
+template <int MG, int CPS, int PR>
+size_t smem3(int SS, int SB, int nslot) {
+    return (size_t)1024 + (size_t)L3<MG, CPS, PR>(SS, SB, SB, nslot).end;
+}
+
+// (the split and TF32 layouts are the same size: two parts per chunk, one chunk per stage)
+size_t smem3_for(int MG, int CPS, int pr, int SS, int SB, int nslot) {
+    if (pr != kPrBF16) return MG == 2 ? smem3<2, 1, kPrSplit>(SS, SB, nslot) : smem3<1, 1, kPrSplit>(SS, SB, nslot);
+    if (MG == 2) return CPS == 2 ? smem3<2, 2, kPrBF16>(SS, SB, nslot) : smem3<2, 1, kPrBF16>(SS, SB, nslot);
+    return CPS == 2 ? smem3<1, 2, kPrBF16>(SS, SB, nslot) : smem3<1, 1, kPrBF16>(SS, SB, nslot);
 }
 
 // The distinct [128 x 64] blocks of G that the pair's MMAs read, as (even CTA's block, odd CTA's
@@ -931,13 +987,14 @@ int distinct_blocks(const __nv_bfloat16* G, int Qp, int MG, cudaStream_t s, unsi
 
 using Tc3Kernel = void (*)(Tc3Args);
 template <bool HEUN>
-Tc3Kernel kernel3_t(int MG, int CPS, bool split) {
-    if (split) return MG == 2 ? step_tc3_kernel<2, 1, true, HEUN> : step_tc3_kernel<1, 1, true, HEUN>;
-    if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2, false, HEUN> : step_tc3_kernel<2, 1, false, HEUN>;
-    return CPS == 2 ? step_tc3_kernel<1, 2, false, HEUN> : step_tc3_kernel<1, 1, false, HEUN>;
+Tc3Kernel kernel3_t(int MG, int CPS, int pr) {
+    if (pr == kPrTF32) return MG == 2 ? step_tc3_kernel<2, 1, kPrTF32, HEUN> : step_tc3_kernel<1, 1, kPrTF32, HEUN>;
+    if (pr == kPrSplit) return MG == 2 ? step_tc3_kernel<2, 1, kPrSplit, HEUN> : step_tc3_kernel<1, 1, kPrSplit, HEUN>;
+    if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2, kPrBF16, HEUN> : step_tc3_kernel<2, 1, kPrBF16, HEUN>;
+    return CPS == 2 ? step_tc3_kernel<1, 2, kPrBF16, HEUN> : step_tc3_kernel<1, 1, kPrBF16, HEUN>;
 }
-Tc3Kernel kernel3(int MG, int CPS, bool split, bool heun) {
-    return heun ? kernel3_t<true>(MG, CPS, split) : kernel3_t<false>(MG, CPS, split);
+Tc3Kernel kernel3(int MG, int CPS, int pr, bool heun) {
+    return heun ? kernel3_t<true>(MG, CPS, pr) : kernel3_t<false>(MG, CPS, pr);
 }
 
 }  // namespace
@@ -946,7 +1003,7 @@ struct Tc3Plan {
     int MG = 0, CPS = 2, SS = 0, SB = 0, SA = 0, grid = 0, total = 0, ntx = 0;
     int nslot = 0;                      // resident kernel-matrix blocks (0: the kernel-matrix ring)
     unsigned long long slots = 0, reps = 0;
-    bool split = false;
+    int pr = kPrBF16;                   // contraction precision of the instance launched
     size_t smem = 0;
     CUtensorMap tm_psi[2], tm_G, tm_Glo;
     const float* buf[2] = {nullptr, nullptr};
@@ -959,21 +1016,23 @@ bool tc3_supported(int Q, int Qp, int Mp, bool split) {
     return (Qp == 256 || Qp == 512) && Mp == Qp;
 }
 
-cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1, const __nv_bfloat16* G,
-                            const __nv_bfloat16* G_lo, int Q, int Qp, int Mp, int nx, int ny, TcRings want,
-                            cudaStream_t stream) {
+cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1, const TcOperands& ops,
+                            int precision, int Q, int Qp, int Mp, int nx, int ny, TcRings want, cudaStream_t stream) {
     *out = nullptr;
-    const bool split = G_lo != nullptr;
+    const int pr = precision == ASSN_BF16 ? kPrBF16 : precision == ASSN_BF16X3 ? kPrSplit
+                 : precision == ASSN_TF32 ? kPrTF32 : -1;
+    if (pr < 0 || (pr == kPrTF32 ? !ops.G32 : !ops.G_hi) || (pr == kPrSplit && !ops.G_lo)) return cudaErrorInvalidValue;
+    const bool split = pr != kPrBF16;   // two operand parts per chunk
     if (!tc3_supported(Q, Qp, Mp, split)) return cudaErrorNotSupported;
     Tc3Plan* p = new Tc3Plan();
     p->MG = Qp / 256;
-    p->split = split;
+    p->pr = pr;
     const size_t limit = 227 * 1024;
     // rings as requested (MPR: 64-ordinate chunks per operand / kernel-matrix stage, 1 or 2), else
     // two chunks per stage, two operand and kernel-matrix stages, and as many staging stages as fit,
     // up to four (measured on the 448^2 lattice at 512 ordinates: the staging depth mattered most,
     // two stages 0.30 ms, three or four 0.24 ms; two chunks per stage cut the per-round waits)
-    p->CPS = (want.MPR == 1 || split) ? 1 : 2;   // split operands: one chunk per stage
+    p->CPS = (want.MPR == 1 || split) ? 1 : 2;   // split or TF32 operands: one chunk per stage
     p->SS = want.SS ? want.SS : 4;
     p->SB = p->SA = want.SB ? want.SB : (want.SA ? want.SA : 2);
     // the kernel matrix resident (no kernel-matrix ring requested, one BF16 part, not while the
@@ -982,10 +1041,10 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (!want.SA && !split && cudaStreamIsCapturing(stream, &cap) == cudaSuccess &&
         cap == cudaStreamCaptureStatusNone) {
-        const int n = distinct_blocks(G, Qp, p->MG, stream, &p->slots, &p->reps);
-        if (n > 0 && smem3_for(p->MG, p->CPS, false, want.SS ? want.SS : 2, p->SB, n) <= limit) p->nslot = n;
+        const int n = distinct_blocks(ops.G_hi, Qp, p->MG, stream, &p->slots, &p->reps);
+        if (n > 0 && smem3_for(p->MG, p->CPS, kPrBF16, want.SS ? want.SS : 2, p->SB, n) <= limit) p->nslot = n;
     }
-    auto need = [&](int) { return smem3_for(p->MG, p->CPS, p->split, p->SS, p->SB, p->nslot); };
+    auto need = [&](int) { return smem3_for(p->MG, p->CPS, p->pr, p->SS, p->SB, p->nslot); };
     if (!want.SS)
         while (p->SS > 2 && need(p->SA) > limit) --p->SS;
     if (need(p->SA) > limit) { delete p; return cudaErrorNotSupported; }
@@ -998,17 +1057,18 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     p->total = p->ntx * ((ny + TH - 1) / TH);
     p->buf[0] = buf0;
     p->buf[1] = buf1;
+    const bool gmap = pr == kPrTF32 ? encode_G5_tf32(&p->tm_G, ops.G32, Qp, p->MG)
+                                    : encode_G5(&p->tm_G, ops.G_hi, Qp, p->MG, p->nslot ? 1 : p->CPS, p->nslot ? 1 : p->MG);
     if (!encode_psi3(&p->tm_psi[0], buf0, Qp, nx, ny, TH / 2) || !encode_psi3(&p->tm_psi[1], buf1, Qp, nx, ny, TH / 2) ||
-        !encode_G5(&p->tm_G, G, Qp, p->MG, p->nslot ? 1 : p->CPS, p->nslot ? 1 : p->MG) ||
-        (split && !encode_G5(&p->tm_Glo, G_lo, Qp, p->MG, p->CPS, p->MG))) {
+        !gmap || (pr == kPrSplit && !encode_G5(&p->tm_Glo, ops.G_lo, Qp, p->MG, p->CPS, p->MG))) {
         delete p;
         return cudaErrorInvalidValue;
     }
     // one pair per two SMs, as many pairs as the device co-schedules (never more than tiles)
-    auto kern = kernel3(p->MG, p->CPS, p->split, false);
+    auto kern = kernel3(p->MG, p->CPS, p->pr, false);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
     if (e == cudaSuccess)   // the Heun-stage instance: same layout and shared memory
-        e = cudaFuncSetAttribute(kernel3(p->MG, p->CPS, p->split, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(kernel3(p->MG, p->CPS, p->pr, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)p->smem);
     if (e != cudaSuccess) { delete p; return e; }
     int dev = 0, sms = 0;
@@ -1065,7 +1125,7 @@ cudaError_t launch3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* 
     memset(&a, 0, sizeof a);
     a.tm_psi = p->tm_psi[parity];
     a.tm_G = p->tm_G;
-    a.tm_Glo = p->split ? p->tm_Glo : p->tm_G;
+    a.tm_Glo = p->pr == kPrSplit ? p->tm_Glo : p->tm_G;
     a.in = p->buf[parity];
     a.out = const_cast<float*>(p->buf[parity ^ 1]);
     a.ord = ord;
@@ -1094,7 +1154,7 @@ cudaError_t launch3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* 
         a.in = in_ext;
         a.out = out_ext;
     }
-    kernel3(p->MG, p->CPS, p->split, heun)<<<p->grid, kThreads3, p->smem, s>>>(a);
+    kernel3(p->MG, p->CPS, p->pr, heun)<<<p->grid, kThreads3, p->smem, s>>>(a);
     return cudaGetLastError();
 }
 }  // namespace

@@ -80,6 +80,10 @@ def test_header_is_plain_c_and_links(tmp_path):
                    '  size_t b = 0;\n'
                    '  if (assn_footprint_bytes(448, 448, 512, ASSN_BF16, &b) != ASSN_OK || b < 822083584u) return 3;\n'
                    '  if (assn_create(NULL, 1, 1, 0, 1, 0, 1, ASSN_BF16, NULL) != ASSN_ERR_ARG) return 4;\n'
+                   '  size_t t = 0, x = 0;  /* TF32 words hold as many bytes as the BF16 hi + lo parts */\n'
+                   '  if (assn_footprint_bytes(448, 448, 512, ASSN_TF32, &t) != ASSN_OK ||\n'
+                   '      assn_footprint_bytes(448, 448, 512, ASSN_BF16X3, &x) != ASSN_OK || t != x || t < b) return 5;\n'
+                   '  if (assn_footprint_bytes(448, 448, 512, ASSN_TF32 + 1, &t) != ASSN_ERR_ARG) return 6;\n'
                    '  puts("ok");\n  return 0;\n}\n')
     exe = tmp_path / "abi"
     r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{inc}", str(src), f"-L{libdir}",

@@ -42,6 +42,16 @@ def test_heun_roofline_counts_20_bytes_per_update(bench):
     assert bench.heun_tc_roofline(wl, 2.0, 0)["kernel"].startswith("step_tc2_kernel")
 
 
+def test_tensor_peak_of_each_operand_type(bench):
+    # BF16 and BF16X3 against the BF16 peak; TF32 against it times the nominal 1.1 / 2.25
+    bf, _ = bench.bf16_peak()
+    assert bench.tensor_peak("bf16")[0] == bench.tensor_peak("bf16x3")[0] == bf
+    tf, src = bench.tensor_peak("tf32")
+    assert tf == pytest.approx(bf * 1.1 / 2.25) and "tf32" in src
+    assert set(bench.TENSOR_PRECISIONS) == {"bf16", "bf16x3", "tf32"}
+    assert bench.BYTES_PER_UPDATE["tf32"] == 8
+
+
 def test_implicit_roofline_counts_source_iterations(bench):
     wl = synth.PAPER_LINE_SOURCE_200_IMPLICIT
     stats = {"source_iterations": 420, "gmres_iterations": 20, "sweeps": 420}
