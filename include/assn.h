@@ -498,7 +498,7 @@ const char* assn_server_last_error(void);
  * Errors: ASSN_ERR_ARG for NULL pointers, elem_bytes not 4 or 8, ncell > ASSN_NOALLOC_MASS_MAX_CELLS
  * or Qp > ASSN_MAX_Q; ASSN_ERR_CUDA if the launch fails (message in assn_noalloc_last_error()).
  * The first call on a device looks up the scratch array's device address (with that device
- * current), so make it before any stream capture.  Every call shares the scratch array and
+ * current); later calls on that device reuse it.  Every call shares the scratch array and
  * overwrites it completely before reading it; calls whose work overlaps on one device race, so
  * serialise them (same stream, or events). */
 #define ASSN_NOALLOC_MASS_CELLS_PER_BLOCK 256

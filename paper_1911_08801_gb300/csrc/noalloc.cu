@@ -4,7 +4,7 @@
 // budget rules out allocator calls (cudaMalloc may block and synchronise the device), and hosts
 // that run the library inside a memory pool they manage themselves.  The reduction's partial sums
 // live in a fixed file-scope device array instead of an allocation; its device address is looked
-// up once per device on the first call there (so that call should come before any stream capture).
+// up once per device, on the first call there, and reused by later calls.
 #include <cstdio>
 #include <mutex>
 
