@@ -72,6 +72,53 @@ def test_error_well_below_bf16(A, npol, naz):
     assert errs["tf32"] <= errs["bf16"] / 4.0, errs
 
 
+def round_sig(x, bits):
+    """Round to nearest with ties to even at `bits` significant bits (normal range)."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 2.0 ** bits), e - bits)
+
+
+def round_tf32(x):
+    """FP64 -> FP32 (to nearest even), then to TF32 by the library's rule: to nearest with ties away
+    from zero at 11 significant bits, on the bit pattern's magnitude."""
+    u = np.asarray(x, dtype=np.float64).astype(np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16)])
+def test_contraction_is_the_product_of_rounded_operands(A, npol, naz, precision):
+    """The tensor cores compute the product of the rounded operands to FP32 accuracy.  Expected
+    step: the oracle's step plus the exact (FP64) change that rounding makes to its artificial
+    gain, dt sigma_as [(G~ psi~ - e~ psi~) - (G psi - e psi)], with G the off-diagonal K, G~ its
+    stored rounding (TF32: FP32 then TF32 with ties away; BF16: to nearest even from FP64), psi~
+    the state's rounding, e~ the generator diagonal of G~ (as FP32).  The GPU step must agree
+    with it to FP32 arithmetic, which is over 5x (TF32) and 40x (BF16) tighter than the rounding
+    terms themselves (checked here), so an MMA that read its operands other than assumed
+    (truncated, fewer bits) fails."""
+    wl = random_workload(48, 40, npol, naz, seed=npol * naz + 3)
+    psi = wl.psi0().astype(np.float32).astype(np.float64)   # the state as the library holds it
+    p = gpu_problem(A, wl, precision, psi0=psi)
+    assert p.variant() == 2
+    dt = 0.9 * p.max_stable_dt()
+    p.step(1, dt)
+    got = p.state()
+    p.close()
+    Om, w, K, sa, ss, q = oracle_setup(wl)
+    G = K - np.diag(np.diag(K))
+    if precision == "tf32":
+        Gr, psir = round_tf32(G), round_tf32(psi)
+    else:
+        Gr, psir = round_sig(G, 8), round_sig(psi, 8)
+    e = (w[:, None] * G).sum(axis=0) / w                       # column normalisation
+    er = ((w[:, None] * Gr).sum(axis=0) / w).astype(np.float32).astype(np.float64)
+    delta = dt * wl.sigma_as * ((psir @ Gr.T - er * psir) - (psi @ G.T - e * psi))
+    want = O.step(psi, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt) + delta
+    tol = 4e-6 * np.abs(psi).max()                             # FP32 arithmetic of the step
+    assert np.abs(delta).max() >= (5 if precision == "tf32" else 40) * tol
+    assert np.abs(got - want).max() <= tol, (np.abs(got - want).max(), np.abs(delta).max())
+
+
 @pytest.mark.parametrize("npol,naz", QUADS)
 @pytest.mark.parametrize("nx,ny", [(70, 37), (16, 8), (1, 1), (5, 90)])
 def test_heun_one_step(A, nx, ny, npol, naz):
