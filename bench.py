@@ -34,8 +34,10 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "cell-ordinate updates/s"
-BYTES_PER_UPDATE = {"fp64": 16, "fp32": 8, "bf16": 8, "bf16x3": 8, "tf32": 8}
-TENSOR_PRECISIONS = ("bf16", "bf16x3", "tf32")
+BYTES_PER_UPDATE = {"fp64": 16, "fp32": 8, "bf16": 8, "bf16x3": 8, "tf32": 8, "bf16x2": 8}
+TENSOR_PRECISIONS = ("bf16", "bf16x3", "tf32", "bf16x2")
+# dense contraction passes per precision (each 2 Mp flops per update at its operand type)
+TENSOR_PASSES = {"bf16": 1, "bf16x3": 3, "tf32": 1, "bf16x2": 2}
 
 
 def parse():
@@ -44,9 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "tf32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "bf16x2", "tf32", "fp32", "fp64"])
     ap.add_argument("--precisions", default="",
-                    help="accuracy: comma-separated precisions to run (default fp64,fp32,bf16,bf16x3,tf32)")
+                    help="accuracy: comma-separated precisions to run (default fp64,fp32,bf16,bf16x3,bf16x2,tf32)")
     ap.add_argument("--workload", default=synth.LATTICE_448.name, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64/e2e/CPU legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -116,7 +118,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 
 def tensor_peak(precision: str):
     """Dense tensor peak of the contraction's own operand type (TFLOP/s) and where it comes from:
-    BF16 (one pass or the three BF16 passes of BF16X3) the measured BF16 figure; TF32 that figure
+    BF16 (one pass, or the passes of BF16X3 and BF16X2) the measured BF16 figure; TF32 that figure
     times the nominal TF32 / BF16 ratio."""
     tf, src = bf16_peak()
     if precision == "tf32":
@@ -378,6 +380,7 @@ def run_ours(args, rank, world, dist):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"bf16": "bf16 contraction, fp32 state", "bf16x3": "bf16x3 contraction, fp32 state",
+                  "bf16x2": "bf16x2 contraction (kernel matrix hi+lo), fp32 state",
                   "tf32": "tf32 contraction, fp32 state", "fp32": "fp32", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded uniform state, analytic %s materials)" % wl.kind.replace("_", "-"),
         "config": {"workload": wl.name, "cells": f"{wl.nx}x{wl.ny}", "Q": wl.Q, "beta": wl.beta,
@@ -418,7 +421,7 @@ def euler_roofline(args, wl, ms_per_step, achieved, hbm, src, variant):
     if args.precision in TENSOR_PRECISIONS:
         qp = (wl.Q + 63) // 64 * 64
         mp = (wl.Q + 127) // 128 * 128
-        flops = 2.0 * mp * qp * wl.nx * wl.ny * (3 if args.precision == "bf16x3" else 1)
+        flops = 2.0 * mp * qp * wl.nx * wl.ny * TENSOR_PASSES[args.precision]
         tf, tsrc = tensor_peak(args.precision)
         ach = flops / (ms_per_step / 1e3) / 1e12
         out["tensor"] = {"achieved_tflops": ach, "peak_tflops": tf, "frac": ach / tf, "peak_source": tsrc,
@@ -889,7 +892,7 @@ def run_accuracy(args):
             phi_ref, t_oracle = oracle_phi(wl)
         row = {"workload": wl.name, "scheme": wl.scheme, "quadrature": wl.quadrature, "Q": wl.Q,
                "normalisation": wl.normalisation, "steps": n, "dt": dt, "oracle_s": t_oracle, "rel_l2": {}}
-        wanted = args.precisions.split(",") if args.precisions else ["fp64", "fp32", "bf16", "bf16x3", "tf32"]
+        wanted = args.precisions.split(",") if args.precisions else ["fp64", "fp32", "bf16", "bf16x3", "bf16x2", "tf32"]
         for prec in wanted:
             if wl.scheme == "implicit" and prec in TENSOR_PRECISIONS:
                 continue
@@ -898,7 +901,7 @@ def run_accuracy(args):
                 p.init_line_source()
             try:
                 p.step(n, dt)
-            except A.AssnError as e:   # TF32 runs at 256 / 512 ordinates only
+            except A.AssnError as e:   # TF32 and BF16X2 run at 256 / 512 ordinates only
                 if e.status != A._lib.ASSN_ERR_UNSUPPORTED:
                     raise
                 row["rel_l2"][prec] = None

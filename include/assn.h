@@ -65,17 +65,20 @@ typedef enum {
  *   ASSN_BF16X3 tcgen05, operands split into BF16 hi+lo, three passes (hi*hi + hi*lo + lo*hi),
  *               FP32 accumulation: about FP32-level accuracy of the contraction.
  *   ASSN_TF32   tcgen05 kind::tf32, both operands rounded to TF32 (10 stored significand bits,
- *               to nearest, ties away from zero), FP32 accumulation, one pass.  Runs on the
- *               paired-SM kernel only (tiling variant 2: 193..256 or 449..512 ordinates), for
- *               the forward-Euler and Heun schemes; other ordinate counts or variants, batches
- *               and the server return ASSN_ERR_UNSUPPORTED.
+ *               to nearest, ties away from zero), FP32 accumulation, one pass.
+ *   ASSN_BF16X2 tcgen05, the kernel matrix split into BF16 hi+lo, the flux in one BF16 part, two
+ *               passes (hi*psi~ + lo*psi~), FP32 accumulation.
+ *   TF32 and BF16X2 run on the paired-SM kernel only (tiling variant 2: 193..256 or 449..512
+ *   ordinates), for the forward-Euler and Heun schemes; other ordinate counts or variants,
+ *   batches, autotune and the server return ASSN_ERR_UNSUPPORTED.
  * K itself is always built in FP64 on the device. */
 typedef enum {
     ASSN_FP64 = 0,
     ASSN_FP32 = 1,
     ASSN_BF16 = 2,
     ASSN_BF16X3 = 3,
-    ASSN_TF32 = 4
+    ASSN_TF32 = 4,
+    ASSN_BF16X2 = 5
 } assn_precision;
 
 /* Kernel shape.  ASSN_KERNEL_GAUSS is the paper's s_eps(mu) ~ exp(-(1-mu)^2/eps^2)

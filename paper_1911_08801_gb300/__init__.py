@@ -10,10 +10,10 @@ import numpy as np
 
 from . import _lib
 from ._lib import (ASSN_BF16, ASSN_BF16X3, ASSN_FP32, ASSN_FP64, ASSN_KERNEL_EXP, ASSN_KERNEL_GAUSS,
-                   ASSN_NORM_COLUMN, ASSN_NORM_ROW, ASSN_TF32, PRECISIONS, AssnError)
+                   ASSN_NORM_COLUMN, ASSN_NORM_ROW, ASSN_TF32, ASSN_BF16X2, PRECISIONS, AssnError)
 
 __all__ = ["Problem", "Batch", "Server", "AssnError", "PRECISIONS", "ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
-           "ASSN_TF32",
+           "ASSN_TF32", "ASSN_BF16X2",
            "ASSN_KERNEL_GAUSS", "ASSN_KERNEL_EXP", "ASSN_NORM_COLUMN", "ASSN_NORM_ROW", "icosahedron_quadrature"]
 
 

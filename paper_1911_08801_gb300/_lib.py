@@ -25,7 +25,7 @@ ASSN_ERR_STATE = -7
 ASSN_ERR_UNSUPPORTED = -8
 ASSN_ERR_CANCELLED = -9
 
-ASSN_FP64, ASSN_FP32, ASSN_BF16, ASSN_BF16X3, ASSN_TF32 = 0, 1, 2, 3, 4
+ASSN_FP64, ASSN_FP32, ASSN_BF16, ASSN_BF16X3, ASSN_TF32, ASSN_BF16X2 = 0, 1, 2, 3, 4, 5
 ASSN_KERNEL_GAUSS, ASSN_KERNEL_EXP = 0, 1
 ASSN_NORM_COLUMN, ASSN_NORM_ROW = 0, 1
 ASSN_SCHEME_EULER_UPWIND, ASSN_SCHEME_HEUN_MINMOD, ASSN_SCHEME_IMPLICIT = 0, 1, 2
@@ -35,7 +35,8 @@ ICO_BASES = {"printed": ASSN_ICO_PRINTED, "regular": ASSN_ICO_REGULAR}
 ICO_MIDPOINTS = {"sphere": 0, "flat": ASSN_ICO_FLAT_MIDPOINTS}
 SCHEMES = {"euler": ASSN_SCHEME_EULER_UPWIND, "heun": ASSN_SCHEME_HEUN_MINMOD, "implicit": ASSN_SCHEME_IMPLICIT}
 
-PRECISIONS = {"fp64": ASSN_FP64, "fp32": ASSN_FP32, "bf16": ASSN_BF16, "bf16x3": ASSN_BF16X3, "tf32": ASSN_TF32}
+PRECISIONS = {"fp64": ASSN_FP64, "fp32": ASSN_FP32, "bf16": ASSN_BF16, "bf16x3": ASSN_BF16X3, "tf32": ASSN_TF32,
+              "bf16x2": ASSN_BF16X2}
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)

@@ -300,7 +300,7 @@ int assn_create(assn_problem** out, int nx, int ny, double x0, double x1, double
     if (!(x1 > x0) || !(y1 > y0)) return fail(nullptr, ASSN_ERR_ARG, "empty domain");
     const double hx = (x1 - x0) / nx, hy = (y1 - y0) / ny;
     if (fabs(hx - hy) > 1e-12 * hx) return fail(nullptr, ASSN_ERR_ARG, "cells must be square (hx=%g, hy=%g)", hx, hy);
-    if (precision < ASSN_FP64 || precision > ASSN_TF32) return fail(nullptr, ASSN_ERR_ARG, "unknown precision %d", precision);
+    if (precision < ASSN_FP64 || precision > ASSN_BF16X2) return fail(nullptr, ASSN_ERR_ARG, "unknown precision %d", precision);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return fail(nullptr, ASSN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
@@ -455,7 +455,7 @@ int assn_set_artificial_scattering(assn_problem* p, double sigma_as, double eps,
         CK(p, cudaMalloc(&p->tc.G32, sizeof(float) * (size_t)p->tc.Mp * Qp));
         CK(p, launch_derive_tf32(p->d_K64, p->d_w64, Q, Qp, p->tc.Mp, normalisation, p->tc.G32, p->d_e, p->stream));
     } else {
-        const bool split = p->precision == ASSN_BF16X3;
+        const bool split = p->precision == ASSN_BF16X3 || p->precision == ASSN_BF16X2;   // G hi + lo
         p->tc.Mp = (Q + 127) / 128 * 128;
         CK(p, cudaMalloc(&p->tc.G_hi, sizeof(__nv_bfloat16) * (size_t)p->tc.Mp * Qp));
         if (split) CK(p, cudaMalloc(&p->tc.G_lo, sizeof(__nv_bfloat16) * (size_t)p->tc.Mp * Qp));
@@ -603,10 +603,10 @@ int assn_max_stable_dt(assn_problem* p, double* dt_out) {
 
 // The tensor-core kernel a step of p runs: the requested variant, or (automatic, -1) the paired-SM
 // kernel where it applies (forward Euler or Heun, 193..256 or 449..512 ordinates), else variant 0.
-// TF32 has the paired-SM kernel only.
+// TF32 and BF16X2 have the paired-SM kernel only.
 static int eff_variant(const assn_problem* p) {
     if (p->variant >= 0) return p->variant;
-    if (p->precision == ASSN_TF32) return 2;
+    if (p->paired_only()) return 2;
     return (p->scheme != ASSN_SCHEME_IMPLICIT &&
             tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision == ASSN_BF16X3)) ? 2 : 0;
 }
@@ -674,10 +674,10 @@ static int step_once(assn_problem* p, const void* in, void* out, double dt) {
 static int ensure_plan(assn_problem* p, double dt, bool need_v1) {
     cudaError_t e = cudaSuccess;
     const int v = eff_variant(p);
-    if (p->precision == ASSN_TF32 && (v != 2 || need_v1))
+    if (p->paired_only() && (v != 2 || need_v1))
         return fail(p, ASSN_ERR_UNSUPPORTED,
-                    "TF32 runs on the paired-SM kernel only (tiling variant 2, its own flux buffers or a 16-byte "
-                    "aligned input)");
+                    "TF32 and BF16X2 run on the paired-SM kernel only (tiling variant 2, its own flux buffers or a "
+                    "16-byte aligned input)");
     if ((v == 1 || need_v1) && !p->plan)
         e = tc_plan_create(&p->plan, p->tc.G_hi, p->tc.G_lo, p->Q, p->Qp, p->tc.Mp, p->nx, p->ny,
                            p->precision == ASSN_BF16X3, p->want_nt, p->want_stages);
@@ -866,8 +866,8 @@ int assn_set_tiling(assn_problem* p, int tile_cells, int stages, int variant) {
         return fail(p, ASSN_ERR_ARG, "tile_cells must be 0, 32, 64, 128 or 256");
     if (stages != 0 && (stages < 2 || stages > 8)) return fail(p, ASSN_ERR_ARG, "stages must be 0 or 2..8");
     if (variant < -1 || variant > 2) return fail(p, ASSN_ERR_ARG, "variant must be -1 (automatic), 0, 1 or 2");
-    if (p->precision == ASSN_TF32 && (variant == 0 || variant == 1))
-        return fail(p, ASSN_ERR_UNSUPPORTED, "TF32 runs on the paired-SM kernel only (variant -1 or 2)");
+    if (p->paired_only() && (variant == 0 || variant == 1))
+        return fail(p, ASSN_ERR_UNSUPPORTED, "TF32 and BF16X2 run on the paired-SM kernel only (variant -1 or 2)");
     p->want_nt = tile_cells;
     p->want_stages = stages;
     p->want_rings = TcRings{stages, stages, stages, 0};
@@ -890,7 +890,7 @@ int assn_set_rings(assn_problem* p, int staging, int operand, int kernel_matrix,
         blocks_per_request != 8)
         return fail(p, ASSN_ERR_ARG, "blocks_per_request must be 0, 1, 2, 4 or 8");
     p->want_rings = TcRings{staging, operand, kernel_matrix, blocks_per_request};
-    if (p->variant != 2) p->variant = p->precision == ASSN_TF32 ? 2 : 0;
+    if (p->variant != 2) p->variant = p->paired_only() ? 2 : 0;
     if (p->plan2) tc2_plan_destroy(p->plan2);
     p->plan2 = nullptr;
     if (p->plan3) tc3_plan_destroy(p->plan3);

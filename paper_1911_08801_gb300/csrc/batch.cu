@@ -625,8 +625,9 @@ const char* assn_batch_last_error(const assn_batch* b) { return b ? b->err.c_str
 int assn_autotune(assn_problem* p, double dt, int use_cache, int* tile_cells, int* stages, double* ms_per_step) {
     if (!p) return ASSN_ERR_ARG;
     if (!p->tensor()) return problem_fail(p, ASSN_ERR_UNSUPPORTED, "autotune applies to the tensor-core precisions");
-    if (p->precision == ASSN_TF32)
-        return problem_fail(p, ASSN_ERR_UNSUPPORTED, "autotune tunes the persistent one-CTA kernel, which has no TF32 form");
+    if (p->paired_only())
+        return problem_fail(p, ASSN_ERR_UNSUPPORTED,
+                            "autotune tunes the persistent one-CTA kernel, which has no TF32 or BF16X2 form");
     int r = problem_prepare(p, dt);
     if (r) return r;
     cudaError_t e = cudaStreamSynchronize(p->stream);

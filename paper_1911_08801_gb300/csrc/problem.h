@@ -71,7 +71,11 @@ struct assn_problem {
 
     size_t ncell() const { return (size_t)nx * ny; }
     size_t elem() const { return precision == ASSN_FP64 ? 8 : 4; }
-    bool tensor() const { return precision == ASSN_BF16 || precision == ASSN_BF16X3 || precision == ASSN_TF32; }
+    bool tensor() const {
+        return precision == ASSN_BF16 || precision == ASSN_BF16X3 || precision == ASSN_TF32 || precision == ASSN_BF16X2;
+    }
+    // precisions with a paired-SM form only (no one-CTA or tile-per-CTA kernel)
+    bool paired_only() const { return precision == ASSN_TF32 || precision == ASSN_BF16X2; }
 };
 
 namespace assn {

@@ -286,7 +286,7 @@ void loop_main(assn_server* s) {
 extern "C" {
 
 int assn_footprint_bytes(int nx, int ny, int Q, int precision, size_t* bytes) {
-    if (!bytes || nx < 1 || ny < 1 || Q < 1 || Q > ASSN_MAX_Q || precision < ASSN_FP64 || precision > ASSN_TF32)
+    if (!bytes || nx < 1 || ny < 1 || Q < 1 || Q > ASSN_MAX_Q || precision < ASSN_FP64 || precision > ASSN_BF16X2)
         return ASSN_ERR_ARG;
     const size_t ncell = (size_t)nx * ny, Qp = (size_t)padq(Q), Mp = (Qp + 127) / 128 * 128;
     const size_t elem = precision == ASSN_FP64 ? 8 : 4;
@@ -295,7 +295,7 @@ int assn_footprint_bytes(int nx, int ny, int Q, int precision, size_t* bytes) {
     b += (size_t)Q * Q * 8 + Qp * 64;            // FP64 K, per-ordinate constants
     if (precision == ASSN_FP64) b += Qp * Qp * 8;
     else if (precision == ASSN_FP32) b += Qp * Qp * 4;
-    else b += Mp * Qp * 2 * (precision == ASSN_BF16 ? 1 : 2);   // BF16 G; hi + lo; TF32 words
+    else b += Mp * Qp * 2 * (precision == ASSN_BF16 ? 1 : 2);   // BF16 G; hi + lo (BF16X3, BF16X2); TF32 words
     b += (size_t)1 << 20;                        // small buffers, descriptors, allocation rounding
     *bytes = (b + ((size_t)2 << 20) - 1) / ((size_t)2 << 20) * ((size_t)2 << 20);
     return ASSN_OK;

@@ -1,6 +1,7 @@
 // Paired-SM tensor-core as-S_N step (sm_103a): one problem, forward Euler with first-order upwind
 // transport (Sec. 3.1-3.2), 256 or 512 ordinates (padded), FP32 state; the contraction in BF16, in
-// BF16X3 (split operands) or in TF32.
+// BF16X3 (both operands split), in BF16X2 (the kernel matrix split, the operand in one BF16 part) or
+// in TF32.
 //
 // A cluster of two CTAs on two SMs (the pair) steps one tile of TW x TH cells per round (TW = 16;
 // TH = 8 at 512 ordinates, 16 at 256; tiles row-major over the grid, pair p takes tiles p, p + P, ...).
@@ -86,8 +87,9 @@ struct Tc3Args {
     float alpha, beta;
 };
 
-// Contraction precision of a kernel instance: one BF16 pass, the BF16X3 split, or one TF32 pass.
-constexpr int kPrBF16 = 0, kPrSplit = 1, kPrTF32 = 2;
+// Contraction precision of a kernel instance: one BF16 pass, the BF16X3 split, one TF32 pass, or
+// BF16X2 (G hi x psi~ + G lo x psi~).
+constexpr int kPrBF16 = 0, kPrSplit = 1, kPrTF32 = 2, kPrX2 = 3;
 
 template <int MG, int CPS_ = 2, int PR = kPrBF16>
 struct L3 {
@@ -100,11 +102,12 @@ struct L3 {
     static constexpr int CPS = CPS_;            // chunks per operand / kernel-matrix stage (one MMA round)
     static constexpr int KR = KC / CPS;         // MMA rounds per tile
     static constexpr int kStg = NTc * 256;      // FP32 staging stage (one chunk)
-    // operand parts of a chunk: hi [+ lo] BF16, or the two 32-ordinate halves of a TF32 chunk (each part
-    // [rows x 128 B], so a TF32 stage has the split contraction's layout)
-    static constexpr int NP = PR == kPrBF16 ? 1 : 2;
-    static constexpr int kB = NP * CPS * NTc * 128;     // operand stage (first parts of the CPS chunks, then second)
-    static constexpr int kA = NP * CPS * MG * kABlock;  // G stage: this CTA's blocks of CPS chunks (first parts, then second)
+    // parts of a chunk: hi [+ lo] BF16, or the two 32-ordinate halves of a TF32 chunk (each part
+    // [rows x 128 B], so a TF32 stage has the split contraction's layout); BF16X2 splits G only
+    static constexpr int NPA = PR == kPrBF16 ? 1 : 2;                   // kernel-matrix parts
+    static constexpr int NPB = PR == kPrBF16 || PR == kPrX2 ? 1 : 2;    // operand parts
+    static constexpr int kB = NPB * CPS * NTc * 128;     // operand stage (first parts of the CPS chunks, then second)
+    static constexpr int kA = NPA * CPS * MG * kABlock;  // G stage: this CTA's blocks of CPS chunks (first parts, then second)
     int stg, b, a, cx, cy, cb, cst, wsm, bars, end;
     __host__ __device__ L3(int SS, int SB, int SA, int nslot) {
         stg = 0;
@@ -144,11 +147,11 @@ __device__ __forceinline__ float minmod3(float a, float b) {
     return a * b > 0.0f ? (fabsf(a) < fabsf(b) ? a : b) : 0.0f;
 }
 
-// psi~ as the contraction sees it: rounded to BF16, itself (split: hi + lo carry it to about 2^-16),
-// or rounded to TF32
+// psi~ as the contraction sees it: rounded to BF16 (BF16, BF16X2), itself (split: hi + lo carry it to
+// about 2^-16), or rounded to TF32
 template <int PR>
 __device__ __forceinline__ float operand_value(float v) {
-    if constexpr (PR == kPrBF16) return bf16_round(v);
+    if constexpr (PR == kPrBF16 || PR == kPrX2) return bf16_round(v);
     else if constexpr (PR == kPrTF32) return tf32_round(v);
     else return v;
 }
@@ -160,7 +163,7 @@ template <int MG, int CPS_, int PR, bool HEUN = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads3, 1)
 step_tc3_kernel(const __grid_constant__ Tc3Args a) {
     using LT = L3<MG, CPS_, PR>;
-    constexpr bool SPLIT = PR == kPrSplit, TF = PR == kPrTF32;
+    constexpr bool SPLIT = PR == kPrSplit, TF = PR == kPrTF32, X2 = PR == kPrX2;
     // converter warps and where the flux-copy producer runs: at 512 ordinates (16-kB chunks) two
     // converter warps keep up and the producer gets warp 3 to itself (as one lane of warp 0, beside
     // the MMA issuer's waits, it issued each copy about a microsecond after its slot was released:
@@ -307,6 +310,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                                         mma_bf16_pair(dd, ah, bh2, idesc, 1u);
                                         mma_bf16_pair(dd, ah2, bh, idesc, 1u);
                                     }
+                                    if (X2) mma_bf16_pair(dd, ah2, bh, idesc, 1u);   // + G lo x psi~
                                 }
                             }
                         }
@@ -365,7 +369,7 @@ step_tc3_kernel(const __grid_constant__ Tc3Args a) {
                     const int gch = TF ? 2 * kr : kr * CPS;
                     tma_load_5d_hint(aring + (size_t)rq.s * LT::kA, &a.tm_G, &st_full[rq.s], 0, 0, (int)rank, 0, gch,
                                      pol);
-                    if (SPLIT || TF)
+                    if (SPLIT || TF || X2)
                         tma_load_5d_hint(aring + (size_t)rq.s * LT::kA + LT::kA / 2, TF ? &a.tm_G : &a.tm_Glo,
                                          &st_full[rq.s], 0, 0, (int)rank, 0, TF ? gch + 1 : gch, pol);
                     armed |= 1u << rq.s;
@@ -944,8 +948,10 @@ size_t smem3(int SS, int SB, int nslot) {
     return (size_t)1024 + (size_t)L3<MG, CPS, PR>(SS, SB, SB, nslot).end;
 }
 
-// (the split and TF32 layouts are the same size: two parts per chunk, one chunk per stage)
+// (the split and TF32 layouts are the same size: two parts per chunk, one chunk per stage; BF16X2
+// has one operand part)
 size_t smem3_for(int MG, int CPS, int pr, int SS, int SB, int nslot) {
+    if (pr == kPrX2) return MG == 2 ? smem3<2, 1, kPrX2>(SS, SB, nslot) : smem3<1, 1, kPrX2>(SS, SB, nslot);
     if (pr != kPrBF16) return MG == 2 ? smem3<2, 1, kPrSplit>(SS, SB, nslot) : smem3<1, 1, kPrSplit>(SS, SB, nslot);
     if (MG == 2) return CPS == 2 ? smem3<2, 2, kPrBF16>(SS, SB, nslot) : smem3<2, 1, kPrBF16>(SS, SB, nslot);
     return CPS == 2 ? smem3<1, 2, kPrBF16>(SS, SB, nslot) : smem3<1, 1, kPrBF16>(SS, SB, nslot);
@@ -989,6 +995,7 @@ using Tc3Kernel = void (*)(Tc3Args);
 template <bool HEUN>
 Tc3Kernel kernel3_t(int MG, int CPS, int pr) {
     if (pr == kPrTF32) return MG == 2 ? step_tc3_kernel<2, 1, kPrTF32, HEUN> : step_tc3_kernel<1, 1, kPrTF32, HEUN>;
+    if (pr == kPrX2) return MG == 2 ? step_tc3_kernel<2, 1, kPrX2, HEUN> : step_tc3_kernel<1, 1, kPrX2, HEUN>;
     if (pr == kPrSplit) return MG == 2 ? step_tc3_kernel<2, 1, kPrSplit, HEUN> : step_tc3_kernel<1, 1, kPrSplit, HEUN>;
     if (MG == 2) return CPS == 2 ? step_tc3_kernel<2, 2, kPrBF16, HEUN> : step_tc3_kernel<2, 1, kPrBF16, HEUN>;
     return CPS == 2 ? step_tc3_kernel<1, 2, kPrBF16, HEUN> : step_tc3_kernel<1, 1, kPrBF16, HEUN>;
@@ -1020,9 +1027,10 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
                             int precision, int Q, int Qp, int Mp, int nx, int ny, TcRings want, cudaStream_t stream) {
     *out = nullptr;
     const int pr = precision == ASSN_BF16 ? kPrBF16 : precision == ASSN_BF16X3 ? kPrSplit
-                 : precision == ASSN_TF32 ? kPrTF32 : -1;
-    if (pr < 0 || (pr == kPrTF32 ? !ops.G32 : !ops.G_hi) || (pr == kPrSplit && !ops.G_lo)) return cudaErrorInvalidValue;
-    const bool split = pr != kPrBF16;   // two operand parts per chunk
+                 : precision == ASSN_TF32 ? kPrTF32 : precision == ASSN_BF16X2 ? kPrX2 : -1;
+    if (pr < 0 || (pr == kPrTF32 ? !ops.G32 : !ops.G_hi) || ((pr == kPrSplit || pr == kPrX2) && !ops.G_lo))
+        return cudaErrorInvalidValue;
+    const bool split = pr != kPrBF16;   // two kernel-matrix parts per chunk
     if (!tc3_supported(Q, Qp, Mp, split)) return cudaErrorNotSupported;
     Tc3Plan* p = new Tc3Plan();
     p->MG = Qp / 256;
@@ -1032,7 +1040,7 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     // two chunks per stage, two operand and kernel-matrix stages, and as many staging stages as fit,
     // up to four (measured on the 448^2 lattice at 512 ordinates: the staging depth mattered most,
     // two stages 0.30 ms, three or four 0.24 ms; two chunks per stage cut the per-round waits)
-    p->CPS = (want.MPR == 1 || split) ? 1 : 2;   // split or TF32 operands: one chunk per stage
+    p->CPS = (want.MPR == 1 || split) ? 1 : 2;   // two kernel-matrix parts: one chunk per stage
     p->SS = want.SS ? want.SS : 4;
     p->SB = p->SA = want.SB ? want.SB : (want.SA ? want.SA : 2);
     // the kernel matrix resident (no kernel-matrix ring requested, one BF16 part, not while the
@@ -1060,7 +1068,7 @@ cudaError_t tc3_plan_create(Tc3Plan** out, const float* buf0, const float* buf1,
     const bool gmap = pr == kPrTF32 ? encode_G5_tf32(&p->tm_G, ops.G32, Qp, p->MG)
                                     : encode_G5(&p->tm_G, ops.G_hi, Qp, p->MG, p->nslot ? 1 : p->CPS, p->nslot ? 1 : p->MG);
     if (!encode_psi3(&p->tm_psi[0], buf0, Qp, nx, ny, TH / 2) || !encode_psi3(&p->tm_psi[1], buf1, Qp, nx, ny, TH / 2) ||
-        !gmap || (pr == kPrSplit && !encode_G5(&p->tm_Glo, ops.G_lo, Qp, p->MG, p->CPS, p->MG))) {
+        !gmap || ((pr == kPrSplit || pr == kPrX2) && !encode_G5(&p->tm_Glo, ops.G_lo, Qp, p->MG, p->CPS, p->MG))) {
         delete p;
         return cudaErrorInvalidValue;
     }
@@ -1125,7 +1133,7 @@ cudaError_t launch3(const Tc3Plan* p, int parity, const OrdF* ord, const CellF* 
     memset(&a, 0, sizeof a);
     a.tm_psi = p->tm_psi[parity];
     a.tm_G = p->tm_G;
-    a.tm_Glo = p->pr == kPrSplit ? p->tm_Glo : p->tm_G;
+    a.tm_Glo = p->pr == kPrSplit || p->pr == kPrX2 ? p->tm_Glo : p->tm_G;
     a.in = p->buf[parity];
     a.out = const_cast<float*>(p->buf[parity ^ 1]);
     a.ord = ord;

@@ -88,7 +88,8 @@ def step_tolerance(precision: str, dt: float, sigma_as: float, scale: float, row
     <= 2^-7 * max|psi|; both enter multiplied by dt * sigma_as.  BF16X3 carries the residuals,
     leaving 2^-16 relative per operand plus the dropped lo*lo product: 2^-14 covers gain and loss.
     TF32: both operands rounded to 11 significant bits (2^-11 relative each, G after an FP32
-    rounding of 2^-24), the same terms with 2^-10 in place of 2^-7.
+    rounding of 2^-24), the same terms with 2^-10 in place of 2^-7.  BF16X2: G carried to 2^-16 by
+    hi + lo, psi~ rounded to BF16 (2^-8), so gain and loss are each off by 2^-8 (1 + 2^-7) of theirs.
     """
     fp32 = 4e-6 * scale
     if precision == "fp64":
@@ -101,6 +102,8 @@ def step_tolerance(precision: str, dt: float, sigma_as: float, scale: float, row
         return dt * sigma_as * 2.0 ** -14 * (rowsum + 1.0) * scale + fp32
     if precision == "tf32":
         return dt * sigma_as * 2.0 ** -10 * ((1.0 + 2.0 ** -10) * rowsum + 1.0) * scale + fp32
+    if precision == "bf16x2":
+        return dt * sigma_as * 2.0 ** -8 * (1.0 + 2.0 ** -7) * (rowsum + 1.0) * scale + fp32
     raise ValueError(precision)
 
 
@@ -110,4 +113,4 @@ def offdiag_rowsum(K) -> float:
 
 
 # relative L2 tolerance on the scalar flux of a whole run against the FP64 oracle
-RUN_TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 1e-5, "tf32": 1e-5, "bf16": 1e-3}
+RUN_TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16x3": 1e-5, "bf16x2": 1e-5, "tf32": 1e-5, "bf16": 1e-3}

@@ -83,7 +83,8 @@ def test_header_is_plain_c_and_links(tmp_path):
                    '  size_t t = 0, x = 0;  /* TF32 words hold as many bytes as the BF16 hi + lo parts */\n'
                    '  if (assn_footprint_bytes(448, 448, 512, ASSN_TF32, &t) != ASSN_OK ||\n'
                    '      assn_footprint_bytes(448, 448, 512, ASSN_BF16X3, &x) != ASSN_OK || t != x || t < b) return 5;\n'
-                   '  if (assn_footprint_bytes(448, 448, 512, ASSN_TF32 + 1, &t) != ASSN_ERR_ARG) return 6;\n'
+                   '  if (assn_footprint_bytes(448, 448, 512, ASSN_BF16X2, &t) != ASSN_OK || t != x) return 6;\n'
+                   '  if (assn_footprint_bytes(448, 448, 512, ASSN_BF16X2 + 1, &t) != ASSN_ERR_ARG) return 7;\n'
                    '  puts("ok");\n  return 0;\n}\n')
     exe = tmp_path / "abi"
     r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{inc}", str(src), f"-L{libdir}",

@@ -48,8 +48,10 @@ def test_tensor_peak_of_each_operand_type(bench):
     assert bench.tensor_peak("bf16")[0] == bench.tensor_peak("bf16x3")[0] == bf
     tf, src = bench.tensor_peak("tf32")
     assert tf == pytest.approx(bf * 1.1 / 2.25) and "tf32" in src
-    assert set(bench.TENSOR_PRECISIONS) == {"bf16", "bf16x3", "tf32"}
-    assert bench.BYTES_PER_UPDATE["tf32"] == 8
+    assert set(bench.TENSOR_PRECISIONS) == {"bf16", "bf16x3", "tf32", "bf16x2"}
+    assert bench.TENSOR_PASSES == {"bf16": 1, "bf16x3": 3, "tf32": 1, "bf16x2": 2}
+    assert bench.tensor_peak("bf16x2")[0] == bf
+    assert bench.BYTES_PER_UPDATE["tf32"] == bench.BYTES_PER_UPDATE["bf16x2"] == 8
 
 
 def test_implicit_roofline_counts_source_iterations(bench):

@@ -41,6 +41,8 @@ CASES = [
     ("bf16x3", 2, "euler", (19, 23), (10, 20)),
     ("tf32", 2, "euler", (70, 37), (10, 50)),
     ("tf32", 2, "heun", (19, 23), (10, 20)),
+    ("bf16x2", 2, "euler", (70, 37), (10, 50)),
+    ("bf16x2", 2, "heun", (19, 23), (10, 20)),
     ("bf16", 0, "euler", (70, 37), (10, 50)),
     ("bf16", 0, "euler", (41, 13), (3, 4)),
     ("bf16x3", 0, "euler", (41, 13), (8, 24)),

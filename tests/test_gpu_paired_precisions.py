@@ -1,13 +1,14 @@
-"""The TF32 contraction (tcgen05 kind::tf32, operands rounded to TF32, FP32 accumulation, one pass)
-on the paired-SM kernel, against the FP64 oracle.
+"""The contractions that only the paired-SM kernel has, against the FP64 oracle:
+- TF32 (tcgen05 kind::tf32, both operands rounded to TF32, FP32 accumulation, one pass);
+- BF16X2 (the kernel matrix split into BF16 hi + lo, the flux in one BF16 part, two passes).
 
-One step from a random state is compared element by element within the derived TF32 one-step bound
-(the BF16 bound's terms with 2^-10 in place of 2^-7), on grids with ragged tiles, interior and
-boundary tiles, at 256 and 512 ordinates and padded ones (Q = 200, 500); the same for one Heun step
-(Sec. 3.1).  The TF32 error must also sit well below the BF16 error of the same step (the contraction
-really runs at the higher precision).  Whole short runs are held to the 1e-5 relative L2 tolerance
-of the FP32 tier, the full-size lattice launch is checked on sampled cells, and every path without a
-TF32 form reports ASSN_ERR_UNSUPPORTED.
+One step from a random state is compared element by element within the derived one-step bound of
+each (`step_tolerance`), on grids with ragged tiles, interior and boundary tiles, at 256 and 512
+ordinates and padded ones (Q = 200, 500); the same for one Heun step (Sec. 3.1).  The contraction
+itself must equal the exact product of the rounded operands to FP32 arithmetic, and the TF32 error
+must sit well below the BF16 error of the same step.  Whole short runs are held to the 1e-5 relative
+L2 tolerance of the FP32 tier, the full-size lattice launch is checked on sampled cells, and every
+path without these forms reports ASSN_ERR_UNSUPPORTED.
 """
 import numpy as np
 import pytest
@@ -44,16 +45,18 @@ def one_step(A, wl, precision, dt=None, scheme="euler"):
 
 
 QUADS = [(16, 32), (16, 16), (10, 50), (10, 20)]
+PRECS = ["tf32", "bf16x2"]
 
 
+@pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("npol,naz", QUADS)
 @pytest.mark.parametrize("nx,ny", [(70, 37), (48, 48), (16, 8), (1, 1), (200, 1), (5, 90)])
-def test_one_step_random_state(A, nx, ny, npol, naz):
+def test_one_step_random_state(A, nx, ny, npol, naz, precision):
     wl = random_workload(nx, ny, npol, naz, seed=nx * 23 + ny + npol)
-    got, dt = one_step(A, wl, "tf32")
+    got, dt = one_step(A, wl, precision)
     Om, w, K, sa, ss, q = oracle_setup(wl)
     ref = O.step(wl.psi0(), K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
-    tol = step_tolerance("tf32", dt, wl.sigma_as, np.abs(wl.psi0()).max(), offdiag_rowsum(K))
+    tol = step_tolerance(precision, dt, wl.sigma_as, np.abs(wl.psi0()).max(), offdiag_rowsum(K))
     err = np.abs(got - ref).max()
     assert err <= tol, (err, tol)
 
@@ -85,14 +88,14 @@ def round_tf32(x):
     return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("precision", ["tf32", "bf16", "bf16x2"])
 @pytest.mark.parametrize("npol,naz", [(16, 32), (16, 16)])
 def test_contraction_is_the_product_of_rounded_operands(A, npol, naz, precision):
     """The tensor cores compute the product of the rounded operands to FP32 accuracy.  Expected
     step: the oracle's step plus the exact (FP64) change that rounding makes to its artificial
     gain, dt sigma_as [(G~ psi~ - e~ psi~) - (G psi - e psi)], with G the off-diagonal K, G~ its
-    stored rounding (TF32: FP32 then TF32 with ties away; BF16: to nearest even from FP64), psi~
-    the state's rounding, e~ the generator diagonal of G~ (as FP32).  The GPU step must agree
+    stored rounding (TF32: FP32 then TF32 with ties away; BF16: to nearest even from FP64; BF16X2:
+    that hi plus its residual's BF16 rounding), psi~ the state's rounding, e~ the generator diagonal of G~ (as FP32).  The GPU step must agree
     with it to FP32 arithmetic, which is over 5x (TF32) and 40x (BF16) tighter than the rounding
     terms themselves (checked here), so an MMA that read its operands other than assumed
     (truncated, fewer bits) fails."""
@@ -108,6 +111,9 @@ def test_contraction_is_the_product_of_rounded_operands(A, npol, naz, precision)
     G = K - np.diag(np.diag(K))
     if precision == "tf32":
         Gr, psir = round_tf32(G), round_tf32(psi)
+    elif precision == "bf16x2":
+        hi = round_sig(G, 8)
+        Gr, psir = hi + round_sig(G - hi, 8), round_sig(psi, 8)
     else:
         Gr, psir = round_sig(G, 8), round_sig(psi, 8)
     e = (w[:, None] * G).sum(axis=0) / w                       # column normalisation
@@ -119,27 +125,29 @@ def test_contraction_is_the_product_of_rounded_operands(A, npol, naz, precision)
     assert np.abs(got - want).max() <= tol, (np.abs(got - want).max(), np.abs(delta).max())
 
 
+@pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("npol,naz", QUADS)
 @pytest.mark.parametrize("nx,ny", [(70, 37), (16, 8), (1, 1), (5, 90)])
-def test_heun_one_step(A, nx, ny, npol, naz):
-    """One Heun step (two stages) against oracle.step_heun within twice the TF32 one-step bound."""
+def test_heun_one_step(A, nx, ny, npol, naz, precision):
+    """One Heun step (two stages) against oracle.step_heun within twice the one-step bound."""
     wl = random_workload(nx, ny, npol, naz, seed=nx * 11 + ny + naz)
     psi0 = wl.psi0()
-    got, dt = one_step(A, wl, "tf32", scheme="heun")
+    got, dt = one_step(A, wl, precision, scheme="heun")
     Om, w, K, sa, ss, q = oracle_setup(wl)
     ref = O.step_heun(psi0, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
     scale = max(1.0, np.abs(ref).max(), np.abs(psi0).max())
-    tol = 2.0 * step_tolerance("tf32", dt, wl.sigma_as, scale, offdiag_rowsum(K))
+    tol = 2.0 * step_tolerance(precision, dt, wl.sigma_as, scale, offdiag_rowsum(K))
     assert np.abs(got - ref).max() <= tol
 
 
+@pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("scheme", ["euler", "heun"])
-def test_line_source_run(A, scheme):
+def test_line_source_run(A, scheme, precision):
     """The 64^2 line source at 256 ordinates to t = 0.25 (forward Euler at CFL 0.5; Heun at 0.95 of
     its admissible dt): relative L2 of Phi against the oracle within 1e-5; the state stays
     non-negative."""
-    wl = synth.line_source(64, 16, 16, 1.0 / 8.0, t_final=0.25, name="tf32_ls64")
-    p = gpu_problem(A, wl, "tf32")
+    wl = synth.line_source(64, 16, 16, 1.0 / 8.0, t_final=0.25, name="paired_ls64")
+    p = gpu_problem(A, wl, precision)
     p.set_scheme(scheme)
     if scheme == "heun":
         n = int(np.ceil(wl.t_final / (0.95 * p.max_stable_dt()) - 1e-12))
@@ -155,12 +163,13 @@ def test_line_source_run(A, scheme):
         psi = O.run_heun(wl.psi0(), n, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
     else:
         psi, w = oracle_run(wl, n, dt)
-    assert rel_l2(phi, psi @ w) <= RUN_TOL["tf32"]
+    assert rel_l2(phi, psi @ w) <= RUN_TOL[precision]
 
 
-def test_lattice_448_sampled_cells(A):
-    """The full-size lattice launch (448 x 448, Q = 512) in TF32: one step from a seeded state
-    against the oracle on sampled cells (tile corners and edges, grid corners, materials)."""
+@pytest.mark.parametrize("precision", PRECS)
+def test_lattice_448_sampled_cells(A, precision):
+    """The full-size lattice launch (448 x 448, Q = 512): one step from a seeded state against the
+    oracle on sampled cells (tile corners and edges, grid corners, materials)."""
     wl = synth.LATTICE_448
     rng = np.random.default_rng(6)
     psi = rng.uniform(0.0, 1.0, size=(wl.ny, wl.nx, wl.Q))
@@ -170,20 +179,21 @@ def test_lattice_448_sampled_cells(A):
     cells += [(int(j), int(i)) for j, i in rng.integers(0, 448, size=(16, 2))]
     Om, w, K, sa, ss, q = oracle_setup(wl)
     ref = O.step_at_cells(psi, cells, K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
-    p = gpu_problem(A, wl, "tf32", psi0=psi)
+    p = gpu_problem(A, wl, precision, psi0=psi)
     p.step(1, dt)
     got = p.state()
     p.close()
-    tol = step_tolerance("tf32", dt, wl.sigma_as, 1.0, offdiag_rowsum(K))
+    tol = step_tolerance(precision, dt, wl.sigma_as, 1.0, offdiag_rowsum(K))
     for n_, (j, i) in enumerate(cells):
         assert np.abs(got[j, i] - ref[n_]).max() <= tol, (j, i)
 
 
-def test_kernel_matrix_streams(A):
-    """TF32 takes the paired-SM kernel by default, with the kernel matrix through its ring (the
-    resident form holds BF16 blocks only), and the ring settings apply."""
+@pytest.mark.parametrize("precision", PRECS)
+def test_kernel_matrix_streams(A, precision):
+    """The paired-SM kernel by default, with the kernel matrix through its ring (the resident form
+    holds one BF16 part only), and the ring settings apply."""
     wl = random_workload(40, 21, 16, 32, seed=9)
-    p = gpu_problem(A, wl, "tf32")
+    p = gpu_problem(A, wl, precision)
     assert p.variant() == 2
     assert p.rings()["kernel_matrix"] >= 2
     p.set_rings(3, 2, 2, 0)
@@ -191,12 +201,13 @@ def test_kernel_matrix_streams(A):
     p.close()
 
 
-def test_step_device_on_caller_buffers(A):
-    """assn_step_device in TF32 between 16-byte aligned caller buffers equals assn_step bitwise."""
+@pytest.mark.parametrize("precision", PRECS)
+def test_step_device_on_caller_buffers(A, precision):
+    """assn_step_device between 16-byte aligned caller buffers equals assn_step bitwise."""
     import torch
 
     wl = random_workload(33, 18, 16, 32, seed=3)
-    p = gpu_problem(A, wl, "tf32")
+    p = gpu_problem(A, wl, precision)
     qpad, _ = p.layout()
     dt = 0.9 * p.max_stable_dt()
     buf = np.zeros((wl.ny, wl.nx, qpad), dtype=np.float32)
@@ -213,18 +224,19 @@ def test_step_device_on_caller_buffers(A):
     assert np.array_equal(out[..., :wl.Q].astype(np.float64), ref)
 
 
-def test_unsupported_paths(A):
-    """Paths without a TF32 form refuse it: other ordinate counts, the one-CTA variants, autotune,
+@pytest.mark.parametrize("precision", PRECS)
+def test_unsupported_paths(A, precision):
+    """Paths without these forms refuse them: other ordinate counts, the one-CTA variants, autotune,
     the implicit scheme, batches and the server."""
     U = A._lib.ASSN_ERR_UNSUPPORTED
     wl = random_workload(20, 20, 8, 16, seed=1)          # Q = 128: no paired-SM form
-    p = gpu_problem(A, wl, "tf32")
+    p = gpu_problem(A, wl, precision)
     with pytest.raises(A.AssnError) as e:
         p.step(1, 0.5 * p.max_stable_dt())
     assert e.value.status == U
     p.close()
     wl = random_workload(20, 20, 16, 32, seed=1)
-    p = gpu_problem(A, wl, "tf32")
+    p = gpu_problem(A, wl, precision)
     for variant in (0, 1):
         with pytest.raises(A.AssnError) as e:
             p.set_tiling(0, 0, variant)
@@ -242,5 +254,5 @@ def test_unsupported_paths(A):
     b.close()
     p.close()
     with pytest.raises(A.AssnError) as e:
-        A.Server("tf32")
+        A.Server(precision)
     assert e.value.status == U

@@ -1,8 +1,8 @@
 """Checkpoint / resume: a solve stepped n1 steps, its state read back, a new problem set up from that
 state and stepped n2 more is bitwise equal to the same solve stepped n1 + n2 steps without a break.
 Forward Euler and the paper's Heun + minmod scheme, on the paired-SM kernel (Q = 512) and the one-CTA
-kernel (Q = 128), in BF16 and BF16X3, and TF32 on the paired-SM kernel; the checkpoint goes through
-the FP32 state copies."""
+kernel (Q = 128), in BF16 and BF16X3, and TF32 and BF16X2 on the paired-SM kernel; the checkpoint
+goes through the FP32 state copies."""
 import numpy as np
 import pytest
 
@@ -19,9 +19,9 @@ def A():
     return A
 
 
-# (precision, n_polar, n_azim, variant): TF32 has the paired-SM kernel only
-CASES = [(prec, npol, naz, v) for prec in ("bf16", "bf16x3", "tf32") for npol, naz, v in ((16, 32, 2), (8, 16, 0))
-         if prec != "tf32" or v == 2]
+# (precision, n_polar, n_azim, variant): TF32 and BF16X2 have the paired-SM kernel only
+CASES = [(prec, npol, naz, v) for prec in ("bf16", "bf16x3", "tf32", "bf16x2")
+         for npol, naz, v in ((16, 32, 2), (8, 16, 0)) if prec in ("bf16", "bf16x3") or v == 2]
 
 
 @pytest.mark.parametrize("scheme", ["euler", "heun"])
