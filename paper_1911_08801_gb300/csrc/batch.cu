@@ -55,6 +55,12 @@ struct assn_batch {
     std::vector<int> graph_shape;       // nmax per class the graph was captured for
     unsigned int* d_err = nullptr;
     cudaEvent_t done = nullptr;
+    // side streams for the paired members' launch chains (created when first needed): forked from
+    // the batch stream by `fork`, joined back by `join`, so that one member's launches overlap the
+    // tails of others' and of the class launches
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
     int want_nt = 0;                    // 0 = automatic (per class)
     int grouping = 0;                   // 0: one class per padded ordinate count; 1: one class
     TcRings want_rings;                 // zero fields automatic (per class)
@@ -352,6 +358,11 @@ int assn_batch_destroy(assn_batch* b) {
     drop_plan(b);
     if (b->d_err) cudaFree(b->d_err);
     if (b->done) cudaEventDestroy(b->done);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (int s = 0; s < assn_batch::kSide; ++s) {
+        if (b->join[s]) cudaEventDestroy(b->join[s]);
+        if (b->side[s]) cudaStreamDestroy(b->side[s]);
+    }
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return ASSN_OK;
@@ -495,29 +506,51 @@ int assn_batch_run(assn_batch* b, int use_graph) {
     for (auto& c : b->classes) shape.push_back(c.nmax);
     int nlaunch = 0;
     for (int v : shape) nlaunch += v;
+    int npaired = 0;
     for (auto& m : b->members)
         if (m.paired) {   // (the launches' buffers follow from the member's current one)
             shape.push_back(lps * m.nsteps);
             shape.push_back(m.p->cur);
             nlaunch += lps * m.nsteps;
+            ++npaired;
         }
+    const int nside = std::min(npaired, (int)assn_batch::kSide);
+    if (nside > 0 && !b->fork) {
+        BK(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        for (int s = 0; s < assn_batch::kSide; ++s) {
+            BK(b, cudaStreamCreateWithFlags(&b->side[s], cudaStreamNonBlocking));
+            BK(b, cudaEventCreateWithFlags(&b->join[s], cudaEventDisableTiming));
+        }
+    }
     auto enqueue = [&]() -> cudaError_t {
-        // steps (Heun: stages) of the classes interleaved, one launch per class and step (stage),
-        // then one per paired member and step (stage)
+        // the classes' steps (Heun: stages) interleaved on the batch stream, one launch per class and
+        // step (stage); each paired member's chain of launches on a side stream forked from it
         cudaError_t e = cudaSuccess;
-        for (int k = 0; k < nmax && e == cudaSuccess; ++k) {
+        if (nside > 0) {
+            e = cudaEventRecord(b->fork, b->stream);
+            for (int s = 0; s < nside && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->side[s], b->fork, 0);
+        }
+        for (int k = 0; k < nmax && e == cudaSuccess; ++k)
             for (auto& c : b->classes)
                 if (k < c.nmax && e == cudaSuccess)
                     e = lps == 2 ? launch_heun_stage_tc2(c.plan, b->d_err, -1, nullptr, 0.0f, 1.0f, b->stream)
                                  : launch_step_tc2(c.plan, b->d_err, -1, b->stream);
-            for (auto& m : b->members) {
-                if (!m.paired || k >= lps * m.nsteps || e != cudaSuccess) continue;
-                const int cur0 = m.p->cur;
+        int j = 0;
+        for (auto& m : b->members) {
+            if (!m.paired) continue;
+            cudaStream_t s = b->side[j++ % nside];
+            const int cur0 = m.p->cur;
+            for (int k = 0; k < lps * m.nsteps && e == cudaSuccess; ++k) {
                 if (lps == 2)   // a Heun step ends in the buffer it started from
-                    e = problem_pair_launch(m.p, m.dt, (k & 1) ? cur0 ^ 1 : cur0, k & 1, b->d_err, b->stream);
+                    e = problem_pair_launch(m.p, m.dt, (k & 1) ? cur0 ^ 1 : cur0, k & 1, b->d_err, s);
                 else
-                    e = problem_pair_launch(m.p, m.dt, (cur0 + k) & 1, -1, b->d_err, b->stream);
+                    e = problem_pair_launch(m.p, m.dt, (cur0 + k) & 1, -1, b->d_err, s);
             }
+        }
+        for (int s = 0; s < nside; ++s) {   // joined even after an error, so that a capture can end
+            cudaError_t e2 = cudaEventRecord(b->join[s], b->side[s]);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(b->stream, b->join[s], 0);
+            if (e == cudaSuccess) e = e2;
         }
         return e;
     };
