@@ -55,9 +55,9 @@ struct assn_batch {
     std::vector<int> graph_shape;       // nmax per class the graph was captured for
     unsigned int* d_err = nullptr;
     cudaEvent_t done = nullptr;
-    // side streams for the paired members' launch chains (created when first needed): forked from
-    // the batch stream by `fork`, joined back by `join`, so that one member's launches overlap the
-    // tails of others' and of the class launches
+    // side streams for the launch chains of the classes and of the paired members (created when
+    // first needed): forked from the batch stream by `fork`, joined back by `join`, so that one
+    // chain's launches overlap the tails of the others'
     static constexpr int kSide = 4;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork = nullptr, join[kSide] = {};
@@ -514,7 +514,8 @@ int assn_batch_run(assn_batch* b, int use_graph) {
             nlaunch += lps * m.nsteps;
             ++npaired;
         }
-    const int nside = std::min(npaired, (int)assn_batch::kSide);
+    const int nchain = npaired + (int)b->classes.size();   // independent launch chains
+    const int nside = std::min(nchain, (int)assn_batch::kSide);
     if (nside > 0 && !b->fork) {
         BK(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
         for (int s = 0; s < assn_batch::kSide; ++s) {
@@ -523,19 +524,20 @@ int assn_batch_run(assn_batch* b, int use_graph) {
         }
     }
     auto enqueue = [&]() -> cudaError_t {
-        // the classes' steps (Heun: stages) interleaved on the batch stream, one launch per class and
-        // step (stage); each paired member's chain of launches on a side stream forked from it
+        // each class's chain of launches (one per step; Heun: per stage) and each paired member's
+        // chain on a side stream forked from the batch stream, round robin
         cudaError_t e = cudaSuccess;
         if (nside > 0) {
             e = cudaEventRecord(b->fork, b->stream);
             for (int s = 0; s < nside && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->side[s], b->fork, 0);
         }
-        for (int k = 0; k < nmax && e == cudaSuccess; ++k)
-            for (auto& c : b->classes)
-                if (k < c.nmax && e == cudaSuccess)
-                    e = lps == 2 ? launch_heun_stage_tc2(c.plan, b->d_err, -1, nullptr, 0.0f, 1.0f, b->stream)
-                                 : launch_step_tc2(c.plan, b->d_err, -1, b->stream);
         int j = 0;
+        for (auto& c : b->classes) {
+            cudaStream_t s = b->side[j++ % nside];
+            for (int k = 0; k < c.nmax && e == cudaSuccess; ++k)
+                e = lps == 2 ? launch_heun_stage_tc2(c.plan, b->d_err, -1, nullptr, 0.0f, 1.0f, s)
+                             : launch_step_tc2(c.plan, b->d_err, -1, s);
+        }
         for (auto& m : b->members) {
             if (!m.paired) continue;
             cudaStream_t s = b->side[j++ % nside];
