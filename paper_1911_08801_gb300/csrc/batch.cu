@@ -58,7 +58,7 @@ struct assn_batch {
     // side streams for the launch chains of the classes and of the paired members (created when
     // first needed): forked from the batch stream by `fork`, joined back by `join`, so that one
     // chain's launches overlap the tails of the others'
-    static constexpr int kSide = 4;
+    static constexpr int kSide = 8;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork = nullptr, join[kSide] = {};
     int want_nt = 0;                    // 0 = automatic (per class)
