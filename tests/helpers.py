@@ -107,6 +107,19 @@ def step_tolerance(precision: str, dt: float, sigma_as: float, scale: float, row
     raise ValueError(precision)
 
 
+def round_sig(x, bits):
+    """Round to nearest with ties to even at `bits` significant bits (normal range): BF16 is 8."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 2.0 ** bits), e - bits)
+
+
+def round_tf32(x):
+    """FP64 -> FP32 (to nearest even), then to TF32 by the library's stated rule: to nearest with
+    ties away from zero at 11 significant bits, on the bit pattern's magnitude."""
+    u = np.asarray(x, dtype=np.float64).astype(np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
+
+
 def offdiag_rowsum(K) -> float:
     K = np.asarray(K)
     return float((K.sum(axis=1) - np.diag(K)).max())

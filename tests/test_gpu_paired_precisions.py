@@ -16,7 +16,7 @@ import pytest
 import oracle as O
 import synth
 from tests.helpers import (RUN_TOL, ensure_built, gpu_problem, offdiag_rowsum, oracle_run, oracle_setup, rel_l2,
-                           step_tolerance)
+                           round_sig, round_tf32, step_tolerance)
 
 pytestmark = pytest.mark.gpu
 
@@ -73,19 +73,6 @@ def test_error_well_below_bf16(A, npol, naz):
         ref = O.step(wl.psi0(), K, Om, w, sa, ss, q, wl.sigma_as, wl.h, dt)
         errs[prec] = float(np.sqrt(np.mean((got - ref) ** 2)))
     assert errs["tf32"] <= errs["bf16"] / 4.0, errs
-
-
-def round_sig(x, bits):
-    """Round to nearest with ties to even at `bits` significant bits (normal range)."""
-    m, e = np.frexp(np.asarray(x, dtype=np.float64))
-    return np.ldexp(np.rint(m * 2.0 ** bits), e - bits)
-
-
-def round_tf32(x):
-    """FP64 -> FP32 (to nearest even), then to TF32 by the library's rule: to nearest with ties away
-    from zero at 11 significant bits, on the bit pattern's magnitude."""
-    u = np.asarray(x, dtype=np.float64).astype(np.float32).view(np.uint32)
-    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
 
 
 @pytest.mark.parametrize("precision", ["tf32", "bf16", "bf16x2"])
