@@ -69,8 +69,9 @@ typedef enum {
  *   ASSN_BF16X2 tcgen05, the kernel matrix split into BF16 hi+lo, the flux in one BF16 part, two
  *               passes (hi*psi~ + lo*psi~), FP32 accumulation.
  *   TF32 and BF16X2 run on the paired-SM kernel only (tiling variant 2: 193..256 or 449..512
- *   ordinates), for the forward-Euler and Heun schemes; other ordinate counts or variants,
- *   batches, autotune and the server return ASSN_ERR_UNSUPPORTED.
+ *   ordinates), for the forward-Euler and Heun schemes, alone or in batches of such members;
+ *   other ordinate counts or variants, the one-launch batch grouping, autotune and the server
+ *   return ASSN_ERR_UNSUPPORTED.
  * K itself is always built in FP64 on the device. */
 typedef enum {
     ASSN_FP64 = 0,
@@ -332,7 +333,8 @@ int assn_check_guards(assn_problem* p, int64_t* guard_bytes_changed, int64_t* pa
 /* ---- Batches: several problems stepped by one persistent launch per step.
  * The members may differ in grid size, quadrature (ordinate count), kernel width eps, cross
  * sections and dt; they share the device and one tensor-core precision (ASSN_BF16 or
- * ASSN_BF16X3) and one explicit scheme (assn_set_scheme: forward-Euler upwind, or the paper's Heun +
+ * ASSN_BF16X3; ASSN_TF32 or ASSN_BF16X2 when every member has 193..256 or 449..512 ordinates and
+ * the grouping is per class, so that each runs on the paired-SM kernel) and one explicit scheme (assn_set_scheme: forward-Euler upwind, or the paper's Heun +
  * minmod of Sec. 3.1).  Each launch applies the same explicit step as assn_step (Sec. 3.2, forward
  * Euler of the as-S_N equations; for Heun + minmod one of the two stages of a Heun step, so a step
  * is two launches) to every member that still has steps left; a member's step count is
@@ -349,7 +351,8 @@ int assn_check_guards(assn_problem* p, int64_t* guard_bytes_changed, int64_t* pa
  * add:        add p, to be advanced nsteps >= 0 steps of size dt per run.  Checks p is complete
  *             and dt admissible (as assn_step).  Errors: ASSN_ERR_ARG (NULL, duplicate, other
  *             device, mixed precision or scheme, more than 1024 members), ASSN_ERR_UNSUPPORTED (not a
- *             tensor-core precision, the implicit scheme), or p's own error
+ *             tensor-core precision, a TF32 / BF16X2 member without a paired-SM form, the implicit
+ *             scheme), or p's own error
  *             (ASSN_ERR_STATE, ASSN_ERR_UNSTABLE).
  * set_steps:  change a member's nsteps / dt for later runs.
  * remove:     drop a member (syncs the batch stream).

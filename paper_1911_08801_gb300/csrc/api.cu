@@ -615,6 +615,9 @@ static int eff_variant(const assn_problem* p) {
 
 namespace assn {
 bool problem_paired(const assn_problem* p) { return p->tensor() && eff_variant(p) == 2; }
+bool problem_pair_supported(const assn_problem* p) {
+    return p->tensor() && tc3_supported(p->Q, p->Qp, p->tc.Mp, p->precision != ASSN_BF16);
+}
 
 cudaError_t problem_pair_launch(assn_problem* p, double dt, int parity, int heun_stage, unsigned int* err_flag,
                                 cudaStream_t s) {

@@ -25,7 +25,7 @@ using namespace assn;
 
 struct assn_batch {
     int dev = 0;
-    int precision = -1;                 // of the members (BF16 or BF16X3)
+    int precision = -1;                 // of the members (BF16 or BF16X3; TF32 or BF16X2 if all are paired)
     int scheme = -1;                    // of the members (forward-Euler upwind or Heun + minmod)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -275,9 +275,19 @@ cudaError_t autotune(const std::vector<Tc2Problem>& probs, const std::vector<int
 
 // Builds the per-class plans for the current membership (targets from each member's state and
 // nsteps), or only refreshes the targets when the plans exist.
+// The one-CTA kernel has no TF32 or BF16X2 form: such a batch must leave every member paired.
+int check_classes(assn_batch* b) {
+    if (!b->classes.empty() && (b->precision == ASSN_TF32 || b->precision == ASSN_BF16X2))
+        return bfail(b, ASSN_ERR_UNSUPPORTED,
+                     "the one-launch grouping steps every member on the one-CTA kernel, which has no TF32 or "
+                     "BF16X2 form");
+    return ASSN_OK;
+}
+
 int ensure_batch_plan(assn_batch* b) {
     if (!b->planned) {
         group(b);
+        if (int r = check_classes(b)) return r;
         for (auto& m : b->members)
             if (m.paired) {
                 const int r = problem_pair_plan(m.p, m.dt);
@@ -371,8 +381,7 @@ int assn_batch_destroy(assn_batch* b) {
 int assn_batch_add(assn_batch* b, assn_problem* p, int nsteps, double dt) {
     if (!b || !p) return bfail(b, ASSN_ERR_ARG, "batch or problem is NULL");
     if (nsteps < 0) return bfail(b, ASSN_ERR_ARG, "nsteps < 0");
-    if (p->precision != ASSN_BF16 && p->precision != ASSN_BF16X3)
-        return bfail(b, ASSN_ERR_UNSUPPORTED, "batches step the tensor-core precisions (BF16, BF16X3) only");
+    if (!p->tensor()) return bfail(b, ASSN_ERR_UNSUPPORTED, "batches step the tensor-core precisions only");
     if (p->scheme != ASSN_SCHEME_EULER_UPWIND && p->scheme != ASSN_SCHEME_HEUN_MINMOD)
         return bfail(b, ASSN_ERR_UNSUPPORTED, "batches take the explicit schemes (forward-Euler upwind, Heun + minmod)");
     if (b->precision >= 0 && p->precision != b->precision)
@@ -384,6 +393,9 @@ int assn_batch_add(assn_batch* b, assn_problem* p, int nsteps, double dt) {
     if ((int)b->members.size() >= 1024) return bfail(b, ASSN_ERR_ARG, "a batch holds at most 1024 problems");
     const int r = problem_prepare(p, dt);
     if (r) return bfail(b, r, "member: %s", p->err.c_str());
+    if (p->paired_only() && !(problem_paired(p) && problem_pair_supported(p)))
+        return bfail(b, ASSN_ERR_UNSUPPORTED,
+                     "TF32 and BF16X2 members run on the paired-SM kernel only (193..256 or 449..512 ordinates)");
     b->precision = p->precision;
     b->scheme = p->scheme;
     b->members.push_back({p, nsteps, dt});
@@ -449,6 +461,7 @@ int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stag
     }
     drop_plan(b);
     group(b);
+    if (int r = check_classes(b)) return r;
     double total_ms = 0.0;
     bool all_cached = true;
     for (auto& c : b->classes) {
@@ -472,9 +485,9 @@ int assn_batch_autotune(assn_batch* b, int use_cache, int* tile_cells, int* stag
     b->want_nt = 0;
     b->want_rings = TcRings{};
     b->tuned = true;
-    // report the class with the most ordinate blocks (the first)
-    if (tile_cells) *tile_cells = b->classes[0].nt;
-    if (stages) *stages = b->classes[0].rings.SA;
+    // report the class with the most ordinate blocks (the first); none when every member is paired
+    if (tile_cells) *tile_cells = b->classes.empty() ? 0 : b->classes[0].nt;
+    if (stages) *stages = b->classes.empty() ? 0 : b->classes[0].rings.SA;
     if (ms_per_launch) *ms_per_launch = all_cached ? -1.0 : total_ms;
     return ASSN_OK;
 }
@@ -611,7 +624,7 @@ int assn_batch_info(assn_batch* b, int* members, int* tile_cells, int* stages, i
         BK(b, cudaSetDevice(b->dev));
         int r = ensure_batch_plan(b);
         if (r) return r;
-        tc2_plan_describe(b->classes[0].plan, &nt, &st, &cols, &sm);
+        if (!b->classes.empty()) tc2_plan_describe(b->classes[0].plan, &nt, &st, &cols, &sm);
         for (auto& c : b->classes) tiles += tc2_plan_total_tiles(c.plan);
     }
     if (tile_cells) *tile_cells = nt;

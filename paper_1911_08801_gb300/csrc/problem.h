@@ -96,6 +96,8 @@ int problem_check_flags(assn_problem* p);
 Tc2Problem problem_tc2(const assn_problem* p, double dt, int target);
 // True when p's steps run on the paired-SM kernel (the variant its own steps resolve to is 2).
 bool problem_paired(const assn_problem* p);
+// True when p's ordinate count has a paired-SM form (193..256 or 449..512 ordinates).
+bool problem_pair_supported(const assn_problem* p);
 // Creates p's paired-SM plan if missing (reads G back once: not while a stream is being captured).
 int problem_pair_plan(assn_problem* p, double dt);
 // Enqueues one launch of p's paired-SM kernel on stream s at step size dt: a forward-Euler step, or

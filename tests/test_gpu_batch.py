@@ -274,3 +274,63 @@ def test_result_independent_of_rings(A):
         p.close()
     for o in out[1:]:
         assert np.array_equal(out[0], o)
+
+
+# members whose every step runs on the paired-SM kernel: 256 / 512 (and padded 200 / 500) ordinates
+PAIRED_SPECS = [(33, 21, 16, 32, 0.9), (40, 17, 16, 16, 0.5), (24, 30, 10, 20, 0.7), (19, 26, 10, 50, 0.4)]
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16x2"])
+@pytest.mark.parametrize("scheme", ["euler", "heun"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_paired_precision_batch_equals_alone(A, precision, scheme, use_graph):
+    """TF32 and BF16X2 have the paired-SM kernel only; a batch of members that all run there steps
+    each by its own chain of launches, and every member ends bitwise equal to its solve alone.  The
+    batch's info and autotune work with no one-CTA class."""
+    wls = [synth.Workload(f"pbatch{k}", "random", nx, ny, 0.0, 0.05 * nx, 0.0, 0.05 * ny, npol, naz, beta, seed=40 + k)
+           for k, (nx, ny, npol, naz, beta) in enumerate(PAIRED_SPECS)]
+    probs = []
+    for wl in wls:
+        p = gpu_problem(A, wl, precision)
+        p.set_scheme(scheme)
+        probs.append(p)
+    dts = [0.9 * p.max_stable_dt() for p in probs]
+    steps = [3, 5, 0, 2]
+    with A.Batch() as b:
+        for p, n, dt in zip(probs, steps, dts):
+            b.add(p, n, dt)
+        b.autotune()
+        b.run(use_graph=use_graph).sync()
+        info = b.info()
+    lps = 2 if scheme == "heun" else 1
+    assert info["members"] == 4 and info["launches"] == lps * sum(steps) and info["total_tiles"] == 0
+    for wl, p, n, dt in zip(wls, probs, steps, dts):
+        q = gpu_problem(A, wl, precision)
+        q.set_scheme(scheme)
+        q.step(n, dt)
+        ref = q.state()
+        q.close()
+        assert np.array_equal(p.state(), ref), (wl.name, n)
+    for p in probs:
+        p.close()
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16x2"])
+def test_paired_precision_batch_refusals(A, precision):
+    """A TF32 / BF16X2 member without a paired-SM form (Q = 128) is refused when added, and the
+    one-launch grouping (every member on the one-CTA kernel) is refused when the batch runs."""
+    U = A._lib.ASSN_ERR_UNSUPPORTED
+    small = synth.Workload("pb_small", "random", 20, 20, 0.0, 1.0, 0.0, 1.0, 8, 16, 0.5, seed=1)
+    big = synth.Workload("pb_big", "random", 20, 20, 0.0, 1.0, 0.0, 1.0, 16, 32, 0.5, seed=2)
+    p, q = gpu_problem(A, small, precision), gpu_problem(A, big, precision)
+    with A.Batch() as b:
+        with pytest.raises(A.AssnError) as e:
+            b.add(p, 1, 0.5 * p.max_stable_dt())
+        assert e.value.status == U
+        b.add(q, 1, 0.5 * q.max_stable_dt())
+        b.set_grouping(one_launch=True)
+        with pytest.raises(A.AssnError) as e:
+            b.run()
+        assert e.value.status == U
+    p.close()
+    q.close()

@@ -214,7 +214,7 @@ def test_step_device_on_caller_buffers(A, precision):
 @pytest.mark.parametrize("precision", PRECS)
 def test_unsupported_paths(A, precision):
     """Paths without these forms refuse them: other ordinate counts, the one-CTA variants, autotune,
-    the implicit scheme, batches and the server."""
+    the implicit scheme and the server."""
     U = A._lib.ASSN_ERR_UNSUPPORTED
     wl = random_workload(20, 20, 8, 16, seed=1)          # Q = 128: no paired-SM form
     p = gpu_problem(A, wl, precision)
@@ -234,12 +234,7 @@ def test_unsupported_paths(A, precision):
     with pytest.raises(A.AssnError) as e:
         p.set_scheme("implicit")
     assert e.value.status == U
-    b = A.Batch()
-    with pytest.raises(A.AssnError) as e:
-        b.add(p, 1, 0.5 * p.max_stable_dt())
-    assert e.value.status == U
-    b.close()
-    p.close()
+    p.close()   # (batches of paired members: tests/test_gpu_batch.py)
     with pytest.raises(A.AssnError) as e:
         A.Server(precision)
     assert e.value.status == U
