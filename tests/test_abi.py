@@ -92,3 +92,19 @@ def test_header_is_plain_c_and_links(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+def test_binding_constants_match_header(lib):
+    """Every enumerator of include/assn.h that the ctypes binding names has the header's value (the
+    precisions, statuses, schemes, kernel kinds and normalisations are passed as plain ints)."""
+    from paper_1911_08801_gb300 import _lib
+
+    text = open(HEADER).read()
+    header = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ASSN_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    named = {k: v for k, v in vars(_lib).items() if k.startswith("ASSN_") and isinstance(v, int) and k in header}
+    for k in ("ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3", "ASSN_TF32", "ASSN_BF16X2", "ASSN_ERR_UNSUPPORTED",
+              "ASSN_ERR_CANCELLED", "ASSN_SCHEME_HEUN_MINMOD", "ASSN_KERNEL_EXP", "ASSN_NORM_ROW"):
+        assert k in named, k
+    assert {k: header[k] for k in named} == named
+    assert set(_lib.PRECISIONS.values()) == {header[k] for k in ("ASSN_FP64", "ASSN_FP32", "ASSN_BF16", "ASSN_BF16X3",
+                                                                  "ASSN_TF32", "ASSN_BF16X2")}
